@@ -65,8 +65,10 @@ def left_env(Lprev, W, A):
 
 
 def right_env(Rnext, W, B):
-    """R_i = R_{i+1} B_i^dagger W_i B_i  (Sec. II)."""
-    return np.einsum("cYy,SXY,Ssbc,sxy->bXx", Rnext, B.conj(), W, B, optimize=True)
+    """R_i = R_{i+1} B_i^dagger W_i B_i  (Sec. II), contracted as the mirror of left_env."""
+    U1 = np.einsum("sxy,cYy->csxY", B, Rnext)          # B . R over the right MPS bond
+    U2 = np.einsum("Ssbc,csxY->SbxY", W, U1)           # . W
+    return np.einsum("SXY,SbxY->bXx", B.conj(), U2)    # . B^dagger
 
 
 def expectation(L, W, R, M):

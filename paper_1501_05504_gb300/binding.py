@@ -1,0 +1,369 @@
+"""ctypes binding of ``libdmrg3s.so`` (the C ABI declared in include/dmrg3s.h).
+
+Argument marshalling only: every contraction runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  If the library has not
+been built the import-time loader raises; there is no fallback.
+
+Python objects mirror the C structs:
+
+* ``Bond(q, dim)``: charge sectors of a bond (``q`` int array (nsec, nsym));
+* ``Site(qp, left, right, data)``: MPS site tensor, ``data`` a CUDA float64
+  tensor in the canonical block layout;
+* ``Env(t, bond, data)``: environment;
+* ``MpoSite(qp, tl, tr, W)``: MPO site tensor, ``W`` a host float64 array
+  indexed ``[s_out, s_in, bl, br]``.
+
+Functions keep the C names: ``dmrg3s_apply_heff``, ``dmrg3s_expand``,
+``dmrg3s_update_env`` ...
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmrg3s.so")
+
+DMRG3S_FP64, DMRG3S_TF32X3, DMRG3S_TF32 = 0, 1, 2
+PRECISIONS = {"fp64": DMRG3S_FP64, "tf32x3": DMRG3S_TF32X3, "tf32": DMRG3S_TF32}
+
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class _Bond(ctypes.Structure):
+    _fields_ = [("nsec", ctypes.c_int32), ("q", i32p), ("dim", i64p)]
+
+
+class _Site(ctypes.Structure):
+    _fields_ = [("nsym", ctypes.c_int32), ("d", ctypes.c_int32), ("qp", i32p),
+                ("left", _Bond), ("right", _Bond), ("data", ctypes.c_void_p)]
+
+
+class _Env(ctypes.Structure):
+    _fields_ = [("nsym", ctypes.c_int32), ("w", ctypes.c_int32), ("t", i32p),
+                ("bond", _Bond), ("data", ctypes.c_void_p)]
+
+
+class _MpoSite(ctypes.Structure):
+    _fields_ = [("nsym", ctypes.c_int32), ("d", ctypes.c_int32), ("wl", ctypes.c_int32),
+                ("wr", ctypes.c_int32), ("qp", i32p), ("tl", i32p), ("tr", i32p), ("W", f64p)]
+
+
+class Dmrg3sError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = "%s failed: %s (status %d)" % (where, _status_string(status), status)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdmrg3s.so is not built (run __graft_entry__.build()); "
+                              "the DMRG3S kernels have no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.dmrg3s_status_string.restype = ctypes.c_char_p
+        L.dmrg3s_last_error.restype = ctypes.c_char_p
+        L.dmrg3s_last_error.argtypes = [ctypes.c_void_p]
+        L.dmrg3s_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]
+        L.dmrg3s_destroy.argtypes = [ctypes.c_void_p]
+        L.dmrg3s_site_size.argtypes = [ctypes.POINTER(_Site), i64p]
+        L.dmrg3s_env_size.argtypes = [ctypes.POINTER(_Env), i64p]
+        L.dmrg3s_site_blocks.argtypes = [ctypes.POINTER(_Site), i64p, i64p]
+        L.dmrg3s_env_blocks.argtypes = [ctypes.POINTER(_Env), i64p, i64p]
+        L.dmrg3s_expanded_bond.argtypes = [ctypes.c_int32, ctypes.POINTER(_Bond), ctypes.c_int32,
+                                           i32p, ctypes.c_int32, i32p, i32p, i64p]
+        L.dmrg3s_apply_heff.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Env),
+                                        ctypes.POINTER(_MpoSite), ctypes.POINTER(_Env),
+                                        ctypes.POINTER(_Site), ctypes.POINTER(_Site),
+                                        ctypes.c_int, ctypes.c_void_p]
+        L.dmrg3s_expand.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_Env),
+                                    ctypes.POINTER(_MpoSite), ctypes.POINTER(_Site),
+                                    ctypes.c_double, ctypes.POINTER(_Site), ctypes.c_int,
+                                    ctypes.c_void_p]
+        L.dmrg3s_update_env.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_Env),
+                                        ctypes.POINTER(_MpoSite), ctypes.POINTER(_Site),
+                                        ctypes.POINTER(_Env), ctypes.c_int, ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _status_string(status):
+    try:
+        return lib().dmrg3s_status_string(int(status)).decode()
+    except Exception:
+        return "status %d" % status
+
+
+# ---- Python-side tensors ------------------------------------------------------------
+
+class Bond:
+    def __init__(self, q, dim):
+        dim = np.ascontiguousarray(dim, dtype=np.int64).reshape(-1)
+        q = np.asarray(q, dtype=np.int32)
+        if q.ndim == 1:
+            q = q.reshape(len(dim), -1) if q.size else np.zeros((len(dim), 0), dtype=np.int32)
+        self.q = np.ascontiguousarray(q, dtype=np.int32)
+        self.dim = dim
+
+    @classmethod
+    def from_neutral(cls, b):
+        return cls(b["q"], b["dim"])
+
+    @property
+    def nsym(self):
+        return self.q.shape[1]
+
+    def _c(self):
+        return _Bond(len(self.dim), self.q.ctypes.data_as(i32p) if self.q.size else None,
+                     self.dim.ctypes.data_as(i64p))
+
+    def __eq__(self, other):
+        return np.array_equal(self.q, other.q) and np.array_equal(self.dim, other.dim)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+class Site:
+    """MPS site tensor M[s](al, ar) with canonical block layout on the device."""
+
+    def __init__(self, qp, left, right, data=None):
+        self.qp = np.ascontiguousarray(np.asarray(qp, dtype=np.int32).reshape(len(qp), -1))
+        self.left, self.right, self.data = left, right, data
+
+    @property
+    def nsym(self):
+        return self.qp.shape[1]
+
+    @property
+    def d(self):
+        return self.qp.shape[0]
+
+    def _c(self):
+        self._keep = (self.left._c(), self.right._c())
+        return _Site(self.nsym, self.d, self.qp.ctypes.data_as(i32p) if self.qp.size else None,
+                     self._keep[0], self._keep[1], _ptr(self.data))
+
+    def size(self):
+        n = ctypes.c_int64()
+        c = self._c()
+        _check(lib().dmrg3s_site_size(ctypes.byref(c), ctypes.byref(n)), "dmrg3s_site_size")
+        return n.value
+
+    def blocks(self):
+        """Canonical block table: rows (s, i, j, offset, rows, cols)."""
+        c = self._c()
+        n = ctypes.c_int64()
+        _check(lib().dmrg3s_site_blocks(ctypes.byref(c), ctypes.byref(n), None), "dmrg3s_site_blocks")
+        tab = np.zeros((n.value, 6), dtype=np.int64)
+        _check(lib().dmrg3s_site_blocks(ctypes.byref(c), ctypes.byref(n), tab.ctypes.data_as(i64p)),
+               "dmrg3s_site_blocks")
+        return tab
+
+
+class Env:
+    """Environment E[b](a_bra, a_ket) on one bond with canonical block layout."""
+
+    def __init__(self, t, bond, data=None):
+        self.t = np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(len(t), -1))
+        self.bond, self.data = bond, data
+
+    @property
+    def nsym(self):
+        return self.t.shape[1]
+
+    @property
+    def w(self):
+        return self.t.shape[0]
+
+    def _c(self):
+        self._keep = self.bond._c()
+        return _Env(self.nsym, self.w, self.t.ctypes.data_as(i32p) if self.t.size else None,
+                    self._keep, _ptr(self.data))
+
+    def size(self):
+        n = ctypes.c_int64()
+        c = self._c()
+        _check(lib().dmrg3s_env_size(ctypes.byref(c), ctypes.byref(n)), "dmrg3s_env_size")
+        return n.value
+
+    def blocks(self):
+        c = self._c()
+        n = ctypes.c_int64()
+        _check(lib().dmrg3s_env_blocks(ctypes.byref(c), ctypes.byref(n), None), "dmrg3s_env_blocks")
+        tab = np.zeros((n.value, 6), dtype=np.int64)
+        _check(lib().dmrg3s_env_blocks(ctypes.byref(c), ctypes.byref(n), tab.ctypes.data_as(i64p)),
+               "dmrg3s_env_blocks")
+        return tab
+
+
+class MpoSite:
+    def __init__(self, qp, tl, tr, W):
+        self.W = np.ascontiguousarray(W, dtype=np.float64)
+        d, _, wl, wr = self.W.shape
+        self.qp = np.ascontiguousarray(np.asarray(qp, dtype=np.int32).reshape(d, -1))
+        self.tl = np.ascontiguousarray(np.asarray(tl, dtype=np.int32).reshape(wl, -1))
+        self.tr = np.ascontiguousarray(np.asarray(tr, dtype=np.int32).reshape(wr, -1))
+
+    def _c(self):
+        nsym = self.qp.shape[1]
+        d, _, wl, wr = self.W.shape
+
+        def p(a):
+            return a.ctypes.data_as(i32p) if a.size else None
+        return _MpoSite(nsym, d, wl, wr, p(self.qp), p(self.tl), p(self.tr),
+                        self.W.ctypes.data_as(f64p))
+
+
+def expanded_bond(bond, t, include_base=False):
+    """Fused bond of the expansion (dmrg3s_expanded_bond)."""
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.int32).reshape(len(t), -1))
+    nsym = bond.nsym
+    cb = bond._c()
+    n = ctypes.c_int32()
+    tp = t.ctypes.data_as(i32p) if t.size else None
+    _check(lib().dmrg3s_expanded_bond(nsym, ctypes.byref(cb), t.shape[0], tp, int(include_base),
+                                      ctypes.byref(n), None, None), "dmrg3s_expanded_bond")
+    q = np.zeros((n.value, nsym), dtype=np.int32)
+    dim = np.zeros(n.value, dtype=np.int64)
+    _check(lib().dmrg3s_expanded_bond(nsym, ctypes.byref(cb), t.shape[0], tp, int(include_base),
+                                      ctypes.byref(n), q.ctypes.data_as(i32p) if q.size else None,
+                                      dim.ctypes.data_as(i64p)), "dmrg3s_expanded_bond")
+    return Bond(q, dim)
+
+
+def _check(status, where, ctx=None):
+    if status != 0:
+        detail = ""
+        if ctx is not None:
+            detail = lib().dmrg3s_last_error(ctx).decode()
+        raise Dmrg3sError(status, where, detail)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+# ---- context and entry points (same names as the C ABI) -------------------------------
+
+class Context:
+    def __init__(self, device=0, workspace_bytes=0):
+        self.handle = ctypes.c_void_p()
+        _check(lib().dmrg3s_create(ctypes.byref(self.handle), int(device), int(workspace_bytes)),
+               "dmrg3s_create")
+
+    def close(self):
+        if self.handle:
+            lib().dmrg3s_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dmrg3s_create(device=0, workspace_bytes=0):
+    return Context(device, workspace_bytes)
+
+
+def dmrg3s_destroy(ctx):
+    ctx.close()
+
+
+def dmrg3s_apply_heff(ctx, L, W, R, A, HA, prec="fp64", stream=None):
+    cL, cR, cA, cH, cW = L._c(), R._c(), A._c(), HA._c(), W._c()
+    _check(lib().dmrg3s_apply_heff(ctx.handle, ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR),
+                                   ctypes.byref(cA), ctypes.byref(cH), _prec(prec), _stream(stream)),
+           "dmrg3s_apply_heff", ctx.handle)
+
+
+def dmrg3s_expand(ctx, direction, env, W, M, alpha, P, prec="fp64", stream=None):
+    ce, cW, cM, cP = env._c(), W._c(), M._c(), P._c()
+    _check(lib().dmrg3s_expand(ctx.handle, int(direction), ctypes.byref(ce), ctypes.byref(cW),
+                               ctypes.byref(cM), float(alpha), ctypes.byref(cP), _prec(prec),
+                               _stream(stream)), "dmrg3s_expand", ctx.handle)
+
+
+def dmrg3s_update_env(ctx, direction, env, W, A, out, prec="fp64", stream=None):
+    ce, cW, cA, co = env._c(), W._c(), A._c(), out._c()
+    _check(lib().dmrg3s_update_env(ctx.handle, int(direction), ctypes.byref(ce), ctypes.byref(cW),
+                                   ctypes.byref(cA), ctypes.byref(co), _prec(prec), _stream(stream)),
+           "dmrg3s_update_env", ctx.handle)
+
+
+# ---- packing between neutral block dictionaries and the canonical layout -----------------
+
+def pack_blocks(table, blocks, keyfn=lambda r: (int(r[0]), int(r[1]), int(r[2]))):
+    """Flat float64 host array holding ``blocks`` in the order of a block table."""
+    n = int(table[-1, 3] + table[-1, 4] * table[-1, 5]) if len(table) else 0
+    flat = np.zeros(n, dtype=np.float64)
+    for r in table:
+        key = keyfn(r)
+        if key in blocks:
+            off, rows, cols = int(r[3]), int(r[4]), int(r[5])
+            flat[off:off + rows * cols] = np.asarray(blocks[key], dtype=np.float64).reshape(-1)
+    return flat
+
+
+def unpack_blocks(table, flat):
+    out = {}
+    for r in table:
+        off, rows, cols = int(r[3]), int(r[4]), int(r[5])
+        out[(int(r[0]), int(r[1]), int(r[2]))] = np.asarray(flat[off:off + rows * cols]).reshape(rows, cols)
+    return out
+
+
+def site_from_neutral(spec, device="cuda"):
+    import torch
+    s = Site(spec["qp"], Bond.from_neutral(spec["left"]), Bond.from_neutral(spec["right"]))
+    flat = pack_blocks(s.blocks(), spec["blocks"])
+    s.data = torch.from_numpy(flat).to(device)
+    return s
+
+
+def env_from_neutral(spec, device="cuda"):
+    import torch
+    e = Env(spec["t"], Bond.from_neutral(spec["bond"] if "bond" in spec else spec["ket"]))
+    flat = pack_blocks(e.blocks(), spec["blocks"])
+    e.data = torch.from_numpy(flat).to(device)
+    return e
+
+
+def empty_site_like(qp, left, right, device="cuda"):
+    import torch
+    s = Site(qp, left, right)
+    s.data = torch.zeros(max(s.size(), 1), dtype=torch.float64, device=device)
+    return s
+
+
+def empty_env(t, bond, device="cuda"):
+    import torch
+    e = Env(t, bond)
+    e.data = torch.zeros(max(e.size(), 1), dtype=torch.float64, device=device)
+    return e
+
+
+def mpo_from_neutral(spec):
+    return MpoSite(spec["qp"], spec["tl"], spec["tr"], spec["W"])

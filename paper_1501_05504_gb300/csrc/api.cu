@@ -1,0 +1,434 @@
+// extern "C" entry points of the contraction part of the C ABI (include/dmrg3s.h).
+#include <cstring>
+#include <new>
+
+#include "context.hpp"
+#include "dmrg3s.h"
+
+using namespace dmrg3s;
+
+namespace dmrg3s {
+
+void Hasher::bond(const Bond& b) {
+  pod(b.nsym);
+  vec(b.q);
+  vec(b.dim);
+}
+void Hasher::site(const SiteLayout& s) {
+  pod(s.nsym);
+  pod(s.d);
+  vec(s.qp);
+  bond(s.left);
+  bond(s.right);
+}
+void Hasher::env(const EnvLayout& e) {
+  pod(e.nsym);
+  pod(e.w);
+  vec(e.t);
+  bond(e.bond);
+}
+void Hasher::mpo(const MpoLayout& w) {
+  pod(w.nsym);
+  pod(w.d);
+  pod(w.wl);
+  pod(w.wr);
+  vec(w.qp);
+  vec(w.tl);
+  vec(w.tr);
+  vec(w.W);
+}
+
+DevicePlan::~DevicePlan() {
+  if (mem) cudaFree(mem);
+}
+
+namespace {
+template <class T>
+size_t bytes_of(const std::vector<T>& v) {
+  return ((v.size() * sizeof(T)) + 255) / 256 * 256;
+}
+template <class T>
+T* place(char* base, size_t* off, const std::vector<T>& v, std::vector<char>* staging) {
+  T* p = reinterpret_cast<T*>(base + *off);
+  if (!v.empty()) std::memcpy(staging->data() + *off, v.data(), v.size() * sizeof(T));
+  *off += bytes_of(v);
+  return v.empty() ? nullptr : p;
+}
+}  // namespace
+
+dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
+  std::unique_ptr<DevicePlan> dp(new (std::nothrow) DevicePlan());
+  if (!dp) return DMRG3S_ERR_OOM;
+  dp->host = std::move(host);
+  const Plan& h = dp->host;
+  size_t total = bytes_of(h.g1.tiles) + bytes_of(h.g1.tasks) + bytes_of(h.g1.segs) +
+                 bytes_of(h.c2.chunks) + bytes_of(h.c2.tasks) + bytes_of(h.c2.terms) +
+                 bytes_of(h.g3.tiles) + bytes_of(h.g3.tasks) + bytes_of(h.g3.segs);
+  if (total == 0) total = 256;
+  if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
+  std::vector<char> staging(total, 0);
+  char* base = static_cast<char*>(dp->mem);
+  size_t off = 0;
+  dp->g1_tiles = place(base, &off, h.g1.tiles, &staging);
+  dp->g1_tasks = place(base, &off, h.g1.tasks, &staging);
+  dp->g1_segs = place(base, &off, h.g1.segs, &staging);
+  dp->c2_chunks = place(base, &off, h.c2.chunks, &staging);
+  dp->c2_tasks = place(base, &off, h.c2.tasks, &staging);
+  dp->c2_terms = place(base, &off, h.c2.terms, &staging);
+  dp->g3_tiles = place(base, &off, h.g3.tiles, &staging);
+  dp->g3_tasks = place(base, &off, h.g3.tasks, &staging);
+  dp->g3_segs = place(base, &off, h.g3.segs, &staging);
+  if (cudaMemcpy(dp->mem, staging.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+    return DMRG3S_ERR_CUDA;
+  *out = std::move(dp);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status run_plan(const DevicePlan& p, const double* g1A, const double* g1B, double* ws1,
+                       double* c2out, double c2scale, const double* g3A, const double* g3B,
+                       double* g3C, cudaStream_t st) {
+  const Plan& h = p.host;
+  launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks, p.g1_segs,
+                  g1A, g1B, ws1, st);
+  launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1, c2out,
+                     c2scale, st);
+  if (h.has_g3)
+    launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks, p.g3_segs,
+                    g3A, g3B, g3C, st);
+  return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
+}
+
+}  // namespace dmrg3s
+
+namespace {
+
+dmrg3s_status fail(Context* c, dmrg3s_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+dmrg3s_status use_device(Context* c) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "cudaGetDevice failed");
+  if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "cudaSetDevice failed");
+  return DMRG3S_OK;
+}
+
+// Fetch a cached plan or build and upload one.
+template <class Build>
+dmrg3s_status get_plan(Context* c, uint64_t key, Build build, const DevicePlan** out) {
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    *out = it->second.get();
+    return DMRG3S_OK;
+  }
+  Plan p;
+  std::string err;
+  dmrg3s_status st = build(&p, &err);
+  if (st != DMRG3S_OK) return fail(c, st, err);
+  std::unique_ptr<DevicePlan> dp;
+  st = upload_plan(std::move(p), &dp);
+  if (st != DMRG3S_OK) return fail(c, st, "uploading a contraction plan failed");
+  *out = dp.get();
+  c->plans[key] = std::move(dp);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status check_ws(Context* c, const Plan& p) {
+  const size_t need = (size_t)(p.ws1 + p.ws2) * sizeof(double);
+  if (need > c->ws_bytes)
+    return fail(c, DMRG3S_ERR_OOM,
+                "context workspace too small: need " + std::to_string(need) + " bytes");
+  return DMRG3S_OK;
+}
+
+dmrg3s_status prec_ok(Context* c, dmrg3s_precision prec) {
+  if (prec == DMRG3S_FP64) return DMRG3S_OK;
+  if (prec == DMRG3S_TF32X3 || prec == DMRG3S_TF32)
+    return fail(c, DMRG3S_ERR_UNSUPPORTED, "this entry point runs in FP64 only");
+  return fail(c, DMRG3S_ERR_ARG, "unknown precision");
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes) {
+  if (!ctx) return DMRG3S_ERR_ARG;
+  *ctx = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DMRG3S_ERR_CUDA;
+  Context* c = new (std::nothrow) Context();
+  if (!c) return DMRG3S_ERR_OOM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return DMRG3S_ERR_CUDA;
+  }
+  c->ws_bytes = workspace_bytes ? workspace_bytes : (size_t)256 << 20;
+  if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
+    delete c;
+    return DMRG3S_ERR_CUDA;
+  }
+  *ctx = reinterpret_cast<dmrg3s_ctx>(c);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c) return DMRG3S_ERR_ARG;
+  use_device(c);
+  cudaDeviceSynchronize();
+  c->plans.clear();
+  if (c->ws) cudaFree(c->ws);
+  delete c;
+  return DMRG3S_OK;
+}
+
+const char* dmrg3s_status_string(dmrg3s_status s) {
+  switch (s) {
+    case DMRG3S_OK: return "ok";
+    case DMRG3S_ERR_ARG: return "invalid argument";
+    case DMRG3S_ERR_SHAPE: return "inconsistent shapes";
+    case DMRG3S_ERR_QN: return "inconsistent charges";
+    case DMRG3S_ERR_OOM: return "out of memory";
+    case DMRG3S_ERR_CUDA: return "CUDA error";
+    case DMRG3S_ERR_NOT_CONVERGED: return "not converged";
+    case DMRG3S_ERR_BREAKDOWN: return "Lanczos breakdown";
+    case DMRG3S_ERR_TIMEOUT: return "device wait timed out";
+    case DMRG3S_ERR_NUMERIC: return "NaN or Inf";
+    case DMRG3S_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* dmrg3s_last_error(dmrg3s_ctx ctx) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  return c ? c->last_error.c_str() : "no context";
+}
+
+dmrg3s_status dmrg3s_site_size(const dmrg3s_site* M, int64_t* nelem) {
+  if (!nelem) return DMRG3S_ERR_ARG;
+  SiteLayout s;
+  std::string err;
+  dmrg3s_status st = make_site(M, &s, &err);
+  if (st != DMRG3S_OK) return st;
+  *nelem = s.size;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_env_size(const dmrg3s_env* E, int64_t* nelem) {
+  if (!nelem) return DMRG3S_ERR_ARG;
+  EnvLayout e;
+  std::string err;
+  dmrg3s_status st = make_env(E, &e, &err);
+  if (st != DMRG3S_OK) return st;
+  *nelem = e.size;
+  return DMRG3S_OK;
+}
+
+static void write_table(const std::vector<Block>& blocks, int64_t* nblocks, int64_t* table) {
+  *nblocks = (int64_t)blocks.size();
+  if (!table) return;
+  for (size_t n = 0; n < blocks.size(); ++n) {
+    const Block& b = blocks[n];
+    int64_t* row = table + 6 * n;
+    row[0] = b.a;
+    row[1] = b.b;
+    row[2] = b.c;
+    row[3] = b.off;
+    row[4] = b.rows;
+    row[5] = b.cols;
+  }
+}
+
+dmrg3s_status dmrg3s_site_blocks(const dmrg3s_site* M, int64_t* nblocks, int64_t* table) {
+  if (!nblocks) return DMRG3S_ERR_ARG;
+  SiteLayout s;
+  std::string err;
+  dmrg3s_status st = make_site(M, &s, &err);
+  if (st != DMRG3S_OK) return st;
+  write_table(s.blocks, nblocks, table);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_env_blocks(const dmrg3s_env* E, int64_t* nblocks, int64_t* table) {
+  if (!nblocks) return DMRG3S_ERR_ARG;
+  EnvLayout e;
+  std::string err;
+  dmrg3s_status st = make_env(E, &e, &err);
+  if (st != DMRG3S_OK) return st;
+  write_table(e.blocks, nblocks, table);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_t w,
+                                   const int32_t* t, int32_t include_base, int32_t* nsec,
+                                   int32_t* q, int64_t* dim) {
+  if (!nsec || w < 1 || (nsym > 0 && !t)) return DMRG3S_ERR_ARG;
+  Bond b;
+  std::string err;
+  dmrg3s_status st = make_bond(nsym, bond, &b, &err);
+  if (st != DMRG3S_OK) return st;
+  std::vector<Charge> tc(w, Charge{});
+  for (int i = 0; i < w; ++i)
+    for (int k = 0; k < nsym; ++k) tc[i][k] = t[(size_t)i * nsym + k];
+  FusedBond f;
+  st = fuse_bond(b, w, tc, include_base != 0, &f);
+  if (st != DMRG3S_OK) return st;
+  *nsec = f.bond.nsec();
+  if (q && nsym > 0)
+    for (int i = 0; i < f.bond.nsec(); ++i)
+      for (int k = 0; k < nsym; ++k) q[(size_t)i * nsym + k] = f.bond.q[i][k];
+  if (dim)
+    for (int i = 0; i < f.bond.nsec(); ++i) dim[i] = f.bond.dim[i];
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                                const dmrg3s_env* R, const dmrg3s_site* A, dmrg3s_site* HA,
+                                dmrg3s_precision prec, dmrg3s_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !L || !W || !R || !A || !HA) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
+  dmrg3s_status st = prec_ok(c, prec);
+  if (st != DMRG3S_OK) return st;
+  std::string err;
+  EnvLayout le, re;
+  MpoLayout w;
+  SiteLayout a, ha;
+  if ((st = make_env(L, &le, &err)) || (st = make_env(R, &re, &err)) ||
+      (st = make_mpo(W, &w, &err)) || (st = make_site(A, &a, &err)) ||
+      (st = make_site(HA, &ha, &err)))
+    return fail(c, st, err);
+  if ((st = check_site_mpo(a, w, &err)) ||
+      (st = check_env(le, a.left, w.wl, w.tl, "L", &err)) ||
+      (st = check_env(re, a.right, w.wr, w.tr, "R", &err)))
+    return fail(c, st, err);
+  if (!same_bond(a.left, ha.left) || !same_bond(a.right, ha.right) || a.d != ha.d ||
+      !same_charges(a.qp, ha.qp))
+    return fail(c, DMRG3S_ERR_SHAPE, "HA must have the structure of A");
+  if (!L->data || !R->data || !A->data || !HA->data)
+    return fail(c, DMRG3S_ERR_ARG, "NULL device data pointer");
+  Hasher h;
+  h.pod((int)Kind::Heff);
+  h.env(le);
+  h.mpo(w);
+  h.env(re);
+  h.site(a);
+  const DevicePlan* p = nullptr;
+  st = get_plan(c, h.h, [&](Plan* pl, std::string* e) { return plan_heff(le, w, re, a, pl, e); },
+                &p);
+  if (st != DMRG3S_OK) return st;
+  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  double* ws2 = ws1 + p->host.ws1;
+  st = run_plan(*p, L->data, A->data, ws1, ws2, 1.0, ws2, R->data, HA->data,
+                reinterpret_cast<cudaStream_t>(stream));
+  return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
+}
+
+dmrg3s_status dmrg3s_expand(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
+                            const dmrg3s_mpo_site* W, const dmrg3s_site* M, double alpha,
+                            dmrg3s_site* P, dmrg3s_precision prec, dmrg3s_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !env || !W || !M || !P) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
+  if (dir != 1 && dir != -1) return fail(c, DMRG3S_ERR_ARG, "dir must be +1 or -1");
+  dmrg3s_status st = prec_ok(c, prec);
+  if (st != DMRG3S_OK) return st;
+  std::string err;
+  EnvLayout e;
+  MpoLayout w;
+  SiteLayout m, pl;
+  if ((st = make_env(env, &e, &err)) || (st = make_mpo(W, &w, &err)) ||
+      (st = make_site(M, &m, &err)) || (st = make_site(P, &pl, &err)))
+    return fail(c, st, err);
+  if ((st = check_site_mpo(m, w, &err))) return fail(c, st, err);
+  if (dir == 1) {
+    if ((st = check_env(e, m.left, w.wl, w.tl, "env (L)", &err))) return fail(c, st, err);
+  } else {
+    if ((st = check_env(e, m.right, w.wr, w.tr, "env (R)", &err))) return fail(c, st, err);
+  }
+  FusedBond f;
+  fuse_bond(dir == 1 ? m.right : m.left, dir == 1 ? w.wr : w.wl, dir == 1 ? w.tr : w.tl, false,
+            &f);
+  const Bond& keep = dir == 1 ? m.left : m.right;
+  const Bond& pkeep = dir == 1 ? pl.left : pl.right;
+  const Bond& pfused = dir == 1 ? pl.right : pl.left;
+  if (!same_bond(keep, pkeep) || !same_bond(f.bond, pfused) || pl.d != m.d ||
+      !same_charges(pl.qp, m.qp))
+    return fail(c, DMRG3S_ERR_SHAPE, "P does not have the expanded structure of M");
+  if (!env->data || !M->data || !P->data) return fail(c, DMRG3S_ERR_ARG, "NULL device data");
+  Hasher h;
+  h.pod(dir == 1 ? (int)Kind::ExpandLR : (int)Kind::ExpandRL);
+  h.env(e);
+  h.mpo(w);
+  h.site(m);
+  const DevicePlan* p = nullptr;
+  st = get_plan(
+      c, h.h,
+      [&](Plan* pn, std::string* er) {
+        return dir == 1 ? plan_expand_lr(e, w, m, pl, f, pn, er)
+                        : plan_expand_rl(e, w, m, pl, f, pn, er);
+      },
+      &p);
+  if (st != DMRG3S_OK) return st;
+  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  const double* g1A = dir == 1 ? env->data : M->data;
+  const double* g1B = dir == 1 ? M->data : env->data;
+  st = run_plan(*p, g1A, g1B, ws1, P->data, alpha, nullptr, nullptr, nullptr,
+                reinterpret_cast<cudaStream_t>(stream));
+  return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
+}
+
+dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
+                                const dmrg3s_mpo_site* W, const dmrg3s_site* A, dmrg3s_env* out,
+                                dmrg3s_precision prec, dmrg3s_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !env || !W || !A || !out) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
+  if (dir != 1 && dir != -1) return fail(c, DMRG3S_ERR_ARG, "dir must be +1 or -1");
+  dmrg3s_status st = prec_ok(c, prec);
+  if (st != DMRG3S_OK) return st;
+  std::string err;
+  EnvLayout e, o;
+  MpoLayout w;
+  SiteLayout a;
+  if ((st = make_env(env, &e, &err)) || (st = make_env(out, &o, &err)) ||
+      (st = make_mpo(W, &w, &err)) || (st = make_site(A, &a, &err)))
+    return fail(c, st, err);
+  if ((st = check_site_mpo(a, w, &err))) return fail(c, st, err);
+  if (dir == 1) {
+    if ((st = check_env(e, a.left, w.wl, w.tl, "env (L_{i-1})", &err)) ||
+        (st = check_env(o, a.right, w.wr, w.tr, "out (L_i)", &err)))
+      return fail(c, st, err);
+  } else {
+    if ((st = check_env(e, a.right, w.wr, w.tr, "env (R_{i+1})", &err)) ||
+        (st = check_env(o, a.left, w.wl, w.tl, "out (R_i)", &err)))
+      return fail(c, st, err);
+  }
+  if (!env->data || !A->data || !out->data) return fail(c, DMRG3S_ERR_ARG, "NULL device data");
+  Hasher h;
+  h.pod(dir == 1 ? (int)Kind::EnvLR : (int)Kind::EnvRL);
+  h.env(e);
+  h.mpo(w);
+  h.site(a);
+  const DevicePlan* p = nullptr;
+  st = get_plan(
+      c, h.h,
+      [&](Plan* pn, std::string* er) {
+        return dir == 1 ? plan_env_lr(e, w, a, o, pn, er) : plan_env_rl(e, w, a, o, pn, er);
+      },
+      &p);
+  if (st != DMRG3S_OK) return st;
+  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  double* ws2 = ws1 + p->host.ws1;
+  const double* g1A = dir == 1 ? env->data : A->data;
+  const double* g1B = dir == 1 ? A->data : env->data;
+  st = run_plan(*p, g1A, g1B, ws1, ws2, 1.0, A->data, ws2, out->data,
+                reinterpret_cast<cudaStream_t>(stream));
+  return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Device task tables and launchers of the block-sparse contraction kernels.
+//
+// All operand addresses are element offsets relative to base pointers passed
+// at launch, so one uploaded table serves every matrix-vector product of a
+// Lanczos run (only the vector pointers change).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dmrg3s {
+
+// One K-segment of a grouped GEMM task: C += scale * op(A) op(B) over K.
+struct GemmSeg {
+  int64_t offA, offB;
+  int32_t lda, ldb, K, pad;
+  double scale;
+};
+
+// One output block C (M x N, row-major with leading dimension ldc) of a
+// grouped GEMM.  Segments [seg0, seg0 + nseg) are summed; nseg == 0 writes 0.
+struct GemmTask {
+  int64_t offC;
+  int32_t ldc, M, N, seg0, nseg, pad;
+};
+
+// One 64 x 64 output tile of a task.
+struct GemmTile {
+  int32_t task, tm, tn, pad;
+};
+
+// Linear combination of blocks: out = sum_k coef_k in_k (rows x cols).
+struct CombTask {
+  int64_t offOut;
+  int32_t ldo, rows, cols, t0, nt, pad;
+};
+struct CombTerm {
+  int64_t offIn;
+  int32_t ldi, pad;
+  double coef;
+};
+// Work unit of the combination kernel: up to kCombRows rows of one task.
+struct CombChunk {
+  int32_t task, row0, nrows, pad;
+};
+constexpr int kCombRows = 16;
+
+enum class Trans { N, T };
+
+// FP64 grouped GEMM on the CUDA cores.  opA = A (M x K, lda) or A^T (A stored
+// K x M); opB = B (K x N, ldb) or B^T (B stored N x K).
+void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, const GemmTask* tasks,
+                     const GemmSeg* segs, const double* A, const double* B, double* C,
+                     cudaStream_t st);
+
+// out = scale * sum_k coef_k in_k for every task.
+void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                        const CombTerm* terms, const double* in, double* out, double scale,
+                        cudaStream_t st);
+
+}  // namespace dmrg3s

@@ -1,0 +1,145 @@
+// FP64 kernels of the block-sparse contraction (CUDA cores).
+//
+// The grouped GEMM computes every block product of one contraction step of
+// the order (((L M) W) R) of Sec. V of arXiv:1501.05504 in one launch: one CTA
+// per 64 x 64 output tile, summing all K-segments of its task.  The
+// combination kernel applies the MPO step (T2 = sum W T1), which costs
+// O(m^2 d^2 w^2) and is bound by memory bandwidth.
+#include "kernels.hpp"
+
+namespace dmrg3s {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <Trans TA, Trans TB>
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTile* __restrict__ tiles,
+                                                      const GemmTask* __restrict__ tasks,
+                                                      const GemmSeg* __restrict__ segs,
+                                                      const double* __restrict__ A,
+                                                      const double* __restrict__ B,
+                                                      double* __restrict__ C) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const GemmTile tile = tiles[blockIdx.x];
+  const GemmTask task = tasks[tile.task];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = tile.tm * BM, n0 = tile.tn * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int sgi = 0; sgi < task.nseg; ++sgi) {
+    const GemmSeg sg = segs[task.seg0 + sgi];
+    const double* Ap = A + sg.offA;
+    const double* Bp = B + sg.offB;
+    for (int k0 = 0; k0 < sg.K; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int m, k;
+        if (TA == Trans::N) {
+          k = tid % 16;
+          m = tid / 16 + 16 * r;
+        } else {
+          m = tid % 64;
+          k = tid / 64 + 4 * r;
+        }
+        const int gm = m0 + m, gk = k0 + k;
+        double v = 0.0;
+        if (gm < task.M && gk < sg.K)
+          v = (TA == Trans::N) ? Ap[(int64_t)gm * sg.lda + gk] : Ap[(int64_t)gk * sg.lda + gm];
+        As[k][m] = v * sg.scale;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int n, k;
+        if (TB == Trans::N) {
+          n = tid % 64;
+          k = tid / 64 + 4 * r;
+        } else {
+          k = tid % 16;
+          n = tid / 16 + 16 * r;
+        }
+        const int gn = n0 + n, gk = k0 + k;
+        double v = 0.0;
+        if (gn < task.N && gk < sg.K)
+          v = (TB == Trans::N) ? Bp[(int64_t)gk * sg.ldb + gn] : Bp[(int64_t)gn * sg.ldb + gk];
+        Bs[k][n] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= task.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn < task.N) C[task.offC + (int64_t)gm * task.ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) combine_f64_kernel(const CombChunk* __restrict__ chunks,
+                                                         const CombTask* __restrict__ tasks,
+                                                         const CombTerm* __restrict__ terms,
+                                                         const double* __restrict__ in,
+                                                         double* __restrict__ out,
+                                                         double scale) {
+  const CombChunk ch = chunks[blockIdx.x];
+  const CombTask t = tasks[ch.task];
+  const int n = ch.nrows * t.cols;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int r = ch.row0 + idx / t.cols, c = idx % t.cols;
+    double acc = 0.0;
+    for (int k = 0; k < t.nt; ++k) {
+      const CombTerm tm = terms[t.t0 + k];
+      acc = fma(tm.coef, in[tm.offIn + (int64_t)r * tm.ldi + c], acc);
+    }
+    out[t.offOut + (int64_t)r * t.ldo + c] = scale * acc;
+  }
+}
+
+}  // namespace
+
+void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, const GemmTask* tasks,
+                     const GemmSeg* segs, const double* A, const double* B, double* C,
+                     cudaStream_t st) {
+  if (ntiles <= 0) return;
+  dim3 grid(ntiles), block(NT);
+  if (ta == Trans::N && tb == Trans::N)
+    gemm_f64_kernel<Trans::N, Trans::N><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
+  else if (ta == Trans::N && tb == Trans::T)
+    gemm_f64_kernel<Trans::N, Trans::T><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
+  else if (ta == Trans::T && tb == Trans::N)
+    gemm_f64_kernel<Trans::T, Trans::N><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
+  else
+    gemm_f64_kernel<Trans::T, Trans::T><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
+}
+
+void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                        const CombTerm* terms, const double* in, double* out, double scale,
+                        cudaStream_t st) {
+  if (nchunks <= 0) return;
+  combine_f64_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out, scale);
+}
+
+}  // namespace dmrg3s

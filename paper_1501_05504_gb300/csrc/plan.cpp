@@ -1,0 +1,329 @@
+// Host-side planning of the block-sparse contractions.  See plan.hpp.
+#include "plan.hpp"
+
+#include <array>
+#include <map>
+
+namespace dmrg3s {
+
+void GemmStage::add(int64_t offC, int ldc, int M, int N, const std::vector<GemmSeg>& s) {
+  if (M <= 0 || N <= 0) return;
+  GemmTask t{};
+  t.offC = offC;
+  t.ldc = ldc;
+  t.M = M;
+  t.N = N;
+  t.seg0 = (int32_t)segs.size();
+  t.nseg = (int32_t)s.size();
+  const int id = (int)tasks.size();
+  tasks.push_back(t);
+  for (const auto& g : s) {
+    segs.push_back(g);
+    flops += 2.0 * M * (double)N * g.K;
+  }
+  const int ntm = (M + 63) / 64, ntn = (N + 63) / 64;
+  for (int a = 0; a < ntm; ++a)
+    for (int b = 0; b < ntn; ++b) tiles.push_back(GemmTile{id, a, b, 0});
+}
+
+void CombStage::add(int64_t offOut, int ldo, int rows, int cols, const std::vector<CombTerm>& t) {
+  if (rows <= 0 || cols <= 0) return;
+  CombTask task{};
+  task.offOut = offOut;
+  task.ldo = ldo;
+  task.rows = rows;
+  task.cols = cols;
+  task.t0 = (int32_t)terms.size();
+  task.nt = (int32_t)t.size();
+  const int id = (int)tasks.size();
+  tasks.push_back(task);
+  terms.insert(terms.end(), t.begin(), t.end());
+  flops += 2.0 * rows * (double)cols * t.size();
+  for (int r = 0; r < rows; r += kCombRows)
+    chunks.push_back(CombChunk{id, r, rows - r < kCombRows ? rows - r : kCombRows, 0});
+}
+
+namespace {
+
+using Key = std::array<int, 4>;
+struct Interm {
+  int64_t off;
+  int rows, cols;
+};
+struct Combo {
+  int rows = 0, cols = 0;
+  std::vector<CombTerm> terms;
+};
+
+inline GemmSeg seg(int64_t offA, int64_t lda, int64_t offB, int64_t ldb, int64_t K) {
+  GemmSeg g{};
+  g.offA = offA;
+  g.offB = offB;
+  g.lda = (int32_t)lda;
+  g.ldb = (int32_t)ldb;
+  g.K = (int32_t)K;
+  g.scale = 1.0;
+  return g;
+}
+
+// Stage 1 + 2 of the left side: T1[bl, s] = L[bl] M[s]; T2 terms.
+void left_stages(const EnvLayout& le, const MpoLayout& W, const SiteLayout& M, Plan* p,
+                 std::map<Key, Interm>* t1, std::map<Key, Combo>* t2) {
+  p->g1.ta = Trans::N;
+  p->g1.tb = Trans::N;
+  int64_t off = 0;
+  for (const Block& lb : le.blocks) {
+    const int bl = lb.a, ip = lb.b, i = lb.c;
+    for (int s = 0; s < M.d; ++s) {
+      const int mb = M.block_of(s, i);
+      if (mb < 0) continue;
+      const Block& blk = M.blocks[mb];
+      const int j = blk.c;
+      const int64_t rows = le.bond.dim[ip], cols = M.right.dim[j], K = M.left.dim[i];
+      (*t1)[Key{bl, s, i, 0}] = Interm{off, (int)rows, (int)cols};
+      p->g1.add(off, (int)cols, (int)rows, (int)cols, {seg(lb.off, K, blk.off, cols, K)});
+      // stage 2 terms
+      for (int so = 0; so < W.d; ++so)
+        for (int br = 0; br < W.wr; ++br) {
+          const double c = W.at(so, s, bl, br);
+          if (c == 0.0) continue;
+          Combo& cb = (*t2)[Key{br, so, ip, j}];
+          cb.rows = (int)rows;
+          cb.cols = (int)cols;
+          CombTerm tm{};
+          tm.offIn = off;
+          tm.ldi = (int32_t)cols;
+          tm.coef = c;
+          cb.terms.push_back(tm);
+        }
+      off += rows * cols;
+    }
+  }
+  p->ws1 = off;
+}
+
+// Stage 1 + 2 of the right side: U1[br, s] = M[s] R[br]^T; U2 terms.
+void right_stages(const EnvLayout& re, const MpoLayout& W, const SiteLayout& M, Plan* p,
+                  std::map<Key, Interm>* u1, std::map<Key, Combo>* u2) {
+  p->g1.ta = Trans::N;
+  p->g1.tb = Trans::T;
+  int64_t off = 0;
+  for (const Block& mb : M.blocks) {
+    const int s = mb.a, i = mb.b, j = mb.c;
+    for (int br = 0; br < re.w; ++br) {
+      const int rb = re.block_of(br, j);
+      if (rb < 0) continue;
+      const Block& rblk = re.blocks[rb];
+      const int jp = rblk.b;
+      const int64_t rows = M.left.dim[i], cols = re.bond.dim[jp], K = M.right.dim[j];
+      (*u1)[Key{br, s, i, 0}] = Interm{off, (int)rows, (int)cols};
+      p->g1.add(off, (int)cols, (int)rows, (int)cols, {seg(mb.off, K, rblk.off, K, K)});
+      for (int so = 0; so < W.d; ++so)
+        for (int bl = 0; bl < W.wl; ++bl) {
+          const double c = W.at(so, s, bl, br);
+          if (c == 0.0) continue;
+          Combo& cb = (*u2)[Key{bl, so, i, jp}];
+          cb.rows = (int)rows;
+          cb.cols = (int)cols;
+          CombTerm tm{};
+          tm.offIn = off;
+          tm.ldi = (int32_t)cols;
+          tm.coef = c;
+          cb.terms.push_back(tm);
+        }
+      off += rows * cols;
+    }
+  }
+  p->ws1 = off;
+}
+
+// Materialise stage-2 blocks contiguously in ws2 (offsets in map order).
+std::map<Key, Interm> materialise(const std::map<Key, Combo>& combos, Plan* p) {
+  std::map<Key, Interm> out;
+  int64_t off = 0;
+  for (const auto& kv : combos) {
+    const Combo& cb = kv.second;
+    out[kv.first] = Interm{off, cb.rows, cb.cols};
+    p->c2.add(off, cb.cols, cb.rows, cb.cols, cb.terms);
+    off += (int64_t)cb.rows * cb.cols;
+  }
+  p->ws2 = off;
+  return out;
+}
+
+}  // namespace
+
+dmrg3s_status check_site_mpo(const SiteLayout& s, const MpoLayout& W, std::string* err) {
+  if (s.nsym != W.nsym) {
+    *err = "site tensor and MPO have different nsym";
+    return DMRG3S_ERR_SHAPE;
+  }
+  if (s.d != W.d) {
+    *err = "site tensor and MPO have different physical dimension";
+    return DMRG3S_ERR_SHAPE;
+  }
+  if (!same_charges(s.qp, W.qp)) {
+    *err = "site tensor and MPO have different physical charges";
+    return DMRG3S_ERR_QN;
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status check_env(const EnvLayout& e, const Bond& bond, int w, const std::vector<Charge>& t,
+                        const char* what, std::string* err) {
+  if (e.nsym != bond.nsym) {
+    *err = std::string(what) + ": nsym differs from the site tensor";
+    return DMRG3S_ERR_SHAPE;
+  }
+  if (!same_bond(e.bond, bond)) {
+    *err = std::string(what) + ": bond differs from the site tensor's bond";
+    return DMRG3S_ERR_SHAPE;
+  }
+  if (e.w != w) {
+    *err = std::string(what) + ": MPO bond dimension differs from W";
+    return DMRG3S_ERR_SHAPE;
+  }
+  if (!same_charges(e.t, t)) {
+    *err = std::string(what) + ": channel charges differ from W";
+    return DMRG3S_ERR_QN;
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status plan_heff(const EnvLayout& le, const MpoLayout& W, const EnvLayout& re,
+                        const SiteLayout& M, Plan* p, std::string* err) {
+  (void)err;
+  p->kind = Kind::Heff;
+  std::map<Key, Interm> t1;
+  std::map<Key, Combo> t2c;
+  left_stages(le, W, M, p, &t1, &t2c);
+  std::map<Key, Interm> t2 = materialise(t2c, p);
+  p->has_g3 = true;
+  p->g3.ta = Trans::N;
+  p->g3.tb = Trans::T;
+  for (const Block& hb : M.blocks) {
+    const int so = hb.a, ip = hb.b, jp = hb.c;
+    std::vector<GemmSeg> segs;
+    for (int br = 0; br < W.wr; ++br) {
+      const int j = M.nsym ? M.right.find(sub(M.right.q[jp], re.t[br])) : 0;
+      if (j < 0) continue;
+      const int rb = re.block_of(br, j);
+      if (rb < 0 || re.blocks[rb].b != jp) continue;
+      auto it = t2.find(Key{br, so, ip, j});
+      if (it == t2.end()) continue;
+      const int64_t K = M.right.dim[j];
+      segs.push_back(seg(it->second.off, K, re.blocks[rb].off, K, K));
+    }
+    p->g3.add(hb.off, (int)hb.cols, (int)hb.rows, (int)hb.cols, segs);
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status plan_expand_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& M,
+                             const SiteLayout& P, const FusedBond& fused, Plan* p,
+                             std::string* err) {
+  (void)err;
+  p->kind = Kind::ExpandLR;
+  std::map<Key, Interm> t1;
+  std::map<Key, Combo> t2c;
+  left_stages(le, W, M, p, &t1, &t2c);
+  const int nsrc = M.right.nsec();
+  for (const Block& pb : P.blocks) {
+    const int so = pb.a, ip = pb.b, k = pb.c;
+    for (int br = 0; br < W.wr; ++br) {
+      const int j = M.nsym ? M.right.find(sub(P.right.q[k], W.tr[br])) : 0;
+      if (j < 0 || fused.target[(size_t)br * nsrc + j] != k) continue;
+      const int64_t coff = fused.offset[(size_t)br * nsrc + j];
+      auto it = t2c.find(Key{br, so, ip, j});
+      static const std::vector<CombTerm> none;
+      p->c2.add(pb.off + coff, (int)pb.cols, (int)pb.rows, (int)M.right.dim[j],
+                it == t2c.end() ? none : it->second.terms);
+    }
+  }
+  p->ws2 = 0;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status plan_env_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& M,
+                          const EnvLayout& out, Plan* p, std::string* err) {
+  (void)err;
+  p->kind = Kind::EnvLR;
+  std::map<Key, Interm> t1;
+  std::map<Key, Combo> t2c;
+  left_stages(le, W, M, p, &t1, &t2c);
+  std::map<Key, Interm> t2 = materialise(t2c, p);
+  p->has_g3 = true;
+  p->g3.ta = Trans::T;
+  p->g3.tb = Trans::N;
+  for (const Block& ob : out.blocks) {
+    const int br = ob.a, ib = ob.b, ik = ob.c;
+    std::vector<GemmSeg> segs;
+    for (int so = 0; so < M.d; ++so) {
+      const int ip = M.nsym ? M.left.find(sub(M.right.q[ib], M.qp[so])) : 0;
+      if (ip < 0) continue;
+      const int ab = M.block_of(so, ip);
+      if (ab < 0 || M.blocks[ab].c != ib) continue;
+      auto it = t2.find(Key{br, so, ip, ik});
+      if (it == t2.end()) continue;
+      const int64_t K = M.left.dim[ip];
+      segs.push_back(seg(M.blocks[ab].off, M.right.dim[ib], it->second.off, M.right.dim[ik], K));
+    }
+    p->g3.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, segs);
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status plan_expand_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& M,
+                             const SiteLayout& P, const FusedBond& fused, Plan* p,
+                             std::string* err) {
+  (void)err;
+  p->kind = Kind::ExpandRL;
+  std::map<Key, Interm> u1;
+  std::map<Key, Combo> u2c;
+  right_stages(re, W, M, p, &u1, &u2c);
+  const int nsrc = M.left.nsec();
+  for (const Block& pb : P.blocks) {
+    const int so = pb.a, k = pb.b, jp = pb.c;
+    for (int bl = 0; bl < W.wl; ++bl) {
+      const int i = M.nsym ? M.left.find(sub(P.left.q[k], W.tl[bl])) : 0;
+      if (i < 0 || fused.target[(size_t)bl * nsrc + i] != k) continue;
+      const int64_t roff = fused.offset[(size_t)bl * nsrc + i];
+      auto it = u2c.find(Key{bl, so, i, jp});
+      static const std::vector<CombTerm> none;
+      p->c2.add(pb.off + roff * pb.cols, (int)pb.cols, (int)M.left.dim[i], (int)pb.cols,
+                it == u2c.end() ? none : it->second.terms);
+    }
+  }
+  p->ws2 = 0;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& M,
+                          const EnvLayout& out, Plan* p, std::string* err) {
+  (void)err;
+  p->kind = Kind::EnvRL;
+  std::map<Key, Interm> u1;
+  std::map<Key, Combo> u2c;
+  right_stages(re, W, M, p, &u1, &u2c);
+  std::map<Key, Interm> u2 = materialise(u2c, p);
+  p->has_g3 = true;
+  p->g3.ta = Trans::N;
+  p->g3.tb = Trans::T;
+  for (const Block& ob : out.blocks) {
+    const int bl = ob.a, ib = ob.b, ik = ob.c;
+    std::vector<GemmSeg> segs;
+    for (int so = 0; so < M.d; ++so) {
+      const int bb = M.block_of(so, ib);
+      if (bb < 0) continue;
+      const int jp = M.blocks[bb].c;
+      auto it = u2.find(Key{bl, so, ik, jp});
+      if (it == u2.end()) continue;
+      const int64_t K = M.right.dim[jp];
+      segs.push_back(seg(M.blocks[bb].off, K, it->second.off, K, K));
+    }
+    p->g3.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, segs);
+  }
+  return DMRG3S_OK;
+}
+
+}  // namespace dmrg3s

@@ -1,0 +1,90 @@
+// Host-side planning of the block-sparse contractions of the DMRG3S hot path.
+//
+// Every contraction is one of two three-stage pipelines that follow the
+// optimal ordering (((L M) W) R) of Sec. V of arXiv:1501.05504:
+//
+//   left side  (H_eff application, expansion term for left-to-right sweeps,
+//               left environment update):
+//     stage 1  T1[bl, s]  = L[bl] . M[s]                       grouped GEMM
+//     stage 2  T2[br, s'] = sum_{bl, s} W[s', s, bl, br] T1     combination
+//     stage 3  HA[s']     = sum_{br} T2[br, s'] . R[br]^T       grouped GEMM
+//           or L_i[br]    = sum_{s'} A[s']^T . T2[br, s']        grouped GEMM
+//           or P          = alpha T2 written into the fused bond (stage 2 only)
+//
+//   right side (expansion term for right-to-left sweeps, right environment):
+//     stage 1  U1[br, s]  = M[s] . R[br]^T                      grouped GEMM
+//     stage 2  U2[bl, s'] = sum_{br, s} W[s', s, bl, br] U1     combination
+//     stage 3  R_{i-1}[bl] = sum_{s'} B[s'] . U2[bl, s']^T       grouped GEMM
+//           or P          = alpha U2 written into the fused bond
+//
+// A plan holds the task tables with element offsets relative to the base
+// pointers of each stage (see the Kind comments), so that it can be reused
+// for every call with the same block structure and MPO.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.hpp"
+#include "layout.hpp"
+
+namespace dmrg3s {
+
+struct GemmStage {
+  Trans ta = Trans::N, tb = Trans::N;
+  std::vector<GemmTask> tasks;
+  std::vector<GemmSeg> segs;
+  std::vector<GemmTile> tiles;
+  double flops = 0.0;
+  void add(int64_t offC, int ldc, int M, int N, const std::vector<GemmSeg>& s);
+};
+
+struct CombStage {
+  std::vector<CombTask> tasks;
+  std::vector<CombTerm> terms;
+  std::vector<CombChunk> chunks;
+  double flops = 0.0;
+  void add(int64_t offOut, int ldo, int rows, int cols, const std::vector<CombTerm>& t);
+};
+
+enum class Kind {
+  Heff,       // g1: A=L B=M C=ws1 | c2: ws1 -> ws2 | g3: A=ws2 B=R C=HA
+  ExpandLR,   // g1 as Heff        | c2: ws1 -> P (scale alpha)
+  EnvLR,      // g1, c2 as Heff    | g3: A=M B=ws2 C=L_out
+  ExpandRL,   // g1: A=M B=R C=ws1 | c2: ws1 -> P (scale alpha)
+  EnvRL       // g1, c2 as ExpandRL, c2 -> ws2 | g3: A=M B=ws2 C=R_out
+};
+
+struct Plan {
+  Kind kind;
+  GemmStage g1, g3;
+  CombStage c2;
+  bool has_g3 = false;
+  int64_t ws1 = 0, ws2 = 0;     // doubles of the stage-1 / stage-2 intermediates
+  double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
+};
+
+// Left-side plans.  `mps` is the site tensor M (or A); `le` its left
+// environment (on mps.left, channels W.tl); `re` the right environment (on
+// mps.right, channels W.tr) for Heff; `out_site` the layout of P for ExpandLR;
+// `out_env` the layout of L_i for EnvLR.
+dmrg3s_status plan_heff(const EnvLayout& le, const MpoLayout& W, const EnvLayout& re,
+                        const SiteLayout& mps, Plan* plan, std::string* err);
+dmrg3s_status plan_expand_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& mps,
+                             const SiteLayout& P, const FusedBond& fused, Plan* plan,
+                             std::string* err);
+dmrg3s_status plan_env_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& mps,
+                          const EnvLayout& out, Plan* plan, std::string* err);
+dmrg3s_status plan_expand_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& mps,
+                             const SiteLayout& P, const FusedBond& fused, Plan* plan,
+                             std::string* err);
+dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& mps,
+                          const EnvLayout& out, Plan* plan, std::string* err);
+
+// Structural compatibility checks shared by the entry points.
+dmrg3s_status check_site_mpo(const SiteLayout& s, const MpoLayout& W, std::string* err);
+dmrg3s_status check_env(const EnvLayout& e, const Bond& bond, int w,
+                        const std::vector<Charge>& t, const char* what, std::string* err);
+
+}  // namespace dmrg3s
