@@ -180,6 +180,145 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
                                 const dmrg3s_mpo_site* W, const dmrg3s_site* A,
                                 dmrg3s_env* out, dmrg3s_precision prec, dmrg3s_stream stream);
 
+/* Local eigensolver, step 1 of Sec. V: the smallest eigenpair (lambda*, M*)
+ * of L_{i-1} R_{i+1} W_i M_i = lambda M_i (Eq. es-iter) by Lanczos with full
+ * reorthogonalisation (classical Gram-Schmidt applied twice), all in FP64 on
+ * the device; the tridiagonal eigenproblem is solved by Sturm bisection and
+ * inverse iteration in a device kernel.  M: start vector on input, the
+ * normalised Ritz vector on output.  Stops when the Ritz residual
+ * |beta_k y_k| <= tol * max(1, |lambda|), when beta_k < 1e-14 or after kmax
+ * (<= 128) products.  Synchronises `stream` once per iteration to test the
+ * stopping rule.  Errors: as dmrg3s_apply_heff, plus BREAKDOWN (zero start
+ * vector) and NUMERIC (NaN). */
+dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                                const dmrg3s_env* R, dmrg3s_site* M, int32_t kmax, double tol,
+                                dmrg3s_precision prec, double* lambda, int32_t* iters,
+                                dmrg3s_stream stream);
+
+/* ---- model MPOs ----------------------------------------------------------------- */
+
+/* Built-in Hamiltonians as MPOs (Sec. II: H = W_1 ... W_l), lower-triangular
+ * finite-state form: channel 0 = all terms finished, last channel = nothing
+ * placed yet; the first site keeps only the last row, the last site only
+ * column 0; a channel's charge is what the operators already placed add.
+ *  XXZ      params {J, Delta}: J sum_i [(S+_i S-_{i+1} + h.c.)/2 + Delta Sz_i Sz_{i+1}],
+ *           w = 5, d = 2 (up, down), one charge 2 S^z.
+ *  HUBBARD  params {t, U}: -t sum_{i,s} (c+_{i,s} c_{i+1,s} + h.c.) + U sum_i n_up n_dn,
+ *           Jordan-Wigner string, w = 6, d = 4 (index 2 n_up + n_dn), charges (N, 2 S^z).
+ *  SPIN_BONDS: sum over `nbonds` pairs bonds[2k] < bonds[2k+1] of
+ *           couplings[2k]/2 (S+ S- + S- S+) + couplings[2k+1] Sz Sz (d = 2), e.g.
+ *           the snake-ordered cylinder; channels (S+, S-, Sz) per open site.
+ * Open boundary conditions.  Host-only. */
+typedef enum dmrg3s_model {
+  DMRG3S_MODEL_XXZ = 0,
+  DMRG3S_MODEL_HUBBARD = 1,
+  DMRG3S_MODEL_SPIN_BONDS = 2
+} dmrg3s_model;
+
+typedef struct dmrg3s_mpo_s* dmrg3s_mpo;
+
+dmrg3s_status dmrg3s_mpo_create(int32_t model, int32_t nsites, const double* params,
+                                int32_t nbonds, const int32_t* bonds, const double* couplings,
+                                dmrg3s_mpo* out);
+dmrg3s_status dmrg3s_mpo_destroy(dmrg3s_mpo mpo);
+/* View of site i (pointers into the handle, valid until dmrg3s_mpo_destroy). */
+dmrg3s_status dmrg3s_mpo_get_site(dmrg3s_mpo mpo, int32_t i, dmrg3s_mpo_site* site);
+
+/* ---- library-owned DMRG3S state: the local update and the sweep ------------- */
+
+typedef struct dmrg3s_state_s* dmrg3s_state;
+
+typedef struct dmrg3s_update_opts {
+  int32_t m_max;            /* bond dimension kept after truncation (Sec. V step 4) */
+  int32_t lanczos_kmax;     /* <= 0: 40                                            */
+  double lanczos_tol;       /* <= 0: 1e-10                                         */
+  double trunc_eps;         /* singular values <= eps * s_max are dropped; <= 0: 1e-14 */
+  dmrg3s_precision precision;
+  int32_t skip_eigensolver; /* != 0: keep M as is (a pure gauge/expansion move)    */
+} dmrg3s_update_opts;
+
+typedef struct dmrg3s_update_info {
+  double lambda;            /* eigensolver value lambda* (step 1)                 */
+  double energy_before;     /* E_i: energy of the state entering the update        */
+  double energy_after;      /* E_f: Rayleigh quotient after truncation (step 7)    */
+  double discarded_weight;  /* sum of the squared discarded singular values        */
+  int32_t lanczos_iters;
+  int32_t new_bond_dim;
+} dmrg3s_update_info;
+
+/* Creates a state for a chain of `nsites` sites: MPO tensors W[0..n-1] (host,
+ * copied) and site tensors M[0..n-1] (device data, copied).  The MPS must be
+ * in mixed-canonical form with orthogonality centre `centre` (sites left of
+ * it left-normalised, right of it right-normalised, Sec. II).  left_env /
+ * right_env are the boundary environments L_0 / R_{l+1} (device data, copied);
+ * NULL means the trivial 1x1x1 environment equal to 1, which requires bond
+ * and MPO bond dimension 1 there.  All environments up to the centre are
+ * built on the device.  Synchronous.  Errors: ARG, SHAPE, QN, CUDA, OOM. */
+dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_mpo_site* W,
+                                  const dmrg3s_site* M, const dmrg3s_env* left_env,
+                                  const dmrg3s_env* right_env, int32_t centre,
+                                  dmrg3s_state* out);
+dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state);
+
+/* One DMRG3S local update at the current centre i (Sec. V, steps 1-7), moving
+ * the centre to i + dir:
+ *   dir = +1: Lanczos for M_i; P_i = alpha L_{i-1} M_i W_i (Eq. subexp-ourt);
+ *     M~ = [M_i P_i], B~_{i+1} = [B_{i+1}; 0] (Sec. IV A); FP64 SVD per charge
+ *     sector, truncation to m_max states; A~_i = U; B~_{i+1} = S V^dagger B~;
+ *     L_i from A~_i; E_f = <B~|H_eff(i+1)|B~> / <B~|B~>.
+ *   dir = -1: the mirror image with P_i = alpha R_{i+1} M_i W_i, M~ = [M_i; P_i].
+ * alpha = 0 skips the expansion (plain single-site update).  Synchronous
+ * (the SVD's singular values are read back to choose the kept states). */
+dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
+                                  const dmrg3s_update_opts* opts, dmrg3s_update_info* info,
+                                  dmrg3s_stream stream);
+
+/* Adaptive mixing factor (Sec. VI).  With dE_O = lambda* - E_i and
+ * dE_T = E_f - lambda*, r = dE_T / |dE_O|, after every local update:
+ *   |dE_O| < 1e-13 |lambda*|       -> alpha *= down
+ *   dE_T < 0 or r < target          -> alpha *= up
+ *   r > 1                           -> alpha *= down^2
+ *   otherwise                       -> alpha *= down
+ * clamped to [alpha_min, alpha_max]; fixed != 0 keeps alpha constant. */
+typedef struct dmrg3s_alpha_rule {
+  double alpha0, target, up, down, alpha_min, alpha_max;
+  int32_t fixed;
+} dmrg3s_alpha_rule;
+
+typedef struct dmrg3s_sweep_opts {
+  int32_t max_sweeps;
+  double conv_tol;          /* stop when |E_k - E_{k-1}| / |E_k| < conv_tol        */
+  dmrg3s_update_opts update;
+} dmrg3s_sweep_opts;
+
+typedef struct dmrg3s_sweep_report {
+  int32_t sweeps, converged, lanczos_iters, pad;
+  double energy, alpha;
+} dmrg3s_sweep_report;
+
+/* Sweeps (Sec. V): each sweep is a right-to-left pass over sites l..2 followed
+ * by a left-to-right pass over sites 1..l-1, one local update per site with
+ * the adaptive alpha; the state's centre must be on the last site.  energies
+ * (may be NULL) receives E_f after every sweep (max_sweeps entries). */
+dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
+                           const dmrg3s_sweep_opts* opts, double* energies,
+                           dmrg3s_sweep_report* report, dmrg3s_stream stream);
+
+/* Current centre and energy (E_f of the last update, or the Rayleigh quotient
+ * at creation). */
+dmrg3s_status dmrg3s_state_centre(dmrg3s_state state, int32_t* centre, double* energy);
+
+/* Bonds of site i (nsec, charges [nsec][nsym], dims) and its element count;
+ * any output may be NULL.  Arrays must hold the current nsec entries (query
+ * with NULL first). */
+dmrg3s_status dmrg3s_state_site_info(dmrg3s_state state, int32_t i, int32_t* nsec_left,
+                                     int32_t* q_left, int64_t* dim_left, int32_t* nsec_right,
+                                     int32_t* q_right, int64_t* dim_right, int64_t* nelem);
+
+/* Copies site i (canonical layout, nelem doubles) to dst (device or host). */
+dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,
+                                     dmrg3s_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

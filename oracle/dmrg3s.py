@@ -295,17 +295,21 @@ class SweepLog:
 class DMRG3S:
     """Driver holding the MPS and the environments of a mixed-canonical state."""
 
-    def __init__(self, mpo, mps, opts):
+    def __init__(self, mpo, mps, opts, left_env=None, right_env=None, centre=None):
+        """``left_env`` / ``right_env`` replace the trivial boundaries L_0 = R_{l+1} = 1
+        (a window of a longer chain); ``centre`` is the orthogonality centre (default l)."""
         self.mpo, self.mps, self.opts = mpo, mps, opts
         self.alpha = opts.alpha.alpha0
         L = mps.L
-        self.Lenv = {}
-        self.Renv = {}
-        Ls = build_left_envs(mpo, mps, L - 1)       # left envs of sites 0..L-1
-        for i, Le in enumerate(Ls):
-            self.Lenv[i] = Le
-        self.Renv[L - 1] = np.ones((1, 1, 1))
-        self.e_in = contract.rayleigh(self.Lenv[L - 1], mpo.W[L - 1], self.Renv[L - 1], mps.M[L - 1])
+        centre = L - 1 if centre is None else centre
+        self.Lenv = {0: np.ones((1, 1, 1)) if left_env is None else left_env}
+        for i in range(centre):
+            self.Lenv[i + 1] = contract.left_env(self.Lenv[i], mpo.W[i], mps.M[i])
+        self.Renv = {L - 1: np.ones((1, 1, 1)) if right_env is None else right_env}
+        for i in range(L - 1, centre, -1):
+            self.Renv[i - 1] = contract.right_env(self.Renv[i], mpo.W[i], mps.M[i])
+        self.e_in = contract.rayleigh(self.Lenv[centre], mpo.W[centre], self.Renv[centre],
+                                      mps.M[centre])
 
     def _eig(self, i):
         Le, Re, W = self.Lenv[i], self.Renv[i], self.mpo.W[i]

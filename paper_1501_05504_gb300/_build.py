@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdmrg3s.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-LIBS = []
+LIBS = ["-lcusolver"]
 
 
 def _nvcc():

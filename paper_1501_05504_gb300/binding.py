@@ -367,3 +367,209 @@ def empty_env(t, bond, device="cuda"):
 
 def mpo_from_neutral(spec):
     return MpoSite(spec["qp"], spec["tl"], spec["tr"], spec["W"])
+
+
+# ---- eigensolver, MPO builders, state, local update, sweep ------------------------------
+
+class _UpdateOpts(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int32), ("lanczos_kmax", ctypes.c_int32),
+                ("lanczos_tol", ctypes.c_double), ("trunc_eps", ctypes.c_double),
+                ("precision", ctypes.c_int), ("skip_eigensolver", ctypes.c_int32)]
+
+
+class _UpdateInfo(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("energy_before", ctypes.c_double),
+                ("energy_after", ctypes.c_double), ("discarded_weight", ctypes.c_double),
+                ("lanczos_iters", ctypes.c_int32), ("new_bond_dim", ctypes.c_int32)]
+
+
+class _AlphaRule(ctypes.Structure):
+    _fields_ = [("alpha0", ctypes.c_double), ("target", ctypes.c_double), ("up", ctypes.c_double),
+                ("down", ctypes.c_double), ("alpha_min", ctypes.c_double),
+                ("alpha_max", ctypes.c_double), ("fixed", ctypes.c_int32)]
+
+
+class _SweepOpts(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int32), ("conv_tol", ctypes.c_double),
+                ("update", _UpdateOpts)]
+
+
+class _SweepReport(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("lanczos_iters", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("energy", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+MODEL_XXZ, MODEL_HUBBARD, MODEL_SPIN_BONDS = 0, 1, 2
+
+
+def _setup_state_api(L):
+    if getattr(L, "_state_api", False):
+        return L
+    L.dmrg3s_eigensolve.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Env), ctypes.POINTER(_MpoSite),
+                                    ctypes.POINTER(_Env), ctypes.POINTER(_Site), ctypes.c_int32,
+                                    ctypes.c_double, ctypes.c_int, f64p, i32p, ctypes.c_void_p]
+    L.dmrg3s_mpo_create.argtypes = [ctypes.c_int32, ctypes.c_int32, f64p, ctypes.c_int32, i32p, f64p,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+    L.dmrg3s_mpo_destroy.argtypes = [ctypes.c_void_p]
+    L.dmrg3s_mpo_get_site.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_MpoSite)]
+    L.dmrg3s_state_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_MpoSite),
+                                      ctypes.POINTER(_Site), ctypes.POINTER(_Env),
+                                      ctypes.POINTER(_Env), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_void_p)]
+    L.dmrg3s_state_destroy.argtypes = [ctypes.c_void_p]
+    L.dmrg3s_local_update.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.POINTER(_UpdateOpts), ctypes.POINTER(_UpdateInfo),
+                                      ctypes.c_void_p]
+    L.dmrg3s_sweep.argtypes = [ctypes.c_void_p, ctypes.POINTER(_AlphaRule), ctypes.POINTER(_SweepOpts),
+                               f64p, ctypes.POINTER(_SweepReport), ctypes.c_void_p]
+    L.dmrg3s_state_centre.argtypes = [ctypes.c_void_p, i32p, f64p]
+    L.dmrg3s_state_site_info.argtypes = [ctypes.c_void_p, ctypes.c_int32, i32p, i32p, i64p, i32p,
+                                         i32p, i64p, i64p]
+    L.dmrg3s_state_site_copy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+    L._state_api = True
+    return L
+
+
+def slib():
+    return _setup_state_api(lib())
+
+
+def dmrg3s_eigensolve(ctx, L, W, R, M, kmax=40, tol=1e-10, prec="fp64", stream=None):
+    """Lanczos on the device; M is overwritten by the Ritz vector.  Returns (lambda, iters)."""
+    cL, cW, cR, cM = L._c(), W._c(), R._c(), M._c()
+    lam = ctypes.c_double()
+    it = ctypes.c_int32()
+    _check(slib().dmrg3s_eigensolve(ctx.handle, ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR),
+                                    ctypes.byref(cM), int(kmax), float(tol), _prec(prec),
+                                    ctypes.byref(lam), ctypes.byref(it), _stream(stream)),
+           "dmrg3s_eigensolve", ctx.handle)
+    return lam.value, it.value
+
+
+class Mpo:
+    """Model MPO built by the library (host arrays owned by the handle)."""
+
+    def __init__(self, model, nsites, params=(), bonds=None, couplings=None):
+        self.handle = ctypes.c_void_p()
+        self.nsites = int(nsites)
+        par = np.ascontiguousarray(params, dtype=np.float64)
+        nb, bp, cp = 0, None, None
+        if bonds is not None:
+            self._b = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+            self._c = np.ascontiguousarray(couplings, dtype=np.float64).reshape(-1, 2)
+            nb, bp, cp = len(self._b), self._b.ctypes.data_as(i32p), self._c.ctypes.data_as(f64p)
+        _check(slib().dmrg3s_mpo_create(int(model), self.nsites, par.ctypes.data_as(f64p) if par.size else None,
+                                        nb, bp, cp, ctypes.byref(self.handle)), "dmrg3s_mpo_create")
+
+    def site(self, i):
+        s = _MpoSite()
+        _check(slib().dmrg3s_mpo_get_site(self.handle, int(i), ctypes.byref(s)), "dmrg3s_mpo_get_site")
+        d, wl, wr, nsym = s.d, s.wl, s.wr, s.nsym
+        W = np.ctypeslib.as_array(s.W, shape=(d * d * wl * wr,)).reshape(d, d, wl, wr).copy()
+
+        def arr(p, n):
+            return np.ctypeslib.as_array(p, shape=(n * nsym,)).reshape(n, nsym).copy() if nsym else np.zeros((n, 0), np.int32)
+        return MpoSite(arr(s.qp, d), arr(s.tl, wl), arr(s.tr, wr), W)
+
+    def sites(self):
+        return [self.site(i) for i in range(self.nsites)]
+
+    def __del__(self):
+        try:
+            if self.handle:
+                slib().dmrg3s_mpo_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def dmrg3s_mpo_create(model, nsites, params=(), bonds=None, couplings=None):
+    return Mpo(model, nsites, params, bonds, couplings)
+
+
+class State:
+    """Library-owned DMRG3S state (dmrg3s_state_create)."""
+
+    def __init__(self, ctx, W, M, left_env=None, right_env=None, centre=0):
+        n = len(W)
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p()
+        cw = (_MpoSite * n)(*[w._c() for w in W])
+        cm = (_Site * n)(*[m._c() for m in M])
+        ce_l = ctypes.byref(left_env._c()) if left_env is not None else None
+        ce_r = ctypes.byref(right_env._c()) if right_env is not None else None
+        self._keep = (W, M, cw, cm)
+        _check(slib().dmrg3s_state_create(ctx.handle, n, cw, cm, ce_l, ce_r, int(centre),
+                                          ctypes.byref(self.handle)), "dmrg3s_state_create", ctx.handle)
+        self.nsites = n
+        self.qp = M[0].qp
+
+    def close(self):
+        if self.handle:
+            slib().dmrg3s_state_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def centre(self):
+        c, e = ctypes.c_int32(), ctypes.c_double()
+        _check(slib().dmrg3s_state_centre(self.handle, ctypes.byref(c), ctypes.byref(e)), "dmrg3s_state_centre")
+        return c.value, e.value
+
+    def site(self, i, device="cuda"):
+        import torch
+        L = slib()
+        nl, nr, ne = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(L.dmrg3s_state_site_info(self.handle, int(i), ctypes.byref(nl), None, None, ctypes.byref(nr),
+                                        None, None, ctypes.byref(ne)), "dmrg3s_state_site_info")
+        nsym = self.qp.shape[1]
+        ql = np.zeros((nl.value, nsym), np.int32)
+        qr = np.zeros((nr.value, nsym), np.int32)
+        dl = np.zeros(nl.value, np.int64)
+        dr = np.zeros(nr.value, np.int64)
+        _check(L.dmrg3s_state_site_info(self.handle, int(i), None, ql.ctypes.data_as(i32p) if ql.size else None,
+                                        dl.ctypes.data_as(i64p), None,
+                                        qr.ctypes.data_as(i32p) if qr.size else None,
+                                        dr.ctypes.data_as(i64p), None), "dmrg3s_state_site_info")
+        data = torch.zeros(max(ne.value, 1), dtype=torch.float64, device=device)
+        _check(L.dmrg3s_state_site_copy(self.handle, int(i), ctypes.c_void_p(data.data_ptr()),
+                                        _stream(None)), "dmrg3s_state_site_copy")
+        torch.cuda.synchronize()
+        return Site(self.qp, Bond(ql, dl), Bond(qr, dr), data)
+
+
+def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0):
+    return State(ctx, W, M, left_env, right_env, centre)
+
+
+def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-14, prec="fp64", skip_eigensolver=False):
+    return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)))
+
+
+def dmrg3s_local_update(state, direction, alpha, opts, stream=None):
+    info = _UpdateInfo()
+    _check(slib().dmrg3s_local_update(state.handle, int(direction), float(alpha), ctypes.byref(opts),
+                                      ctypes.byref(info), _stream(stream)), "dmrg3s_local_update",
+           state.ctx.handle)
+    return {"lambda": info.lambda_, "energy_before": info.energy_before, "energy_after": info.energy_after,
+            "discarded_weight": info.discarded_weight, "lanczos_iters": info.lanczos_iters,
+            "new_bond_dim": info.new_bond_dim}
+
+
+def alpha_rule(alpha0=1e-2, target=0.3, up=1.25, down=0.8, alpha_min=1e-14, alpha_max=1.0, fixed=False):
+    return _AlphaRule(alpha0, target, up, down, alpha_min, alpha_max, int(bool(fixed)))
+
+
+def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, stream=None):
+    so = _SweepOpts(int(max_sweeps), float(conv_tol), opts)
+    rep = _SweepReport()
+    en = np.zeros(max_sweeps, dtype=np.float64)
+    _check(slib().dmrg3s_sweep(state.handle, ctypes.byref(rule), ctypes.byref(so), en.ctypes.data_as(f64p),
+                               ctypes.byref(rep), _stream(stream)), "dmrg3s_sweep", state.ctx.handle)
+    return {"energies": en[:rep.sweeps].tolist(), "sweeps": rep.sweeps, "converged": bool(rep.converged),
+            "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters}

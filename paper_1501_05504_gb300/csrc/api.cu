@@ -102,19 +102,6 @@ dmrg3s_status run_plan(const DevicePlan& p, const double* g1A, const double* g1B
 
 namespace {
 
-dmrg3s_status fail(Context* c, dmrg3s_status st, const std::string& msg) {
-  if (c) c->last_error = msg;
-  return st;
-}
-
-dmrg3s_status use_device(Context* c) {
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "cudaGetDevice failed");
-  if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess)
-    return fail(c, DMRG3S_ERR_CUDA, "cudaSetDevice failed");
-  return DMRG3S_OK;
-}
-
 // Fetch a cached plan or build and upload one.
 template <class Build>
 dmrg3s_status get_plan(Context* c, uint64_t key, Build build, const DevicePlan** out) {
@@ -134,6 +121,56 @@ dmrg3s_status get_plan(Context* c, uint64_t key, Build build, const DevicePlan**
   c->plans[key] = std::move(dp);
   return DMRG3S_OK;
 }
+
+}  // namespace
+
+namespace dmrg3s {
+dmrg3s_status heff_plan(Context* c, const EnvLayout& le, const MpoLayout& w, const EnvLayout& re,
+                        const SiteLayout& a, const DevicePlan** out) {
+  Hasher h;
+  h.pod((int)Kind::Heff);
+  h.env(le);
+  h.mpo(w);
+  h.env(re);
+  h.site(a);
+  return get_plan(c, h.h, [&](Plan* pl, std::string* e) { return plan_heff(le, w, re, a, pl, e); },
+                  out);
+}
+
+dmrg3s_status expand_plan(Context* c, int dir, const EnvLayout& e, const MpoLayout& w,
+                          const SiteLayout& m, const SiteLayout& pl, const FusedBond& f,
+                          const DevicePlan** out) {
+  Hasher h;
+  h.pod(dir == 1 ? (int)Kind::ExpandLR : (int)Kind::ExpandRL);
+  h.env(e);
+  h.mpo(w);
+  h.site(m);
+  return get_plan(
+      c, h.h,
+      [&](Plan* pn, std::string* er) {
+        return dir == 1 ? plan_expand_lr(e, w, m, pl, f, pn, er)
+                        : plan_expand_rl(e, w, m, pl, f, pn, er);
+      },
+      out);
+}
+
+dmrg3s_status env_plan(Context* c, int dir, const EnvLayout& e, const MpoLayout& w,
+                       const SiteLayout& a, const EnvLayout& o, const DevicePlan** out) {
+  Hasher h;
+  h.pod(dir == 1 ? (int)Kind::EnvLR : (int)Kind::EnvRL);
+  h.env(e);
+  h.mpo(w);
+  h.site(a);
+  return get_plan(
+      c, h.h,
+      [&](Plan* pn, std::string* er) {
+        return dir == 1 ? plan_env_lr(e, w, a, o, pn, er) : plan_env_rl(e, w, a, o, pn, er);
+      },
+      out);
+}
+}  // namespace dmrg3s
+
+namespace {
 
 dmrg3s_status check_ws(Context* c, const Plan& p) {
   const size_t need = (size_t)(p.ws1 + p.ws2) * sizeof(double);
@@ -171,6 +208,17 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
     delete c;
     return DMRG3S_ERR_CUDA;
   }
+  // keep freed stream-ordered allocations in the pool (no release at every sync)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (cudaMallocHost(&c->pinned, 64 * sizeof(double)) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return DMRG3S_ERR_CUDA;
+  }
   *ctx = reinterpret_cast<dmrg3s_ctx>(c);
   return DMRG3S_OK;
 }
@@ -182,6 +230,7 @@ dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
   cudaDeviceSynchronize();
   c->plans.clear();
   if (c->ws) cudaFree(c->ws);
+  if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
   return DMRG3S_OK;
 }
@@ -310,15 +359,8 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
     return fail(c, DMRG3S_ERR_SHAPE, "HA must have the structure of A");
   if (!L->data || !R->data || !A->data || !HA->data)
     return fail(c, DMRG3S_ERR_ARG, "NULL device data pointer");
-  Hasher h;
-  h.pod((int)Kind::Heff);
-  h.env(le);
-  h.mpo(w);
-  h.env(re);
-  h.site(a);
   const DevicePlan* p = nullptr;
-  st = get_plan(c, h.h, [&](Plan* pl, std::string* e) { return plan_heff(le, w, re, a, pl, e); },
-                &p);
+  st = heff_plan(c, le, w, re, a, &p);
   if (st != DMRG3S_OK) return st;
   if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
@@ -359,19 +401,8 @@ dmrg3s_status dmrg3s_expand(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
       !same_charges(pl.qp, m.qp))
     return fail(c, DMRG3S_ERR_SHAPE, "P does not have the expanded structure of M");
   if (!env->data || !M->data || !P->data) return fail(c, DMRG3S_ERR_ARG, "NULL device data");
-  Hasher h;
-  h.pod(dir == 1 ? (int)Kind::ExpandLR : (int)Kind::ExpandRL);
-  h.env(e);
-  h.mpo(w);
-  h.site(m);
   const DevicePlan* p = nullptr;
-  st = get_plan(
-      c, h.h,
-      [&](Plan* pn, std::string* er) {
-        return dir == 1 ? plan_expand_lr(e, w, m, pl, f, pn, er)
-                        : plan_expand_rl(e, w, m, pl, f, pn, er);
-      },
-      &p);
+  st = expand_plan(c, dir, e, w, m, pl, f, &p);
   if (st != DMRG3S_OK) return st;
   if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
@@ -408,18 +439,8 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
       return fail(c, st, err);
   }
   if (!env->data || !A->data || !out->data) return fail(c, DMRG3S_ERR_ARG, "NULL device data");
-  Hasher h;
-  h.pod(dir == 1 ? (int)Kind::EnvLR : (int)Kind::EnvRL);
-  h.env(e);
-  h.mpo(w);
-  h.site(a);
   const DevicePlan* p = nullptr;
-  st = get_plan(
-      c, h.h,
-      [&](Plan* pn, std::string* er) {
-        return dir == 1 ? plan_env_lr(e, w, a, o, pn, er) : plan_env_rl(e, w, a, o, pn, er);
-      },
-      &p);
+  st = env_plan(c, dir, e, w, a, o, &p);
   if (st != DMRG3S_OK) return st;
   if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);

@@ -33,6 +33,7 @@ struct Context {
   int device = 0;
   char* ws = nullptr;           // workspace arena
   size_t ws_bytes = 0;
+  double* pinned = nullptr;     // small pinned host buffer for scalar read-backs (64 doubles)
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;
   std::string last_error;
 };
@@ -59,6 +60,48 @@ struct Hasher {
   void env(const EnvLayout& e);
   void mpo(const MpoLayout& w);
 };
+
+inline dmrg3s_status fail(Context* c, dmrg3s_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+inline dmrg3s_status use_device(Context* c) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "cudaGetDevice failed");
+  if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "cudaSetDevice failed");
+  return DMRG3S_OK;
+}
+
+// Cached plans.  Each returns the device plan for the given structures,
+// building and uploading it on first use.
+dmrg3s_status heff_plan(Context* c, const EnvLayout& le, const MpoLayout& w, const EnvLayout& re,
+                        const SiteLayout& a, const DevicePlan** out);
+dmrg3s_status expand_plan(Context* c, int dir, const EnvLayout& e, const MpoLayout& w,
+                          const SiteLayout& m, const SiteLayout& P, const FusedBond& f,
+                          const DevicePlan** out);
+dmrg3s_status env_plan(Context* c, int dir, const EnvLayout& e, const MpoLayout& w,
+                       const SiteLayout& a, const EnvLayout& o, const DevicePlan** out);
+
+// Bump allocator over the context workspace: returns an aligned pointer at
+// byte offset *cursor and advances it; DMRG3S_ERR_OOM when it does not fit.
+inline dmrg3s_status carve(Context* c, size_t* cursor, size_t bytes, void** out) {
+  size_t off = (*cursor + 255) / 256 * 256;
+  if (off + bytes > c->ws_bytes)
+    return fail(c, DMRG3S_ERR_OOM, "context workspace too small (need " +
+                                       std::to_string(off + bytes) + " bytes)");
+  *out = c->ws + off;
+  *cursor = off + bytes;
+  return DMRG3S_OK;
+}
+
+// Lanczos with CGS2 for the smallest eigenpair of H_eff (step 1 of Sec. V).
+// x: start vector on input, normalised Ritz vector on output (n doubles).
+// The workspace from byte offset `cursor` on is used for the Krylov basis.
+dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldata,
+                          const double* Rdata, double* x, int64_t n, int kmax, double tol,
+                          size_t cursor, cudaStream_t st, double* theta, int* iters);
 
 // Upload a host plan (allocates the device tables).  Returns CUDA errors.
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);

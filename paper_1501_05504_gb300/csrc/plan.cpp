@@ -1,6 +1,8 @@
 // Host-side planning of the block-sparse contractions.  See plan.hpp.
 #include "plan.hpp"
 
+#include "validate.hpp"
+
 #include <array>
 #include <map>
 
@@ -151,6 +153,19 @@ std::map<Key, Interm> materialise(const std::map<Key, Combo>& combos, Plan* p) {
   return out;
 }
 
+// Bounds of every table against the buffers the stages address.
+dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
+                     int64_t nC3, std::string* err) {
+  const int64_t w1 = p->ws1 > 0 ? p->ws1 : 1;
+  if (!gemm_ok(p->g1.ta, p->g1.tb, p->g1.tasks, p->g1.segs, nA1, nB1, w1, err) ||
+      !comb_ok(p->c2.tasks, p->c2.terms, w1, nOut2, err) ||
+      (p->has_g3 && !gemm_ok(p->g3.ta, p->g3.tb, p->g3.tasks, p->g3.segs, nA3, nB3, nC3, err))) {
+    *err = "internal planning error: " + *err;
+    return DMRG3S_ERR_SHAPE;
+  }
+  return DMRG3S_OK;
+}
+
 }  // namespace
 
 dmrg3s_status check_site_mpo(const SiteLayout& s, const MpoLayout& W, std::string* err) {
@@ -192,7 +207,6 @@ dmrg3s_status check_env(const EnvLayout& e, const Bond& bond, int w, const std::
 
 dmrg3s_status plan_heff(const EnvLayout& le, const MpoLayout& W, const EnvLayout& re,
                         const SiteLayout& M, Plan* p, std::string* err) {
-  (void)err;
   p->kind = Kind::Heff;
   std::map<Key, Interm> t1;
   std::map<Key, Combo> t2c;
@@ -216,13 +230,12 @@ dmrg3s_status plan_heff(const EnvLayout& le, const MpoLayout& W, const EnvLayout
     }
     p->g3.add(hb.off, (int)hb.cols, (int)hb.rows, (int)hb.cols, segs);
   }
-  return DMRG3S_OK;
+  return finish(p, le.size, M.size, p->ws2, p->ws2, re.size, M.size, err);
 }
 
 dmrg3s_status plan_expand_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& M,
                              const SiteLayout& P, const FusedBond& fused, Plan* p,
                              std::string* err) {
-  (void)err;
   p->kind = Kind::ExpandLR;
   std::map<Key, Interm> t1;
   std::map<Key, Combo> t2c;
@@ -241,12 +254,11 @@ dmrg3s_status plan_expand_lr(const EnvLayout& le, const MpoLayout& W, const Site
     }
   }
   p->ws2 = 0;
-  return DMRG3S_OK;
+  return finish(p, le.size, M.size, P.size, 0, 0, 0, err);
 }
 
 dmrg3s_status plan_env_lr(const EnvLayout& le, const MpoLayout& W, const SiteLayout& M,
                           const EnvLayout& out, Plan* p, std::string* err) {
-  (void)err;
   p->kind = Kind::EnvLR;
   std::map<Key, Interm> t1;
   std::map<Key, Combo> t2c;
@@ -270,13 +282,12 @@ dmrg3s_status plan_env_lr(const EnvLayout& le, const MpoLayout& W, const SiteLay
     }
     p->g3.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, segs);
   }
-  return DMRG3S_OK;
+  return finish(p, le.size, M.size, p->ws2, M.size, p->ws2, out.size, err);
 }
 
 dmrg3s_status plan_expand_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& M,
                              const SiteLayout& P, const FusedBond& fused, Plan* p,
                              std::string* err) {
-  (void)err;
   p->kind = Kind::ExpandRL;
   std::map<Key, Interm> u1;
   std::map<Key, Combo> u2c;
@@ -295,12 +306,11 @@ dmrg3s_status plan_expand_rl(const EnvLayout& re, const MpoLayout& W, const Site
     }
   }
   p->ws2 = 0;
-  return DMRG3S_OK;
+  return finish(p, M.size, re.size, P.size, 0, 0, 0, err);
 }
 
 dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& M,
                           const EnvLayout& out, Plan* p, std::string* err) {
-  (void)err;
   p->kind = Kind::EnvRL;
   std::map<Key, Interm> u1;
   std::map<Key, Combo> u2c;
@@ -323,7 +333,7 @@ dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLay
     }
     p->g3.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, segs);
   }
-  return DMRG3S_OK;
+  return finish(p, M.size, re.size, p->ws2, M.size, p->ws2, out.size, err);
 }
 
 }  // namespace dmrg3s

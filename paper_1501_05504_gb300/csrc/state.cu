@@ -1,0 +1,791 @@
+// DMRG3S state (library-owned MPS + environments), the local update of Sec. V
+// of arXiv:1501.05504 and the sweep driver with the adaptive mixing factor of
+// Sec. VI.
+//
+// Local update, left-to-right, at site i (right-to-left is the mirror image):
+//   1. Lanczos for the smallest eigenpair of H_eff (Eq. es-iter)        [eig.cu]
+//   2. expansion term alpha P_i = alpha L_{i-1} M_i W_i (Eq. subexp-ourt) [plan]
+//   3. M~ = [M* P] per charge sector of the expanded right bond; the neighbour
+//      is padded with zero rows (never materialised: the zero rows only meet
+//      the P columns, so step 5 multiplies with the M* part only)
+//   4. FP64 SVD of every sector (cuSOLVER gesvdj) and global truncation to
+//      m_max states: A~ = U
+//   5. B~_{i+1} = (S V^dagger)[:, M part] . B_{i+1}                     [grouped GEMM]
+//   6. L_i = L_{i-1} A~^dagger W_i A~                                   [plan]
+//   7. E_f = <B~|H_eff(i+1)|B~> / <B~|B~> (Rayleigh quotient after truncation)
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+
+#include "context.hpp"
+#include "dmrg3s.h"
+#include "validate.hpp"
+#include "vecops.hpp"
+
+namespace dmrg3s {
+
+namespace {
+
+struct DevSite {
+  SiteLayout lay;
+  double* data = nullptr;
+};
+struct DevEnv {
+  EnvLayout lay;
+  double* data = nullptr;
+  bool valid = false;
+};
+
+}  // namespace
+
+struct State {
+  Context* c = nullptr;
+  int n = 0;
+  std::vector<MpoLayout> W;
+  std::vector<DevSite> M;
+  std::vector<DevEnv> Lenv;   // Lenv[i]: sites < i, on M[i].left, channels W[i].tl
+  std::vector<DevEnv> Renv;   // Renv[i]: sites > i, on M[i].right, channels W[i].tr
+  int centre = 0;
+  double e_in = 0.0;
+  cusolverDnHandle_t solver = nullptr;
+  gesvdjInfo_t svdj = nullptr;
+};
+
+namespace {
+
+dmrg3s_status cuda_ok(Context* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DMRG3S_OK;
+  return fail(c, DMRG3S_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+dmrg3s_status dalloc(Context* c, double** p, int64_t n, cudaStream_t st) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  return cuda_ok(c, cudaMallocAsync((void**)p, (size_t)n * sizeof(double), st), "cudaMallocAsync");
+}
+
+void dfree(double* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+template <class T>
+dmrg3s_status upload(Context* c, const std::vector<T>& v, T** dev, cudaStream_t st) {
+  *dev = nullptr;
+  if (v.empty()) return DMRG3S_OK;
+  cudaError_t e = cudaMallocAsync((void**)dev, v.size() * sizeof(T), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  return cuda_ok(c, e, "table upload");
+}
+
+// Run a host-built grouped GEMM stage (tables uploaded for this call only).
+dmrg3s_status run_gemm(Context* c, const GemmStage& g, const double* A, int64_t nA, const double* B,
+                       int64_t nB, double* C, int64_t nC, cudaStream_t st) {
+  if (g.tiles.empty()) return DMRG3S_OK;
+  std::string err;
+  if (!gemm_ok(g.ta, g.tb, g.tasks, g.segs, nA, nB, nC, &err))
+    return fail(c, DMRG3S_ERR_SHAPE, "internal planning error: " + err);
+  GemmTile* dt;
+  GemmTask* dk;
+  GemmSeg* ds;
+  dmrg3s_status s;
+  if ((s = upload(c, g.tiles, &dt, st)) || (s = upload(c, g.tasks, &dk, st)) ||
+      (s = upload(c, g.segs, &ds, st)))
+    return s;
+  launch_gemm_f64(g.ta, g.tb, dt, (int)g.tiles.size(), dk, ds, A, B, C, st);
+  cudaFreeAsync(dt, st);
+  cudaFreeAsync(dk, st);
+  if (ds) cudaFreeAsync(ds, st);
+  return cuda_ok(c, cudaGetLastError(), "grouped GEMM");
+}
+
+dmrg3s_status run_copies(Context* c, const std::vector<CopyTask>& t, const double* src, int64_t nsrc,
+                         double* dst, int64_t ndst, const double* scale, int64_t nscale,
+                         cudaStream_t st) {
+  if (t.empty()) return DMRG3S_OK;
+  std::string err;
+  if (!copies_ok(t, nsrc, ndst, nscale, &err))
+    return fail(c, DMRG3S_ERR_SHAPE, "internal planning error: " + err);
+  CopyTask* dt;
+  dmrg3s_status s = upload(c, t, &dt, st);
+  if (s) return s;
+  launch_copy_blocks(dt, (int)t.size(), src, dst, scale, st);
+  cudaFreeAsync(dt, st);
+  return cuda_ok(c, cudaGetLastError(), "block copy");
+}
+
+CopyTask copy_task(int64_t off_s, int64_t ld_s, int64_t off_d, int64_t ld_d, int64_t rows,
+                   int64_t cols, bool trans, int rs = -1, int cs = -1) {
+  CopyTask t{};
+  t.off_s = off_s;
+  t.off_d = off_d;
+  t.ld_s = (int32_t)ld_s;
+  t.ld_d = (int32_t)ld_d;
+  t.rows = (int32_t)rows;
+  t.cols = (int32_t)cols;
+  t.trans = trans ? 1 : 0;
+  t.rs = rs;
+  t.cs = cs;
+  return t;
+}
+
+// <x, y> on the host (synchronises the stream)
+dmrg3s_status dot_host(Context* c, const double* x, const double* y, int64_t n, cudaStream_t st,
+                       double* out) {
+  double *part, *h;
+  dmrg3s_status s;
+  if ((s = dalloc(c, &part, kRedBlocks, st)) || (s = dalloc(c, &h, 1, st))) return s;
+  launch_multidot(x, 0, 1, y, n, part, h, nullptr, st);
+  cudaMemcpyAsync(c->pinned, h, sizeof(double), cudaMemcpyDeviceToHost, st);
+  dfree(part, st);
+  dfree(h, st);
+  if ((s = cuda_ok(c, cudaStreamSynchronize(st), "dot"))) return s;
+  *out = c->pinned[0];
+  return DMRG3S_OK;
+}
+
+dmrg3s_status build_env(State& S, int i, int dir, cudaStream_t st) {
+  Context* c = S.c;
+  const MpoLayout& w = S.W[i];
+  const DevSite& a = S.M[i];
+  DevEnv& src = dir == 1 ? S.Lenv[i] : S.Renv[i];
+  if (!src.valid) return fail(c, DMRG3S_ERR_ARG, "environment recursion from an invalid environment");
+  DevEnv& dst = dir == 1 ? S.Lenv[i + 1] : S.Renv[i - 1];
+  EnvLayout ol;
+  make_env_from(a.lay.nsym, dir == 1 ? w.wr : w.wl, dir == 1 ? w.tr : w.tl,
+                dir == 1 ? a.lay.right : a.lay.left, &ol);
+  const DevicePlan* p;
+  dmrg3s_status s = env_plan(c, dir, src.lay, w, a.lay, ol, &p);
+  if (s) return s;
+  if ((size_t)(p->host.ws1 + p->host.ws2) * sizeof(double) > c->ws_bytes)
+    return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the environment update");
+  double* nd;
+  if ((s = dalloc(c, &nd, ol.size, st))) return s;
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  double* ws2 = ws1 + p->host.ws1;
+  const double* g1A = dir == 1 ? src.data : a.data;
+  const double* g1B = dir == 1 ? a.data : src.data;
+  if ((s = run_plan(*p, g1A, g1B, ws1, ws2, 1.0, a.data, ws2, nd, st)))
+    return fail(c, s, "environment update launch");
+  dfree(dst.data, st);
+  dst.data = nd;
+  dst.lay = ol;
+  dst.valid = true;
+  return DMRG3S_OK;
+}
+
+// Rayleigh quotient <x|H_eff(i)|x>/<x|x> at site i with the current environments.
+dmrg3s_status rayleigh(State& S, int i, const double* x, cudaStream_t st, double* e) {
+  Context* c = S.c;
+  const DevicePlan* p;
+  dmrg3s_status s = heff_plan(c, S.Lenv[i].lay, S.W[i], S.Renv[i].lay, S.M[i].lay, &p);
+  if (s) return s;
+  if ((size_t)(p->host.ws1 + p->host.ws2) * sizeof(double) > c->ws_bytes)
+    return fail(c, DMRG3S_ERR_OOM, "context workspace too small for H_eff");
+  const int64_t n = S.M[i].lay.size;
+  double* hx;
+  if ((s = dalloc(c, &hx, n, st))) return s;
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  double* ws2 = ws1 + p->host.ws1;
+  if ((s = run_plan(*p, S.Lenv[i].data, x, ws1, ws2, 1.0, ws2, S.Renv[i].data, hx, st))) return s;
+  double num = 0.0, den = 0.0;
+  if ((s = dot_host(c, x, hx, n, st, &num)) || (s = dot_host(c, x, x, n, st, &den))) return s;
+  dfree(hx, st);
+  *e = den > 0.0 ? num / den : 0.0;
+  return DMRG3S_OK;
+}
+
+struct Opts {
+  int m_max = 64;
+  int kmax = 40;
+  double tol = 1e-10;
+  double eps = 1e-14;
+  bool optimise = true;
+};
+
+struct Info {
+  double lambda = 0.0, e_f = 0.0, discarded = 0.0;
+  int iters = 0, new_dim = 0;
+};
+
+// One sector of M~ for the SVD: a (rows x cols) row-major matrix.
+struct Sector {
+  Charge q;
+  int64_t rows = 0, cols = 0, base = 0;   // base = size of the M* part (cols for L->R, rows for R->L)
+  int64_t off = 0;                        // offset of X in the X buffer
+  int64_t r = 0;                          // min(rows, cols)
+  int64_t offU = 0, offV = 0, offS = 0;   // outputs of gesvdj
+  int keep = 0;
+  int jbase = -1;                         // old bond sector of the M* part, -1 if none
+};
+
+dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info* info,
+                           cudaStream_t st) {
+  Context* c = S.c;
+  const int i = S.centre;
+  const int nb = i + dir;
+  if (nb < 0 || nb >= S.n) return fail(c, DMRG3S_ERR_ARG, "local update would leave the chain");
+  if (!S.Lenv[i].valid || !S.Renv[i].valid)
+    return fail(c, DMRG3S_ERR_ARG, "environments of the centre site are not built");
+  dmrg3s_status s;
+  DevSite& m = S.M[i];
+  const MpoLayout& w = S.W[i];
+  // ---- 1. eigensolver
+  if (o.optimise) {
+    const DevicePlan* hp;
+    if ((s = heff_plan(c, S.Lenv[i].lay, w, S.Renv[i].lay, m.lay, &hp))) return s;
+    size_t cursor = (size_t)(hp->host.ws1 + hp->host.ws2) * sizeof(double);
+    double lam = 0.0;
+    int it = 0;
+    if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, m.data, m.lay.size, o.kmax, o.tol,
+                         cursor, st, &lam, &it)))
+      return s;
+    info->lambda = lam;
+    info->iters = it;
+  } else {
+    if ((s = rayleigh(S, i, m.data, st, &info->lambda))) return s;
+    info->iters = 0;
+  }
+  // ---- 2. expansion term
+  const bool expand = alpha != 0.0;
+  const Bond& old = dir == 1 ? m.lay.right : m.lay.left;
+  FusedBond fp;      // P part only
+  SiteLayout pl;
+  double* P = nullptr;
+  if (expand) {
+    fuse_bond(old, dir == 1 ? w.wr : w.wl, dir == 1 ? w.tr : w.tl, false, &fp);
+    if (dir == 1)
+      make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, m.lay.left, fp.bond, &pl);
+    else
+      make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, fp.bond, m.lay.right, &pl);
+    const DevicePlan* ep;
+    const DevEnv& env = dir == 1 ? S.Lenv[i] : S.Renv[i];
+    if ((s = expand_plan(c, dir, env.lay, w, m.lay, pl, fp, &ep))) return s;
+    if ((size_t)ep->host.ws1 * sizeof(double) > c->ws_bytes)
+      return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the expansion");
+    if ((s = dalloc(c, &P, pl.size, st))) return s;
+    const double* g1A = dir == 1 ? env.data : m.data;
+    const double* g1B = dir == 1 ? m.data : env.data;
+    if ((s = run_plan(*ep, g1A, g1B, reinterpret_cast<double*>(c->ws), P, alpha, nullptr, nullptr,
+                      nullptr, st)))
+      return s;
+  }
+  // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L)
+  std::vector<Charge> charges;
+  for (int k = 0; k < old.nsec(); ++k) charges.push_back(old.q[k]);
+  if (expand)
+    for (int k = 0; k < fp.bond.nsec(); ++k) charges.push_back(fp.bond.q[k]);
+  std::sort(charges.begin(), charges.end());
+  charges.erase(std::unique(charges.begin(), charges.end()), charges.end());
+  const Bond& keepb = dir == 1 ? m.lay.left : m.lay.right;   // the bond that is not expanded
+  std::vector<Sector> secs;
+  std::vector<CopyTask> gather_m, gather_p;
+  int64_t xoff = 0;
+  for (const Charge& q : charges) {
+    Sector sc;
+    sc.q = q;
+    sc.jbase = old.find(q);
+    if (m.lay.nsym == 0) sc.jbase = 0;
+    const int kp = expand ? (m.lay.nsym ? fp.bond.find(q) : 0) : -1;
+    const int64_t pwidth = kp >= 0 ? fp.bond.dim[kp] : 0;
+    sc.base = sc.jbase >= 0 ? old.dim[sc.jbase] : 0;
+    const int64_t exp_dim = sc.base + pwidth;
+    // the other dimension: sum over physical states of the matching sector of keepb
+    int64_t other = 0;
+    std::vector<std::pair<int, int64_t>> parts;   // (s, offset along the other dimension)
+    for (int ss = 0; ss < m.lay.d; ++ss) {
+      Charge qo = dir == 1 ? sub(q, m.lay.qp[ss]) : add(q, m.lay.qp[ss]);
+      const int io = m.lay.nsym ? keepb.find(qo) : 0;
+      if (io < 0) continue;
+      parts.push_back({ss, other});
+      other += keepb.dim[io];
+    }
+    if (other == 0 || exp_dim == 0) continue;
+    sc.rows = dir == 1 ? other : exp_dim;
+    sc.cols = dir == 1 ? exp_dim : other;
+    sc.off = xoff;
+    xoff += sc.rows * sc.cols;
+    for (auto& pr : parts) {
+      const int ss = pr.first;
+      const int64_t o2 = pr.second;
+      Charge qo = dir == 1 ? sub(q, m.lay.qp[ss]) : add(q, m.lay.qp[ss]);
+      const int io = m.lay.nsym ? keepb.find(qo) : 0;
+      const int64_t dio = keepb.dim[io];
+      if (sc.jbase >= 0) {
+        // M* block (ss, io, jbase) for L->R; (ss, jbase, io) for R->L
+        const int bi = dir == 1 ? m.lay.block_of(ss, io) : m.lay.block_of(ss, sc.jbase);
+        if (bi >= 0) {
+          const Block& bk = m.lay.blocks[bi];
+          const bool match = dir == 1 ? bk.c == sc.jbase : bk.c == io;
+          if (match) {
+            if (dir == 1)
+              gather_m.push_back(copy_task(bk.off, bk.cols, sc.off + o2 * sc.cols, sc.cols, dio, sc.base, false));
+            else
+              gather_m.push_back(copy_task(bk.off, bk.cols, sc.off + o2, sc.cols, sc.base, dio, false));
+          }
+        }
+      }
+      if (kp >= 0) {
+        const int bi = dir == 1 ? pl.block_of(ss, io) : pl.block_of(ss, kp);
+        if (bi >= 0) {
+          const Block& bk = pl.blocks[bi];
+          const bool match = dir == 1 ? bk.c == kp : bk.c == io;
+          if (match) {
+            if (dir == 1)
+              gather_p.push_back(copy_task(bk.off, bk.cols, sc.off + o2 * sc.cols + sc.base, sc.cols, dio, pwidth, false));
+            else
+              gather_p.push_back(copy_task(bk.off, bk.cols, sc.off + sc.base * sc.cols + o2, sc.cols, pwidth, dio, false));
+          }
+        }
+      }
+    }
+    secs.push_back(sc);
+  }
+  double* X;
+  if ((s = dalloc(c, &X, xoff, st))) return s;
+  cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(xoff, 1) * sizeof(double), st);
+  if ((s = run_copies(c, gather_m, m.data, m.lay.size, X, xoff, nullptr, 0, st))) return s;
+  if (expand && (s = run_copies(c, gather_p, P, pl.size, X, xoff, nullptr, 0, st))) return s;
+  dfree(P, st);
+  // ---- 4. SVD per sector.  X (rows x cols, row-major) is the column-major
+  // matrix X^T (cols x rows); gesvdj(X^T) = U' S V'^T gives X = V' S U'^T.
+  int64_t uoff = 0, voff = 0, soff = 0;
+  int lwork_max = 0;
+  cusolverDnSetStream(S.solver, st);
+  for (Sector& sc : secs) {
+    sc.r = std::min(sc.rows, sc.cols);
+    sc.offU = uoff;
+    uoff += sc.cols * sc.r;     // U' : cols x r (ld cols)
+    sc.offV = voff;
+    voff += sc.rows * sc.r;     // V' : rows x r (ld rows)
+    sc.offS = soff;
+    soff += sc.r;
+    int lw = 0;
+    if (cusolverDnDgesvdj_bufferSize(S.solver, CUSOLVER_EIG_MODE_VECTOR, 1, (int)sc.cols,
+                                     (int)sc.rows, nullptr, (int)sc.cols, nullptr, nullptr,
+                                     (int)sc.cols, nullptr, (int)sc.rows, &lw, S.svdj) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return fail(c, DMRG3S_ERR_CUDA, "gesvdj buffer size");
+    lwork_max = std::max(lwork_max, lw);
+  }
+  double *U, *V, *Sv, *work;
+  int* dinfo;
+  if ((s = dalloc(c, &U, uoff, st)) || (s = dalloc(c, &V, voff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
+      (s = dalloc(c, &work, lwork_max, st)) || (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
+    return s;
+  for (size_t k = 0; k < secs.size(); ++k) {
+    Sector& sc = secs[k];
+    if (cusolverDnDgesvdj(S.solver, CUSOLVER_EIG_MODE_VECTOR, 1, (int)sc.cols, (int)sc.rows,
+                          X + sc.off, (int)sc.cols, Sv + sc.offS, U + sc.offU, (int)sc.cols,
+                          V + sc.offV, (int)sc.rows, work, lwork_max, dinfo + k, S.svdj) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return fail(c, DMRG3S_ERR_CUDA, "gesvdj");
+  }
+  std::vector<double> hs(std::max<int64_t>(soff, 1));
+  if ((s = cuda_ok(c, cudaMemcpyAsync(hs.data(), Sv, soff * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "singular values")) ||
+      (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
+    return s;
+  dfree(X, st);
+  dfree(work, st);
+  dfree((double*)dinfo, st);
+  // global selection: order by (-s, sector, index), cut at eps * s_max and m_max
+  std::vector<std::tuple<double, int, int>> cand;
+  double smax = 0.0, total = 0.0;
+  for (size_t k = 0; k < secs.size(); ++k)
+    for (int64_t j = 0; j < secs[k].r; ++j) {
+      const double v = hs[secs[k].offS + j];
+      if (!(v == v)) return fail(c, DMRG3S_ERR_NUMERIC, "NaN singular value");
+      cand.emplace_back(-v, (int)k, (int)j);
+      smax = std::max(smax, v);
+      total += v * v;
+    }
+  std::sort(cand.begin(), cand.end());
+  double kept_w = 0.0;
+  int nkeep = 0;
+  for (auto& t : cand) {
+    const double v = -std::get<0>(t);
+    if (!(v > o.eps * smax) || nkeep >= o.m_max) break;
+    secs[std::get<1>(t)].keep++;
+    kept_w += v * v;
+    ++nkeep;
+  }
+  info->discarded = total - kept_w;
+  info->new_dim = nkeep;
+  if (nkeep == 0) return fail(c, DMRG3S_ERR_NUMERIC, "truncation kept no state");
+  // ---- new bond
+  Bond nbnd;
+  nbnd.nsym = m.lay.nsym;
+  std::vector<int> sec_of_new;
+  for (size_t k = 0; k < secs.size(); ++k)
+    if (secs[k].keep > 0) {
+      nbnd.q.push_back(secs[k].q);
+      nbnd.dim.push_back(secs[k].keep);
+      sec_of_new.push_back((int)k);
+    }
+  nbnd.off.assign(nbnd.dim.size() + 1, 0);
+  for (size_t k = 0; k < nbnd.dim.size(); ++k) nbnd.off[k + 1] = nbnd.off[k] + nbnd.dim[k];
+  nbnd.total = nbnd.off.back();
+  if (nbnd.nsym == 0) nbnd.q.assign(1, Charge{});
+  // ---- new centre tensor A~ (L->R) or B~ (R->L), and the remainder SV / US
+  SiteLayout nl;
+  if (dir == 1)
+    make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, m.lay.left, nbnd, &nl);
+  else
+    make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, nbnd, m.lay.right, &nl);
+  std::vector<CopyTask> cp_new, cp_rem;
+  std::vector<int64_t> rem_off(nbnd.nsec(), 0);
+  int64_t rem_size = 0;
+  for (int kn = 0; kn < nbnd.nsec(); ++kn) {
+    const Sector& sc = secs[sec_of_new[kn]];
+    const int64_t nk = sc.keep;
+    rem_off[kn] = rem_size;
+    rem_size += nk * sc.base;
+    int64_t o2 = 0;
+    for (int ss = 0; ss < m.lay.d; ++ss) {
+      Charge qo = dir == 1 ? sub(sc.q, m.lay.qp[ss]) : add(sc.q, m.lay.qp[ss]);
+      const int io = m.lay.nsym ? keepb.find(qo) : 0;
+      if (io < 0) continue;
+      const int64_t dio = keepb.dim[io];
+      const int bi = dir == 1 ? nl.block_of(ss, io) : nl.block_of(ss, kn);
+      if (bi >= 0) {
+        const Block& bk = nl.blocks[bi];
+        if (dir == 1)   // A~ block (dio x nk): element (a, c) = V'[c * rows + o2 + a]
+          cp_new.push_back(copy_task(sc.offV + o2, sc.rows, bk.off, bk.cols, dio, nk, true));
+        else            // B~ block (nk x dio): element (c, a) = U'[c * cols + o2 + a]
+          cp_new.push_back(copy_task(sc.offU + o2, sc.cols, bk.off, bk.cols, nk, dio, false));
+      }
+      o2 += dio;
+    }
+    if (sc.base > 0) {
+      if (dir == 1)     // SV (nk x base): S[c] U'[c * cols + col]
+        cp_rem.push_back(copy_task(sc.offU, sc.cols, rem_off[kn], sc.base, nk, sc.base, false,
+                                   (int)sc.offS, -1));
+      else              // US (base x nk): V'[c * rows + row] S[c]
+        cp_rem.push_back(copy_task(sc.offV, sc.rows, rem_off[kn], nk, sc.base, nk, true, -1,
+                                   (int)sc.offS));
+    }
+  }
+  double *ndata, *rem;
+  if ((s = dalloc(c, &ndata, nl.size, st)) || (s = dalloc(c, &rem, rem_size, st))) return s;
+  cudaMemsetAsync(ndata, 0, (size_t)std::max<int64_t>(nl.size, 1) * sizeof(double), st);
+  if ((s = run_copies(c, cp_new, dir == 1 ? V : U, dir == 1 ? voff : uoff, ndata, nl.size, Sv, soff,
+                      st)) ||
+      (s = run_copies(c, cp_rem, dir == 1 ? U : V, dir == 1 ? uoff : voff, rem, rem_size, Sv, soff,
+                      st)))
+    return s;
+  dfree(U, st);
+  dfree(V, st);
+  dfree(Sv, st);
+  // ---- 5. remainder into the neighbour
+  DevSite& nbs = S.M[nb];
+  SiteLayout nnl;
+  if (dir == 1)
+    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbnd, nbs.lay.right, &nnl);
+  else
+    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbs.lay.left, nbnd, &nnl);
+  GemmStage g;
+  for (const Block& ob : nnl.blocks) {
+    const int ss = ob.a;
+    std::vector<GemmSeg> sg;
+    if (dir == 1) {       // B~[s](kn, j2) = SV_kn (nk x base) . B[s](jbase, j2)
+      const int kn = ob.b;
+      const Sector& sc = secs[sec_of_new[kn]];
+      if (sc.base > 0) {
+        const int bi = nbs.lay.block_of(ss, sc.jbase);
+        if (bi >= 0 && nbs.lay.blocks[bi].c == ob.c) {
+          GemmSeg q{};
+          q.offA = rem_off[kn];
+          q.lda = (int32_t)sc.base;
+          q.offB = nbs.lay.blocks[bi].off;
+          q.ldb = (int32_t)nbs.lay.blocks[bi].cols;
+          q.K = (int32_t)sc.base;
+          q.scale = 1.0;
+          sg.push_back(q);
+        }
+      }
+    } else {              // A~[s](i2, kn) = A[s](i2, jbase) . US_kn (base x nk)
+      const int kn = ob.c;
+      const Sector& sc = secs[sec_of_new[kn]];
+      if (sc.base > 0) {
+        const int bi = nbs.lay.block_of(ss, ob.b);
+        if (bi >= 0 && nbs.lay.blocks[bi].c == sc.jbase) {
+          GemmSeg q{};
+          q.offA = nbs.lay.blocks[bi].off;
+          q.lda = (int32_t)nbs.lay.blocks[bi].cols;
+          q.offB = rem_off[kn];
+          q.ldb = (int32_t)sc.keep;
+          q.K = (int32_t)sc.base;
+          q.scale = 1.0;
+          sg.push_back(q);
+        }
+      }
+    }
+    g.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, sg);
+  }
+  double* nbdata;
+  if ((s = dalloc(c, &nbdata, nnl.size, st))) return s;
+  if (dir == 1) {
+    if ((s = run_gemm(c, g, rem, rem_size, nbs.data, nbs.lay.size, nbdata, nnl.size, st))) return s;
+  } else {
+    if ((s = run_gemm(c, g, nbs.data, nbs.lay.size, rem, rem_size, nbdata, nnl.size, st))) return s;
+  }
+  dfree(rem, st);
+  dfree(m.data, st);
+  dfree(nbs.data, st);
+  m.lay = nl;
+  m.data = ndata;
+  nbs.lay = nnl;
+  nbs.data = nbdata;
+  // ---- 6. environment of the truncated tensor; the neighbour's old one is stale
+  if (dir == 1) {
+    S.Renv[i].valid = false;
+    if ((s = build_env(S, i, 1, st))) return s;
+  } else {
+    S.Lenv[i].valid = false;
+    if ((s = build_env(S, i, -1, st))) return s;
+  }
+  S.centre = nb;
+  // ---- 7. energy after truncation at the neighbour
+  if ((s = rayleigh(S, nb, nbs.data, st, &info->e_f))) return s;
+  return cuda_ok(c, cudaGetLastError(), "local update");
+}
+
+dmrg3s_status boundary_env(State& S, const dmrg3s_env* user, bool left, cudaStream_t st) {
+  Context* c = S.c;
+  const int i = left ? 0 : S.n - 1;
+  DevEnv& e = left ? S.Lenv[0] : S.Renv[S.n - 1];
+  const SiteLayout& a = S.M[i].lay;
+  const MpoLayout& w = S.W[i];
+  std::string err;
+  dmrg3s_status s;
+  if (user) {
+    EnvLayout el;
+    if ((s = make_env(user, &el, &err))) return fail(c, s, err);
+    if ((s = check_env(el, left ? a.left : a.right, left ? w.wl : w.wr, left ? w.tl : w.tr,
+                       left ? "left boundary" : "right boundary", &err)))
+      return fail(c, s, err);
+    if (!user->data) return fail(c, DMRG3S_ERR_ARG, "boundary environment without data");
+    if ((s = dalloc(c, &e.data, el.size, st))) return s;
+    cudaMemcpyAsync(e.data, user->data, (size_t)el.size * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    e.lay = el;
+  } else {
+    const Bond& b = left ? a.left : a.right;
+    if ((left ? w.wl : w.wr) != 1 || b.total != 1)
+      return fail(c, DMRG3S_ERR_SHAPE, "a trivial boundary needs a bond and an MPO bond of dimension 1");
+    EnvLayout el;
+    make_env_from(a.nsym, 1, left ? w.tl : w.tr, b, &el);
+    if (el.size != 1) return fail(c, DMRG3S_ERR_QN, "trivial boundary charges do not match");
+    if ((s = dalloc(c, &e.data, 1, st))) return s;
+    static const double one = 1.0;
+    cudaMemcpyAsync(e.data, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    e.lay = el;
+  }
+  e.valid = true;
+  return DMRG3S_OK;
+}
+
+}  // namespace
+}  // namespace dmrg3s
+
+using namespace dmrg3s;
+
+extern "C" {
+
+dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_mpo_site* W,
+                                  const dmrg3s_site* M, const dmrg3s_env* left_env,
+                                  const dmrg3s_env* right_env, int32_t centre,
+                                  dmrg3s_state* out) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !W || !M || !out || nsites < 1) return fail(c, DMRG3S_ERR_ARG, "bad argument");
+  if (centre < 0 || centre >= nsites) return fail(c, DMRG3S_ERR_ARG, "centre out of range");
+  *out = nullptr;
+  dmrg3s_status s;
+  if ((s = use_device(c))) return s;
+  std::unique_ptr<State> S(new State());
+  S->c = c;
+  S->n = nsites;
+  S->W.resize(nsites);
+  S->M.resize(nsites);
+  S->Lenv.resize(nsites);
+  S->Renv.resize(nsites);
+  std::string err;
+  cudaStream_t st = nullptr;
+  for (int i = 0; i < nsites; ++i) {
+    if ((s = make_mpo(&W[i], &S->W[i], &err)) || (s = make_site(&M[i], &S->M[i].lay, &err)) ||
+        (s = check_site_mpo(S->M[i].lay, S->W[i], &err)))
+      return fail(c, s, "site " + std::to_string(i) + ": " + err);
+    if (i > 0) {
+      if (!same_bond(S->M[i - 1].lay.right, S->M[i].lay.left))
+        return fail(c, DMRG3S_ERR_SHAPE, "bond " + std::to_string(i) + " differs between sites");
+      if (S->W[i - 1].wr != S->W[i].wl || !same_charges(S->W[i - 1].tr, S->W[i].tl))
+        return fail(c, DMRG3S_ERR_SHAPE, "MPO bond " + std::to_string(i) + " differs between sites");
+    }
+    if (!M[i].data) return fail(c, DMRG3S_ERR_ARG, "site without data");
+    if ((s = dalloc(c, &S->M[i].data, S->M[i].lay.size, st))) return s;
+    cudaMemcpyAsync(S->M[i].data, M[i].data, (size_t)S->M[i].lay.size * sizeof(double),
+                    cudaMemcpyDeviceToDevice, st);
+  }
+  if (cusolverDnCreate(&S->solver) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, DMRG3S_ERR_CUDA, "cusolverDnCreate");
+  cusolverDnCreateGesvdjInfo(&S->svdj);
+  cusolverDnXgesvdjSetTolerance(S->svdj, 1e-15);
+  cusolverDnXgesvdjSetMaxSweeps(S->svdj, 100);
+  if ((s = boundary_env(*S, left_env, true, st)) || (s = boundary_env(*S, right_env, false, st)))
+    return s;
+  for (int i = 0; i < centre; ++i)
+    if ((s = build_env(*S, i, 1, st))) return s;
+  for (int i = nsites - 1; i > centre; --i)
+    if ((s = build_env(*S, i, -1, st))) return s;
+  S->centre = centre;
+  if ((s = rayleigh(*S, centre, S->M[centre].data, st, &S->e_in))) return s;
+  *out = reinterpret_cast<dmrg3s_state>(S.release());
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S) return DMRG3S_ERR_ARG;
+  use_device(S->c);
+  cudaDeviceSynchronize();
+  for (auto& m : S->M) cudaFree(m.data);
+  for (auto& e : S->Lenv) cudaFree(e.data);
+  for (auto& e : S->Renv) cudaFree(e.data);
+  if (S->svdj) cusolverDnDestroyGesvdjInfo(S->svdj);
+  if (S->solver) cusolverDnDestroy(S->solver);
+  delete S;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
+                                  const dmrg3s_update_opts* opts, dmrg3s_update_info* info,
+                                  dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || !opts || !info) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  if (dir != 1 && dir != -1) return fail(c, DMRG3S_ERR_ARG, "dir must be +1 or -1");
+  if (opts->precision != DMRG3S_FP64)
+    return fail(c, DMRG3S_ERR_UNSUPPORTED, "local update precision");
+  if (opts->m_max < 1) return fail(c, DMRG3S_ERR_ARG, "m_max must be >= 1");
+  dmrg3s_status s;
+  if ((s = use_device(c))) return s;
+  Opts o;
+  o.m_max = opts->m_max;
+  o.kmax = opts->lanczos_kmax > 0 ? opts->lanczos_kmax : 40;
+  o.tol = opts->lanczos_tol > 0 ? opts->lanczos_tol : 1e-10;
+  o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-14;
+  o.optimise = opts->skip_eigensolver == 0;
+  Info inf;
+  s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));
+  if (s != DMRG3S_OK) return s;
+  info->lambda = inf.lambda;
+  info->energy_after = inf.e_f;
+  info->energy_before = S->e_in;
+  info->discarded_weight = inf.discarded;
+  info->lanczos_iters = inf.iters;
+  info->new_bond_dim = inf.new_dim;
+  S->e_in = inf.e_f;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_state_centre(dmrg3s_state state, int32_t* centre, double* energy) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S) return DMRG3S_ERR_ARG;
+  if (centre) *centre = S->centre;
+  if (energy) *energy = S->e_in;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_state_site_info(dmrg3s_state state, int32_t i, int32_t* nsec_left,
+                                     int32_t* q_left, int64_t* dim_left, int32_t* nsec_right,
+                                     int32_t* q_right, int64_t* dim_right, int64_t* nelem) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || i < 0 || i >= S->n) return DMRG3S_ERR_ARG;
+  const SiteLayout& l = S->M[i].lay;
+  auto put = [&](const Bond& b, int32_t* ns, int32_t* q, int64_t* dim) {
+    if (ns) *ns = b.nsec();
+    if (q && b.nsym)
+      for (int k = 0; k < b.nsec(); ++k)
+        for (int j = 0; j < b.nsym; ++j) q[(size_t)k * b.nsym + j] = b.q[k][j];
+    if (dim)
+      for (int k = 0; k < b.nsec(); ++k) dim[k] = b.dim[k];
+  };
+  put(l.left, nsec_left, q_left, dim_left);
+  put(l.right, nsec_right, q_right, dim_right);
+  if (nelem) *nelem = l.size;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,
+                                     dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || i < 0 || i >= S->n || !dst) return DMRG3S_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(dst, S->M[i].data, (size_t)S->M[i].lay.size * sizeof(double),
+                                  cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DMRG3S_OK : fail(S->c, DMRG3S_ERR_CUDA, "site copy");
+}
+
+}  // extern "C"
+
+namespace {
+// Adaptive mixing factor of Sec. VI with the thresholds documented in
+// include/dmrg3s.h (dmrg3s_alpha_rule).
+double alpha_update(const dmrg3s_alpha_rule& r, double alpha, double e_in, double lam, double e_f) {
+  if (r.fixed) return alpha;
+  const double d_o = lam - e_in, d_t = e_f - lam;
+  if (std::fabs(d_o) < 1e-13 * std::max(std::fabs(lam), 1e-300))
+    alpha *= r.down;
+  else if (d_t < 0.0 || d_t / std::fabs(d_o) < r.target)
+    alpha *= r.up;
+  else if (d_t / std::fabs(d_o) > 1.0)
+    alpha *= r.down * r.down;
+  else
+    alpha *= r.down;
+  return std::min(std::max(alpha, r.alpha_min), r.alpha_max);
+}
+}  // namespace
+
+extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
+                                      const dmrg3s_sweep_opts* opts, double* energies,
+                                      dmrg3s_sweep_report* report, dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || !rule || !opts || !report) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  if (S->n < 2) return fail(c, DMRG3S_ERR_ARG, "a sweep needs at least two sites");
+  if (S->centre != S->n - 1)
+    return fail(c, DMRG3S_ERR_ARG, "a sweep starts with the centre on the last site");
+  if (opts->max_sweeps < 1) return fail(c, DMRG3S_ERR_ARG, "max_sweeps must be >= 1");
+  double alpha = rule->alpha0;
+  report->sweeps = 0;
+  report->converged = 0;
+  report->lanczos_iters = 0;
+  double prev = 0.0;
+  for (int sw = 0; sw < opts->max_sweeps; ++sw) {
+    double e = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int dir = pass == 0 ? -1 : 1;
+      for (int k = 0; k < S->n - 1; ++k) {
+        dmrg3s_update_info inf{};
+        dmrg3s_status s = dmrg3s_local_update(state, dir, alpha, &opts->update, &inf, stream);
+        if (s != DMRG3S_OK) return s;
+        alpha = alpha_update(*rule, alpha, inf.energy_before, inf.lambda, inf.energy_after);
+        report->lanczos_iters += inf.lanczos_iters;
+        e = inf.energy_after;
+      }
+    }
+    if (energies) energies[sw] = e;
+    report->sweeps = sw + 1;
+    report->energy = e;
+    report->alpha = alpha;
+    if (sw > 0 && std::fabs(e - prev) / std::fabs(e) < opts->conv_tol) {
+      report->converged = 1;
+      break;
+    }
+    prev = e;
+  }
+  return DMRG3S_OK;
+}

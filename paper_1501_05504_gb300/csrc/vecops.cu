@@ -1,0 +1,268 @@
+// Dense vector kernels of the local eigensolver and the truncation step.
+//
+// Reductions are deterministic: a fixed grid of kRedBlocks CTAs writes one
+// partial sum per CTA (warp-shuffle reduction inside the CTA) and a second
+// kernel adds the partials in a fixed order.
+#include <cmath>
+
+#include "vecops.hpp"
+
+namespace dmrg3s {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) multidot_partial(const double* __restrict__ V,
+                                                             int64_t ldv, int k,
+                                                             const double* __restrict__ w,
+                                                             int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = 0; j < k; ++j) {
+    const double* v = V + (int64_t)j * ldv;
+    double acc = 0.0;
+    for (int64_t e = start; e < n; e += stride) acc = fma(v[e], w[e], acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void multidot_final(const double* __restrict__ partial, int nblk, int k,
+                               double* __restrict__ h, double* __restrict__ copy_last) {
+  __shared__ double sh[32];
+  for (int j = 0; j < k; ++j) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(int64_t)j * nblk + b];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      h[j] = s;
+      if (copy_last && j == k - 1) *copy_last = s;
+    }
+  }
+}
+
+__global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ldv, int k,
+                                  const double* __restrict__ h, double* __restrict__ w, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    double acc = w[e];
+    for (int j = 0; j < k; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
+    w[e] = acc;
+  }
+}
+
+__global__ void combine_vectors_kernel(const double* __restrict__ V, int64_t ldv, int k,
+                                       const double* __restrict__ c, double* __restrict__ y,
+                                       int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(c[j], V[(int64_t)j * ldv + e], acc);
+    y[e] = acc;
+  }
+}
+
+__global__ void normalise_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                                 const double* __restrict__ nrm2) {
+  const double s = 1.0 / sqrt(*nrm2);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    y[e] = x[e] * s;
+}
+
+// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T pivots).
+__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;    // x hit an eigenvalue of a leading block: perturb
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void tridiag_smallest_kernel(const double* __restrict__ alpha, double* __restrict__ beta,
+                                        int k, const double* __restrict__ nrm2,
+                                        double* __restrict__ y, TridiagOut* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double bl = sqrt(*nrm2);
+  beta[k - 1] = bl;
+  // Gershgorin interval
+  double lo = 1e300, hi = -1e300;
+  bool bad = false;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < k - 1 ? fabs(beta[i]) : 0.0);
+    lo = fmin(lo, alpha[i] - r);
+    hi = fmax(hi, alpha[i] + r);
+    if (!(alpha[i] == alpha[i])) bad = true;
+  }
+  if (bad || !(bl == bl)) {
+    out->theta = 0.0;
+    out->resid = 0.0;
+    out->beta_last = bl;
+    out->nan_seen = 1.0;
+    return;
+  }
+  const double span = fmax(hi - lo, 1e-300);
+  lo -= 1e-12 * span;
+  hi += 1e-12 * span;
+  // bisection for the smallest eigenvalue: count(x) >= 1 means x is above it
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  const double theta = 0.5 * (lo + hi);
+  // inverse iteration: solve (T - theta I) z = y with a pivoted tridiagonal LU
+  // (partial pivoting keeps the elimination stable at the near-singular shift)
+  double dl[128], dd[128], du[128], du2[128];
+  int piv[128];
+  const int kk = k <= 128 ? k : 128;
+  for (int i = 0; i < kk; ++i) y[i] = 1.0 / sqrt((double)kk);
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int i = 0; i < kk; ++i) {
+      dd[i] = alpha[i] - theta;
+      du[i] = i < kk - 1 ? beta[i] : 0.0;
+      dl[i] = i < kk - 1 ? beta[i] : 0.0;
+      du2[i] = 0.0;
+    }
+    for (int i = 0; i < kk - 1; ++i) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        piv[i] = i;
+        if (dd[i] == 0.0) dd[i] = 1e-300;
+        const double f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+      } else {
+        piv[i] = i + 1;
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const double t = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = t - f * dd[i + 1];
+        if (i < kk - 2) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+      }
+    }
+    if (dd[kk - 1] == 0.0) dd[kk - 1] = 1e-300;
+    // forward: apply row interchanges and L
+    for (int i = 0; i < kk - 1; ++i) {
+      if (piv[i] == i) {
+        y[i + 1] -= dl[i] * y[i];
+      } else {
+        const double t = y[i];
+        y[i] = y[i + 1];
+        y[i + 1] = t - dl[i] * y[i];
+      }
+    }
+    // back substitution with U (diagonal dd, super du, second super du2)
+    y[kk - 1] /= dd[kk - 1];
+    if (kk > 1) y[kk - 2] = (y[kk - 2] - du[kk - 2] * y[kk - 1]) / dd[kk - 2];
+    for (int i = kk - 3; i >= 0; --i)
+      y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
+    double nrm = 0.0;
+    for (int i = 0; i < kk; ++i) nrm += y[i] * y[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < kk; ++i) y[i] /= nrm;
+  }
+  // fix the sign: largest component positive (only the subspace is defined)
+  int imax = 0;
+  for (int i = 1; i < kk; ++i)
+    if (fabs(y[i]) > fabs(y[imax])) imax = i;
+  if (y[imax] < 0.0)
+    for (int i = 0; i < kk; ++i) y[i] = -y[i];
+  out->theta = theta;
+  out->resid = fabs(bl * y[kk - 1]);
+  out->beta_last = bl;
+  out->nan_seen = 0.0;
+}
+
+__global__ void copy_blocks_kernel(const CopyTask* __restrict__ tasks,
+                                   const double* __restrict__ src, double* __restrict__ dst,
+                                   const double* __restrict__ scale) {
+  const CopyTask t = tasks[blockIdx.x];
+  const int n = t.rows * t.cols;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int r, c;
+    if (t.trans) {      // walk the source contiguously
+      c = idx / t.rows;
+      r = idx % t.rows;
+    } else {
+      r = idx / t.cols;
+      c = idx % t.cols;
+    }
+    double v = t.trans ? src[t.off_s + (int64_t)c * t.ld_s + r] : src[t.off_s + (int64_t)r * t.ld_s + c];
+    if (t.rs >= 0) v *= scale[t.rs + r];
+    if (t.cs >= 0) v *= scale[t.cs + c];
+    dst[t.off_d + (int64_t)r * t.ld_d + c] = v;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 4 * 152) g = 4 * 152;
+  return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                     double* partial, double* h, double* copy_last, cudaStream_t st) {
+  multidot_partial<<<kRedBlocks, kThreads, 0, st>>>(V, ldv, k, w, n, partial);
+  multidot_final<<<1, kThreads, 0, st>>>(partial, kRedBlocks, k, h, copy_last);
+}
+
+void launch_multi_axpy(const double* V, int64_t ldv, int k, const double* h, double* w, int64_t n,
+                       cudaStream_t st) {
+  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, h, w, n);
+}
+
+void launch_combine_vectors(const double* V, int64_t ldv, int k, const double* c, double* y,
+                            int64_t n, cudaStream_t st) {
+  combine_vectors_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, c, y, n);
+}
+
+void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2, cudaStream_t st) {
+  normalise_kernel<<<grid_for(n), kThreads, 0, st>>>(x, y, n, nrm2);
+}
+
+void launch_tridiag_smallest(const double* alpha, double* beta, int k, const double* nrm2,
+                             double* y, TridiagOut* out, cudaStream_t st) {
+  tridiag_smallest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, nrm2, y, out);
+}
+
+void launch_copy_blocks(const CopyTask* tasks, int ntasks, const double* src, double* dst,
+                        const double* scale, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  copy_blocks_kernel<<<ntasks, 256, 0, st>>>(tasks, src, dst, scale);
+}
+
+}  // namespace dmrg3s

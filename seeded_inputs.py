@@ -141,6 +141,19 @@ def random_mpo_site(rng, qp, tl, tr, density=1.0):
     return {"qp": qp, "tl": tl, "tr": tr, "W": W}
 
 
+def symmetric_mpo_site(rng, qp, tl, tr, density=1.0):
+    """Random W with W[s, s', b_bar, c_bar] = W[s', s, b, c] (a symmetric H_eff).
+
+    Left and right channels are paired by charge negation (``conjugate_channels``).
+    """
+    W = random_mpo_site(rng, qp, tl, tr, density)
+    pl, pr = conjugate_channels(np.asarray(tl)), conjugate_channels(np.asarray(tr))
+    A = W["W"]
+    B = np.transpose(A, (1, 0, 2, 3))[:, :, pl, :][:, :, :, pr]
+    W["W"] = 0.5 * (A + B)
+    return W
+
+
 def conjugate_channels(t):
     """Pairing b -> b_bar with t[b_bar] = -t[b] (first match, self-paired when t == 0)."""
     w = t.shape[0]
@@ -191,6 +204,35 @@ def random_dense_mps(rng, L, d, m_max):
     """N(0,1) site tensors with bond dims min(d^i, d^(l-i), m_max) (not normalised)."""
     dims = [min(d ** i, d ** (L - i), m_max) for i in range(L + 1)]
     return [rng.standard_normal((d, dims[i], dims[i + 1])) for i in range(L)]
+
+
+def product_state_sites(qp, local_states):
+    """Neutral site tensors (m = 1) of a product state |s_1 ... s_l>.
+
+    The bond charges accumulate the local charges from the left, as the
+    selection rule of a site tensor requires.
+    """
+    qp = np.asarray(qp, dtype=np.int64)
+    nsym = qp.shape[1]
+    q = np.zeros(nsym, dtype=np.int64)
+    sites = []
+    for s in local_states:
+        left = {"q": q.reshape(1, nsym).copy(), "dim": np.array([1], dtype=np.int64)}
+        q = q + qp[s]
+        right = {"q": q.reshape(1, nsym).copy(), "dim": np.array([1], dtype=np.int64)}
+        sites.append({"qp": qp, "left": left, "right": right, "blocks": {(int(s), 0, 0): np.ones((1, 1))}})
+    return sites
+
+
+def dense_mps_sites(tensors):
+    """Neutral site tensors (no symmetry) of dense arrays M[s, al, ar]."""
+    out = []
+    for T in tensors:
+        d, ml, mr = T.shape
+        out.append({"qp": np.zeros((d, 0), dtype=np.int64), "left": dense_bond(ml),
+                    "right": dense_bond(mr),
+                    "blocks": {(s, 0, 0): np.array(T[s]) for s in range(d)}})
+    return out
 
 
 # ---- named workloads ---------------------------------------------------------------

@@ -1,0 +1,200 @@
+"""GPU parity of the eigensolver, the DMRG3S local update and full sweeps.
+
+The eigensolver value is unique (non-degenerate ground state of a random
+symmetric H_eff); vectors are compared up to sign.  After a local update the
+new basis is only defined up to a per-sector orthogonal rotation and sign,
+so the comparison uses gauge-invariant quantities: lambda*, E_f, the
+discarded weight, the kept dimension per charge sector and the two-site
+wavefunction A~ B~ (up to a global sign).  Full sweeps are compared with the
+oracle's converged energy and with exact diagonalisation.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import seeded_inputs as si  # noqa: E402
+from oracle import contract, dmrg3s as odm, exact, io, models  # noqa: E402
+from parity import rel_err, site_to_dense  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def b():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_05504_gb300 import binding
+    binding.slib()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(b):
+    c = b.dmrg3s_create(0, 1 << 30)
+    yield c
+    c.close()
+
+
+def _window(kind, seed, m=48):
+    """Two-site window: random symmetric boundary environments and MPO tensors."""
+    rng = si.rng_for(seed)
+    if kind == "dense":
+        b0, b1, b2 = si.dense_bond(m), si.dense_bond(m + 3), si.dense_bond(m - 5)
+        qp = np.zeros((2, 0), dtype=np.int64)
+        t = np.zeros((5, 0), dtype=np.int64)
+    elif kind == "u1":
+        b0 = si.gaussian_bond(m, (1,), (2.5,), (2,), (4,))
+        b1 = si.gaussian_bond(m + 4, (0,), (2.5,), (2,), (4,))
+        b2 = si.gaussian_bond(m - 6, (1,), (2.5,), (2,), (4,))
+        qp, t = si.XXZ_QP, si.XXZ_T
+    else:
+        b0 = si._parity_filter(si.gaussian_bond(m, (3, 1), (1.5, 1.5), (1, 2), (3, 3)), m)
+        b1 = si._parity_filter(si.gaussian_bond(m + 4, (4, 0), (1.5, 1.5), (1, 2), (3, 3)), m + 4)
+        b2 = si._parity_filter(si.gaussian_bond(m - 6, (5, 1), (1.5, 1.5), (1, 2), (3, 3)), m - 6)
+        qp, t = si.HUB_QP, si.HUB_T
+    Le = si.symmetric_env(rng, t, b0)
+    Re = si.symmetric_env(rng, t, b2)
+    W0 = si.symmetric_mpo_site(rng, qp, t, t)
+    W1 = si.symmetric_mpo_site(rng, qp, t, t)
+    M0 = si.random_site(rng, qp, b0, b1)
+    M1 = si.random_site(rng, qp, b1, b2)
+    return dict(L=Le, R=Re, W=[W0, W1], M=[M0, M1], qp=qp, t=t)
+
+
+def _oracle_window(w, centre, m_max, alpha):
+    mpo = models.MPO([w["W"][0]["W"], w["W"][1]["W"]], w["qp"], [w["t"], w["t"], w["t"]])
+    Ms, qs = [], []
+    for k, M in enumerate(w["M"]):
+        D, ql, qr = io.site_dense(M)
+        Ms.append(D)
+        if k == 0:
+            qs.append(ql)
+        qs.append(qr)
+    mps = odm.MPS(Ms, qs, w["qp"])
+    o = odm.SweepOptions(m_max=m_max)
+    o.alpha = odm.AlphaRule(alpha0=alpha, fixed=True)
+    return odm.DMRG3S(mpo, mps, o, left_env=io.env_dense(w["L"]), right_env=io.env_dense(w["R"]),
+                      centre=centre)
+
+
+def _gpu_window(b, ctx, w, centre):
+    W = [b.mpo_from_neutral(x) for x in w["W"]]
+    M = [b.site_from_neutral(x) for x in w["M"]]
+    return b.dmrg3s_state_create(ctx, W, M, b.env_from_neutral(w["L"]), b.env_from_neutral(w["R"]),
+                                 centre)
+
+
+def _sector_dims(bond):
+    return sorted((tuple(int(v) for v in q), int(d)) for q, d in zip(bond.q, bond.dim))
+
+
+def _oracle_sector_dims(q):
+    out = {}
+    for row in q:
+        k = tuple(int(v) for v in row)
+        out[k] = out.get(k, 0) + 1
+    return sorted(out.items())
+
+
+@pytest.mark.parametrize("kind,seed", [("dense", 1), ("u1", 2), ("u1u1", 3)])
+def test_eigensolve_matches_oracle(b, ctx, kind, seed):
+    w = _window(kind, seed)
+    # a one-site problem: L on M0.left, a symmetric random R on M0.right
+    R1 = si.symmetric_env(si.rng_for(seed + 100), w["t"], w["M"][0]["right"])
+    gL, gR1 = b.env_from_neutral(w["L"]), b.env_from_neutral(R1)
+    gW = b.mpo_from_neutral(w["W"][0])
+    gM = b.site_from_neutral(w["M"][0])
+    lam, it = b.dmrg3s_eigensolve(ctx, gL, gW, gR1, gM, kmax=80, tol=1e-12)
+    Ld, Rd, Md = io.env_dense(w["L"]), io.env_dense(R1), io.site_dense(w["M"][0])[0]
+    lam_o, x_o, it_o = odm.lanczos_ground(lambda v: contract.apply_heff(Ld, w["W"][0]["W"], Rd, v), Md,
+                                          kmax=80, tol=1e-12)
+    assert abs(lam - lam_o) < 1e-10 * max(1.0, abs(lam_o))
+    x_p = site_to_dense(b, gM)
+    assert abs(abs(np.vdot(x_p, x_o)) - 1.0) < 1e-8
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+@pytest.mark.parametrize("kind,seed", [("dense", 11), ("u1", 12), ("u1u1", 13)])
+def test_local_update_matches_oracle(b, ctx, kind, seed, direction):
+    w = _window(kind, seed)
+    centre = 0 if direction == 1 else 1
+    m_max, alpha = 40, 0.15
+    orc = _oracle_window(w, centre, m_max, alpha)
+    lam_o, ef_o = orc.update_lr(0) if direction == 1 else orc.update_rl(1)
+    st = _gpu_window(b, ctx, w, centre)
+    info = b.dmrg3s_local_update(st, direction, alpha, b.update_opts(m_max, kmax=80, tol=1e-12))
+    assert abs(info["lambda"] - lam_o) < 1e-9 * max(1.0, abs(lam_o))
+    assert abs(info["energy_after"] - ef_o) < 1e-8 * max(1.0, abs(ef_o))
+    g0, g1 = st.site(0), st.site(1)
+    new_bond = g0.right
+    qn = orc.mps.q[1]
+    assert _sector_dims(new_bond) == _oracle_sector_dims(qn)
+    psi_p = np.einsum("sxa,tay->sxty", site_to_dense(b, g0), site_to_dense(b, g1))
+    psi_o = np.einsum("sxa,tay->sxty", orc.mps.M[0], orc.mps.M[1])
+    err = min(rel_err(psi_p, psi_o), rel_err(-psi_p, psi_o))
+    assert err < 1e-8
+    st.close()
+
+
+def _neel_state(b, ctx, mpo_sites, L):
+    spec = si.product_state_sites(si.XXZ_QP, [0, 1] * (L // 2))
+    M = [b.site_from_neutral(x) for x in spec]
+    return b.dmrg3s_state_create(ctx, mpo_sites, M, None, None, L - 1)
+
+
+def test_sweep_u1_heisenberg_reaches_ed(b, ctx):
+    L = 10
+    W = b.Mpo(b.MODEL_XXZ, L, (1.0, 1.0)).sites()
+    st = _neel_state(b, ctx, W, L)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 8, 1e-9, b.update_opts(32))
+    e0 = exact.ed_ground_energy(models.dense_xxz(L, 1.0, 1.0),
+                                models.dense_charges(models.SPIN_HALF_Q, L), [0])
+    assert rep["converged"]
+    assert abs(rep["energy"] - e0) < 1e-10 * abs(e0)
+    # the oracle on the same start reaches the same energy
+    mpo = models.mpo_xxz(L, 1.0, 1.0)
+    olog = odm.DMRG3S(mpo, odm.product_state(mpo.qphys, [0, 1] * (L // 2)),
+                      odm.SweepOptions(m_max=32, max_sweeps=8)).run()
+    assert abs(rep["energy"] - olog.energies[-1]) < 1e-10 * abs(e0)
+    st.close()
+
+
+def test_sweep_alpha_zero_stays_stuck(b, ctx):
+    L = 10
+    W = b.Mpo(b.MODEL_XXZ, L, (1.0, 1.0)).sites()
+    st = _neel_state(b, ctx, W, L)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(0.0, fixed=True), 2, 1e-9, b.update_opts(32))
+    assert abs(rep["energy"] - (-(L - 1) / 4.0)) < 1e-12
+    st.close()
+
+
+def test_sweep_hubbard_matches_ed(b, ctx):
+    L, U = 4, 8.0
+    W = b.Mpo(b.MODEL_HUBBARD, L, (1.0, U)).sites()
+    spec = si.product_state_sites(si.HUB_QP, [2, 1] * (L // 2))
+    st = b.dmrg3s_state_create(ctx, W, [b.site_from_neutral(x) for x in spec], None, None, L - 1)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 10, 1e-10, b.update_opts(64))
+    e0 = exact.ed_ground_energy(models.dense_hubbard(L, 1.0, U), models.dense_charges(models.HUB_Q, L),
+                                [L, 0])
+    assert abs(rep["energy"] - e0) < 1e-9 * abs(e0)
+    st.close()
+
+
+def test_sweep_dense_random_start(b, ctx):
+    """No symmetry, random start (left-normalised on the device by gauge moves)."""
+    L, m = 10, 32
+    W = b.Mpo(b.MODEL_XXZ, L, (1.0, 1.0)).sites()
+    for s in W:     # the dense problem drops the charges
+        s.qp = np.zeros((2, 0), np.int32)
+        s.tl = np.zeros((s.tl.shape[0], 0), np.int32)
+        s.tr = np.zeros((s.tr.shape[0], 0), np.int32)
+    Ms = si.random_dense_mps(si.rng_for(1001), L, 2, m)
+    st = b.dmrg3s_state_create(ctx, W, [b.site_from_neutral(x) for x in si.dense_mps_sites(Ms)],
+                               None, None, 0)
+    gauge = b.update_opts(10 ** 6, skip_eigensolver=True)
+    for _ in range(L - 1):
+        b.dmrg3s_local_update(st, 1, 0.0, gauge)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 8, 1e-10, b.update_opts(m))
+    e0 = exact.ed_ground_energy(models.dense_xxz(L, 1.0, 1.0))
+    assert abs(rep["energy"] - e0) < 1e-10 * abs(e0)
+    st.close()
