@@ -13,8 +13,10 @@ Readings of points the paper leaves open (each is a documented choice):
 
 * eigensolver: Lanczos with full classical Gram-Schmidt reorthogonalisation
   applied twice (CGS2), started from the current site tensor;
-* truncation keeps ``min(m_max, #{s > 1e-14 s_max})`` singular values, ordered
-  by (-s, charge sector, index inside the sector);
+* truncation keeps ``min(m_max, #{s > 1e-12 s_max})`` singular values, ordered
+  by (-s, charge sector, index inside the sector); 1e-12 s_max is the
+  numerical zero of an FP64 SVD (rounding noise of the factorisation sits
+  near 1e-14 s_max and must not be kept as states);
 * the energy after truncation is the Rayleigh quotient of the neighbour
   tensor (it is not normalised after step 5) with the environments of the
   neighbour site;
@@ -88,7 +90,7 @@ def _ordered_keep(svals, m_max, eps):
     return keep[:m_max]
 
 
-def truncate_lr(Mt, qphys, ql, qr, m_max, eps=1e-14):
+def truncate_lr(Mt, qphys, ql, qr, m_max, eps=1e-12):
     """SVD of Mt reshaped to ((s, al), ar) per charge sector; keep m_max states.
 
     Returns (A, SV, q_new): A (d, m_l, k) left-normalised, SV (k, m_r) = S V^dagger.
@@ -122,7 +124,7 @@ def truncate_lr(Mt, qphys, ql, qr, m_max, eps=1e-14):
     return A.reshape(d, ml, k), SV, qn
 
 
-def truncate_rl(Mt, qphys, ql, qr, m_max, eps=1e-14):
+def truncate_rl(Mt, qphys, ql, qr, m_max, eps=1e-12):
     """SVD of Mt reshaped to (al, (s, ar)) per charge sector; keep m_max states.
 
     Returns (B, US, q_new): B (d, k, m_r) right-normalised, US (m_l, k) = U S.

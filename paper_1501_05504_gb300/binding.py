@@ -547,7 +547,7 @@ def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0):
     return State(ctx, W, M, left_env, right_env, centre)
 
 
-def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-14, prec="fp64", skip_eigensolver=False):
+def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False):
     return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)))
 
 

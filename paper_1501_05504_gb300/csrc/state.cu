@@ -202,7 +202,7 @@ struct Opts {
   int m_max = 64;
   int kmax = 40;
   double tol = 1e-10;
-  double eps = 1e-14;
+  double eps = 1e-12;
   bool optimise = true;
 };
 
@@ -677,7 +677,7 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   o.m_max = opts->m_max;
   o.kmax = opts->lanczos_kmax > 0 ? opts->lanczos_kmax : 40;
   o.tol = opts->lanczos_tol > 0 ? opts->lanczos_tol : 1e-10;
-  o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-14;
+  o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-12;
   o.optimise = opts->skip_eigensolver == 0;
   Info inf;
   s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));

@@ -113,26 +113,52 @@ def test_eigensolve_matches_oracle(b, ctx, kind, seed):
     assert abs(abs(np.vdot(x_p, x_o)) - 1.0) < 1e-8
 
 
+def _cut_gap(orc, direction, alpha, m_max):
+    """Relative gap s_k - s_{k+1} of the expanded tensor's spectrum at the cut k = m_max."""
+    i = 0 if direction == 1 else 1
+    Le, Re, W = orc.Lenv[i], orc.Renv[i], orc.mpo.W[i]
+    lam, Ms, _ = odm.lanczos_ground(lambda v: contract.apply_heff(Le, W, Re, v), orc.mps.M[i],
+                                    kmax=80, tol=1e-12)
+    if direction == 1:
+        Mt = np.concatenate([Ms, contract.expansion_term_lr(Le, W, Ms, alpha)], axis=2)
+        X = Mt.reshape(-1, Mt.shape[2])
+    else:
+        Mt = np.concatenate([Ms, contract.expansion_term_rl(Re, W, Ms, alpha)], axis=1)
+        X = np.transpose(Mt, (1, 0, 2)).reshape(Mt.shape[1], -1)
+    s = np.linalg.svd(X, compute_uv=False)
+    if len(s) <= m_max:
+        return 1.0
+    return (s[m_max - 1] - s[m_max]) / s[0]
+
+
 @pytest.mark.parametrize("direction", [1, -1])
 @pytest.mark.parametrize("kind,seed", [("dense", 11), ("u1", 12), ("u1u1", 13)])
-def test_local_update_matches_oracle(b, ctx, kind, seed, direction):
+@pytest.mark.parametrize("m_max", [40, 100000])
+def test_local_update_matches_oracle(b, ctx, kind, seed, direction, m_max):
+    """m_max = 100000 keeps every state (no truncation): the state must be reproduced
+    exactly.  m_max = 40 truncates: the kept subspace is then defined only up to
+    the first-order perturbation eps / gap of the spectrum at the cut, and the
+    two-site state is compared within 1e-9 / gap."""
     w = _window(kind, seed)
     centre = 0 if direction == 1 else 1
-    m_max, alpha = 40, 0.15
+    alpha = 0.15
     orc = _oracle_window(w, centre, m_max, alpha)
+    gap = _cut_gap(orc, direction, alpha, m_max)
     lam_o, ef_o = orc.update_lr(0) if direction == 1 else orc.update_rl(1)
     st = _gpu_window(b, ctx, w, centre)
     info = b.dmrg3s_local_update(st, direction, alpha, b.update_opts(m_max, kmax=80, tol=1e-12))
     assert abs(info["lambda"] - lam_o) < 1e-9 * max(1.0, abs(lam_o))
     assert abs(info["energy_after"] - ef_o) < 1e-8 * max(1.0, abs(ef_o))
     g0, g1 = st.site(0), st.site(1)
-    new_bond = g0.right
-    qn = orc.mps.q[1]
-    assert _sector_dims(new_bond) == _oracle_sector_dims(qn)
+    assert _sector_dims(g0.right) == _oracle_sector_dims(orc.mps.q[1])
     psi_p = np.einsum("sxa,tay->sxty", site_to_dense(b, g0), site_to_dense(b, g1))
     psi_o = np.einsum("sxa,tay->sxty", orc.mps.M[0], orc.mps.M[1])
     err = min(rel_err(psi_p, psi_o), rel_err(-psi_p, psi_o))
-    assert err < 1e-8
+    assert err < min(1e-3, 1e-9 / gap)
+    # the new centre-side tensor is orthonormal (A~ left-, B~ right-normalised)
+    T = site_to_dense(b, g0 if direction == 1 else g1)
+    G = np.einsum("sxa,sxb->ab", T, T) if direction == 1 else np.einsum("sax,sbx->ab", T, T)
+    assert np.abs(G - np.eye(G.shape[0])).max() < 1e-12
     st.close()
 
 
