@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the DMRG3S hot path on one GB300 (or N independent replicas).
+
+A *step* is one DMRG3S local update (Sec. V of arXiv:1501.05504, steps 1-7):
+Lanczos eigensolver over H_eff = L W A R, expansion term alpha L M W,
+per-sector FP64 SVD truncation to m_max, S V^dagger into the neighbour,
+environment update and the energy after truncation.  Workload: the central
+two-site window of the S=1/2 Heisenberg (XXZ, Delta = 1) chain with L = 100,
+d = 2, w = 5, U(1) S^z blocks and m_max = 512; the boundary environments are
+seeded synthetic symmetric block tensors with Gaussian sector dimensions (a
+stand-in for converged environments; see the design doc for the recipe).  Steps
+alternate direction (left-to-right, right-to-left) so every step is a full
+update of the same window.
+
+Metric: algorithmic TFLOP/s of the step's contractions (grouped-GEMM block
+products + MPO combinations, counted as sum 2 M N K over the block tasks;
+the SVD is not counted).  ``e2e`` repeats the step through the C ABI with the
+window's tensors in pinned host memory, copied in and out every step.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (H_eff applications, the step's dominant cost) on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+WORKLOAD = "xxz_l100_m512_u1"
+M_MAX = 512
+ALPHA = 1e-2
+SEED = 1002
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def window_specs(seed=SEED):
+    """Neutral specs of the central window (sites 50, 51 of the L = 100 chain)."""
+    rng = si.rng_for(seed)
+    b0, b1 = si.central_bonds(WORKLOAD)                      # bonds 49 (odd charges) and 50 (even)
+    b2 = si.gaussian_bond(M_MAX, (1,), (3.0,), (2,), (6,))    # bond 51 (odd)
+    Le = si.symmetric_env(rng, si.XXZ_T, b0, identity_channels=(4,))
+    Re = si.symmetric_env(rng, si.XXZ_T, b2, identity_channels=(0,))
+    M0 = si.random_site(rng, si.XXZ_QP, b0, b1)
+    M1 = si.random_site(rng, si.XXZ_QP, b1, b2)
+    return {"L": Le, "R": Re, "M": [M0, M1], "bonds": [b0, b1, b2]}
+
+
+def heff_flops(qp, t, W, left, right):
+    """Algorithmic flops of one block-sparse H_eff application, order (((L A) W) R)."""
+    def find(b, q):
+        hit = np.nonzero(np.all(b["q"] == q[None, :], axis=1))[0]
+        return int(hit[0]) if len(hit) else -1
+    f = 0.0
+    t2 = {}
+    for bl in range(t.shape[0]):
+        for ik in range(len(left["dim"])):
+            ib = find(left, left["q"][ik] + t[bl])
+            if ib < 0:
+                continue
+            for s in range(qp.shape[0]):
+                j = find(right, left["q"][ik] + qp[s])
+                if j < 0:
+                    continue
+                rows, cols, K = left["dim"][ib], right["dim"][j], left["dim"][ik]
+                f += 2.0 * rows * cols * K                            # stage 1
+                for so in range(qp.shape[0]):
+                    for br in range(t.shape[0]):
+                        if W[so, s, bl, br] != 0.0:
+                            f += 2.0 * rows * cols                  # stage 2 term
+                            t2[(br, so, ib, j)] = (rows, cols)
+    for (br, so, ib, j), (rows, cols) in t2.items():
+        jp = find(right, right["q"][j] + t[br])
+        if jp >= 0:
+            f += 2.0 * rows * right["dim"][jp] * cols                 # stage 3
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for ln in out.splitlines():
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) >= 9:
+                self.samples.append(p)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(p[1]) for p in self.samples if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in self.samples if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in self.samples for k in range(4) if p[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        mp = json.load(f)
+    src = "measured"
+    bf16 = mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops")
+    hbm = mp.get("hbm_gbs")
+    if bf16 is None:
+        bf16, src = 1700.0, "fallback"
+    # other dtypes: the measured bf16 dense peak times the nominal ratio of the
+    # GB300 datasheet (bf16 2.25, tf32 1.1, fp64 1.25e-3 PFLOP/s dense)
+    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "fp64": bf16 * 1.25e-3 / 2.25, "hbm": hbm,
+            "source": src}
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    ent = t.get(kernel)
+    return ent.get("bytes_per_launch") if ent else None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_1501_05504_gb300 import binding as b
+    dev = torch.cuda.current_device()
+    ctx = b.dmrg3s_create(dev, 1 << 30)
+    spec = window_specs(SEED + rank)
+    mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
+    W = [mpo.site(50), mpo.site(51)]
+    opts = b.update_opts(M_MAX, kmax=40, tol=1e-10, prec=args.precision)
+    gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
+    gM = [b.site_from_neutral(x) for x in spec["M"]]
+    state = b.dmrg3s_state_create(ctx, W, gM, gL, gR, 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(st):
+        c, _ = st.centre()
+        return b.dmrg3s_local_update(st, 1 if c == 0 else -1, ALPHA, opts)
+
+    for _ in range(args.warmup):
+        step(state)
+    torch.cuda.synchronize()
+    # ---- device-resident timed region
+    b.dmrg3s_profile(ctx, True)
+    n0 = b.dmrg3s_launch_count()
+    times, iters = [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step(state)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(info["lanczos_iters"])
+    torch.cuda.synchronize()
+    launches = b.dmrg3s_launch_count() - n0
+    g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
+    cmb = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
+    b.dmrg3s_profile(ctx, False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops_step = (g["flops"] + cmb["flops"]) / args.steps
+    ms_step = total_ms / args.steps
+    value = flops_step * world / (ms_step * 1e-3) / 1e12
+    pk = peaks()
+    prec = args.precision
+    peak = pk["fp64"] if prec == "fp64" else pk["tf32"] / (3.0 if prec == "tf32x3" else 1.0)
+    achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else None
+    kname = "gemm_f64_kernel" if prec == "fp64" else "gemm_tc_kernel"
+    roofline = {"kernel": kname, "bound": "alu" if prec == "fp64" else "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic_for(kname), "launches": g["launches"],
+                "avg_launch_us": 1e3 * g["ms"] / max(g["launches"], 1),
+                "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (pk["source"], prec),
+                "share_of_step": g["ms"] / total_ms if total_ms else None}
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {"L": gL.data.cpu().pin_memory(), "R": gR.data.cpu().pin_memory(),
+                "M": [m.data.cpu().pin_memory() for m in gM]}
+        bi = sum(x.numel() * 8 for x in [host["L"], host["R"]] + host["M"])
+        torch.cuda.synchronize()
+        et = []
+        bo = 0
+        for k in range(max(2, args.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gL.data.copy_(host["L"], non_blocking=True)
+            gR.data.copy_(host["R"], non_blocking=True)
+            for m, h in zip(gM, host["M"]):
+                m.data.copy_(h, non_blocking=True)
+            st = b.dmrg3s_state_create(ctx, W, gM, gL, gR, 0)
+            step(st)
+            outs = [st.site(0), st.site(1)]
+            res = [o.data.to("cpu", non_blocking=True) for o in outs]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bo = sum(r.numel() * 8 for r in res)
+            et.append(e0.elapsed_time(e1))
+            st.close()
+        ems = statistics.mean(et)
+        e2e = {"value": flops_step * world / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+    state.close()
+    if rank != 0:
+        return None
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.cpu_sample_s)
+    return {"metric": "Heff.A TFLOP/s of one DMRG3S local update (algorithmic block-sparse flops)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "tf32x3": "tf32x3",
+                                                             "tf32": "tf32"}[prec],
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": "xxz_l100_m512_u1 central two-site window, one local update per step",
+                       "model": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z", "m_max": M_MAX,
+                       "alpha": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
+                       "lanczos_iters_mean": statistics.mean(iters), "flops_per_step": flops_step,
+                       "precision": prec, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary()}
+
+
+def cpu_baseline(sample_s=15.0):
+    """The FP64 oracle on the host cores: H_eff applications on the same window."""
+    from oracle import contract, io, models
+    spec = window_specs(SEED)
+    W = models.mpo_xxz(100, 1.0, 1.0).W[50]
+    L, R = io.env_dense(spec["L"]), io.env_dense(spec["R"])
+    # the right environment of site 50 inside the window: R_51 contracted with M_51
+    W1 = models.mpo_xxz(100, 1.0, 1.0).W[51]
+    M1 = io.site_dense(spec["M"][1])[0]
+    R50 = contract.right_env(R, W1, M1)
+    M0 = io.site_dense(spec["M"][0])[0]
+    t0 = time.time()
+    n = 0
+    while time.time() - t0 < sample_s or n == 0:
+        contract.apply_heff(L, W, R50, M0)
+        n += 1
+    dt = (time.time() - t0) / n
+    f = heff_flops(si.XXZ_QP, si.XXZ_T, W, spec["bonds"][0], spec["bonds"][1])
+    return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d H_eff applications of the window's centre site (dense FP64 einsum, %.2f s each)"
+                      % (n, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return None
+    t0 = time.time()
+    cb = cpu_baseline(max(args.cpu_sample_s, 1.0) * max(args.steps, 1) / 10.0)
+    return {"metric": "Heff.A TFLOP/s of one DMRG3S local update (algorithmic block-sparse flops)",
+            "value": cb["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "xxz_l100_m512_u1 central two-site window (oracle sample)"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "TFLOP/s",
+                                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.time() - t0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "tf32"])
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,26 @@ const char* dmrg3s_status_string(dmrg3s_status status);
  * call on ctx; "" when none). */
 const char* dmrg3s_last_error(dmrg3s_ctx ctx);
 
+/* Kernel timing.  While enabled, the context records CUDA events on the
+ * launching stream around every grouped-GEMM launch (kernel 0: the block
+ * products of stages 1 and 3 of the contraction order of Sec. V, and the
+ * S V^dagger product of the truncation) and every MPO combination launch
+ * (kernel 1: stage 2).  dmrg3s_profile(ctx, 1) resets and enables, 0
+ * disables; dmrg3s_profile_read synchronises on the recorded events and
+ * returns, for one kernel, the number of launches, their summed device time
+ * and their summed algorithmic flops and bytes (each distinct operand block
+ * read once, each output written once). */
+typedef struct dmrg3s_kernel_stats {
+  int64_t launches;
+  double ms, flops, bytes;
+} dmrg3s_kernel_stats;
+dmrg3s_status dmrg3s_profile(dmrg3s_ctx ctx, int32_t enable);
+dmrg3s_status dmrg3s_profile_read(dmrg3s_ctx ctx, int32_t kernel, dmrg3s_kernel_stats* out);
+
+/* Process-wide number of kernels this library has launched (its own kernels
+ * only; cuSOLVER's are not counted). */
+dmrg3s_status dmrg3s_launch_count(int64_t* n);
+
 /* Number of doubles a site tensor / environment occupies in canonical layout.
  * Pure host functions (no CUDA call); they also validate the charge tables. */
 dmrg3s_status dmrg3s_site_size(const dmrg3s_site* M, int64_t* nelem);

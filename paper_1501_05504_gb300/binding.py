@@ -573,3 +573,34 @@ def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, stream=None):
                                ctypes.byref(rep), _stream(stream)), "dmrg3s_sweep", state.ctx.handle)
     return {"energies": en[:rep.sweeps].tolist(), "sweeps": rep.sweeps, "converged": bool(rep.converged),
             "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters}
+
+
+class _KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+KERNEL_GEMM, KERNEL_COMBINE = 0, 1
+
+
+def dmrg3s_profile(ctx, enable):
+    L = lib()
+    L.dmrg3s_profile.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    _check(L.dmrg3s_profile(ctx.handle, int(bool(enable))), "dmrg3s_profile", ctx.handle)
+
+
+def dmrg3s_profile_read(ctx, kernel):
+    L = lib()
+    L.dmrg3s_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_KernelStats)]
+    st = _KernelStats()
+    _check(L.dmrg3s_profile_read(ctx.handle, int(kernel), ctypes.byref(st)), "dmrg3s_profile_read",
+           ctx.handle)
+    return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes}
+
+
+def dmrg3s_launch_count():
+    L = lib()
+    L.dmrg3s_launch_count.argtypes = [i64p]
+    n = ctypes.c_int64()
+    _check(L.dmrg3s_launch_count(ctypes.byref(n)), "dmrg3s_launch_count")
+    return n.value

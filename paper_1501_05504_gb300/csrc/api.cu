@@ -84,17 +84,29 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   return DMRG3S_OK;
 }
 
-dmrg3s_status run_plan(const DevicePlan& p, const double* g1A, const double* g1B, double* ws1,
-                       double* c2out, double c2scale, const double* g3A, const double* g3B,
-                       double* g3C, cudaStream_t st) {
+dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
+                       double* ws1, double* c2out, double c2scale, const double* g3A,
+                       const double* g3B, double* g3C, cudaStream_t st) {
   const Plan& h = p.host;
-  launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks, p.g1_segs,
-                  g1A, g1B, ws1, st);
-  launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1, c2out,
-                     c2scale, st);
-  if (h.has_g3)
+  Profiler& pr = c->prof;
+  if (!h.g1.tiles.empty()) {
+    if (pr.on) pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st);
+    launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks, p.g1_segs,
+                    g1A, g1B, ws1, st);
+    if (pr.on) pr.end(st);
+  }
+  if (!h.c2.chunks.empty()) {
+    if (pr.on) pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st);
+    launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1, c2out,
+                       c2scale, st);
+    if (pr.on) pr.end(st);
+  }
+  if (h.has_g3 && !h.g3.tiles.empty()) {
+    if (pr.on) pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st);
     launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks, p.g3_segs,
                     g3A, g3B, g3C, st);
+    if (pr.on) pr.end(st);
+  }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
 }
 
@@ -257,6 +269,38 @@ const char* dmrg3s_last_error(dmrg3s_ctx ctx) {
   return c ? c->last_error.c_str() : "no context";
 }
 
+dmrg3s_status dmrg3s_profile(dmrg3s_ctx ctx, int32_t enable) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c) return DMRG3S_ERR_ARG;
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_profile_read(dmrg3s_ctx ctx, int32_t kernel, dmrg3s_kernel_stats* out) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !out || kernel < 0 || kernel >= kProfKinds) return DMRG3S_ERR_ARG;
+  out->launches = 0;
+  out->ms = out->flops = out->bytes = 0.0;
+  for (const ProfRec& r : c->prof.recs) {
+    if (r.kind != kernel) continue;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "profile events");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    out->launches += 1;
+    out->ms += ms;
+    out->flops += r.flops;
+    out->bytes += r.bytes;
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_launch_count(int64_t* n) {
+  if (!n) return DMRG3S_ERR_ARG;
+  *n = launch_count();
+  return DMRG3S_OK;
+}
+
 dmrg3s_status dmrg3s_site_size(const dmrg3s_site* M, int64_t* nelem) {
   if (!nelem) return DMRG3S_ERR_ARG;
   SiteLayout s;
@@ -365,7 +409,7 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
   if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
-  st = run_plan(*p, L->data, A->data, ws1, ws2, 1.0, ws2, R->data, HA->data,
+  st = run_plan(c, *p, L->data, A->data, ws1, ws2, 1.0, ws2, R->data, HA->data,
                 reinterpret_cast<cudaStream_t>(stream));
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }
@@ -408,7 +452,7 @@ dmrg3s_status dmrg3s_expand(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
   double* ws1 = reinterpret_cast<double*>(c->ws);
   const double* g1A = dir == 1 ? env->data : M->data;
   const double* g1B = dir == 1 ? M->data : env->data;
-  st = run_plan(*p, g1A, g1B, ws1, P->data, alpha, nullptr, nullptr, nullptr,
+  st = run_plan(c, *p, g1A, g1B, ws1, P->data, alpha, nullptr, nullptr, nullptr,
                 reinterpret_cast<cudaStream_t>(stream));
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }
@@ -447,7 +491,7 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
   double* ws2 = ws1 + p->host.ws1;
   const double* g1A = dir == 1 ? env->data : A->data;
   const double* g1B = dir == 1 ? A->data : env->data;
-  st = run_plan(*p, g1A, g1B, ws1, ws2, 1.0, A->data, ws2, out->data,
+  st = run_plan(c, *p, g1A, g1B, ws1, ws2, 1.0, A->data, ws2, out->data,
                 reinterpret_cast<cudaStream_t>(stream));
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }

@@ -29,7 +29,49 @@ struct DevicePlan {
   ~DevicePlan();
 };
 
+// Per-kernel timing with CUDA events recorded on the launching stream around
+// every grouped-GEMM and combination launch while profiling is on.
+enum ProfKind { kProfGemm = 0, kProfCombine = 1, kProfKinds = 2 };
+struct ProfRec {
+  int kind;
+  cudaEvent_t e0, e1;
+  double flops, bytes;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t take() {
+    cudaEvent_t e;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void begin(int kind, double flops, double bytes, cudaStream_t st) {
+    ProfRec r{kind, take(), take(), flops, bytes};
+    cudaEventRecord(r.e0, st);
+    recs.push_back(r);
+  }
+  void end(cudaStream_t st) { cudaEventRecord(recs.back().e1, st); }
+  void reset() {
+    for (auto& r : recs) {
+      pool.push_back(r.e0);
+      pool.push_back(r.e1);
+    }
+    recs.clear();
+  }
+  ~Profiler() {
+    reset();
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Context {
+  Profiler prof;
   int device = 0;
   char* ws = nullptr;           // workspace arena
   size_t ws_bytes = 0;
@@ -107,8 +149,8 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 
 // Enqueue the stages of a plan.  Bases as documented for each plan Kind.
-dmrg3s_status run_plan(const DevicePlan& p, const double* g1A, const double* g1B, double* ws1,
-                       double* c2out, double c2scale, const double* g3A, const double* g3B,
-                       double* g3C, cudaStream_t st);
+dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
+                       double* ws1, double* c2out, double c2scale, const double* g3A,
+                       const double* g3B, double* g3C, cudaStream_t st);
 
 }  // namespace dmrg3s

@@ -53,7 +53,7 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   TridiagOut res{};
   for (;; ++k) {
     double* vk = V + (int64_t)k * n;
-    dmrg3s_status rs = run_plan(heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st);
+    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st);
     if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
     launch_multidot(V, n, k + 1, w, n, part, h, alpha + k, st);   // alpha_k = <v_k, H v_k>
     launch_multi_axpy(V, n, k + 1, h, w, n, st);

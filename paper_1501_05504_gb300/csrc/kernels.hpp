@@ -47,6 +47,10 @@ constexpr int kCombRows = 16;
 
 enum class Trans { N, T };
 
+// Process-wide count of kernels launched by this library.
+int64_t launch_count();
+void count_launch(int n = 1);
+
 // FP64 grouped GEMM on the CUDA cores.  opA = A (M x K, lda) or A^T (A stored
 // K x M); opB = B (K x N, ldb) or B^T (B stored N x K).
 void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, const GemmTask* tasks,

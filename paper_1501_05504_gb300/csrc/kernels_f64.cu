@@ -5,6 +5,8 @@
 // per 64 x 64 output tile, summing all K-segments of its task.  The
 // combination kernel applies the MPO step (T2 = sum W T1), which costs
 // O(m^2 d^2 w^2) and is bound by memory bandwidth.
+#include <atomic>
+
 #include "kernels.hpp"
 
 namespace dmrg3s {
@@ -118,12 +120,18 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombChunk* __res
   }
 }
 
+std::atomic<int64_t> g_launches{0};
+
 }  // namespace
+
+int64_t launch_count() { return g_launches.load(); }
+void count_launch(int n) { g_launches += n; }
 
 void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, const GemmTask* tasks,
                      const GemmSeg* segs, const double* A, const double* B, double* C,
                      cudaStream_t st) {
   if (ntiles <= 0) return;
+  count_launch();
   dim3 grid(ntiles), block(NT);
   if (ta == Trans::N && tb == Trans::N)
     gemm_f64_kernel<Trans::N, Trans::N><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
@@ -139,6 +147,7 @@ void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* ta
                         const CombTerm* terms, const double* in, double* out, double scale,
                         cudaStream_t st) {
   if (nchunks <= 0) return;
+  count_launch();
   combine_f64_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out, scale);
 }
 

@@ -5,6 +5,7 @@
 
 #include <array>
 #include <map>
+#include <set>
 
 namespace dmrg3s {
 
@@ -28,6 +29,22 @@ void GemmStage::add(int64_t offC, int ldc, int M, int N, const std::vector<GemmS
     for (int b = 0; b < ntn; ++b) tiles.push_back(GemmTile{id, a, b, 0});
 }
 
+void GemmStage::finalize_bytes(Trans, Trans) {
+  std::set<std::pair<int64_t, int64_t>> a, b;
+  double elems = 0.0;
+  for (const GemmTask& t : tasks) {
+    elems += (double)t.M * t.N;
+    for (int k = 0; k < t.nseg; ++k) {
+      const GemmSeg& g = segs[t.seg0 + k];
+      a.insert({g.offA, (int64_t)t.M * g.K});
+      b.insert({g.offB, (int64_t)t.N * g.K});
+    }
+  }
+  for (auto& x : a) elems += (double)x.second;
+  for (auto& x : b) elems += (double)x.second;
+  bytes = 8.0 * elems;
+}
+
 void CombStage::add(int64_t offOut, int ldo, int rows, int cols, const std::vector<CombTerm>& t) {
   if (rows <= 0 || cols <= 0) return;
   CombTask task{};
@@ -41,6 +58,7 @@ void CombStage::add(int64_t offOut, int ldo, int rows, int cols, const std::vect
   tasks.push_back(task);
   terms.insert(terms.end(), t.begin(), t.end());
   flops += 2.0 * rows * (double)cols * t.size();
+  bytes += 8.0 * rows * (double)cols * (1 + t.size());
   for (int r = 0; r < rows; r += kCombRows)
     chunks.push_back(CombChunk{id, r, rows - r < kCombRows ? rows - r : kCombRows, 0});
 }
@@ -156,6 +174,8 @@ std::map<Key, Interm> materialise(const std::map<Key, Combo>& combos, Plan* p) {
 // Bounds of every table against the buffers the stages address.
 dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
                      int64_t nC3, std::string* err) {
+  p->g1.finalize_bytes(p->g1.ta, p->g1.tb);
+  if (p->has_g3) p->g3.finalize_bytes(p->g3.ta, p->g3.tb);
   const int64_t w1 = p->ws1 > 0 ? p->ws1 : 1;
   if (!gemm_ok(p->g1.ta, p->g1.tb, p->g1.tasks, p->g1.segs, nA1, nB1, w1, err) ||
       !comb_ok(p->c2.tasks, p->c2.terms, w1, nOut2, err) ||

@@ -37,7 +37,9 @@ struct GemmStage {
   std::vector<GemmSeg> segs;
   std::vector<GemmTile> tiles;
   double flops = 0.0;
+  double bytes = 0.0;     // algorithmic: distinct operand blocks read once + output written once
   void add(int64_t offC, int ldc, int M, int N, const std::vector<GemmSeg>& s);
+  void finalize_bytes(Trans ta, Trans tb);
 };
 
 struct CombStage {
@@ -45,6 +47,7 @@ struct CombStage {
   std::vector<CombTerm> terms;
   std::vector<CombChunk> chunks;
   double flops = 0.0;
+  double bytes = 0.0;     // algorithmic: distinct input blocks read once + output written once
   void add(int64_t offOut, int ldo, int rows, int cols, const std::vector<CombTerm>& t);
 };
 

@@ -95,7 +95,9 @@ dmrg3s_status run_gemm(Context* c, const GemmStage& g, const double* A, int64_t 
   if ((s = upload(c, g.tiles, &dt, st)) || (s = upload(c, g.tasks, &dk, st)) ||
       (s = upload(c, g.segs, &ds, st)))
     return s;
+  if (c->prof.on) c->prof.begin(kProfGemm, g.flops, g.bytes, st);
   launch_gemm_f64(g.ta, g.tb, dt, (int)g.tiles.size(), dk, ds, A, B, C, st);
+  if (c->prof.on) c->prof.end(st);
   cudaFreeAsync(dt, st);
   cudaFreeAsync(dk, st);
   if (ds) cudaFreeAsync(ds, st);
@@ -168,7 +170,7 @@ dmrg3s_status build_env(State& S, int i, int dir, cudaStream_t st) {
   double* ws2 = ws1 + p->host.ws1;
   const double* g1A = dir == 1 ? src.data : a.data;
   const double* g1B = dir == 1 ? a.data : src.data;
-  if ((s = run_plan(*p, g1A, g1B, ws1, ws2, 1.0, a.data, ws2, nd, st)))
+  if ((s = run_plan(c, *p, g1A, g1B, ws1, ws2, 1.0, a.data, ws2, nd, st)))
     return fail(c, s, "environment update launch");
   dfree(dst.data, st);
   dst.data = nd;
@@ -190,7 +192,7 @@ dmrg3s_status rayleigh(State& S, int i, const double* x, cudaStream_t st, double
   if ((s = dalloc(c, &hx, n, st))) return s;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
-  if ((s = run_plan(*p, S.Lenv[i].data, x, ws1, ws2, 1.0, ws2, S.Renv[i].data, hx, st))) return s;
+  if ((s = run_plan(c, *p, S.Lenv[i].data, x, ws1, ws2, 1.0, ws2, S.Renv[i].data, hx, st))) return s;
   double num = 0.0, den = 0.0;
   if ((s = dot_host(c, x, hx, n, st, &num)) || (s = dot_host(c, x, x, n, st, &den))) return s;
   dfree(hx, st);
@@ -269,7 +271,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     if ((s = dalloc(c, &P, pl.size, st))) return s;
     const double* g1A = dir == 1 ? env.data : m.data;
     const double* g1B = dir == 1 ? m.data : env.data;
-    if ((s = run_plan(*ep, g1A, g1B, reinterpret_cast<double*>(c->ws), P, alpha, nullptr, nullptr,
+    if ((s = run_plan(c, *ep, g1A, g1B, reinterpret_cast<double*>(c->ws), P, alpha, nullptr, nullptr,
                       nullptr, st)))
       return s;
   }

@@ -5,6 +5,7 @@
 // kernel adds the partials in a fixed order.
 #include <cmath>
 
+#include "kernels.hpp"
 #include "vecops.hpp"
 
 namespace dmrg3s {
@@ -236,32 +237,38 @@ int grid_for(int64_t n) {
 
 void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                      double* partial, double* h, double* copy_last, cudaStream_t st) {
+  count_launch(2);
   multidot_partial<<<kRedBlocks, kThreads, 0, st>>>(V, ldv, k, w, n, partial);
   multidot_final<<<1, kThreads, 0, st>>>(partial, kRedBlocks, k, h, copy_last);
 }
 
 void launch_multi_axpy(const double* V, int64_t ldv, int k, const double* h, double* w, int64_t n,
                        cudaStream_t st) {
+  count_launch();
   multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, h, w, n);
 }
 
 void launch_combine_vectors(const double* V, int64_t ldv, int k, const double* c, double* y,
                             int64_t n, cudaStream_t st) {
+  count_launch();
   combine_vectors_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, c, y, n);
 }
 
 void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2, cudaStream_t st) {
+  count_launch();
   normalise_kernel<<<grid_for(n), kThreads, 0, st>>>(x, y, n, nrm2);
 }
 
 void launch_tridiag_smallest(const double* alpha, double* beta, int k, const double* nrm2,
                              double* y, TridiagOut* out, cudaStream_t st) {
+  count_launch();
   tridiag_smallest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, nrm2, y, out);
 }
 
 void launch_copy_blocks(const CopyTask* tasks, int ntasks, const double* src, double* dst,
                         const double* scale, cudaStream_t st) {
   if (ntasks <= 0) return;
+  count_launch();
   copy_blocks_kernel<<<ntasks, 256, 0, st>>>(tasks, src, dst, scale);
 }
 
