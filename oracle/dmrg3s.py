@@ -282,6 +282,7 @@ class SweepOptions:
     conv_tol: float = 1e-9
     lanczos_kmax: int = 40
     lanczos_tol: float = 1e-10
+    trunc_eps: float = 1e-12
     alpha: AlphaRule = field(default_factory=AlphaRule)
 
 
@@ -326,7 +327,7 @@ class DMRG3S:
         P = contract.expansion_term_lr(self.Lenv[i], mpo.W[i], Mstar, self.alpha)   # 2
         Mt = np.concatenate([Mstar, P], axis=2)                             # 3
         qr_t = np.concatenate([mps.q[i + 1], combine(mpo.t[i + 1], mps.q[i + 1])], axis=0)
-        A, SV, qn = truncate_lr(Mt, mps.qphys, mps.q[i], qr_t, o.m_max)      # 4
+        A, SV, qn = truncate_lr(Mt, mps.qphys, mps.q[i], qr_t, o.m_max, o.trunc_eps)   # 4
         mr = mps.M[i].shape[2]
         Bn = np.einsum("kx,sxy->sky", SV[:, :mr], mps.M[i + 1])              # 5
         mps.M[i], mps.M[i + 1], mps.q[i + 1] = A, Bn, qn
@@ -343,7 +344,7 @@ class DMRG3S:
         P = contract.expansion_term_rl(self.Renv[i], mpo.W[i], Mstar, self.alpha)
         Mt = np.concatenate([Mstar, P], axis=1)
         ql_t = np.concatenate([mps.q[i], combine(mpo.t[i], mps.q[i])], axis=0)
-        B, US, qn = truncate_rl(Mt, mps.qphys, ql_t, mps.q[i + 1], o.m_max)
+        B, US, qn = truncate_rl(Mt, mps.qphys, ql_t, mps.q[i + 1], o.m_max, o.trunc_eps)
         ml = mps.M[i].shape[1]
         An = np.einsum("sxy,yk->sxk", mps.M[i - 1], US[:ml, :])
         mps.M[i], mps.M[i - 1], mps.q[i] = B, An, qn
