@@ -268,12 +268,16 @@ def _prec(p):
 
 class Context:
     def __init__(self, device=0, workspace_bytes=0):
+        import weakref
         self.handle = ctypes.c_void_p()
+        self._states = weakref.WeakSet()     # states must be destroyed before their context
         _check(lib().dmrg3s_create(ctypes.byref(self.handle), int(device), int(workspace_bytes)),
                "dmrg3s_create")
 
     def close(self):
         if self.handle:
+            for st in list(self._states):
+                st.close()
             lib().dmrg3s_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
@@ -494,6 +498,7 @@ class State:
     def __init__(self, ctx, W, M, left_env=None, right_env=None, centre=0):
         n = len(W)
         self.ctx = ctx
+        ctx._states.add(self)
         self.handle = ctypes.c_void_p()
         cw = (_MpoSite * n)(*[w._c() for w in W])
         cm = (_Site * n)(*[m._c() for m in M])

@@ -106,44 +106,88 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
-__global__ void tridiag_smallest_kernel(const double* __restrict__ alpha, double* __restrict__ beta,
-                                        int k, const double* __restrict__ nrm2,
-                                        double* __restrict__ y, TridiagOut* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void tridiag_vector(const double* alpha, const double* beta, int k, double bl,
+                               double theta, double span, double lo, double hi, double* y,
+                               TridiagOut* out);
+
+// Multisection variant: all threads of the block evaluate Sturm counts at
+// equally spaced points of the bracket, shrinking it by blockDim.x + 1 per
+// round; thread 0 then runs the inverse iteration.
+__global__ void tridiag_multisection_kernel(const double* __restrict__ alpha,
+                                            double* __restrict__ beta, int k,
+                                            const double* __restrict__ nrm2,
+                                            double* __restrict__ y, TridiagOut* __restrict__ out) {
+  __shared__ double sh_lo, sh_hi, sh_span;
+  __shared__ int sh_bad, sh_first;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const double bl = sqrt(*nrm2);
-  beta[k - 1] = bl;
-  // Gershgorin interval
-  double lo = 1e300, hi = -1e300;
-  bool bad = false;
-  for (int i = 0; i < k; ++i) {
-    const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < k - 1 ? fabs(beta[i]) : 0.0);
-    lo = fmin(lo, alpha[i] - r);
-    hi = fmax(hi, alpha[i] + r);
-    if (!(alpha[i] == alpha[i])) bad = true;
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    int bad = 0;
+    for (int i = 0; i < k; ++i) {
+      const double bi = i < k - 1 ? beta[i] : 0.0;
+      const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + fabs(bi);
+      lo = fmin(lo, alpha[i] - r);
+      hi = fmax(hi, alpha[i] + r);
+      if (!(alpha[i] == alpha[i])) bad = 1;
+    }
+    if (!(bl == bl)) bad = 1;
+    const double span = fmax(hi - lo, 1e-300);
+    sh_lo = lo - 1e-12 * span;
+    sh_hi = hi + 1e-12 * span;
+    sh_span = span;
+    sh_bad = bad;
+    beta[k - 1] = bl;
   }
-  if (bad || !(bl == bl)) {
-    out->theta = 0.0;
-    out->resid = 0.0;
-    out->beta_last = bl;
-    out->nan_seen = 1.0;
+  __syncthreads();
+  if (sh_bad) {
+    if (tid == 0) {
+      out->theta = 0.0;
+      out->resid = 0.0;
+      out->beta_last = bl;
+      out->nan_seen = 1.0;
+    }
     return;
   }
-  const double span = fmax(hi - lo, 1e-300);
-  lo -= 1e-12 * span;
-  hi += 1e-12 * span;
-  // bisection for the smallest eigenvalue: count(x) >= 1 means x is above it
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid;
-    else lo = mid;
+  for (int round = 0; round < 16; ++round) {
+    const double lo = sh_lo, hi = sh_hi;
+    const double h = (hi - lo) / (nt + 1);
+    if (!(h > 0.0) || lo + h <= lo) break;
+    if (tid == 0) sh_first = nt;
+    __syncthreads();
+    const double x = lo + h * (tid + 1);
+    if (sturm_count(alpha, beta, k, x) >= 1) atomicMin(&sh_first, tid);
+    __syncthreads();
+    if (tid == 0) {
+      const int f = sh_first;            // first point above the smallest eigenvalue
+      sh_hi = f < nt ? lo + h * (f + 1) : hi;
+      sh_lo = f > 0 ? lo + h * f : lo;
+    }
+    __syncthreads();
   }
-  const double theta = 0.5 * (lo + hi);
+  if (tid == 0)
+    tridiag_vector(alpha, beta, k, bl, 0.5 * (sh_lo + sh_hi), sh_span, sh_lo, sh_hi, y, out);
+}
+
+__device__ void tridiag_vector(const double* alpha, const double* beta, int k, double bl,
+                               double theta, double span, double lo, double hi, double* y,
+                               TridiagOut* out) {
+  const int kk = k <= 128 ? k : 128;
+  if (kk == 1) {                 // the Ritz vector of a 1x1 matrix
+    y[0] = 1.0;
+    out->theta = theta;
+    out->resid = fabs(bl);
+    out->beta_last = bl;
+    out->nan_seen = 0.0;
+    return;
+  }
   // inverse iteration: solve (T - theta I) z = y with a pivoted tridiagonal LU
-  // (partial pivoting keeps the elimination stable at the near-singular shift)
+  // (partial pivoting keeps the elimination stable at the near-singular shift);
+  // an exactly zero pivot is replaced by 1e-15 of the matrix scale, which keeps
+  // the solution finite (of order 1e15 times the scale) before normalisation
+  const double tiny = 1e-15 * fmax(span, fmax(fabs(lo), fabs(hi)));
   double dl[128], dd[128], du[128], du2[128];
   int piv[128];
-  const int kk = k <= 128 ? k : 128;
   for (int i = 0; i < kk; ++i) y[i] = 1.0 / sqrt((double)kk);
   for (int sweep = 0; sweep < 3; ++sweep) {
     for (int i = 0; i < kk; ++i) {
@@ -155,7 +199,7 @@ __global__ void tridiag_smallest_kernel(const double* __restrict__ alpha, double
     for (int i = 0; i < kk - 1; ++i) {
       if (fabs(dd[i]) >= fabs(dl[i])) {
         piv[i] = i;
-        if (dd[i] == 0.0) dd[i] = 1e-300;
+        if (dd[i] == 0.0) dd[i] = tiny;
         const double f = dl[i] / dd[i];
         dl[i] = f;
         dd[i + 1] -= f * du[i];
@@ -173,7 +217,8 @@ __global__ void tridiag_smallest_kernel(const double* __restrict__ alpha, double
         }
       }
     }
-    if (dd[kk - 1] == 0.0) dd[kk - 1] = 1e-300;
+    for (int i = 0; i < kk; ++i)
+      if (dd[i] == 0.0) dd[i] = tiny;
     // forward: apply row interchanges and L
     for (int i = 0; i < kk - 1; ++i) {
       if (piv[i] == i) {
@@ -189,8 +234,18 @@ __global__ void tridiag_smallest_kernel(const double* __restrict__ alpha, double
     if (kk > 1) y[kk - 2] = (y[kk - 2] - du[kk - 2] * y[kk - 1]) / dd[kk - 2];
     for (int i = kk - 3; i >= 0; --i)
       y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
+    // normalise: scale by the largest component first (no overflow in the squares)
+    double big = 0.0;
+    for (int i = 0; i < kk; ++i) big = fmax(big, fabs(y[i]));
+    if (!(big > 0.0) || !(big < 1e308)) {   // degenerate solve: restart from e_0
+      for (int i = 0; i < kk; ++i) y[i] = i == 0 ? 1.0 : 0.0;
+      continue;
+    }
     double nrm = 0.0;
-    for (int i = 0; i < kk; ++i) nrm += y[i] * y[i];
+    for (int i = 0; i < kk; ++i) {
+      y[i] /= big;
+      nrm += y[i] * y[i];
+    }
     nrm = sqrt(nrm);
     for (int i = 0; i < kk; ++i) y[i] /= nrm;
   }
@@ -262,7 +317,7 @@ void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2,
 void launch_tridiag_smallest(const double* alpha, double* beta, int k, const double* nrm2,
                              double* y, TridiagOut* out, cudaStream_t st) {
   count_launch();
-  tridiag_smallest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, nrm2, y, out);
+  tridiag_multisection_kernel<<<1, 256, 0, st>>>(alpha, beta, k, nrm2, y, out);
 }
 
 void launch_copy_blocks(const CopyTask* tasks, int ntasks, const double* src, double* dst,
