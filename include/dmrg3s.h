@@ -58,7 +58,8 @@ typedef enum dmrg3s_status {
   DMRG3S_ERR_BREAKDOWN = 7,     /* Lanczos start vector is zero                 */
   DMRG3S_ERR_TIMEOUT = 8,       /* a bounded device wait gave up                */
   DMRG3S_ERR_NUMERIC = 9,       /* NaN or Inf detected                          */
-  DMRG3S_ERR_UNSUPPORTED = 10   /* valid request this build does not implement  */
+  DMRG3S_ERR_UNSUPPORTED = 10,  /* valid request this build does not implement  */
+  DMRG3S_ERR_LIMIT = 11         /* request exceeds a fixed static capacity      */
 } dmrg3s_status;
 
 typedef enum dmrg3s_precision {
@@ -177,6 +178,36 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
 dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
                                 const dmrg3s_env* R, const dmrg3s_site* A, dmrg3s_site* HA,
                                 dmrg3s_precision prec, dmrg3s_stream stream);
+
+/* H_eff application for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of
+ * dmrg3s_apply_heff.  Code running while a CUDA graph is being captured, hosts
+ * whose device memory is reserved up front by another allocator, and
+ * real-time callers cannot call cudaMalloc, and so cannot create a context
+ * (whose workspace is allocated).  This entry point needs no context and
+ * allocates nothing on the device: it computes exactly what
+ * dmrg3s_apply_heff computes in DMRG3S_FP64, keeping its intermediates
+ * (T1 = L A, T2 = W T1) and task tables in fixed-size static device arrays of
+ * this library (DMRG3S_NOALLOC_SCRATCH_DOUBLES doubles of scratch plus about
+ * 16 MiB of tables), which every GPU that loads the library holds until the
+ * process exits.  The caller passes inputs and output as for
+ * dmrg3s_apply_heff, on the current CUDA device.
+ *  - The first call on a device looks up the arrays' device addresses (a
+ *    one-time set-up with that device current); make that first call before
+ *    any stream capture.
+ *  - All calls share the arrays, which keep the last call's contents: calls
+ *    that overlap on the GPU (different streams, or threads) race and give
+ *    wrong results.  Every intermediate element is written before it is read,
+ *    so nothing has to be cleared between calls.
+ *  - Returns DMRG3S_ERR_LIMIT, before touching the device, when the
+ *    intermediates need more than DMRG3S_NOALLOC_SCRATCH_DOUBLES doubles or
+ *    the block structure needs more tasks than the static tables hold.
+ * Errors: ARG, SHAPE, QN, LIMIT, CUDA. */
+#define DMRG3S_NOALLOC_SCRATCH_DOUBLES 2097152
+dmrg3s_status dmrg3s_apply_heff_noalloc(const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                                        const dmrg3s_env* R, const dmrg3s_site* A,
+                                        dmrg3s_site* HA, dmrg3s_stream stream);
 
 /* Expansion term of Sec. IV B (Eq. subexp-ourt):
  *   dir = +1 (left-to-right sweep): P = alpha L_{i-1} M_i W_i, in (d, m_{i-1}, w_i m_i),

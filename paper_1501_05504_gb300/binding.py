@@ -580,6 +580,18 @@ def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, stream=None):
             "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters}
 
 
+def dmrg3s_apply_heff_noalloc(L, W, R, A, HA, stream=None):
+    """H_eff application without a context and without device allocation (static scratch)."""
+    lb = lib()
+    lb.dmrg3s_apply_heff_noalloc.argtypes = [ctypes.POINTER(_Env), ctypes.POINTER(_MpoSite),
+                                             ctypes.POINTER(_Env), ctypes.POINTER(_Site),
+                                             ctypes.POINTER(_Site), ctypes.c_void_p]
+    cL, cW, cR, cA, cH = L._c(), W._c(), R._c(), A._c(), HA._c()
+    _check(lb.dmrg3s_apply_heff_noalloc(ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR),
+                                        ctypes.byref(cA), ctypes.byref(cH), _stream(stream)),
+           "dmrg3s_apply_heff_noalloc")
+
+
 class _KernelStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
                 ("bytes", ctypes.c_double)]

@@ -260,6 +260,7 @@ const char* dmrg3s_status_string(dmrg3s_status s) {
     case DMRG3S_ERR_TIMEOUT: return "device wait timed out";
     case DMRG3S_ERR_NUMERIC: return "NaN or Inf";
     case DMRG3S_ERR_UNSUPPORTED: return "unsupported";
+    case DMRG3S_ERR_LIMIT: return "exceeds a fixed static capacity";
   }
   return "unknown status";
 }
