@@ -204,6 +204,9 @@ def run_ours(args):
     launches = b.dmrg3s_launch_count() - n0
     g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
     cmb = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
+    phases = {name: b.dmrg3s_profile_read(ctx, k)["ms"] / args.steps
+              for k, name in enumerate(["eigensolver", "expansion", "svd_truncation", "remainder",
+                                        "environment", "energy"], start=2)}
     b.dmrg3s_profile(ctx, False)
     total_ms = sum(times)
     if world > 1:
@@ -269,6 +272,7 @@ def run_ours(args):
                        "model": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z", "m_max": M_MAX,
                        "alpha": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "lanczos_iters_mean": statistics.mean(iters), "flops_per_step": flops_step,
+                       "phase_ms_per_step": phases,
                        "precision": prec, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

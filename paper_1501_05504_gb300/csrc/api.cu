@@ -90,22 +90,22 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   const Plan& h = p.host;
   Profiler& pr = c->prof;
   if (!h.g1.tiles.empty()) {
-    if (pr.on) pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st);
+    const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
     launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks, p.g1_segs,
                     g1A, g1B, ws1, st);
-    if (pr.on) pr.end(st);
+    if (id >= 0) pr.end(id, st);
   }
   if (!h.c2.chunks.empty()) {
-    if (pr.on) pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st);
+    const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
     launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1, c2out,
                        c2scale, st);
-    if (pr.on) pr.end(st);
+    if (id >= 0) pr.end(id, st);
   }
   if (h.has_g3 && !h.g3.tiles.empty()) {
-    if (pr.on) pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st);
+    const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
     launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks, p.g3_segs,
                     g3A, g3B, g3C, st);
-    if (pr.on) pr.end(st);
+    if (id >= 0) pr.end(id, st);
   }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
 }

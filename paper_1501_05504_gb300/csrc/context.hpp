@@ -31,7 +31,17 @@ struct DevicePlan {
 
 // Per-kernel timing with CUDA events recorded on the launching stream around
 // every grouped-GEMM and combination launch while profiling is on.
-enum ProfKind { kProfGemm = 0, kProfCombine = 1, kProfKinds = 2 };
+enum ProfKind {
+  kProfGemm = 0,        // grouped-GEMM launches
+  kProfCombine = 1,     // MPO combination launches
+  kProfEig = 2,         // phases of a local update: eigensolver
+  kProfExpand = 3,      //   expansion term
+  kProfSvd = 4,         //   gather of M~, per-sector SVD, selection, new tensors
+  kProfRemainder = 5,   //   S V^dagger (or U S) into the neighbour
+  kProfEnv = 6,         //   environment update
+  kProfEnergy = 7,      //   energy after truncation
+  kProfKinds = 8
+};
 struct ProfRec {
   int kind;
   cudaEvent_t e0, e1;
@@ -51,12 +61,13 @@ struct Profiler {
     }
     return e;
   }
-  void begin(int kind, double flops, double bytes, cudaStream_t st) {
+  int begin(int kind, double flops, double bytes, cudaStream_t st) {
     ProfRec r{kind, take(), take(), flops, bytes};
     cudaEventRecord(r.e0, st);
     recs.push_back(r);
+    return (int)recs.size() - 1;
   }
-  void end(cudaStream_t st) { cudaEventRecord(recs.back().e1, st); }
+  void end(int id, cudaStream_t st) { cudaEventRecord(recs[id].e1, st); }
   void reset() {
     for (auto& r : recs) {
       pool.push_back(r.e0);

@@ -95,9 +95,9 @@ dmrg3s_status run_gemm(Context* c, const GemmStage& g, const double* A, int64_t 
   if ((s = upload(c, g.tiles, &dt, st)) || (s = upload(c, g.tasks, &dk, st)) ||
       (s = upload(c, g.segs, &ds, st)))
     return s;
-  if (c->prof.on) c->prof.begin(kProfGemm, g.flops, g.bytes, st);
+  const int id = c->prof.on ? c->prof.begin(kProfGemm, g.flops, g.bytes, st) : -1;
   launch_gemm_f64(g.ta, g.tb, dt, (int)g.tiles.size(), dk, ds, A, B, C, st);
-  if (c->prof.on) c->prof.end(st);
+  if (id >= 0) c->prof.end(id, st);
   cudaFreeAsync(dt, st);
   cudaFreeAsync(dk, st);
   if (ds) cudaFreeAsync(ds, st);
@@ -235,7 +235,13 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   dmrg3s_status s;
   DevSite& m = S.M[i];
   const MpoLayout& w = S.W[i];
+  Profiler& pr = c->prof;
+  auto phase = [&](int kind) { return pr.on ? pr.begin(kind, 0.0, 0.0, st) : -1; };
+  auto done = [&](int id) {
+    if (id >= 0) pr.end(id, st);
+  };
   // ---- 1. eigensolver
+  int ph = phase(kProfEig);
   if (o.optimise) {
     const DevicePlan* hp;
     if ((s = heff_plan(c, S.Lenv[i].lay, w, S.Renv[i].lay, m.lay, &hp))) return s;
@@ -251,7 +257,9 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     if ((s = rayleigh(S, i, m.data, st, &info->lambda))) return s;
     info->iters = 0;
   }
+  done(ph);
   // ---- 2. expansion term
+  ph = phase(kProfExpand);
   const bool expand = alpha != 0.0;
   const Bond& old = dir == 1 ? m.lay.right : m.lay.left;
   FusedBond fp;      // P part only
@@ -275,6 +283,8 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
                       nullptr, st)))
       return s;
   }
+  done(ph);
+  ph = phase(kProfSvd);
   // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L)
   std::vector<Charge> charges;
   for (int k = 0; k < old.nsec(); ++k) charges.push_back(old.q[k]);
@@ -482,6 +492,8 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   dfree(U, st);
   dfree(V, st);
   dfree(Sv, st);
+  done(ph);
+  ph = phase(kProfRemainder);
   // ---- 5. remainder into the neighbour
   DevSite& nbs = S.M[nb];
   SiteLayout nnl;
@@ -542,6 +554,8 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   m.data = ndata;
   nbs.lay = nnl;
   nbs.data = nbdata;
+  done(ph);
+  ph = phase(kProfEnv);
   // ---- 6. environment of the truncated tensor; the neighbour's old one is stale
   if (dir == 1) {
     S.Renv[i].valid = false;
@@ -551,8 +565,11 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     if ((s = build_env(S, i, -1, st))) return s;
   }
   S.centre = nb;
+  done(ph);
+  ph = phase(kProfEnergy);
   // ---- 7. energy after truncation at the neighbour
   if ((s = rayleigh(S, nb, nbs.data, st, &info->e_f))) return s;
+  done(ph);
   return cuda_ok(c, cudaGetLastError(), "local update");
 }
 
