@@ -8,7 +8,8 @@
 //   3. M~ = [M* P] per charge sector of the expanded right bond; the neighbour
 //      is padded with zero rows (never materialised: the zero rows only meet
 //      the P columns, so step 5 multiplies with the M* part only)
-//   4. FP64 SVD of every sector (cuSOLVER gesvdj) and global truncation to
+//   4. FP64 SVD of every sector (cuSOLVER gesvd, sectors concurrently on
+//      several streams) and global truncation to
 //      m_max states: A~ = U
 //   5. B~_{i+1} = (S V^dagger)[:, M part] . B_{i+1}                     [grouped GEMM]
 //   6. L_i = L_{i-1} A~^dagger W_i A~                                   [plan]
@@ -18,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <tuple>
 
 #include "context.hpp"
@@ -41,6 +43,18 @@ struct DevEnv {
 
 }  // namespace
 
+// One concurrent SVD lane: its own cuSOLVER handle, stream and workspaces.
+struct SvdWorker {
+  cusolverDnHandle_t h = nullptr;
+  cusolverDnParams_t p = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  void* dwork = nullptr;
+  size_t dbytes = 0;
+  std::vector<char> hwork;
+};
+constexpr int kSvdWorkers = 4;
+
 struct State {
   Context* c = nullptr;
   int n = 0;
@@ -50,8 +64,8 @@ struct State {
   std::vector<DevEnv> Renv;   // Renv[i]: sites > i, on M[i].right, channels W[i].tr
   int centre = 0;
   double e_in = 0.0;
-  cusolverDnHandle_t solver = nullptr;
-  gesvdjInfo_t svdj = nullptr;
+  std::vector<SvdWorker> svd;
+  cudaEvent_t svd_in = nullptr;
 };
 
 namespace {
@@ -217,12 +231,83 @@ struct Info {
 struct Sector {
   Charge q;
   int64_t rows = 0, cols = 0, base = 0;   // base = size of the M* part (cols for L->R, rows for R->L)
-  int64_t off = 0;                        // offset of X in the X buffer
-  int64_t r = 0;                          // min(rows, cols)
-  int64_t offU = 0, offV = 0, offS = 0;   // outputs of gesvdj
+  bool tall = true;                       // rows >= cols: X is factorised, else X^T
+  int64_t m = 0, n = 0, r = 0;            // factorised matrix m x n (m >= n), r = n
+  int64_t off = 0;                        // offset of the matrix in the X buffer
+  int64_t offU = 0, offVT = 0, offS = 0;  // U (m x r), VT (r x n), S (r) in the output buffers
   int keep = 0;
   int jbase = -1;                         // old bond sector of the M* part, -1 if none
 };
+
+// FP64 SVD X_tall = U S VT of every sector (cuSOLVER gesvd, jobs 'S'),
+// spread over the worker streams, largest sectors first; `st` waits for all.
+dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, double* F,
+                          double* Sv, int* info, cudaStream_t st) {
+  Context* c = S.c;
+  if (secs.empty()) return DMRG3S_OK;
+  size_t dmax = 1, hmax = 1;
+  for (const Sector& sc : secs) {
+    size_t wd = 0, wh = 0;
+    if (cusolverDnXgesvd_bufferSize(S.svd[0].h, S.svd[0].p, 'S', 'S', sc.m, sc.n, CUDA_R_64F, nullptr,
+                                    sc.m, CUDA_R_64F, nullptr, CUDA_R_64F, nullptr, sc.m, CUDA_R_64F,
+                                    nullptr, sc.r, CUDA_R_64F, &wd, &wh) != CUSOLVER_STATUS_SUCCESS)
+      return fail(c, DMRG3S_ERR_CUDA, "gesvd buffer size");
+    dmax = std::max(dmax, wd);
+    hmax = std::max(hmax, wh);
+  }
+  for (SvdWorker& w : S.svd) {
+    if (w.dbytes < dmax) {
+      if (w.dwork) cudaFree(w.dwork);
+      w.dwork = nullptr;
+      w.dbytes = 0;
+      if (cudaMalloc(&w.dwork, dmax) != cudaSuccess)
+        return fail(c, DMRG3S_ERR_CUDA, "SVD workspace");
+      w.dbytes = dmax;
+    }
+    if (w.hwork.size() < hmax) w.hwork.resize(hmax);
+  }
+  // greedy assignment by cost m n^2, largest first
+  std::vector<int> order(secs.size());
+  for (size_t k = 0; k < secs.size(); ++k) order[k] = (int)k;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)secs[a].m * secs[a].n * secs[a].n > (double)secs[b].m * secs[b].n * secs[b].n;
+  });
+  const int nw = (int)S.svd.size();
+  std::vector<std::vector<int>> jobs(nw);
+  std::vector<double> load(nw, 0.0);
+  for (int k : order) {
+    const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    jobs[w].push_back(k);
+    load[w] += (double)secs[k].m * secs[k].n * secs[k].n + 1e5;
+  }
+  if (cudaEventRecord(S.svd_in, st) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "SVD event");
+  std::vector<int> bad(nw, 0);
+  auto run = [&](int w) {
+    SvdWorker& wk = S.svd[w];
+    cudaSetDevice(c->device);
+    cudaStreamWaitEvent(wk.s, S.svd_in, 0);
+    cusolverDnSetStream(wk.h, wk.s);
+    for (int k : jobs[w]) {
+      const Sector& sc = secs[k];
+      if (cusolverDnXgesvd(wk.h, wk.p, 'S', 'S', sc.m, sc.n, CUDA_R_64F, X + sc.off, sc.m,
+                           CUDA_R_64F, Sv + sc.offS, CUDA_R_64F, F + sc.offU, sc.m, CUDA_R_64F,
+                           F + sc.offVT, sc.r, CUDA_R_64F, wk.dwork, wk.dbytes, wk.hwork.data(),
+                           wk.hwork.size(), info + k) != CUSOLVER_STATUS_SUCCESS)
+        bad[w] = 1;
+    }
+    cudaEventRecord(wk.ev, wk.s);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nw; ++w)
+    if (!jobs[w].empty()) th.emplace_back(run, w);
+  if (!jobs[0].empty()) run(0);
+  for (auto& t : th) t.join();
+  for (int w = 0; w < nw; ++w) {
+    if (bad[w]) return fail(c, DMRG3S_ERR_CUDA, "gesvd");
+    if (!jobs[w].empty()) cudaStreamWaitEvent(st, S.svd[w].ev, 0);
+  }
+  return cuda_ok(c, cudaGetLastError(), "SVD launch");
+}
 
 dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info* info,
                            cudaStream_t st) {
@@ -286,6 +371,10 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   done(ph);
   ph = phase(kProfSvd);
   // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L)
+  // Sector k of M~ is a rows x cols matrix X (rows: (s, a_l) for L->R, the
+  // expanded left states for R->L).  It is gathered column-major in the tall
+  // orientation m >= n that the FP64 SVD routine needs: X itself when
+  // rows >= cols, X^T otherwise.
   std::vector<Charge> charges;
   for (int k = 0; k < old.nsec(); ++k) charges.push_back(old.q[k]);
   if (expand)
@@ -296,6 +385,13 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   std::vector<Sector> secs;
   std::vector<CopyTask> gather_m, gather_p;
   int64_t xoff = 0;
+  // task placing a row-major block (rb x cb) at (row0, col0) of sector sc's X
+  auto place = [](const Sector& sc, int64_t src_off, int64_t rb, int64_t cb, int64_t row0,
+                  int64_t col0) {
+    if (sc.tall)   // column-major X (ld rows): write X^T rows = block columns
+      return copy_task(src_off, cb, sc.off + col0 * sc.rows + row0, sc.rows, cb, rb, true);
+    return copy_task(src_off, cb, sc.off + row0 * sc.cols + col0, sc.cols, rb, cb, false);
+  };
   for (const Charge& q : charges) {
     Sector sc;
     sc.q = q;
@@ -318,6 +414,10 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     if (other == 0 || exp_dim == 0) continue;
     sc.rows = dir == 1 ? other : exp_dim;
     sc.cols = dir == 1 ? exp_dim : other;
+    sc.tall = sc.rows >= sc.cols;
+    sc.m = sc.tall ? sc.rows : sc.cols;
+    sc.n = sc.tall ? sc.cols : sc.rows;
+    sc.r = sc.n;
     sc.off = xoff;
     xoff += sc.rows * sc.cols;
     for (auto& pr : parts) {
@@ -334,9 +434,9 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
           const bool match = dir == 1 ? bk.c == sc.jbase : bk.c == io;
           if (match) {
             if (dir == 1)
-              gather_m.push_back(copy_task(bk.off, bk.cols, sc.off + o2 * sc.cols, sc.cols, dio, sc.base, false));
+              gather_m.push_back(place(sc, bk.off, dio, sc.base, o2, 0));
             else
-              gather_m.push_back(copy_task(bk.off, bk.cols, sc.off + o2, sc.cols, sc.base, dio, false));
+              gather_m.push_back(place(sc, bk.off, sc.base, dio, 0, o2));
           }
         }
       }
@@ -347,9 +447,9 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
           const bool match = dir == 1 ? bk.c == kp : bk.c == io;
           if (match) {
             if (dir == 1)
-              gather_p.push_back(copy_task(bk.off, bk.cols, sc.off + o2 * sc.cols + sc.base, sc.cols, dio, pwidth, false));
+              gather_p.push_back(place(sc, bk.off, dio, pwidth, o2, sc.base));
             else
-              gather_p.push_back(copy_task(bk.off, bk.cols, sc.off + sc.base * sc.cols + o2, sc.cols, pwidth, dio, false));
+              gather_p.push_back(place(sc, bk.off, pwidth, dio, sc.base, o2));
           }
         }
       }
@@ -362,48 +462,36 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if ((s = run_copies(c, gather_m, m.data, m.lay.size, X, xoff, nullptr, 0, st))) return s;
   if (expand && (s = run_copies(c, gather_p, P, pl.size, X, xoff, nullptr, 0, st))) return s;
   dfree(P, st);
-  // ---- 4. SVD per sector.  X (rows x cols, row-major) is the column-major
-  // matrix X^T (cols x rows); gesvdj(X^T) = U' S V'^T gives X = V' S U'^T.
-  int64_t uoff = 0, voff = 0, soff = 0;
-  int lwork_max = 0;
-  cusolverDnSetStream(S.solver, st);
+  // ---- 4. SVD per sector (FP64, cuSOLVER gesvd on the tall orientation):
+  // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n.  The
+  // sectors are independent and run concurrently on the workers' streams.
+  int64_t foff = 0, soff = 0;
   for (Sector& sc : secs) {
-    sc.r = std::min(sc.rows, sc.cols);
-    sc.offU = uoff;
-    uoff += sc.cols * sc.r;     // U' : cols x r (ld cols)
-    sc.offV = voff;
-    voff += sc.rows * sc.r;     // V' : rows x r (ld rows)
+    sc.offU = foff;
+    foff += sc.m * sc.r;
+    sc.offVT = foff;
+    foff += sc.r * sc.n;
     sc.offS = soff;
     soff += sc.r;
-    int lw = 0;
-    if (cusolverDnDgesvdj_bufferSize(S.solver, CUSOLVER_EIG_MODE_VECTOR, 1, (int)sc.cols,
-                                     (int)sc.rows, nullptr, (int)sc.cols, nullptr, nullptr,
-                                     (int)sc.cols, nullptr, (int)sc.rows, &lw, S.svdj) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return fail(c, DMRG3S_ERR_CUDA, "gesvdj buffer size");
-    lwork_max = std::max(lwork_max, lw);
   }
-  double *U, *V, *Sv, *work;
+  double *F, *Sv;
   int* dinfo;
-  if ((s = dalloc(c, &U, uoff, st)) || (s = dalloc(c, &V, voff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
-      (s = dalloc(c, &work, lwork_max, st)) || (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
+  if ((s = dalloc(c, &F, foff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
+      (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
     return s;
-  for (size_t k = 0; k < secs.size(); ++k) {
-    Sector& sc = secs[k];
-    if (cusolverDnDgesvdj(S.solver, CUSOLVER_EIG_MODE_VECTOR, 1, (int)sc.cols, (int)sc.rows,
-                          X + sc.off, (int)sc.cols, Sv + sc.offS, U + sc.offU, (int)sc.cols,
-                          V + sc.offV, (int)sc.rows, work, lwork_max, dinfo + k, S.svdj) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return fail(c, DMRG3S_ERR_CUDA, "gesvdj");
-  }
+  if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st))) return s;
   std::vector<double> hs(std::max<int64_t>(soff, 1));
+  std::vector<int> hinfo(secs.size() + 1, 0);
   if ((s = cuda_ok(c, cudaMemcpyAsync(hs.data(), Sv, soff * sizeof(double), cudaMemcpyDeviceToHost, st),
                    "singular values")) ||
+      (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
+                                      cudaMemcpyDeviceToHost, st), "SVD info")) ||
       (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
     return s;
   dfree(X, st);
-  dfree(work, st);
   dfree((double*)dinfo, st);
+  for (size_t k = 0; k < secs.size(); ++k)
+    if (hinfo[k] != 0) return fail(c, DMRG3S_ERR_NUMERIC, "SVD did not converge in a sector");
   // global selection: order by (-s, sector, index), cut at eps * s_max and m_max
   std::vector<std::tuple<double, int, int>> cand;
   double smax = 0.0, total = 0.0;
@@ -442,12 +530,25 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   for (size_t k = 0; k < nbnd.dim.size(); ++k) nbnd.off[k + 1] = nbnd.off[k] + nbnd.dim[k];
   nbnd.total = nbnd.off.back();
   if (nbnd.nsym == 0) nbnd.q.assign(1, Charge{});
-  // ---- new centre tensor A~ (L->R) or B~ (R->L), and the remainder SV / US
+  // ---- new centre tensor A~ (L->R) or B~ (R->L), and the remainder SV / US.
+  // With X = U_X S V_X^T: tall sectors have U_X = U, V_X = VT^T; wide ones
+  // (X^T was factorised) have U_X = VT^T, V_X = U.
   SiteLayout nl;
   if (dir == 1)
     make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, m.lay.left, nbnd, &nl);
   else
     make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, nbnd, m.lay.right, &nl);
+  // copy tasks reading U_X[row0 + a, c] (dst a x c) and V_X[col0 + a, c] (dst c x a, or a x c)
+  auto ux = [](const Sector& sc, int64_t row0, int64_t dst, int64_t ldd, int64_t na, int64_t nc,
+               int cs) {   // dst (na x nc): U_X[row0 + a, c] * S[c]
+    if (sc.tall) return copy_task(sc.offU + row0, sc.m, dst, ldd, na, nc, true, -1, cs);
+    return copy_task(sc.offVT + row0 * sc.r, sc.r, dst, ldd, na, nc, false, -1, cs);
+  };
+  auto vxt = [](const Sector& sc, int64_t col0, int64_t dst, int64_t ldd, int64_t nc, int64_t na,
+                int rs) {  // dst (nc x na): V_X[col0 + a, c] * S[c]
+    if (sc.tall) return copy_task(sc.offVT + col0 * sc.r, sc.r, dst, ldd, nc, na, true, rs, -1);
+    return copy_task(sc.offU + col0, sc.m, dst, ldd, nc, na, false, rs, -1);
+  };
   std::vector<CopyTask> cp_new, cp_rem;
   std::vector<int64_t> rem_off(nbnd.nsec(), 0);
   int64_t rem_size = 0;
@@ -465,32 +566,27 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
       const int bi = dir == 1 ? nl.block_of(ss, io) : nl.block_of(ss, kn);
       if (bi >= 0) {
         const Block& bk = nl.blocks[bi];
-        if (dir == 1)   // A~ block (dio x nk): element (a, c) = V'[c * rows + o2 + a]
-          cp_new.push_back(copy_task(sc.offV + o2, sc.rows, bk.off, bk.cols, dio, nk, true));
-        else            // B~ block (nk x dio): element (c, a) = U'[c * cols + o2 + a]
-          cp_new.push_back(copy_task(sc.offU + o2, sc.cols, bk.off, bk.cols, nk, dio, false));
+        if (dir == 1)   // A~ block (dio x nk) = U_X[o2 + a, c]
+          cp_new.push_back(ux(sc, o2, bk.off, bk.cols, dio, nk, -1));
+        else            // B~ block (nk x dio) = V_X[o2 + a, c]^T
+          cp_new.push_back(vxt(sc, o2, bk.off, bk.cols, nk, dio, -1));
       }
       o2 += dio;
     }
     if (sc.base > 0) {
-      if (dir == 1)     // SV (nk x base): S[c] U'[c * cols + col]
-        cp_rem.push_back(copy_task(sc.offU, sc.cols, rem_off[kn], sc.base, nk, sc.base, false,
-                                   (int)sc.offS, -1));
-      else              // US (base x nk): V'[c * rows + row] S[c]
-        cp_rem.push_back(copy_task(sc.offV, sc.rows, rem_off[kn], nk, sc.base, nk, true, -1,
-                                   (int)sc.offS));
+      if (dir == 1)     // SV (nk x base) = S[c] V_X[col, c]^T
+        cp_rem.push_back(vxt(sc, 0, rem_off[kn], sc.base, nk, sc.base, (int)sc.offS));
+      else              // US (base x nk) = U_X[row, c] S[c]
+        cp_rem.push_back(ux(sc, 0, rem_off[kn], nk, sc.base, nk, (int)sc.offS));
     }
   }
   double *ndata, *rem;
   if ((s = dalloc(c, &ndata, nl.size, st)) || (s = dalloc(c, &rem, rem_size, st))) return s;
   cudaMemsetAsync(ndata, 0, (size_t)std::max<int64_t>(nl.size, 1) * sizeof(double), st);
-  if ((s = run_copies(c, cp_new, dir == 1 ? V : U, dir == 1 ? voff : uoff, ndata, nl.size, Sv, soff,
-                      st)) ||
-      (s = run_copies(c, cp_rem, dir == 1 ? U : V, dir == 1 ? uoff : voff, rem, rem_size, Sv, soff,
-                      st)))
+  if ((s = run_copies(c, cp_new, F, foff, ndata, nl.size, Sv, soff, st)) ||
+      (s = run_copies(c, cp_rem, F, foff, rem, rem_size, Sv, soff, st)))
     return s;
-  dfree(U, st);
-  dfree(V, st);
+  dfree(F, st);
   dfree(Sv, st);
   done(ph);
   ph = phase(kProfRemainder);
@@ -649,11 +745,16 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
     cudaMemcpyAsync(S->M[i].data, M[i].data, (size_t)S->M[i].lay.size * sizeof(double),
                     cudaMemcpyDeviceToDevice, st);
   }
-  if (cusolverDnCreate(&S->solver) != CUSOLVER_STATUS_SUCCESS)
-    return fail(c, DMRG3S_ERR_CUDA, "cusolverDnCreate");
-  cusolverDnCreateGesvdjInfo(&S->svdj);
-  cusolverDnXgesvdjSetTolerance(S->svdj, 1e-15);
-  cusolverDnXgesvdjSetMaxSweeps(S->svdj, 100);
+  S->svd.resize(kSvdWorkers);
+  for (SvdWorker& w : S->svd) {
+    if (cusolverDnCreate(&w.h) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnCreateParams(&w.p) != CUSOLVER_STATUS_SUCCESS ||
+        cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, DMRG3S_ERR_CUDA, "SVD worker set-up");
+  }
+  if (cudaEventCreateWithFlags(&S->svd_in, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "SVD event");
   if ((s = boundary_env(*S, left_env, true, st)) || (s = boundary_env(*S, right_env, false, st)))
     return s;
   for (int i = 0; i < centre; ++i)
@@ -674,8 +775,14 @@ dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state) {
   for (auto& m : S->M) cudaFree(m.data);
   for (auto& e : S->Lenv) cudaFree(e.data);
   for (auto& e : S->Renv) cudaFree(e.data);
-  if (S->svdj) cusolverDnDestroyGesvdjInfo(S->svdj);
-  if (S->solver) cusolverDnDestroy(S->solver);
+  for (SvdWorker& w : S->svd) {
+    if (w.dwork) cudaFree(w.dwork);
+    if (w.p) cusolverDnDestroyParams(w.p);
+    if (w.h) cusolverDnDestroy(w.h);
+    if (w.ev) cudaEventDestroy(w.ev);
+    if (w.s) cudaStreamDestroy(w.s);
+  }
+  if (S->svd_in) cudaEventDestroy(S->svd_in);
   delete S;
   return DMRG3S_OK;
 }
