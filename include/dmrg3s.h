@@ -62,10 +62,16 @@ typedef enum dmrg3s_status {
   DMRG3S_ERR_LIMIT = 11         /* request exceeds a fixed static capacity      */
 } dmrg3s_status;
 
+/* Arithmetic of the block products (stages 1 and 3 of the order of Sec. V).
+ * The MPO combination (stage 2), the eigensolver's vector algebra, the SVD and
+ * all data in memory stay FP64 in every mode.  In the tensor-core modes each
+ * FP64 operand element is split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi)
+ * while it is staged in shared memory; 3xTF32 sums hi*hi + hi*lo + lo*hi
+ * (relative error of a block product ~1e-6), TF32 only hi*hi (~1e-3). */
 typedef enum dmrg3s_precision {
-  DMRG3S_FP64 = 0,    /* all contractions in double precision (CUDA cores)          */
-  DMRG3S_TF32X3 = 1,  /* 3xTF32 split products on tcgen05 tensor cores, FP32 accum. */
-  DMRG3S_TF32 = 2     /* single-pass TF32 on tcgen05 tensor cores, FP32 accumulate  */
+  DMRG3S_FP64 = 0,    /* double precision on the CUDA cores                          */
+  DMRG3S_TF32X3 = 1,  /* 3xTF32 split products on tcgen05 tensor cores, FP32 accum.  */
+  DMRG3S_TF32 = 2     /* single-pass TF32 on tcgen05 tensor cores, FP32 accumulate   */
 } dmrg3s_precision;
 
 #define DMRG3S_MAX_NSYM 2
@@ -116,6 +122,12 @@ const char* dmrg3s_status_string(dmrg3s_status status);
 /* Message of the last error a call on `ctx` returned (valid until the next
  * call on ctx; "" when none). */
 const char* dmrg3s_last_error(dmrg3s_ctx ctx);
+
+/* Synchronises `stream` and returns the device-side error latched by the
+ * context's kernels since the last call: DMRG3S_ERR_TIMEOUT when a
+ * tensor-core kernel gave up a bounded wait (its output is then invalid).
+ * The latch is cleared.  Errors: ARG, CUDA, TIMEOUT. */
+dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
 
 /* Kernel timing.  While enabled, the context records CUDA events on the
  * launching stream around every grouped-GEMM launch (kernel 0: the block

@@ -616,6 +616,13 @@ def dmrg3s_profile_read(ctx, kernel):
     return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes}
 
 
+def dmrg3s_sync(ctx, stream=None):
+    """Synchronise and surface a latched device-side error (DMRG3S_ERR_TIMEOUT)."""
+    L = lib()
+    L.dmrg3s_sync.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    _check(L.dmrg3s_sync(ctx.handle, _stream(stream)), "dmrg3s_sync", ctx.handle)
+
+
 def dmrg3s_launch_count():
     L = lib()
     L.dmrg3s_launch_count.argtypes = [i64p]

@@ -63,7 +63,8 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   const Plan& h = dp->host;
   size_t total = bytes_of(h.g1.tiles) + bytes_of(h.g1.tasks) + bytes_of(h.g1.segs) +
                  bytes_of(h.c2.chunks) + bytes_of(h.c2.tasks) + bytes_of(h.c2.terms) +
-                 bytes_of(h.g3.tiles) + bytes_of(h.g3.tasks) + bytes_of(h.g3.segs);
+                 bytes_of(h.g3.tiles) + bytes_of(h.g3.tasks) + bytes_of(h.g3.segs) +
+                 bytes_of(h.g1.tiles_tc) + bytes_of(h.g3.tiles_tc);
   if (total == 0) total = 256;
   if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
   std::vector<char> staging(total, 0);
@@ -78,6 +79,8 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   dp->g3_tiles = place(base, &off, h.g3.tiles, &staging);
   dp->g3_tasks = place(base, &off, h.g3.tasks, &staging);
   dp->g3_segs = place(base, &off, h.g3.segs, &staging);
+  dp->g1_tiles_tc = place(base, &off, h.g1.tiles_tc, &staging);
+  dp->g3_tiles_tc = place(base, &off, h.g3.tiles_tc, &staging);
   if (cudaMemcpy(dp->mem, staging.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
     return DMRG3S_ERR_CUDA;
   *out = std::move(dp);
@@ -86,13 +89,18 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
 
 dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
                        double* ws1, double* c2out, double c2scale, const double* g3A,
-                       const double* g3B, double* g3C, cudaStream_t st) {
+                       const double* g3B, double* g3C, cudaStream_t st, dmrg3s_precision prec) {
   const Plan& h = p.host;
   Profiler& pr = c->prof;
+  const int passes = prec == DMRG3S_TF32X3 ? 3 : prec == DMRG3S_TF32 ? 1 : 0;
   if (!h.g1.tiles.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
-    launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks, p.g1_segs,
-                    g1A, g1B, ws1, st);
+    if (passes)
+      launch_gemm_tc(passes, h.g1.ta, h.g1.tb, p.g1_tiles_tc, (int)h.g1.tiles_tc.size(),
+                     p.g1_tasks, p.g1_segs, g1A, g1B, ws1, c->d_err, st);
+    else
+      launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks,
+                      p.g1_segs, g1A, g1B, ws1, st);
     if (id >= 0) pr.end(id, st);
   }
   if (!h.c2.chunks.empty()) {
@@ -103,8 +111,12 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   }
   if (h.has_g3 && !h.g3.tiles.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
-    launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks, p.g3_segs,
-                    g3A, g3B, g3C, st);
+    if (passes)
+      launch_gemm_tc(passes, h.g3.ta, h.g3.tb, p.g3_tiles_tc, (int)h.g3.tiles_tc.size(),
+                     p.g3_tasks, p.g3_segs, g3A, g3B, g3C, c->d_err, st);
+    else
+      launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks,
+                      p.g3_segs, g3A, g3B, g3C, st);
     if (id >= 0) pr.end(id, st);
   }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
@@ -193,9 +205,7 @@ dmrg3s_status check_ws(Context* c, const Plan& p) {
 }
 
 dmrg3s_status prec_ok(Context* c, dmrg3s_precision prec) {
-  if (prec == DMRG3S_FP64) return DMRG3S_OK;
-  if (prec == DMRG3S_TF32X3 || prec == DMRG3S_TF32)
-    return fail(c, DMRG3S_ERR_UNSUPPORTED, "this entry point runs in FP64 only");
+  if (prec == DMRG3S_FP64 || prec == DMRG3S_TF32X3 || prec == DMRG3S_TF32) return DMRG3S_OK;
   return fail(c, DMRG3S_ERR_ARG, "unknown precision");
 }
 
@@ -226,6 +236,12 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return DMRG3S_ERR_CUDA;
+  }
   if (cudaMallocHost(&c->pinned, 64 * sizeof(double)) != cudaSuccess) {
     cudaFree(c->ws);
     delete c;
@@ -243,6 +259,7 @@ dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
   c->plans.clear();
   if (c->ws) cudaFree(c->ws);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->d_err) cudaFree(c->d_err);
   delete c;
   return DMRG3S_OK;
 }
@@ -268,6 +285,26 @@ const char* dmrg3s_status_string(dmrg3s_status s) {
 const char* dmrg3s_last_error(dmrg3s_ctx ctx) {
   Context* c = reinterpret_cast<Context*>(ctx);
   return c ? c->last_error.c_str() : "no context";
+}
+
+dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c) return DMRG3S_ERR_ARG;
+  dmrg3s_status st = use_device(c);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int flag = 0;
+  if (cudaMemcpyAsync(&c->pinned[0], c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "synchronisation failed");
+  std::memcpy(&flag, &c->pinned[0], sizeof(int));
+  if (flag) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return fail(c, DMRG3S_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+  }
+  return DMRG3S_OK;
 }
 
 dmrg3s_status dmrg3s_profile(dmrg3s_ctx ctx, int32_t enable) {
@@ -411,7 +448,7 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
   st = run_plan(c, *p, L->data, A->data, ws1, ws2, 1.0, ws2, R->data, HA->data,
-                reinterpret_cast<cudaStream_t>(stream));
+                reinterpret_cast<cudaStream_t>(stream), prec);
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }
 
@@ -454,7 +491,7 @@ dmrg3s_status dmrg3s_expand(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
   const double* g1A = dir == 1 ? env->data : M->data;
   const double* g1B = dir == 1 ? M->data : env->data;
   st = run_plan(c, *p, g1A, g1B, ws1, P->data, alpha, nullptr, nullptr, nullptr,
-                reinterpret_cast<cudaStream_t>(stream));
+                reinterpret_cast<cudaStream_t>(stream), prec);
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }
 
@@ -493,7 +530,7 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
   const double* g1A = dir == 1 ? env->data : A->data;
   const double* g1B = dir == 1 ? A->data : env->data;
   st = run_plan(c, *p, g1A, g1B, ws1, ws2, 1.0, A->data, ws2, out->data,
-                reinterpret_cast<cudaStream_t>(stream));
+                reinterpret_cast<cudaStream_t>(stream), prec);
   return st == DMRG3S_OK ? st : fail(c, st, "kernel launch failed");
 }
 

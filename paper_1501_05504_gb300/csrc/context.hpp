@@ -18,12 +18,14 @@ struct DevicePlan {
   Plan host;
   void* mem = nullptr;      // one allocation holding every table
   GemmTile* g1_tiles = nullptr;
+  GemmTile* g1_tiles_tc = nullptr;
   GemmTask* g1_tasks = nullptr;
   GemmSeg* g1_segs = nullptr;
   CombChunk* c2_chunks = nullptr;
   CombTask* c2_tasks = nullptr;
   CombTerm* c2_terms = nullptr;
   GemmTile* g3_tiles = nullptr;
+  GemmTile* g3_tiles_tc = nullptr;
   GemmTask* g3_tasks = nullptr;
   GemmSeg* g3_segs = nullptr;
   ~DevicePlan();
@@ -87,6 +89,7 @@ struct Context {
   char* ws = nullptr;           // workspace arena
   size_t ws_bytes = 0;
   double* pinned = nullptr;     // small pinned host buffer for scalar read-backs (64 doubles)
+  int* d_err = nullptr;         // device error word latched by bounded waits (tensor-core kernel)
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;
   std::string last_error;
 };
@@ -154,14 +157,18 @@ inline dmrg3s_status carve(Context* c, size_t* cursor, size_t bytes, void** out)
 // The workspace from byte offset `cursor` on is used for the Krylov basis.
 dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldata,
                           const double* Rdata, double* x, int64_t n, int kmax, double tol,
-                          size_t cursor, cudaStream_t st, double* theta, int* iters);
+                          size_t cursor, cudaStream_t st, double* theta, int* iters,
+                          dmrg3s_precision prec = DMRG3S_FP64);
 
 // Upload a host plan (allocates the device tables).  Returns CUDA errors.
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 
 // Enqueue the stages of a plan.  Bases as documented for each plan Kind.
+// `prec` selects the grouped-GEMM kernel of stages 1 and 3 (the combination
+// of stage 2 is always FP64).
 dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
                        double* ws1, double* c2out, double c2scale, const double* g3A,
-                       const double* g3B, double* g3C, cudaStream_t st);
+                       const double* g3B, double* g3C, cudaStream_t st,
+                       dmrg3s_precision prec = DMRG3S_FP64);
 
 }  // namespace dmrg3s

@@ -16,7 +16,8 @@ namespace dmrg3s {
 
 dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldata,
                           const double* Rdata, double* x, int64_t n, int kmax, double tol,
-                          size_t cursor, cudaStream_t st, double* theta, int* iters) {
+                          size_t cursor, cudaStream_t st, double* theta, int* iters,
+                          dmrg3s_precision prec) {
   if (kmax < 1 || kmax > 128) return fail(c, DMRG3S_ERR_ARG, "kmax must be in [1, 128]");
   const size_t vbytes = (size_t)n * sizeof(double);
   void *pV, *pw, *ppart, *ph, *palpha, *pbeta, *py, *pn2, *pout;
@@ -53,7 +54,7 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   TridiagOut res{};
   for (;; ++k) {
     double* vk = V + (int64_t)k * n;
-    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st);
+    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st, prec);
     if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
     launch_multidot(V, n, k + 1, w, n, part, h, alpha + k, st);   // alpha_k = <v_k, H v_k>
     launch_multi_axpy(V, n, k + 1, h, w, n, st);
@@ -62,8 +63,15 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
     launch_multidot(w, 0, 1, w, n, part, nrm2, nullptr, st);
     launch_tridiag_smallest(alpha, beta, k + 1, nrm2, y, out, st);
     cudaMemcpyAsync(c->pinned, out, sizeof(TridiagOut), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c->pinned + 8, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos step");
     std::memcpy(&res, c->pinned, sizeof(res));
+    int dev_err = 0;
+    std::memcpy(&dev_err, c->pinned + 8, sizeof(int));
+    if (dev_err) {
+      cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+      return fail(c, DMRG3S_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+    }
     if (res.nan_seen != 0.0) return fail(c, DMRG3S_ERR_NUMERIC, "NaN in the Lanczos recursion");
     const bool conv = res.resid <= tol * std::fmax(1.0, std::fabs(res.theta));
     if (conv || res.beta_last < 1e-14 || k + 1 == kmax) break;
@@ -90,9 +98,8 @@ extern "C" dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L,
                                            dmrg3s_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !L || !W || !R || !M || !lambda) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
-  if (prec != DMRG3S_FP64)
-    return fail(c, prec == DMRG3S_TF32X3 || prec == DMRG3S_TF32 ? DMRG3S_ERR_UNSUPPORTED : DMRG3S_ERR_ARG,
-                "eigensolver precision");
+  if (prec != DMRG3S_FP64 && prec != DMRG3S_TF32X3 && prec != DMRG3S_TF32)
+    return fail(c, DMRG3S_ERR_ARG, "eigensolver precision");
   std::string err;
   EnvLayout le, re;
   MpoLayout w;
@@ -113,7 +120,7 @@ extern "C" dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L,
   int it = 0;
   double theta = 0.0;
   st = lanczos_run(c, *p, L->data, R->data, M->data, a.size, kmax, tol, cursor,
-                   reinterpret_cast<cudaStream_t>(stream), &theta, &it);
+                   reinterpret_cast<cudaStream_t>(stream), &theta, &it, prec);
   if (st != DMRG3S_OK) return st;
   *lambda = theta;
   if (iters) *iters = it;

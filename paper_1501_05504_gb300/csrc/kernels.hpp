@@ -58,6 +58,12 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
                      cudaStream_t st);
 
 // out = scale * sum_k coef_k in_k for every task.
+// Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32); err is a
+// device flag set to 1 when a bounded wait timed out.
+void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
+                    const GemmTask* tasks, const GemmSeg* segs, const double* A, const double* B,
+                    double* C, int* err, cudaStream_t st);
+
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
                         const CombTerm* terms, const double* in, double* out, double scale,
                         cudaStream_t st);

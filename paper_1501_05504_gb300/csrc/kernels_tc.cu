@@ -1,0 +1,303 @@
+// Tensor-core grouped GEMM for sm_103a (tcgen05, TMEM accumulators).
+//
+// Same task tables as the FP64 kernel (one output block per task, K-segments
+// summed), computed on the 5th-generation tensor cores in TF32 with FP32
+// accumulation.  Operands stay FP64 in memory; the load stage splits every
+// element into x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (Ootomo and
+// Yokota's split, 2022) while writing the K-major canonical shared-memory
+// layout, so no separate conversion pass is needed:
+//   kPasses = 1: C = A_hi B_hi                                  (TF32)
+//   kPasses = 3: C = A_hi B_hi + A_hi B_lo + A_lo B_hi          (3xTF32)
+//
+// CTA tile 128 x 64 (M x N), K chunks of 32, two shared-memory stages.  All
+// 128 threads load and convert; one elected thread issues tcgen05.mma and
+// commits each stage to an mbarrier; the accumulator (64 FP32 columns) lives
+// in tensor memory and is read back with tcgen05.ld by the four warps.  Every
+// wait on an mbarrier is bounded: on time-out the CTA records an error code,
+// frees its tensor memory and returns.
+#include <cstdint>
+
+#include "kernels.hpp"
+
+namespace dmrg3s {
+
+namespace {
+
+constexpr int TBM = 128, TBN = 64, TBK = 32, TNT = 128;
+constexpr int kStageA = TBM * TBK * 4;            // bytes of one A tile (hi or lo)
+constexpr int kStageB = TBN * TBK * 4;            // bytes of one B tile
+constexpr uint32_t kTmemCols = 64;
+constexpr long long kSpinLimit = 1ll << 28;       // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row, k) in the K-major, non-swizzled canonical
+// layout: core matrices of 8 rows x 16 bytes; K-adjacent core matrices 128 B
+// apart (leading byte offset), 8-row groups 1024 B apart (stride byte offset).
+__device__ __forceinline__ uint32_t canon_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = 1024;
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split(double x, float& hi, float& lo) {
+  hi = to_tf32((float)x);
+  lo = to_tf32((float)(x - (double)hi));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+template <Trans TA, Trans TB, int kPasses>
+__global__ void __launch_bounds__(TNT, 1)
+    gemm_tc_kernel(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
+                   const GemmSeg* __restrict__ segs, const double* __restrict__ A,
+                   const double* __restrict__ B, double* __restrict__ C, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int kLo = kPasses == 3 ? 1 : 0;
+  constexpr int kStage = (kStageA + kStageB) * (1 + kLo);
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const GemmTile tile = tiles[blockIdx.x];
+  const GemmTask task = tasks[tile.task];
+  const int m0 = tile.tm * TBM, n0 = tile.tn * TBN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t dtmem = tmem_base;
+  constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
+  bool ok = true;
+  int it = 0;
+
+  for (int sgi = 0; sgi < task.nseg && ok; ++sgi) {
+    const GemmSeg sg = segs[task.seg0 + sgi];
+    const double* Ap = A + sg.offA;
+    const double* Bp = B + sg.offB;
+    for (int k0 = 0; k0 < sg.K && ok; k0 += TBK, ++it) {
+      const int st = it & 1;
+      if (it >= 2) ok = mbar_wait(&bars[st], (uint32_t)(((it - 2) >> 1) & 1));
+      if (!ok) break;
+      unsigned char* base = smem + st * kStage;
+      unsigned char* a_hi = base;
+      unsigned char* a_lo = base + kStageA;
+      unsigned char* b_hi = base + kStageA * (1 + kLo);
+      unsigned char* b_lo = b_hi + kStageB;
+      // ---- load + split A (rows m0.., k0..)
+      if (TA == Trans::N) {
+        const int k = lane;
+        for (int r = warp; r < TBM; r += 4) {
+          const int gm = m0 + r, gk = k0 + k;
+          const double v = (gm < task.M && gk < sg.K) ? Ap[(int64_t)gm * sg.lda + gk] : 0.0;
+          float hi, lo;
+          split(v, hi, lo);
+          const uint32_t o = canon_off(r, k);
+          *reinterpret_cast<float*>(a_hi + o) = hi;
+          if (kLo) *reinterpret_cast<float*>(a_lo + o) = lo;
+        }
+      } else {
+        const int r = tid;
+        for (int k = 0; k < TBK; ++k) {
+          const int gm = m0 + r, gk = k0 + k;
+          const double v = (gm < task.M && gk < sg.K) ? Ap[(int64_t)gk * sg.lda + gm] : 0.0;
+          float hi, lo;
+          split(v, hi, lo);
+          const uint32_t o = canon_off(r, k);
+          *reinterpret_cast<float*>(a_hi + o) = hi;
+          if (kLo) *reinterpret_cast<float*>(a_lo + o) = lo;
+        }
+      }
+      // ---- load + split B as an N x K (K-major) tile
+      if (TB == Trans::T) {
+        const int k = lane;
+        for (int r = warp; r < TBN; r += 4) {
+          const int gn = n0 + r, gk = k0 + k;
+          const double v = (gn < task.N && gk < sg.K) ? Bp[(int64_t)gn * sg.ldb + gk] : 0.0;
+          float hi, lo;
+          split(v, hi, lo);
+          const uint32_t o = canon_off(r, k);
+          *reinterpret_cast<float*>(b_hi + o) = hi;
+          if (kLo) *reinterpret_cast<float*>(b_lo + o) = lo;
+        }
+      } else {
+        const int r = tid & (TBN - 1);
+        for (int k = tid >> 6; k < TBK; k += 2) {
+          const int gn = n0 + r, gk = k0 + k;
+          const double v = (gn < task.N && gk < sg.K) ? Bp[(int64_t)gk * sg.ldb + gn] : 0.0;
+          float hi, lo;
+          split(v, hi, lo);
+          const uint32_t o = canon_off(r, k);
+          *reinterpret_cast<float*>(b_hi + o) = hi;
+          if (kLo) *reinterpret_cast<float*>(b_lo + o) = lo;
+        }
+      }
+      // make the generic-proxy stores visible to the tensor core (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+        const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+        for (int kk = 0; kk < TBK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
+          const uint32_t off = kk * 256;             // two core matrices along K
+          const uint32_t acc = (it == 0 && kk == 0) ? 0u : 1u;
+          if (kLo) {
+            mma_tf32(dtmem, smem_desc(al + off), smem_desc(bh + off), idesc, acc);
+            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+          } else {
+            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
+          }
+        }
+        mma_commit(&bars[st]);
+      }
+      __syncthreads();
+    }
+  }
+  // wait for the last commit (it covers every earlier MMA)
+  if (ok && it > 0) ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    // ---- epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w + 31
+    const int row = warp * 32 + lane;
+    const int gm = m0 + row;
+#pragma unroll
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      uint32_t v[16];
+      if (it > 0) {
+        const uint32_t taddr = dtmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+      }
+      if (gm < task.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int gn = n0 + c0 + j;
+          if (gn < task.N) C[task.offC + (int64_t)gm * task.ldc + gn] = (double)__uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+template <Trans TA, Trans TB, int P>
+void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const GemmSeg* segs,
+                const double* A, const double* B, double* C, int* err, cudaStream_t st) {
+  constexpr int kLo = P == 3 ? 1 : 0;
+  constexpr int smem = 2 * (kStageA + kStageB) * (1 + kLo);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gemm_tc_kernel<TA, TB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    attr = true;
+  }
+  gemm_tc_kernel<TA, TB, P><<<ntiles, TNT, smem, st>>>(tiles, tasks, segs, A, B, C, err);
+}
+
+}  // namespace
+
+void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
+                    const GemmTask* tasks, const GemmSeg* segs, const double* A, const double* B,
+                    double* C, int* err, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  count_launch();
+#define DMRG3S_TC(TA_, TB_)                                                           \
+  if (ta == Trans::TA_ && tb == Trans::TB_) {                                         \
+    if (passes == 3)                                                                  \
+      launch_one<Trans::TA_, Trans::TB_, 3>(tiles, ntiles, tasks, segs, A, B, C, err, st); \
+    else                                                                              \
+      launch_one<Trans::TA_, Trans::TB_, 1>(tiles, ntiles, tasks, segs, A, B, C, err, st); \
+    return;                                                                           \
+  }
+  DMRG3S_TC(N, N)
+  DMRG3S_TC(N, T)
+  DMRG3S_TC(T, N)
+  DMRG3S_TC(T, T)
+#undef DMRG3S_TC
+}
+
+}  // namespace dmrg3s

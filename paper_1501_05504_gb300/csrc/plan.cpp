@@ -27,6 +27,9 @@ void GemmStage::add(int64_t offC, int ldc, int M, int N, const std::vector<GemmS
   const int ntm = (M + 63) / 64, ntn = (N + 63) / 64;
   for (int a = 0; a < ntm; ++a)
     for (int b = 0; b < ntn; ++b) tiles.push_back(GemmTile{id, a, b, 0});
+  const int ntm_tc = (M + 127) / 128;
+  for (int a = 0; a < ntm_tc; ++a)
+    for (int b = 0; b < ntn; ++b) tiles_tc.push_back(GemmTile{id, a, b, 0});
 }
 
 void GemmStage::finalize_bytes(Trans, Trans) {

@@ -35,7 +35,8 @@ struct GemmStage {
   Trans ta = Trans::N, tb = Trans::N;
   std::vector<GemmTask> tasks;
   std::vector<GemmSeg> segs;
-  std::vector<GemmTile> tiles;
+  std::vector<GemmTile> tiles;      // 64 x 64 tiles (FP64 kernel)
+  std::vector<GemmTile> tiles_tc;   // 128 x 64 tiles (tensor-core kernel)
   double flops = 0.0;
   double bytes = 0.0;     // algorithmic: distinct operand blocks read once + output written once
   void add(int64_t offC, int ldc, int M, int N, const std::vector<GemmSeg>& s);

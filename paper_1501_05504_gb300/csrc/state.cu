@@ -220,6 +220,7 @@ struct Opts {
   double tol = 1e-10;
   double eps = 1e-12;
   bool optimise = true;
+  dmrg3s_precision prec = DMRG3S_FP64;   // arithmetic of the eigensolver's H_eff products
 };
 
 struct Info {
@@ -334,7 +335,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     double lam = 0.0;
     int it = 0;
     if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, m.data, m.lay.size, o.kmax, o.tol,
-                         cursor, st, &lam, &it)))
+                         cursor, st, &lam, &it, o.prec)))
       return s;
     info->lambda = lam;
     info->iters = it;
@@ -794,8 +795,9 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   if (!S || !opts || !info) return DMRG3S_ERR_ARG;
   Context* c = S->c;
   if (dir != 1 && dir != -1) return fail(c, DMRG3S_ERR_ARG, "dir must be +1 or -1");
-  if (opts->precision != DMRG3S_FP64)
-    return fail(c, DMRG3S_ERR_UNSUPPORTED, "local update precision");
+  if (opts->precision != DMRG3S_FP64 && opts->precision != DMRG3S_TF32X3 &&
+      opts->precision != DMRG3S_TF32)
+    return fail(c, DMRG3S_ERR_ARG, "local update precision");
   if (opts->m_max < 1) return fail(c, DMRG3S_ERR_ARG, "m_max must be >= 1");
   dmrg3s_status s;
   if ((s = use_device(c))) return s;
@@ -805,6 +807,7 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   o.tol = opts->lanczos_tol > 0 ? opts->lanczos_tol : 1e-10;
   o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-12;
   o.optimise = opts->skip_eigensolver == 0;
+  o.prec = opts->precision;
   Info inf;
   s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));
   if (s != DMRG3S_OK) return s;

@@ -1,0 +1,127 @@
+"""GPU parity of the tcgen05 tensor-core path (TF32 and 3xTF32) against the FP64 oracle.
+
+The operands stay FP64 in memory and are split into TF32 pairs in shared
+memory; 3xTF32 keeps the relative Frobenius error of an H_eff application at
+the 1e-6 level (the tolerance stated for the mixed-precision H_eff), single
+TF32 at 1e-3.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import bench  # noqa: E402
+import seeded_inputs as si  # noqa: E402
+from oracle import contract, dmrg3s as odm, io  # noqa: E402
+from parity import (TF32X3_TOL, env_to_dense, fused_permutation, problem, rel_err,  # noqa: E402
+                    site_to_dense)
+
+TF32_TOL = 2e-3
+CASES = [("dense", 31, {}), ("u1", 32, {}), ("u1u1", 33, {}), ("u1", 34, {"m_left": 9, "m_right": 7}),
+         ("xxz_l100_m512_u1", 1002, {})]
+
+
+@pytest.fixture(scope="module")
+def b():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_05504_gb300 import binding
+    binding.slib()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(b):
+    c = b.dmrg3s_create(0, 1 << 30)
+    yield c
+    c.close()
+
+
+def _gpu(b, pb):
+    return (b.env_from_neutral(pb["L"]), b.mpo_from_neutral(pb["W"]), b.env_from_neutral(pb["R"]),
+            b.site_from_neutral(pb["A"]))
+
+
+def _dense(pb):
+    return (io.env_dense(pb["L"]), pb["W"]["W"], io.env_dense(pb["R"]), io.site_dense(pb["A"])[0])
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32x3", TF32X3_TOL), ("tf32", TF32_TOL)])
+@pytest.mark.parametrize("kind,seed,kw", CASES)
+def test_apply_heff_tensor_core(b, ctx, kind, seed, kw, prec, tol):
+    pb = problem(kind, seed, **kw)
+    gL, gW, gR, gA = _gpu(b, pb)
+    gH = b.empty_site_like(gA.qp, gA.left, gA.right)
+    b.dmrg3s_apply_heff(ctx, gL, gW, gR, gA, gH, prec)
+    b.dmrg3s_sync(ctx)
+    L, W, R, A = _dense(pb)
+    assert rel_err(site_to_dense(b, gH), contract.apply_heff(L, W, R, A)) < tol
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+@pytest.mark.parametrize("kind,seed,kw", CASES[:3])
+def test_expand_and_env_tf32x3(b, ctx, kind, seed, kw, direction):
+    pb = problem(kind, seed, **kw)
+    gL, gW, gR, gA = _gpu(b, pb)
+    L, W, R, A = _dense(pb)
+    if direction == 1:
+        fused = b.expanded_bond(gA.right, pb["t"], False)
+        gP = b.empty_site_like(gA.qp, gA.left, fused)
+        b.dmrg3s_expand(ctx, 1, gL, gW, gA, 0.5, gP, "tf32x3")
+        refP = contract.expansion_term_lr(L, W, A, 0.5)[:, :, fused_permutation(
+            pb["right"], pb["t"], fused.q.astype(np.int64))]
+        gO = b.empty_env(gW.tr, gA.right)
+        b.dmrg3s_update_env(ctx, 1, gL, gW, gA, gO, "tf32x3")
+        refO = contract.left_env(L, W, A)
+    else:
+        fused = b.expanded_bond(gA.left, pb["t"], False)
+        gP = b.empty_site_like(gA.qp, fused, gA.right)
+        b.dmrg3s_expand(ctx, -1, gR, gW, gA, 0.5, gP, "tf32x3")
+        refP = contract.expansion_term_rl(R, W, A, 0.5)[:, fused_permutation(
+            pb["left"], pb["t"], fused.q.astype(np.int64)), :]
+        gO = b.empty_env(gW.tl, gA.left)
+        b.dmrg3s_update_env(ctx, -1, gR, gW, gA, gO, "tf32x3")
+        refO = contract.right_env(R, W, A)
+    b.dmrg3s_sync(ctx)
+    assert rel_err(site_to_dense(b, gP), refP) < TF32X3_TOL
+    assert rel_err(env_to_dense(b, gO), refO) < TF32X3_TOL
+
+
+def test_eigensolve_tf32x3(b, ctx):
+    rng = si.rng_for(41)
+    left = si.gaussian_bond(60, (1,), (2.5,), (2,), (4,))
+    right = si.gaussian_bond(64, (0,), (2.5,), (2,), (4,))
+    Le = si.symmetric_env(rng, si.XXZ_T, left, identity_channels=(4,))
+    Re = si.symmetric_env(rng, si.XXZ_T, right, identity_channels=(0,))
+    W = si.symmetric_mpo_site(rng, si.XXZ_QP, si.XXZ_T, si.XXZ_T)
+    M = si.random_site(rng, si.XXZ_QP, left, right)
+    gM = b.site_from_neutral(M)
+    lam, it = b.dmrg3s_eigensolve(ctx, b.env_from_neutral(Le), b.mpo_from_neutral(W),
+                                  b.env_from_neutral(Re), gM, kmax=80, tol=1e-6, prec="tf32x3")
+    b.dmrg3s_sync(ctx)
+    Ld, Rd, Md = io.env_dense(Le), io.env_dense(Re), io.site_dense(M)[0]
+    lam_o, x_o, _ = odm.lanczos_ground(lambda v: contract.apply_heff(Ld, W["W"], Rd, v), Md,
+                                       kmax=80, tol=1e-12)
+    assert abs(lam - lam_o) < 1e-6 * abs(lam_o)
+    assert abs(abs(np.vdot(site_to_dense(b, gM), x_o)) - 1.0) < 1e-4
+
+
+def test_profiler_flops_match_the_benchmark_count(b, ctx):
+    """The algorithmic flop count of bench.py equals the library's own count."""
+    spec = bench.window_specs(1002)
+    W = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0)).site(50)
+    b0, b1, _ = spec["bonds"]
+    rng = si.rng_for(5)
+    Le = si.symmetric_env(rng, si.XXZ_T, b0)
+    Re = si.symmetric_env(rng, si.XXZ_T, b1)
+    gL, gR, gA = b.env_from_neutral(Le), b.env_from_neutral(Re), b.site_from_neutral(spec["M"][0])
+    gH = b.empty_site_like(gA.qp, gA.left, gA.right)
+    b.dmrg3s_profile(ctx, True)
+    b.dmrg3s_apply_heff(ctx, gL, W, gR, gA, gH, "tf32x3")
+    g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
+    c = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
+    b.dmrg3s_profile(ctx, False)
+    want = bench.heff_flops(si.XXZ_QP, si.XXZ_T, W.W, b0, b1)
+    assert abs(g["flops"] + c["flops"] - want) <= 1e-9 * want
+    assert g["launches"] == 2 and c["launches"] == 1
