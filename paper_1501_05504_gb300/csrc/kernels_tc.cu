@@ -9,12 +9,13 @@
 //   kPasses = 1: C = A_hi B_hi                                  (TF32)
 //   kPasses = 3: C = A_hi B_hi + A_hi B_lo + A_lo B_hi          (3xTF32)
 //
-// CTA tile 128 x 64 (M x N), K chunks of 32, two shared-memory stages.  All
-// 128 threads load and convert; one elected thread issues tcgen05.mma and
-// commits each stage to an mbarrier; the accumulator (64 FP32 columns) lives
-// in tensor memory and is read back with tcgen05.ld by the four warps.  Every
-// wait on an mbarrier is bounded: on time-out the CTA records an error code,
-// frees its tensor memory and returns.
+// CTA tile 128 x 64 (M x N), K chunks of 32, two shared-memory stages and two
+// TMEM accumulator buffers.  All 128 threads load and convert; one thread
+// issues tcgen05.mma and commits each stage to an mbarrier; while the tensor
+// core works on chunk k the four warps drain chunk k-1's FP32 accumulator
+// (tcgen05.ld) into FP64 registers.  Every wait on an mbarrier is bounded: on
+// time-out the CTA records an error code, frees its tensor memory and
+// returns.
 #include <cstdint>
 
 #include "kernels.hpp"
@@ -26,19 +27,18 @@ namespace {
 constexpr int TBM = 128, TBN = 64, TBK = 32, TNT = 128;
 constexpr int kStageA = TBM * TBK * 4;            // bytes of one A tile (hi or lo)
 constexpr int kStageB = TBN * TBK * 4;            // bytes of one B tile
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 2 * TBN;          // two FP32 accumulator buffers
 constexpr long long kSpinLimit = 1ll << 28;       // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Byte offset of element (row, k) in the K-major, non-swizzled canonical
-// layout: core matrices of 8 rows x 16 bytes; K-adjacent core matrices 128 B
-// apart (leading byte offset), 8-row groups 1024 B apart (stride byte offset).
-__device__ __forceinline__ uint32_t canon_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
+// Operand tiles use the K-major, non-swizzled canonical layout: core matrices
+// of 8 rows x 16 bytes; element (row, k) at byte (row / 8) * 1024 +
+// (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4, i.e. K-adjacent core matrices
+// 128 B apart (leading byte offset) and 8-row groups 1024 B apart (stride
+// byte offset).
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading and
 // stride byte offsets (all >> 4), descriptor version 1, no swizzle.
@@ -101,14 +101,75 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// Load one operand tile (ROWS x 32, K-major canonical layout) from FP64
+// global memory, split into TF32 hi / lo.  kContig: the source is contiguous
+// along K (element (row, k) at src[row * ld + k]); otherwise along the row
+// index (src[k * ld + row]).  Lanes cover one 8 x 4 core matrix per step (a
+// 128-byte contiguous shared store), with the fast lane index along the
+// source's contiguous direction.
+template <int ROWS, bool kContig, bool kLo>
+__device__ __forceinline__ void load_tile(const double* __restrict__ src, int ld, int row0,
+                                          int nrow, int k0, int nk, unsigned char* hi,
+                                          unsigned char* lo, int warp, int lane) {
+  const int r8 = kContig ? (lane >> 2) : (lane & 7);
+  const int k4 = kContig ? (lane & 3) : (lane >> 3);
+#pragma unroll
+  for (int g = warp; g < ROWS / 8; g += 4) {
+    const int row = g * 8 + r8;
+    const bool rok = row0 + row < nrow;
+    double v[8];
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+      const int k = k0 + kc * 4 + k4;
+      v[kc] = (rok && k < nk)
+                  ? (kContig ? src[(int64_t)(row0 + row) * ld + k] : src[(int64_t)k * ld + row0 + row])
+                  : 0.0;
+    }
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+      float h, l;
+      split(v[kc], h, l);
+      const uint32_t o = (uint32_t)(g * 1024 + kc * 128 + r8 * 16 + k4 * 4);
+      *reinterpret_cast<float*>(hi + o) = h;
+      if (kLo) *reinterpret_cast<float*>(lo + o) = l;
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// Add the FP32 accumulator of one K chunk (TMEM columns col0 .. col0 + 63 of
+// this warp's lanes) into the thread's FP64 accumulators.
+__device__ __forceinline__ void drain(uint32_t dtmem, int warp, uint32_t col0, double (&acc)[TBN]) {
+#pragma unroll
+  for (int c0 = 0; c0 < TBN; c0 += 16) {
+    uint32_t v[16];
+    tmem_ld16(dtmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)c0, v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[c0 + j] += (double)__uint_as_float(v[j]);
+  }
+}
+
+// Every 32-wide K chunk is accumulated by the tensor core into its own FP32
+// TMEM buffer (two buffers, alternating) and then added into FP64 registers,
+// so FP32 rounding only ever sees 32-term sums.
 template <Trans TA, Trans TB, int kPasses>
-__global__ void __launch_bounds__(TNT, 1)
+__global__ void __launch_bounds__(TNT, 2)
     gemm_tc_kernel(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                    const GemmSeg* __restrict__ segs, const double* __restrict__ A,
                    const double* __restrict__ B, double* __restrict__ C, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int kLo = kPasses == 3 ? 1 : 0;
-  constexpr int kStage = (kStageA + kStageB) * (1 + kLo);
+  constexpr bool kLo = kPasses == 3;
+  constexpr int kStage = (kStageA + kStageB) * (kLo ? 2 : 1);
   __shared__ uint64_t bars[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -133,6 +194,9 @@ __global__ void __launch_bounds__(TNT, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t dtmem = tmem_base;
   constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
+  double acc[TBN];
+#pragma unroll
+  for (int j = 0; j < TBN; ++j) acc[j] = 0.0;
   bool ok = true;
   int it = 0;
 
@@ -142,118 +206,67 @@ __global__ void __launch_bounds__(TNT, 1)
     const double* Bp = B + sg.offB;
     for (int k0 = 0; k0 < sg.K && ok; k0 += TBK, ++it) {
       const int st = it & 1;
+      // stage st and TMEM buffer st were last used by chunk it - 2
       if (it >= 2) ok = mbar_wait(&bars[st], (uint32_t)(((it - 2) >> 1) & 1));
       if (!ok) break;
       unsigned char* base = smem + st * kStage;
       unsigned char* a_hi = base;
       unsigned char* a_lo = base + kStageA;
-      unsigned char* b_hi = base + kStageA * (1 + kLo);
+      unsigned char* b_hi = base + kStageA * (kLo ? 2 : 1);
       unsigned char* b_lo = b_hi + kStageB;
-      // ---- load + split A (rows m0.., k0..)
-      if (TA == Trans::N) {
-        const int k = lane;
-        for (int r = warp; r < TBM; r += 4) {
-          const int gm = m0 + r, gk = k0 + k;
-          const double v = (gm < task.M && gk < sg.K) ? Ap[(int64_t)gm * sg.lda + gk] : 0.0;
-          float hi, lo;
-          split(v, hi, lo);
-          const uint32_t o = canon_off(r, k);
-          *reinterpret_cast<float*>(a_hi + o) = hi;
-          if (kLo) *reinterpret_cast<float*>(a_lo + o) = lo;
-        }
-      } else {
-        const int r = tid;
-        for (int k = 0; k < TBK; ++k) {
-          const int gm = m0 + r, gk = k0 + k;
-          const double v = (gm < task.M && gk < sg.K) ? Ap[(int64_t)gk * sg.lda + gm] : 0.0;
-          float hi, lo;
-          split(v, hi, lo);
-          const uint32_t o = canon_off(r, k);
-          *reinterpret_cast<float*>(a_hi + o) = hi;
-          if (kLo) *reinterpret_cast<float*>(a_lo + o) = lo;
-        }
-      }
-      // ---- load + split B as an N x K (K-major) tile
-      if (TB == Trans::T) {
-        const int k = lane;
-        for (int r = warp; r < TBN; r += 4) {
-          const int gn = n0 + r, gk = k0 + k;
-          const double v = (gn < task.N && gk < sg.K) ? Bp[(int64_t)gn * sg.ldb + gk] : 0.0;
-          float hi, lo;
-          split(v, hi, lo);
-          const uint32_t o = canon_off(r, k);
-          *reinterpret_cast<float*>(b_hi + o) = hi;
-          if (kLo) *reinterpret_cast<float*>(b_lo + o) = lo;
-        }
-      } else {
-        const int r = tid & (TBN - 1);
-        for (int k = tid >> 6; k < TBK; k += 2) {
-          const int gn = n0 + r, gk = k0 + k;
-          const double v = (gn < task.N && gk < sg.K) ? Bp[(int64_t)gk * sg.ldb + gn] : 0.0;
-          float hi, lo;
-          split(v, hi, lo);
-          const uint32_t o = canon_off(r, k);
-          *reinterpret_cast<float*>(b_hi + o) = hi;
-          if (kLo) *reinterpret_cast<float*>(b_lo + o) = lo;
-        }
-      }
+      load_tile<TBM, TA == Trans::N, kLo>(Ap, sg.lda, m0, task.M, k0, sg.K, a_hi, a_lo, warp, lane);
+      load_tile<TBN, TB == Trans::T, kLo>(Bp, sg.ldb, n0, task.N, k0, sg.K, b_hi, b_lo, warp, lane);
       // make the generic-proxy stores visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
         const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        const uint32_t d = dtmem + (uint32_t)(st * TBN);
 #pragma unroll
         for (int kk = 0; kk < TBK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
           const uint32_t off = kk * 256;             // two core matrices along K
-          const uint32_t acc = (it == 0 && kk == 0) ? 0u : 1u;
           if (kLo) {
-            mma_tf32(dtmem, smem_desc(al + off), smem_desc(bh + off), idesc, acc);
-            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+            mma_tf32(d, smem_desc(al + off), smem_desc(bh + off), idesc, kk == 0 ? 0u : 1u);
+            mma_tf32(d, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+            mma_tf32(d, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
           } else {
-            mma_tf32(dtmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
+            mma_tf32(d, smem_desc(ah + off), smem_desc(bh + off), idesc, kk == 0 ? 0u : 1u);
           }
         }
         mma_commit(&bars[st]);
       }
-      __syncthreads();
+      // meanwhile drain the previous chunk's accumulator into FP64
+      if (it >= 1) {
+        ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), acc);
+        }
+      }
     }
   }
-  // wait for the last commit (it covers every earlier MMA)
-  if (ok && it > 0) ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // the last chunk
+  if (ok && it > 0) {
+    ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), acc);
+    }
+  }
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
   } else {
-    // ---- epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w + 31
-    const int row = warp * 32 + lane;
-    const int gm = m0 + row;
+    // ---- epilogue: thread (warp, lane) owns accumulator row 32 warp + lane
+    const int gm = m0 + warp * 32 + lane;
+    if (gm < task.M) {
+      double* crow = C + task.offC + (int64_t)gm * task.ldc + n0;
+      const int nv = task.N - n0 < TBN ? task.N - n0 : TBN;
 #pragma unroll
-    for (int c0 = 0; c0 < TBN; c0 += 16) {
-      uint32_t v[16];
-      if (it > 0) {
-        const uint32_t taddr = dtmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-            "%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0u;
-      }
-      if (gm < task.M) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int gn = n0 + c0 + j;
-          if (gn < task.N) C[task.offC + (int64_t)gm * task.ldc + gn] = (double)__uint_as_float(v[j]);
-        }
-      }
+      for (int j = 0; j < TBN; ++j)
+        if (j < nv) crow[j] = acc[j];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
