@@ -89,34 +89,93 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
 
 dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
                        double* ws1, double* c2out, double c2scale, const double* g3A,
-                       const double* g3B, double* g3C, cudaStream_t st, dmrg3s_precision prec) {
+                       const double* g3B, double* g3C, cudaStream_t st, dmrg3s_precision prec,
+                       const SplitHints* hints) {
   const Plan& h = p.host;
   Profiler& pr = c->prof;
   const int passes = prec == DMRG3S_TF32X3 ? 3 : prec == DMRG3S_TF32 ? 1 : 0;
-  if (!h.g1.tiles.empty()) {
-    const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
-    if (passes)
-      launch_gemm_tc(passes, h.g1.ta, h.g1.tb, p.g1_tiles_tc, (int)h.g1.tiles_tc.size(),
-                     p.g1_tasks, p.g1_segs, g1A, g1B, ws1, c->d_err, st);
-    else
+  if (!passes) {
+    if (!h.g1.tiles.empty()) {
+      const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
       launch_gemm_f64(h.g1.ta, h.g1.tb, p.g1_tiles, (int)h.g1.tiles.size(), p.g1_tasks,
                       p.g1_segs, g1A, g1B, ws1, st);
-    if (id >= 0) pr.end(id, st);
-  }
-  if (!h.c2.chunks.empty()) {
-    const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
-    launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1, c2out,
-                       c2scale, st);
-    if (id >= 0) pr.end(id, st);
-  }
-  if (h.has_g3 && !h.g3.tiles.empty()) {
-    const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
-    if (passes)
-      launch_gemm_tc(passes, h.g3.ta, h.g3.tb, p.g3_tiles_tc, (int)h.g3.tiles_tc.size(),
-                     p.g3_tasks, p.g3_segs, g3A, g3B, g3C, c->d_err, st);
-    else
+      if (id >= 0) pr.end(id, st);
+    }
+    if (!h.c2.chunks.empty()) {
+      const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
+      launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1,
+                         c2out, c2scale, st);
+      if (id >= 0) pr.end(id, st);
+    }
+    if (h.has_g3 && !h.g3.tiles.empty()) {
+      const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
       launch_gemm_f64(h.g3.ta, h.g3.tb, p.g3_tiles, (int)h.g3.tiles.size(), p.g3_tasks,
                       p.g3_segs, g3A, g3B, g3C, st);
+      if (id >= 0) pr.end(id, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
+  }
+  // ---- tensor-core mode: split the operands into FP32 (hi, lo) pairs
+  const TcSlots sl = tc_slots(h);
+  double* base = reinterpret_cast<double*>(c->ws);
+  auto hi = [&](int64_t slot) { return reinterpret_cast<float*>(base + slot); };
+  auto lo = [&](int64_t slot, int64_t n) {
+    return passes == 3 ? reinterpret_cast<float*>(base + slot) + n : nullptr;
+  };
+  const SplitHints none;
+  const SplitHints& hn = hints ? *hints : none;
+  if (!hn.g1A) launch_split(g1A, hi(sl.a1), lo(sl.a1, h.nA1), h.nA1, st);
+  if (!hn.g1B) launch_split(g1B, hi(sl.b1), lo(sl.b1, h.nB1), h.nB1, st);
+  if (!h.g1.tiles.empty()) {
+    const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
+    launch_gemm_tc(passes, h.g1.ta, h.g1.tb, p.g1_tiles_tc, (int)h.g1.tiles_tc.size(), p.g1_tasks,
+                   p.g1_segs, hi(sl.a1), lo(sl.a1, h.nA1), hi(sl.b1), lo(sl.b1, h.nB1), ws1,
+                   c->d_err, st);
+    if (id >= 0) pr.end(id, st);
+  }
+  if (!h.has_g3) {
+    if (!h.c2.chunks.empty()) {
+      const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
+      launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1,
+                         c2out, c2scale, st);
+      if (id >= 0) pr.end(id, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
+  }
+  // stage 2 writes T2 directly as a split operand of stage 3
+  if (!h.c2.chunks.empty()) {
+    const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
+    launch_combine_split(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1,
+                         hi(sl.t2s), lo(sl.t2s, h.ws2), c2scale, st);
+    if (id >= 0) pr.end(id, st);
+  }
+  // stage 3: the operand that is T2 (ws2 in the FP64 layout) uses the split T2;
+  // an operand equal to a stage-1 operand reuses that split
+  const double* ws2 = ws1 + h.ws1;
+  auto operand = [&](const double* x, int64_t slot, int64_t n, bool hinted, const float** ph,
+                     const float** pl) {
+    if (x == ws2) {
+      *ph = hi(sl.t2s);
+      *pl = lo(sl.t2s, h.ws2);
+    } else if (x == g1A) {
+      *ph = hi(sl.a1);
+      *pl = lo(sl.a1, h.nA1);
+    } else if (x == g1B) {
+      *ph = hi(sl.b1);
+      *pl = lo(sl.b1, h.nB1);
+    } else {
+      if (!hinted) launch_split(x, hi(slot), lo(slot, n), n, st);
+      *ph = hi(slot);
+      *pl = lo(slot, n);
+    }
+  };
+  const float *a3h, *a3l, *b3h, *b3l;
+  operand(g3A, sl.a3, h.nA3, hn.g3A, &a3h, &a3l);
+  operand(g3B, sl.b3, h.nB3, hn.g3B, &b3h, &b3l);
+  if (!h.g3.tiles.empty()) {
+    const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
+    launch_gemm_tc(passes, h.g3.ta, h.g3.tb, p.g3_tiles_tc, (int)h.g3.tiles_tc.size(), p.g3_tasks,
+                   p.g3_segs, a3h, a3l, b3h, b3l, g3C, c->d_err, st);
     if (id >= 0) pr.end(id, st);
   }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
@@ -196,8 +255,8 @@ dmrg3s_status env_plan(Context* c, int dir, const EnvLayout& e, const MpoLayout&
 
 namespace {
 
-dmrg3s_status check_ws(Context* c, const Plan& p) {
-  const size_t need = (size_t)(p.ws1 + p.ws2) * sizeof(double);
+dmrg3s_status check_ws(Context* c, const Plan& p, dmrg3s_precision prec) {
+  const size_t need = (size_t)plan_ws_doubles(p, prec) * sizeof(double);
   if (need > c->ws_bytes)
     return fail(c, DMRG3S_ERR_OOM,
                 "context workspace too small: need " + std::to_string(need) + " bytes");
@@ -444,7 +503,7 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
   const DevicePlan* p = nullptr;
   st = heff_plan(c, le, w, re, a, &p);
   if (st != DMRG3S_OK) return st;
-  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  if ((st = check_ws(c, p->host, prec)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
   st = run_plan(c, *p, L->data, A->data, ws1, ws2, 1.0, ws2, R->data, HA->data,
@@ -486,7 +545,7 @@ dmrg3s_status dmrg3s_expand(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* env,
   const DevicePlan* p = nullptr;
   st = expand_plan(c, dir, e, w, m, pl, f, &p);
   if (st != DMRG3S_OK) return st;
-  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  if ((st = check_ws(c, p->host, prec)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   const double* g1A = dir == 1 ? env->data : M->data;
   const double* g1B = dir == 1 ? M->data : env->data;
@@ -524,7 +583,7 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
   const DevicePlan* p = nullptr;
   st = env_plan(c, dir, e, w, a, o, &p);
   if (st != DMRG3S_OK) return st;
-  if ((st = check_ws(c, p->host)) || (st = use_device(c))) return st;
+  if ((st = check_ws(c, p->host, prec)) || (st = use_device(c))) return st;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
   const double* g1A = dir == 1 ? env->data : A->data;

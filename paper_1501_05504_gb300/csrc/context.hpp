@@ -164,11 +164,38 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 
 // Enqueue the stages of a plan.  Bases as documented for each plan Kind.
+// Tensor-core mode: the operands of stages 1 and 3 are split into FP32
+// (hi, lo) arrays in the workspace, laid out after the FP64 intermediates:
+//   [T1: ws1][T2: ws2][T2 split: ws2][g1A split][g1B split][g3A split][g3B split]
+// (in units of doubles; a split of n elements takes n doubles of space).  A
+// caller that has already split an operand into its slot passes a hint and
+// run_plan skips that split (the Lanczos loop splits L and R once).
+struct SplitHints {
+  bool g1A = false, g1B = false, g3A = false, g3B = false;
+};
+struct TcSlots {
+  int64_t t2s, a1, b1, a3, b3, end;    // offsets in doubles from the workspace start
+};
+inline TcSlots tc_slots(const Plan& p) {
+  TcSlots s;
+  s.t2s = p.ws1 + p.ws2;
+  s.a1 = s.t2s + p.ws2;
+  s.b1 = s.a1 + p.nA1;
+  s.a3 = s.b1 + p.nB1;
+  s.b3 = s.a3 + p.nA3;
+  s.end = s.b3 + p.nB3;
+  return s;
+}
+// Workspace (in doubles) a plan needs in the given precision.
+inline int64_t plan_ws_doubles(const Plan& p, dmrg3s_precision prec) {
+  return prec == DMRG3S_FP64 ? p.ws1 + p.ws2 : tc_slots(p).end;
+}
+
 // `prec` selects the grouped-GEMM kernel of stages 1 and 3 (the combination
 // of stage 2 is always FP64).
 dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const double* g1B,
                        double* ws1, double* c2out, double c2scale, const double* g3A,
                        const double* g3B, double* g3C, cudaStream_t st,
-                       dmrg3s_precision prec = DMRG3S_FP64);
+                       dmrg3s_precision prec = DMRG3S_FP64, const SplitHints* hints = nullptr);
 
 }  // namespace dmrg3s

@@ -10,6 +10,7 @@
 
 #include "context.hpp"
 #include "dmrg3s.h"
+#include "kernels.hpp"
 #include "vecops.hpp"
 
 namespace dmrg3s {
@@ -42,6 +43,18 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   TridiagOut* out = (TridiagOut*)pout;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + heff.host.ws1;
+  // tensor-core products: split the environments once for the whole run
+  SplitHints hints;
+  if (prec != DMRG3S_FP64) {
+    const TcSlots sl = tc_slots(heff.host);
+    const int64_t nL = heff.host.nA1, nR = heff.host.nB3;
+    float* Ls = reinterpret_cast<float*>(ws1 + sl.a1);
+    float* Rs = reinterpret_cast<float*>(ws1 + sl.b3);
+    launch_split(Ldata, Ls, prec == DMRG3S_TF32X3 ? Ls + nL : nullptr, nL, st);
+    launch_split(Rdata, Rs, prec == DMRG3S_TF32X3 ? Rs + nR : nullptr, nR, st);
+    hints.g1A = true;
+    hints.g3B = true;
+  }
 
   // v_0 = x / |x|
   launch_multidot(x, 0, 1, x, n, part, nrm2, nullptr, st);
@@ -54,7 +67,7 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   TridiagOut res{};
   for (;; ++k) {
     double* vk = V + (int64_t)k * n;
-    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st, prec);
+    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st, prec, &hints);
     if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
     launch_multidot(V, n, k + 1, w, n, part, h, alpha + k, st);   // alpha_k = <v_k, H v_k>
     launch_multi_axpy(V, n, k + 1, h, w, n, st);
@@ -116,7 +129,7 @@ extern "C" dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L,
   if ((st = use_device(c))) return st;
   const DevicePlan* p = nullptr;
   if ((st = heff_plan(c, le, w, re, a, &p))) return st;
-  size_t cursor = (size_t)(p->host.ws1 + p->host.ws2) * sizeof(double);
+  size_t cursor = (size_t)plan_ws_doubles(p->host, prec) * sizeof(double);
   int it = 0;
   double theta = 0.0;
   st = lanczos_run(c, *p, L->data, R->data, M->data, a.size, kmax, tol, cursor,

@@ -58,11 +58,23 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
                      cudaStream_t st);
 
 // out = scale * sum_k coef_k in_k for every task.
-// Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32); err is a
-// device flag set to 1 when a bounded wait timed out.
+// Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32).  The
+// operands are pre-split FP32 arrays (hi = tf32(x), lo = tf32(x - hi)) with
+// the offsets of the FP64 layout; lo may be null when passes == 1.  C is FP64.
+// err is a device flag set to 1 when a bounded wait timed out.
 void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
-                    const GemmTask* tasks, const GemmSeg* segs, const double* A, const double* B,
-                    double* C, int* err, cudaStream_t st);
+                    const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
+                    const float* Alo, const float* Bhi, const float* Blo, double* C, int* err,
+                    cudaStream_t st);
+
+// hi[i] = tf32(x[i]), lo[i] = tf32(x[i] - hi[i]) (the 3xTF32 split of an FP64 array).
+void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t st);
+
+// As launch_combine_f64, but the output is written split (hi, lo) for a
+// following tensor-core stage instead of in FP64.
+void launch_combine_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                          const CombTerm* terms, const double* in, float* out_hi,
+                          float* out_lo, double scale, cudaStream_t st);
 
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
                         const CombTerm* terms, const double* in, double* out, double scale,

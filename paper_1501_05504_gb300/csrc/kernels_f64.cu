@@ -120,6 +120,35 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombChunk* __res
   }
 }
 
+__global__ void __launch_bounds__(256) combine_split_kernel(const CombChunk* __restrict__ chunks,
+                                                           const CombTask* __restrict__ tasks,
+                                                           const CombTerm* __restrict__ terms,
+                                                           const double* __restrict__ in,
+                                                           float* __restrict__ out_hi,
+                                                           float* __restrict__ out_lo,
+                                                           double scale) {
+  const CombChunk ch = chunks[blockIdx.x];
+  const CombTask t = tasks[ch.task];
+  const int n = ch.nrows * t.cols;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int r = ch.row0 + idx / t.cols, c = idx % t.cols;
+    double acc = 0.0;
+    for (int k = 0; k < t.nt; ++k) {
+      const CombTerm tm = terms[t.t0 + k];
+      acc = fma(tm.coef, in[tm.offIn + (int64_t)r * tm.ldi + c], acc);
+    }
+    acc *= scale;
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"((float)acc));
+    const float hf = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"((float)(acc - (double)hf)));
+    const int64_t o = t.offOut + (int64_t)r * t.ldo + c;
+    out_hi[o] = hf;
+    if (out_lo) out_lo[o] = __uint_as_float(l);
+  }
+}
+
 std::atomic<int64_t> g_launches{0};
 
 }  // namespace
@@ -141,6 +170,14 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
     gemm_f64_kernel<Trans::T, Trans::N><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
   else
     gemm_f64_kernel<Trans::T, Trans::T><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
+}
+
+void launch_combine_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                          const CombTerm* terms, const double* in, float* out_hi,
+                          float* out_lo, double scale, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  count_launch();
+  combine_split_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out_hi, out_lo, scale);
 }
 
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,

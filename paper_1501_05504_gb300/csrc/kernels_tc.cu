@@ -2,10 +2,11 @@
 //
 // Same task tables as the FP64 kernel (one output block per task, K-segments
 // summed), computed on the 5th-generation tensor cores in TF32 with FP32
-// accumulation.  Operands stay FP64 in memory; the load stage splits every
-// element into x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (Ootomo and
-// Yokota's split, 2022) while writing the K-major canonical shared-memory
-// layout, so no separate conversion pass is needed:
+// accumulation per 32-wide K chunk and double-float accumulation across
+// chunks.  Operands are FP64 tensors pre-split into x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi) (Ootomo and Yokota's split, 2022) by
+// split_kernel or by the MPO combination, so the GEMM itself does no FP64
+// arithmetic (GB300's FP64 rate is ~1/1000 of its TF32 rate):
 //   kPasses = 1: C = A_hi B_hi                                  (TF32)
 //   kPasses = 3: C = A_hi B_hi + A_hi B_lo + A_lo B_hi          (3xTF32)
 //
@@ -101,37 +102,38 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// Load one operand tile (ROWS x 32, K-major canonical layout) from FP64
-// global memory, split into TF32 hi / lo.  kContig: the source is contiguous
-// along K (element (row, k) at src[row * ld + k]); otherwise along the row
-// index (src[k * ld + row]).  Lanes cover one 8 x 4 core matrix per step (a
+// Load one operand tile (ROWS x 32, K-major canonical layout) from the
+// pre-split FP32 arrays.  kContig: the source is contiguous along K (element
+// (row, k) at src[row * ld + k]); otherwise along the row index
+// (src[k * ld + row]).  Lanes cover one 8 x 4 core matrix per step (a
 // 128-byte contiguous shared store), with the fast lane index along the
-// source's contiguous direction.
+// source's contiguous direction.  No FP64 arithmetic: GB300's FP64 rate would
+// otherwise bound the kernel.
 template <int ROWS, bool kContig, bool kLo>
-__device__ __forceinline__ void load_tile(const double* __restrict__ src, int ld, int row0,
-                                          int nrow, int k0, int nk, unsigned char* hi,
-                                          unsigned char* lo, int warp, int lane) {
+__device__ __forceinline__ void load_tile(const float* __restrict__ shi, const float* __restrict__ slo,
+                                          int ld, int row0, int nrow, int k0, int nk,
+                                          unsigned char* hi, unsigned char* lo, int warp,
+                                          int lane) {
   const int r8 = kContig ? (lane >> 2) : (lane & 7);
   const int k4 = kContig ? (lane & 3) : (lane >> 3);
 #pragma unroll
   for (int g = warp; g < ROWS / 8; g += 4) {
     const int row = g * 8 + r8;
     const bool rok = row0 + row < nrow;
-    double v[8];
+    float vh[8], vl[8];
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
       const int k = k0 + kc * 4 + k4;
-      v[kc] = (rok && k < nk)
-                  ? (kContig ? src[(int64_t)(row0 + row) * ld + k] : src[(int64_t)k * ld + row0 + row])
-                  : 0.0;
+      const int64_t o = kContig ? (int64_t)(row0 + row) * ld + k : (int64_t)k * ld + row0 + row;
+      const bool ok = rok && k < nk;
+      vh[kc] = ok ? shi[o] : 0.f;
+      if (kLo) vl[kc] = ok ? slo[o] : 0.f;
     }
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
-      float h, l;
-      split(v[kc], h, l);
       const uint32_t o = (uint32_t)(g * 1024 + kc * 128 + r8 * 16 + k4 * 4);
-      *reinterpret_cast<float*>(hi + o) = h;
-      if (kLo) *reinterpret_cast<float*>(lo + o) = l;
+      *reinterpret_cast<float*>(hi + o) = vh[kc];
+      if (kLo) *reinterpret_cast<float*>(lo + o) = vl[kc];
     }
   }
 }
@@ -147,26 +149,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 // Add the FP32 accumulator of one K chunk (TMEM columns col0 .. col0 + 63 of
-// this warp's lanes) into the thread's FP64 accumulators.
-__device__ __forceinline__ void drain(uint32_t dtmem, int warp, uint32_t col0, double (&acc)[TBN]) {
+// this warp's lanes) into the thread's double-float accumulators (hi, lo),
+// with Knuth's two-sum so that no rounding error is lost between chunks.
+__device__ __forceinline__ void drain(uint32_t dtmem, int warp, uint32_t col0, float (&ah)[TBN],
+                                      float (&al)[TBN]) {
 #pragma unroll
   for (int c0 = 0; c0 < TBN; c0 += 16) {
     uint32_t v[16];
     tmem_ld16(dtmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)c0, v);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[c0 + j] += (double)__uint_as_float(v[j]);
+    for (int j = 0; j < 16; ++j) {
+      const float x = __uint_as_float(v[j]), a = ah[c0 + j];
+      const float s = __fadd_rn(a, x);
+      const float bb = __fsub_rn(s, a);
+      const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+      ah[c0 + j] = s;
+      al[c0 + j] = __fadd_rn(al[c0 + j], e);
+    }
   }
 }
 
 // Every 32-wide K chunk is accumulated by the tensor core into its own FP32
-// TMEM buffer (two buffers, alternating) and then added into FP64 registers,
-// so FP32 rounding only ever sees 32-term sums.
+// TMEM buffer (two buffers, alternating) and then added into double-float
+// registers, so FP32 rounding only ever sees 32-term sums.
 template <Trans TA, Trans TB, int kPasses>
 __global__ void __launch_bounds__(TNT, 2)
     gemm_tc_kernel(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
-                   const GemmSeg* __restrict__ segs, const double* __restrict__ A,
-                   const double* __restrict__ B, double* __restrict__ C, int* __restrict__ err) {
+                   const GemmSeg* __restrict__ segs, const float* __restrict__ Ahi,
+                   const float* __restrict__ Alo, const float* __restrict__ Bhi,
+                   const float* __restrict__ Blo, double* __restrict__ C, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr bool kLo = kPasses == 3;
   constexpr int kStage = (kStageA + kStageB) * (kLo ? 2 : 1);
@@ -194,16 +206,17 @@ __global__ void __launch_bounds__(TNT, 2)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t dtmem = tmem_base;
   constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
-  double acc[TBN];
+  float ah[TBN], al[TBN];
 #pragma unroll
-  for (int j = 0; j < TBN; ++j) acc[j] = 0.0;
+  for (int j = 0; j < TBN; ++j) {
+    ah[j] = 0.f;
+    al[j] = 0.f;
+  }
   bool ok = true;
   int it = 0;
 
   for (int sgi = 0; sgi < task.nseg && ok; ++sgi) {
     const GemmSeg sg = segs[task.seg0 + sgi];
-    const double* Ap = A + sg.offA;
-    const double* Bp = B + sg.offB;
     for (int k0 = 0; k0 < sg.K && ok; k0 += TBK, ++it) {
       const int st = it & 1;
       // stage st and TMEM buffer st were last used by chunk it - 2
@@ -214,36 +227,38 @@ __global__ void __launch_bounds__(TNT, 2)
       unsigned char* a_lo = base + kStageA;
       unsigned char* b_hi = base + kStageA * (kLo ? 2 : 1);
       unsigned char* b_lo = b_hi + kStageB;
-      load_tile<TBM, TA == Trans::N, kLo>(Ap, sg.lda, m0, task.M, k0, sg.K, a_hi, a_lo, warp, lane);
-      load_tile<TBN, TB == Trans::T, kLo>(Bp, sg.ldb, n0, task.N, k0, sg.K, b_hi, b_lo, warp, lane);
+      load_tile<TBM, TA == Trans::N, kLo>(Ahi + sg.offA, kLo ? Alo + sg.offA : nullptr, sg.lda, m0,
+                                          task.M, k0, sg.K, a_hi, a_lo, warp, lane);
+      load_tile<TBN, TB == Trans::T, kLo>(Bhi + sg.offB, kLo ? Blo + sg.offB : nullptr, sg.ldb, n0,
+                                          task.N, k0, sg.K, b_hi, b_lo, warp, lane);
       // make the generic-proxy stores visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
-        const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        const uint32_t sah = smem_u32(a_hi), sal = smem_u32(a_lo);
+        const uint32_t sbh = smem_u32(b_hi), sbl = smem_u32(b_lo);
         const uint32_t d = dtmem + (uint32_t)(st * TBN);
 #pragma unroll
         for (int kk = 0; kk < TBK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
           const uint32_t off = kk * 256;             // two core matrices along K
           if (kLo) {
-            mma_tf32(d, smem_desc(al + off), smem_desc(bh + off), idesc, kk == 0 ? 0u : 1u);
-            mma_tf32(d, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-            mma_tf32(d, smem_desc(ah + off), smem_desc(bh + off), idesc, 1u);
+            mma_tf32(d, smem_desc(sal + off), smem_desc(sbh + off), idesc, kk == 0 ? 0u : 1u);
+            mma_tf32(d, smem_desc(sah + off), smem_desc(sbl + off), idesc, 1u);
+            mma_tf32(d, smem_desc(sah + off), smem_desc(sbh + off), idesc, 1u);
           } else {
-            mma_tf32(d, smem_desc(ah + off), smem_desc(bh + off), idesc, kk == 0 ? 0u : 1u);
+            mma_tf32(d, smem_desc(sah + off), smem_desc(sbh + off), idesc, kk == 0 ? 0u : 1u);
           }
         }
         mma_commit(&bars[st]);
       }
-      // meanwhile drain the previous chunk's accumulator into FP64
+      // meanwhile drain the previous chunk's accumulator
       if (it >= 1) {
         ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
         if (ok) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), acc);
+          drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), ah, al);
         }
       }
     }
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(TNT, 2)
     ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), acc);
+      drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), ah, al);
     }
   }
   if (!ok) {
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(TNT, 2)
       const int nv = task.N - n0 < TBN ? task.N - n0 : TBN;
 #pragma unroll
       for (int j = 0; j < TBN; ++j)
-        if (j < nv) crow[j] = acc[j];
+        if (j < nv) crow[j] = (double)ah[j] + (double)al[j];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -277,9 +292,21 @@ __global__ void __launch_bounds__(TNT, 2)
                  : "memory");
 }
 
+__global__ void split_kernel(const double* __restrict__ x, float* __restrict__ hi,
+                             float* __restrict__ lo, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float h, l;
+    split(x[i], h, l);
+    hi[i] = h;
+    if (lo) lo[i] = l;
+  }
+}
+
 template <Trans TA, Trans TB, int P>
 void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const GemmSeg* segs,
-                const double* A, const double* B, double* C, int* err, cudaStream_t st) {
+                const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
+                int* err, cudaStream_t st) {
   constexpr int kLo = P == 3 ? 1 : 0;
   constexpr int smem = 2 * (kStageA + kStageB) * (1 + kLo);
   static bool attr = false;
@@ -288,22 +315,33 @@ void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const 
                          smem);
     attr = true;
   }
-  gemm_tc_kernel<TA, TB, P><<<ntiles, TNT, smem, st>>>(tiles, tasks, segs, A, B, C, err);
+  gemm_tc_kernel<TA, TB, P><<<ntiles, TNT, smem, st>>>(tiles, tasks, segs, Ah, Al, Bh, Bl, C, err);
 }
 
 }  // namespace
 
+void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  int64_t g = (n + 255) / 256;
+  if (g > 4 * 152) g = 4 * 152;
+  split_kernel<<<(int)g, 256, 0, st>>>(x, hi, lo, n);
+}
+
 void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
-                    const GemmTask* tasks, const GemmSeg* segs, const double* A, const double* B,
-                    double* C, int* err, cudaStream_t st) {
+                    const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
+                    const float* Alo, const float* Bhi, const float* Blo, double* C, int* err,
+                    cudaStream_t st) {
   if (ntiles <= 0) return;
   count_launch();
 #define DMRG3S_TC(TA_, TB_)                                                           \
   if (ta == Trans::TA_ && tb == Trans::TB_) {                                         \
     if (passes == 3)                                                                  \
-      launch_one<Trans::TA_, Trans::TB_, 3>(tiles, ntiles, tasks, segs, A, B, C, err, st); \
+      launch_one<Trans::TA_, Trans::TB_, 3>(tiles, ntiles, tasks, segs, Ahi, Alo, Bhi, Blo, C, \
+                                            err, st);                                   \
     else                                                                              \
-      launch_one<Trans::TA_, Trans::TB_, 1>(tiles, ntiles, tasks, segs, A, B, C, err, st); \
+      launch_one<Trans::TA_, Trans::TB_, 1>(tiles, ntiles, tasks, segs, Ahi, Alo, Bhi, Blo, C, \
+                                            err, st);                                   \
     return;                                                                           \
   }
   DMRG3S_TC(N, N)

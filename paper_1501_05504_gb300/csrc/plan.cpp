@@ -177,6 +177,10 @@ std::map<Key, Interm> materialise(const std::map<Key, Combo>& combos, Plan* p) {
 // Bounds of every table against the buffers the stages address.
 dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
                      int64_t nC3, std::string* err) {
+  p->nA1 = nA1;
+  p->nB1 = nB1;
+  p->nA3 = p->has_g3 ? nA3 : 0;
+  p->nB3 = p->has_g3 ? nB3 : 0;
   p->g1.finalize_bytes(p->g1.ta, p->g1.tb);
   if (p->has_g3) p->g3.finalize_bytes(p->g3.ta, p->g3.tb);
   const int64_t w1 = p->ws1 > 0 ? p->ws1 : 1;

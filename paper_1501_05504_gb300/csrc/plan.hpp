@@ -66,6 +66,8 @@ struct Plan {
   CombStage c2;
   bool has_g3 = false;
   int64_t ws1 = 0, ws2 = 0;     // doubles of the stage-1 / stage-2 intermediates
+  int64_t nA1 = 0, nB1 = 0;     // elements of the stage-1 operand arrays
+  int64_t nA3 = 0, nB3 = 0;     // elements of the stage-3 operand arrays (0 without stage 3)
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
 

@@ -331,7 +331,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if (o.optimise) {
     const DevicePlan* hp;
     if ((s = heff_plan(c, S.Lenv[i].lay, w, S.Renv[i].lay, m.lay, &hp))) return s;
-    size_t cursor = (size_t)(hp->host.ws1 + hp->host.ws2) * sizeof(double);
+    size_t cursor = (size_t)plan_ws_doubles(hp->host, o.prec) * sizeof(double);
     double lam = 0.0;
     int it = 0;
     if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, m.data, m.lay.size, o.kmax, o.tol,
