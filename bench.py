@@ -279,6 +279,41 @@ def run_ours(args):
             "clocks": clk.summary()}
 
 
+def run_heff_only(args):
+    """Kernel view: repeated H_eff applications on the window's centre site."""
+    import torch
+    from paper_1501_05504_gb300 import binding as b
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
+    spec = window_specs(SEED)
+    mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
+    W0, W1 = mpo.site(50), mpo.site(51)
+    gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
+    gM0, gM1 = (b.site_from_neutral(x) for x in spec["M"])
+    gR0 = b.empty_env(W0.tr, gM0.right)                     # right environment of site 50
+    b.dmrg3s_update_env(ctx, -1, gR, W1, gM1, gR0, "fp64")
+    gH = b.empty_site_like(gM0.qp, gM0.left, gM0.right)
+    for _ in range(args.warmup):
+        b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, args.precision)
+    b.dmrg3s_sync(ctx)
+    b.dmrg3s_profile(ctx, True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, args.precision)
+    e1.record(s)
+    b.dmrg3s_sync(ctx)
+    g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
+    c = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
+    b.dmrg3s_profile(ctx, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = (g["flops"] + c["flops"]) / args.steps
+    return {"metric": "H_eff application on the m=512 window (kernel view)", "value": flops / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "ms_per_heff": ms, "flops_per_heff": flops, "precision": args.precision,
+            "gemm_ms_per_heff": g["ms"] / args.steps, "combine_ms_per_heff": c["ms"] / args.steps,
+            "gemm_launches": g["launches"], "l2": "not flushed (kernel view)"}
+
+
 def cpu_baseline(sample_s=15.0):
     """The FP64 oracle on the host cores: H_eff applications on the same window."""
     from oracle import contract, io, models
@@ -328,10 +363,15 @@ def main():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--heff-only", action="store_true",
+                    help="kernel view: time repeated H_eff applications instead of local updates")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.heff_only:
+        res = run_heff_only(args)
+    else:
+        res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res))
 

@@ -64,7 +64,9 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   size_t total = bytes_of(h.g1.tiles) + bytes_of(h.g1.tasks) + bytes_of(h.g1.segs) +
                  bytes_of(h.c2.chunks) + bytes_of(h.c2.tasks) + bytes_of(h.c2.terms) +
                  bytes_of(h.g3.tiles) + bytes_of(h.g3.tasks) + bytes_of(h.g3.segs) +
-                 bytes_of(h.g1.tiles_tc) + bytes_of(h.g3.tiles_tc);
+                 bytes_of(h.g1.tiles_tc) + bytes_of(h.g3.tiles_tc) + bytes_of(h.g3s.tiles_tc) +
+                 bytes_of(h.g3s.tasks) + bytes_of(h.g3s.segs) + bytes_of(h.c3r.chunks) +
+                 bytes_of(h.c3r.tasks) + bytes_of(h.c3r.terms);
   if (total == 0) total = 256;
   if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
   std::vector<char> staging(total, 0);
@@ -81,6 +83,12 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   dp->g3_segs = place(base, &off, h.g3.segs, &staging);
   dp->g1_tiles_tc = place(base, &off, h.g1.tiles_tc, &staging);
   dp->g3_tiles_tc = place(base, &off, h.g3.tiles_tc, &staging);
+  dp->g3s_tiles = place(base, &off, h.g3s.tiles_tc, &staging);
+  dp->g3s_tasks = place(base, &off, h.g3s.tasks, &staging);
+  dp->g3s_segs = place(base, &off, h.g3s.segs, &staging);
+  dp->c3r_chunks = place(base, &off, h.c3r.chunks, &staging);
+  dp->c3r_tasks = place(base, &off, h.c3r.tasks, &staging);
+  dp->c3r_terms = place(base, &off, h.c3r.terms, &staging);
   if (cudaMemcpy(dp->mem, staging.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
     return DMRG3S_ERR_CUDA;
   *out = std::move(dp);
@@ -172,10 +180,18 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   const float *a3h, *a3l, *b3h, *b3l;
   operand(g3A, sl.a3, h.nA3, hn.g3A, &a3h, &a3l);
   operand(g3B, sl.b3, h.nB3, hn.g3B, &b3h, &b3l);
-  if (!h.g3.tiles.empty()) {
-    const int id = pr.on ? pr.begin(kProfGemm, h.g3.flops, h.g3.bytes, st) : -1;
-    launch_gemm_tc(passes, h.g3.ta, h.g3.tb, p.g3_tiles_tc, (int)h.g3.tiles_tc.size(), p.g3_tasks,
-                   p.g3_segs, a3h, a3l, b3h, b3l, g3C, c->d_err, st);
+  // split-K: one CTA per (tile, K-segment) into FP64 partials, then a fixed-order sum
+  double* part = base + sl.p3;
+  if (!h.g3s.tiles_tc.empty()) {
+    const int id = pr.on ? pr.begin(kProfGemm, h.g3s.flops, h.g3s.bytes, st) : -1;
+    launch_gemm_tc(passes, h.g3s.ta, h.g3s.tb, p.g3s_tiles, (int)h.g3s.tiles_tc.size(),
+                   p.g3s_tasks, p.g3s_segs, a3h, a3l, b3h, b3l, part, c->d_err, st);
+    if (id >= 0) pr.end(id, st);
+  }
+  if (!h.c3r.chunks.empty()) {
+    const int id = pr.on ? pr.begin(kProfCombine, 0.0, 0.0, st) : -1;
+    launch_combine_f64(p.c3r_chunks, (int)h.c3r.chunks.size(), p.c3r_tasks, p.c3r_terms, part,
+                       g3C, 1.0, st);
     if (id >= 0) pr.end(id, st);
   }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;

@@ -26,6 +26,12 @@ struct DevicePlan {
   CombTerm* c2_terms = nullptr;
   GemmTile* g3_tiles = nullptr;
   GemmTile* g3_tiles_tc = nullptr;
+  GemmTile* g3s_tiles = nullptr;     // split-K stage 3 (tensor-core tiles)
+  GemmTask* g3s_tasks = nullptr;
+  GemmSeg* g3s_segs = nullptr;
+  CombChunk* c3r_chunks = nullptr;
+  CombTask* c3r_tasks = nullptr;
+  CombTerm* c3r_terms = nullptr;
   GemmTask* g3_tasks = nullptr;
   GemmSeg* g3_segs = nullptr;
   ~DevicePlan();
@@ -167,6 +173,7 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 // Tensor-core mode: the operands of stages 1 and 3 are split into FP32
 // (hi, lo) arrays in the workspace, laid out after the FP64 intermediates:
 //   [T1: ws1][T2: ws2][T2 split: ws2][g1A split][g1B split][g3A split][g3B split]
+//   [stage-3 partial products: ws3]
 // (in units of doubles; a split of n elements takes n doubles of space).  A
 // caller that has already split an operand into its slot passes a hint and
 // run_plan skips that split (the Lanczos loop splits L and R once).
@@ -174,7 +181,7 @@ struct SplitHints {
   bool g1A = false, g1B = false, g3A = false, g3B = false;
 };
 struct TcSlots {
-  int64_t t2s, a1, b1, a3, b3, end;    // offsets in doubles from the workspace start
+  int64_t t2s, a1, b1, a3, b3, p3, end;    // offsets in doubles from the workspace start
 };
 inline TcSlots tc_slots(const Plan& p) {
   TcSlots s;
@@ -183,7 +190,8 @@ inline TcSlots tc_slots(const Plan& p) {
   s.b1 = s.a1 + p.nA1;
   s.a3 = s.b1 + p.nB1;
   s.b3 = s.a3 + p.nA3;
-  s.end = s.b3 + p.nB3;
+  s.p3 = s.b3 + p.nB3;
+  s.end = s.p3 + p.ws3;
   return s;
 }
 // Workspace (in doubles) a plan needs in the given precision.

@@ -183,6 +183,36 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
   p->nB3 = p->has_g3 ? nB3 : 0;
   p->g1.finalize_bytes(p->g1.ta, p->g1.tb);
   if (p->has_g3) p->g3.finalize_bytes(p->g3.ta, p->g3.tb);
+  if (p->has_g3) {
+    // split-K form of stage 3: every (task, segment) becomes its own task
+    p->g3s.ta = p->g3.ta;
+    p->g3s.tb = p->g3.tb;
+    int64_t poff = 0;
+    for (const GemmTask& t : p->g3.tasks) {
+      std::vector<CombTerm> terms;
+      for (int k = 0; k < t.nseg; ++k) {
+        p->g3s.add(poff, t.N, t.M, t.N, {p->g3.segs[t.seg0 + k]});
+        CombTerm tm{};
+        tm.offIn = poff;
+        tm.ldi = t.N;
+        tm.coef = 1.0;
+        terms.push_back(tm);
+        poff += (int64_t)t.M * t.N;
+      }
+      p->c3r.add(t.offC, t.ldc, t.M, t.N, terms);
+    }
+    p->ws3 = poff;
+    p->g3s.flops = p->g3.flops;        // same algorithmic work as stage 3
+    p->g3s.bytes = p->g3.bytes;
+    p->c3r.flops = 0.0;                // the partial sums are bookkeeping, not algorithm
+    p->c3r.bytes = 0.0;
+    const int64_t w3 = poff > 0 ? poff : 1;
+    if (!gemm_ok(p->g3s.ta, p->g3s.tb, p->g3s.tasks, p->g3s.segs, nA3, nB3, w3, err) ||
+        !comb_ok(p->c3r.tasks, p->c3r.terms, w3, nC3, err)) {
+      *err = "internal planning error: " + *err;
+      return DMRG3S_ERR_SHAPE;
+    }
+  }
   const int64_t w1 = p->ws1 > 0 ? p->ws1 : 1;
   if (!gemm_ok(p->g1.ta, p->g1.tb, p->g1.tasks, p->g1.segs, nA1, nB1, w1, err) ||
       !comb_ok(p->c2.tasks, p->c2.terms, w1, nOut2, err) ||

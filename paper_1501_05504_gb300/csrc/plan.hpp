@@ -68,6 +68,11 @@ struct Plan {
   int64_t ws1 = 0, ws2 = 0;     // doubles of the stage-1 / stage-2 intermediates
   int64_t nA1 = 0, nB1 = 0;     // elements of the stage-1 operand arrays
   int64_t nA3 = 0, nB3 = 0;     // elements of the stage-3 operand arrays (0 without stage 3)
+  // Split-K form of stage 3 for the tensor-core kernel: one task per (output
+  // block, K-segment) writing an FP64 partial block, then a deterministic sum.
+  GemmStage g3s;                // partial products (C base = the partial buffer)
+  CombStage c3r;                // sum of the partials into the output
+  int64_t ws3 = 0;              // doubles of the partial buffer
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
 
