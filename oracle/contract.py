@@ -88,4 +88,8 @@ def mpo_gradient(L, R, M):
     W_i taken out.  Divided by <Psi|Psi> it gives the Hellmann-Feynman
     derivative of the energy with respect to the entries of W_i.
     """
-    return np.einsum("bXx,SXY,sxy,cYy->Ssbc", L, M.conj(), M, R, optimize=True)
+    # the same sum, associated pairwise (a single four-operand einsum falls back
+    # to the naive loop over all eight indices at large m)
+    T1 = np.einsum("bXx,sxy->bsXy", L, M)              # ket copy of M through L
+    Y = np.einsum("SXY,cYy->ScXy", M.conj(), R)        # bra copy of M through R
+    return np.einsum("bsXy,ScXy->Ssbc", T1, Y)
