@@ -246,11 +246,26 @@ dmrg3s_status dmrg3s_update_env(dmrg3s_ctx ctx, int32_t dir, const dmrg3s_env* e
                                 const dmrg3s_mpo_site* W, const dmrg3s_site* A,
                                 dmrg3s_env* out, dmrg3s_precision prec, dmrg3s_stream stream);
 
+/* MPO-entry gradient of <M|H_eff|M> (the network of Sec. II with W_i taken
+ * out; <Psi|H|Psi> is linear in each W_i):
+ *   G[s', s, bl, br] = sum L[bl](al', al) M[s'](al', ar') M[s](al, ar) R[br](ar', ar)
+ * L, W, R, M as for dmrg3s_apply_heff (only W's structure is used, not its
+ * values).  G: device, d*d*wl*wr doubles in the layout of W (row-major
+ * [s'][s][bl][br]); overwritten, zero where the charge rule forbids an entry.
+ * With L, R the environments of the current MPS and M its orthogonality
+ * centre, sum_{entries} G * dW/dtheta / <M|M> is the Hellmann-Feynman
+ * derivative of the energy.  FP64 on the CUDA cores; intermediates in the
+ * context workspace.  Errors as dmrg3s_apply_heff. */
+dmrg3s_status dmrg3s_mpo_grad_site(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                                   const dmrg3s_env* R, const dmrg3s_site* M, double* G,
+                                   dmrg3s_stream stream);
+
 /* Local eigensolver, step 1 of Sec. V: the smallest eigenpair (lambda*, M*)
  * of L_{i-1} R_{i+1} W_i M_i = lambda M_i (Eq. es-iter) by Lanczos with full
  * reorthogonalisation (classical Gram-Schmidt applied twice), all in FP64 on
- * the device; the tridiagonal eigenproblem is solved by Sturm bisection and
- * inverse iteration in a device kernel.  M: start vector on input, the
+ * the device; the tridiagonal eigenproblem is solved in a device kernel by
+ * Sturm multisection (double-float counts), inverse iteration and the
+ * Rayleigh quotient of the resulting vector.  M: start vector on input, the
  * normalised Ritz vector on output.  Stops when the Ritz residual
  * |beta_k y_k| <= tol * max(1, |lambda|), when beta_k < 1e-14 or after kmax
  * (<= 128) products.  Synchronises `stream` once per iteration to test the
@@ -380,6 +395,19 @@ dmrg3s_status dmrg3s_state_centre(dmrg3s_state state, int32_t* centre, double* e
 dmrg3s_status dmrg3s_state_site_info(dmrg3s_state state, int32_t i, int32_t* nsec_left,
                                      int32_t* q_left, int64_t* dim_left, int32_t* nsec_right,
                                      int32_t* q_right, int64_t* dim_right, int64_t* nelem);
+
+/* MPO-entry gradients of <Psi|H|Psi> for every site of the state's current
+ * MPS (mixed canonical around its centre): G_i as dmrg3s_mpo_grad_site, with
+ * the stored environments on the near side of the centre and environments
+ * of the current tensors rebuilt on the far side.  G (HOST, may be NULL)
+ * receives the G_i concatenated in site order, each d*d*wl_i*wr_i doubles;
+ * dW (HOST, may be NULL) holds dW_i/dtheta in the same layout, and
+ *   *dE = sum_i <G_i, dW_i/dtheta> / <Psi|Psi>
+ * (0 when dW is NULL).  len is the summed size (checked when G or dW is
+ * given).  *norm2 = <Psi|Psi> = <M_c|M_c>.  Synchronous.
+ * Errors: ARG, SHAPE, OOM, CUDA, NUMERIC (zero norm). */
+dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
+                              double* dE, double* norm2);
 
 /* Copies site i (canonical layout, nelem doubles) to dst (device or host). */
 dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,

@@ -93,15 +93,52 @@ __global__ void normalise_kernel(const double* __restrict__ x, double* __restric
     y[e] = x[e] * s;
 }
 
-// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T pivots).
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+// Double-float numbers (an unevaluated sum hi + lo of two floats, about 44
+// significant bits) carry the Sturm counts: GB300 issues FP32 at ~60x its
+// FP64 rate, and the count only needs the sign of each pivot. Two-sum is
+// Knuth's error-free addition; the quotient takes one correction step with
+// an FMA residual (Dekker's double-length division).
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  const float s = a.hi - b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (-b.hi - bb);
+  e += a.lo - b.lo;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float rb = 1.0f / b.hi;
+  const float q1 = a.hi * rb;
+  const float p = q1 * b.hi;
+  const float pe = fmaf(q1, b.hi, -p);
+  const float r = (((a.hi - p) - pe) + a.lo) - q1 * b.lo;
+  const float q2 = r * rb;
+  const float h = q1 + q2;
+  return {h, q2 - (h - q1)};
+}
+
+// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T
+// pivots). The matrix arrives shifted and scaled, sa[i] = (alpha_i - c)/s and
+// sbb[i] = (beta_{i-1}/s)^2, so every quantity is O(1) and x is (x - c)/s.
+__device__ int sturm_count_df(const DF* sa, const DF* sbb, int k, DF x) {
   int cnt = 0;
-  double d = 1.0;
+  DF d = {1.f, 0.f};
   for (int i = 0; i < k; ++i) {
-    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
-    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
-    if (d == 0.0) d = -1e-300;    // x hit an eigenvalue of a leading block: perturb
-    if (d < 0.0) ++cnt;
+    DF t = df_sub(sa[i], x);
+    if (i > 0) t = df_sub(t, df_div(sbb[i], d));
+    if (t.hi == 0.f) t = {-1e-30f, 0.f};   // x hit an eigenvalue of a leading block: perturb
+    if (t.hi < 0.f) ++cnt;
+    d = t;
   }
   return cnt;
 }
@@ -110,15 +147,19 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
                                double theta, double span, double lo, double hi, double* y,
                                TridiagOut* out);
 
-// Multisection variant: all threads of the block evaluate Sturm counts at
-// equally spaced points of the bracket, shrinking it by blockDim.x + 1 per
-// round; thread 0 then runs the inverse iteration.
+// Multisection: all threads of the block evaluate Sturm counts at equally
+// spaced points of the bracket, shrinking it by blockDim.x + 1 per round
+// until it reaches the resolution of double-float counts (~1e-13 of the
+// Gershgorin span); thread 0 then runs the inverse iteration in FP64 and
+// returns the Rayleigh quotient of the vector, which is accurate to FP64
+// rounding whatever the width of the bracket was.
 __global__ void tridiag_multisection_kernel(const double* __restrict__ alpha,
                                             double* __restrict__ beta, int k,
                                             const double* __restrict__ nrm2,
                                             double* __restrict__ y, TridiagOut* __restrict__ out) {
-  __shared__ double sh_lo, sh_hi, sh_span;
+  __shared__ double sh_lo, sh_hi, sh_span, sh_c;
   __shared__ int sh_bad, sh_first;
+  __shared__ DF sa[128], sbb[128];
   const int tid = threadIdx.x, nt = blockDim.x;
   const double bl = sqrt(*nrm2);
   if (tid == 0) {
@@ -136,6 +177,7 @@ __global__ void tridiag_multisection_kernel(const double* __restrict__ alpha,
     sh_lo = lo - 1e-12 * span;
     sh_hi = hi + 1e-12 * span;
     sh_span = span;
+    sh_c = 0.5 * (lo + hi);
     sh_bad = bad;
     beta[k - 1] = bl;
   }
@@ -149,14 +191,21 @@ __global__ void tridiag_multisection_kernel(const double* __restrict__ alpha,
     }
     return;
   }
-  for (int round = 0; round < 16; ++round) {
+  const double c = sh_c, inv_s = 1.0 / sh_span;
+  for (int i = tid; i < k; i += nt) {
+    sa[i] = df_from((alpha[i] - c) * inv_s);
+    const double bs = i > 0 ? beta[i - 1] * inv_s : 0.0;
+    sbb[i] = df_from(bs * bs);
+  }
+  __syncthreads();
+  for (int round = 0; round < 8; ++round) {
     const double lo = sh_lo, hi = sh_hi;
     const double h = (hi - lo) / (nt + 1);
-    if (!(h > 0.0) || lo + h <= lo) break;
+    if (!(h > 1e-14 * sh_span)) break;
     if (tid == 0) sh_first = nt;
     __syncthreads();
-    const double x = lo + h * (tid + 1);
-    if (sturm_count(alpha, beta, k, x) >= 1) atomicMin(&sh_first, tid);
+    const DF x = df_from((lo + h * (tid + 1) - c) * inv_s);
+    if (sturm_count_df(sa, sbb, k, x) >= 1) atomicMin(&sh_first, tid);
     __syncthreads();
     if (tid == 0) {
       const int f = sh_first;            // first point above the smallest eigenvalue
@@ -241,13 +290,14 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
       for (int i = 0; i < kk; ++i) y[i] = i == 0 ? 1.0 : 0.0;
       continue;
     }
+    const double ib = 1.0 / big;
     double nrm = 0.0;
     for (int i = 0; i < kk; ++i) {
-      y[i] /= big;
+      y[i] *= ib;
       nrm += y[i] * y[i];
     }
-    nrm = sqrt(nrm);
-    for (int i = 0; i < kk; ++i) y[i] /= nrm;
+    const double in = 1.0 / sqrt(nrm);
+    for (int i = 0; i < kk; ++i) y[i] *= in;
   }
   // fix the sign: largest component positive (only the subspace is defined)
   int imax = 0;
@@ -255,6 +305,16 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
     if (fabs(y[i]) > fabs(y[imax])) imax = i;
   if (y[imax] < 0.0)
     for (int i = 0; i < kk; ++i) y[i] = -y[i];
+  // Rayleigh quotient y^T T y (y has unit norm): second-order accurate in the
+  // error of the vector, so the bracket's width does not limit the Ritz value
+  double rq = 0.0;
+  for (int i = 0; i < kk; ++i) {
+    double ty = alpha[i] * y[i];
+    if (i > 0) ty += beta[i - 1] * y[i - 1];
+    if (i < kk - 1) ty += beta[i] * y[i + 1];
+    rq += y[i] * ty;
+  }
+  if (rq == rq) theta = rq;
   out->theta = theta;
   out->resid = fabs(bl * y[kk - 1]);
   out->beta_last = bl;
