@@ -629,3 +629,42 @@ def dmrg3s_launch_count():
     n = ctypes.c_int64()
     _check(L.dmrg3s_launch_count(ctypes.byref(n)), "dmrg3s_launch_count")
     return n.value
+
+
+def dmrg3s_mpo_grad_site(ctx, L, W, R, M, G, stream=None):
+    """G (device float64 tensor of d*d*wl*wr) = d<M|H_eff|M>/dW in the layout of W."""
+    lb = lib()
+    lb.dmrg3s_mpo_grad_site.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Env), ctypes.POINTER(_MpoSite),
+                                        ctypes.POINTER(_Env), ctypes.POINTER(_Site), ctypes.c_void_p,
+                                        ctypes.c_void_p]
+    cL, cW, cR, cM = L._c(), W._c(), R._c(), M._c()
+    _check(lb.dmrg3s_mpo_grad_site(ctx.handle, ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR),
+                                   ctypes.byref(cM), _ptr(G), _stream(stream)),
+           "dmrg3s_mpo_grad_site", ctx.handle)
+
+
+def dmrg3s_mpo_grad(state, dW=None, shapes=None):
+    """MPO-entry gradients of <Psi|H|Psi> at every site of the state.
+
+    dW: optional list of per-site arrays dW_i/dtheta (shape (d, d, wl, wr)).
+    shapes: the per-site (d, d, wl, wr) of the state's MPO (needed to split G).
+    Returns (G list, dE/dtheta, <Psi|Psi>)."""
+    lb = lib()
+    lb.dmrg3s_mpo_grad.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int64, f64p, f64p]
+    sizes = [int(np.prod(s)) for s in shapes]
+    total = sum(sizes)
+    G = np.zeros(max(total, 1), np.float64)
+    dw = None
+    if dW is not None:
+        dw = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).ravel() for x in dW]))
+        if dw.size != total:
+            raise ValueError("dW does not match the MPO shapes")
+    dE, n2 = ctypes.c_double(), ctypes.c_double()
+    _check(lb.dmrg3s_mpo_grad(state.handle, G.ctypes.data_as(f64p),
+                              dw.ctypes.data_as(f64p) if dw is not None else None, total,
+                              ctypes.byref(dE), ctypes.byref(n2)), "dmrg3s_mpo_grad", state.ctx.handle)
+    out, off = [], 0
+    for s, n in zip(shapes, sizes):
+        out.append(G[off:off + n].reshape(s))
+        off += n
+    return out, dE.value, n2.value

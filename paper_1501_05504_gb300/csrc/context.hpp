@@ -206,4 +206,9 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
                        const double* g3B, double* g3C, cudaStream_t st,
                        dmrg3s_precision prec = DMRG3S_FP64, const SplitHints* hints = nullptr);
 
+// MPO-entry gradient G (d*d*wl*wr doubles, device, layout of W) of
+// <M|H_eff|M> for the given environments; intermediates in the workspace.
+dmrg3s_status run_mpo_grad(Context* c, const GradPlan& p, const double* L, const double* M,
+                           const double* R, double* G, cudaStream_t st);
+
 }  // namespace dmrg3s

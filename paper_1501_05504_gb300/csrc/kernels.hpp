@@ -47,6 +47,16 @@ constexpr int kCombRows = 16;
 
 enum class Trans { N, T };
 
+// Blockwise inner products: out[task.out] = sum over the task's segments of
+// <A[offA .. offA+len), B[offB .. offB+len)> (FP64, fixed summation order).
+struct DotSeg {
+  int64_t offA, offB, len;
+};
+struct DotTask {
+  int64_t out;
+  int32_t seg0, nseg;
+};
+
 // Process-wide count of kernels launched by this library.
 int64_t launch_count();
 void count_launch(int n = 1);
@@ -79,5 +89,9 @@ void launch_combine_split(const CombChunk* chunks, int nchunks, const CombTask* 
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
                         const CombTerm* terms, const double* in, double* out, double scale,
                         cudaStream_t st);
+
+// One CTA per task; deterministic (no atomics).
+void launch_dots(const DotTask* tasks, int ntasks, const DotSeg* segs, const double* A,
+                 const double* B, double* out, cudaStream_t st);
 
 }  // namespace dmrg3s

@@ -151,6 +151,29 @@ __global__ void __launch_bounds__(256) combine_split_kernel(const CombChunk* __r
 
 std::atomic<int64_t> g_launches{0};
 
+__global__ void __launch_bounds__(256) dots_kernel(const DotTask* __restrict__ tasks,
+                                                   const DotSeg* __restrict__ segs,
+                                                   const double* __restrict__ A,
+                                                   const double* __restrict__ B,
+                                                   double* __restrict__ out) {
+  const DotTask t = tasks[blockIdx.x];
+  double acc = 0.0;
+  for (int k = 0; k < t.nseg; ++k) {
+    const DotSeg g = segs[t.seg0 + k];
+    for (int64_t e = threadIdx.x; e < g.len; e += blockDim.x)
+      acc = fma(A[g.offA + e], B[g.offB + e], acc);
+  }
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    out[t.out] = sum;
+  }
+}
+
 }  // namespace
 
 int64_t launch_count() { return g_launches.load(); }
@@ -186,6 +209,13 @@ void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* ta
   if (nchunks <= 0) return;
   count_launch();
   combine_f64_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out, scale);
+}
+
+void launch_dots(const DotTask* tasks, int ntasks, const DotSeg* segs, const double* A,
+                 const double* B, double* out, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  count_launch();
+  dots_kernel<<<ntasks, 256, 0, st>>>(tasks, segs, A, B, out);
 }
 
 }  // namespace dmrg3s

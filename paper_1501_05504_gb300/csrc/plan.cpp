@@ -393,4 +393,80 @@ dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLay
   return finish(p, M.size, re.size, p->ws2, M.size, p->ws2, out.size, err);
 }
 
+dmrg3s_status plan_mpo_grad(const EnvLayout& le, const MpoLayout& W, const EnvLayout& re,
+                            const SiteLayout& M, GradPlan* p, std::string* err) {
+  // stage 1 exactly as for H_eff; the T1 blocks are then indexed by (bl, s)
+  Plan tmp;
+  std::map<Key, Interm> t1;
+  std::map<Key, Combo> unused;
+  left_stages(le, W, M, &tmp, &t1, &unused);
+  p->g1 = tmp.g1;
+  p->ws1 = tmp.ws1;
+  struct T1Blk {
+    int ip, j;
+    int64_t off, len;
+  };
+  std::map<std::pair<int, int>, std::vector<T1Blk>> by_bl_s;
+  for (const auto& kv : t1) {
+    const int bl = kv.first[0], s = kv.first[1], i = kv.first[2];
+    const int lb = le.block_of(bl, i), mb = M.block_of(s, i);
+    if (lb < 0 || mb < 0) continue;
+    by_bl_s[{bl, s}].push_back(T1Blk{le.blocks[lb].b, M.blocks[mb].c, kv.second.off,
+                                     (int64_t)kv.second.rows * kv.second.cols});
+  }
+  // Y[br, s'](al', ar) = M[s'](al', ar') R[br](ar', ar)
+  p->gy.ta = Trans::N;
+  p->gy.tb = Trans::N;
+  std::map<Key, Interm> y;
+  int64_t off = 0;
+  for (const Block& mb : M.blocks) {
+    const int so = mb.a, ip = mb.b, jp = mb.c;
+    for (int br = 0; br < W.wr; ++br) {
+      const int j = M.nsym ? M.right.find(sub(M.right.q[jp], re.t[br])) : 0;
+      if (j < 0) continue;
+      const int rb = re.block_of(br, j);
+      if (rb < 0 || re.blocks[rb].b != jp) continue;
+      const int64_t rows = M.left.dim[ip], cols = M.right.dim[j], K = M.right.dim[jp];
+      y[Key{br, so, ip, j}] = Interm{off, (int)rows, (int)cols};
+      p->gy.add(off, (int)cols, (int)rows, (int)cols, {seg(mb.off, K, re.blocks[rb].off, cols, K)});
+      off += rows * cols;
+    }
+  }
+  p->wsy = off;
+  p->nG = (int64_t)W.d * W.d * W.wl * W.wr;
+  for (int so = 0; so < W.d; ++so)
+    for (int s = 0; s < W.d; ++s)
+      for (int bl = 0; bl < W.wl; ++bl)
+        for (int br = 0; br < W.wr; ++br) {
+          DotTask t{};
+          t.out = (((int64_t)so * W.d + s) * W.wl + bl) * W.wr + br;
+          t.seg0 = (int32_t)p->segs.size();
+          auto it = by_bl_s.find({bl, s});
+          if (it != by_bl_s.end())
+            for (const T1Blk& b : it->second) {
+              auto yt = y.find(Key{br, so, b.ip, b.j});
+              if (yt == y.end()) continue;
+              p->segs.push_back(DotSeg{b.off, yt->second.off, b.len});
+              p->dot_flops += 2.0 * b.len;
+            }
+          t.nseg = (int32_t)p->segs.size() - t.seg0;
+          p->tasks.push_back(t);
+        }
+  p->g1.finalize_bytes(p->g1.ta, p->g1.tb);
+  p->gy.finalize_bytes(p->gy.ta, p->gy.tb);
+  const int64_t w1 = p->ws1 > 0 ? p->ws1 : 1, wy = p->wsy > 0 ? p->wsy : 1;
+  if (!gemm_ok(p->g1.ta, p->g1.tb, p->g1.tasks, p->g1.segs, le.size, M.size, w1, err) ||
+      !gemm_ok(p->gy.ta, p->gy.tb, p->gy.tasks, p->gy.segs, M.size, re.size, wy, err)) {
+    *err = "internal planning error: " + *err;
+    return DMRG3S_ERR_SHAPE;
+  }
+  for (const DotSeg& g : p->segs)
+    if (g.offA < 0 || g.offB < 0 || g.len < 0 || g.offA + g.len > p->ws1 ||
+        g.offB + g.len > p->wsy) {
+      *err = "internal planning error: gradient segment out of bounds";
+      return DMRG3S_ERR_SHAPE;
+    }
+  return DMRG3S_OK;
+}
+
 }  // namespace dmrg3s

@@ -93,6 +93,24 @@ dmrg3s_status plan_expand_rl(const EnvLayout& re, const MpoLayout& W, const Site
 dmrg3s_status plan_env_rl(const EnvLayout& re, const MpoLayout& W, const SiteLayout& mps,
                           const EnvLayout& out, Plan* plan, std::string* err);
 
+// MPO-entry gradient of <M|H_eff|M> (the contraction of Sec. II with W_i
+// taken out):
+//   G[s', s, bl, br] = sum L[bl](al', al) M[s'](al', ar') M[s](al, ar) R[br](ar', ar)
+// in three stages:
+//   g1    T1[bl, s] = L[bl] . M[s]          (stage 1 of H_eff)    C = ws1
+//   gy    Y[br, s'] = M[s'] . R[br]         (bra side through R)  C = wsy
+//   dots  G[s', s, bl, br] = sum over the (al', ar) blocks of <T1[bl, s], Y[br, s']>
+struct GradPlan {
+  GemmStage g1, gy;
+  std::vector<DotTask> tasks;     // one per entry of G, row-major [s'][s][bl][br]
+  std::vector<DotSeg> segs;       // A = ws1, B = wsy
+  int64_t ws1 = 0, wsy = 0, nG = 0;
+  double dot_flops = 0.0;
+  double flops() const { return g1.flops + gy.flops + dot_flops; }
+};
+dmrg3s_status plan_mpo_grad(const EnvLayout& le, const MpoLayout& W, const EnvLayout& re,
+                            const SiteLayout& mps, GradPlan* plan, std::string* err);
+
 // Structural compatibility checks shared by the entry points.
 dmrg3s_status check_site_mpo(const SiteLayout& s, const MpoLayout& W, std::string* err);
 dmrg3s_status check_env(const EnvLayout& e, const Bond& bond, int w,

@@ -163,29 +163,44 @@ dmrg3s_status dot_host(Context* c, const double* x, const double* y, int64_t n, 
   return DMRG3S_OK;
 }
 
-dmrg3s_status build_env(State& S, int i, int dir, cudaStream_t st) {
+// One step of the environment recursion of Sec. II with the current tensor
+// of site i: dir = +1 turns the left environment `src` of site i into that of
+// site i + 1, dir = -1 the right environment of site i into that of site
+// i - 1.  The result is freshly allocated (stream ordered).
+dmrg3s_status env_step(State& S, int i, int dir, const EnvLayout& src_lay, const double* src,
+                       EnvLayout* out_lay, double** out, cudaStream_t st) {
   Context* c = S.c;
   const MpoLayout& w = S.W[i];
   const DevSite& a = S.M[i];
-  DevEnv& src = dir == 1 ? S.Lenv[i] : S.Renv[i];
-  if (!src.valid) return fail(c, DMRG3S_ERR_ARG, "environment recursion from an invalid environment");
-  DevEnv& dst = dir == 1 ? S.Lenv[i + 1] : S.Renv[i - 1];
-  EnvLayout ol;
   make_env_from(a.lay.nsym, dir == 1 ? w.wr : w.wl, dir == 1 ? w.tr : w.tl,
-                dir == 1 ? a.lay.right : a.lay.left, &ol);
+                dir == 1 ? a.lay.right : a.lay.left, out_lay);
   const DevicePlan* p;
-  dmrg3s_status s = env_plan(c, dir, src.lay, w, a.lay, ol, &p);
+  dmrg3s_status s = env_plan(c, dir, src_lay, w, a.lay, *out_lay, &p);
   if (s) return s;
   if ((size_t)(p->host.ws1 + p->host.ws2) * sizeof(double) > c->ws_bytes)
     return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the environment update");
-  double* nd;
-  if ((s = dalloc(c, &nd, ol.size, st))) return s;
+  if ((s = dalloc(c, out, out_lay->size, st))) return s;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
-  const double* g1A = dir == 1 ? src.data : a.data;
-  const double* g1B = dir == 1 ? a.data : src.data;
-  if ((s = run_plan(c, *p, g1A, g1B, ws1, ws2, 1.0, a.data, ws2, nd, st)))
+  const double* g1A = dir == 1 ? src : a.data;
+  const double* g1B = dir == 1 ? a.data : src;
+  if ((s = run_plan(c, *p, g1A, g1B, ws1, ws2, 1.0, a.data, ws2, *out, st))) {
+    dfree(*out, st);
+    *out = nullptr;
     return fail(c, s, "environment update launch");
+  }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status build_env(State& S, int i, int dir, cudaStream_t st) {
+  DevEnv& src = dir == 1 ? S.Lenv[i] : S.Renv[i];
+  if (!src.valid)
+    return fail(S.c, DMRG3S_ERR_ARG, "environment recursion from an invalid environment");
+  DevEnv& dst = dir == 1 ? S.Lenv[i + 1] : S.Renv[i - 1];
+  EnvLayout ol;
+  double* nd;
+  dmrg3s_status s = env_step(S, i, dir, src.lay, src.data, &ol, &nd, st);
+  if (s) return s;
   dfree(dst.data, st);
   dst.data = nd;
   dst.lay = ol;
@@ -856,6 +871,83 @@ dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,
   cudaError_t e = cudaMemcpyAsync(dst, S->M[i].data, (size_t)S->M[i].lay.size * sizeof(double),
                                   cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? DMRG3S_OK : fail(S->c, DMRG3S_ERR_CUDA, "site copy");
+}
+
+dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
+                              double* dE, double* norm2) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  int64_t total = 0;
+  std::vector<int64_t> goff(S->n);
+  for (int i = 0; i < S->n; ++i) {
+    goff[i] = total;
+    total += (int64_t)S->W[i].d * S->W[i].d * S->W[i].wl * S->W[i].wr;
+  }
+  if ((G || dW) && len != total)
+    return fail(c, DMRG3S_ERR_SHAPE, "len must be the summed d*d*wl*wr over the sites");
+  dmrg3s_status s;
+  if ((s = use_device(c))) return s;
+  cudaStream_t st = nullptr;
+  const int cen = S->centre;
+  if (!S->Lenv[cen].valid || !S->Renv[cen].valid)
+    return fail(c, DMRG3S_ERR_ARG, "environments of the centre are not valid");
+  double* dG;
+  if ((s = dalloc(c, &dG, total, st))) return s;
+  // G_i for the centre and, walking outwards, for every other site with the
+  // environment of the current tensors on the far side of the centre
+  auto grad_at = [&](int i, const EnvLayout& ll, const double* L, const EnvLayout& rl,
+                     const double* R) -> dmrg3s_status {
+    GradPlan p;
+    std::string err;
+    dmrg3s_status r = plan_mpo_grad(ll, S->W[i], rl, S->M[i].lay, &p, &err);
+    if (r) return fail(c, r, "site " + std::to_string(i) + ": " + err);
+    return run_mpo_grad(c, p, L, S->M[i].data, R, dG + goff[i], st);
+  };
+  s = grad_at(cen, S->Lenv[cen].lay, S->Lenv[cen].data, S->Renv[cen].lay, S->Renv[cen].data);
+  for (int dir = -1; dir <= 1 && !s; dir += 2) {
+    // dir = -1: sites left of the centre (left environments stored, right
+    // ones rebuilt); dir = +1: the mirror image
+    EnvLayout lay = dir == -1 ? S->Renv[cen].lay : S->Lenv[cen].lay;
+    const double* cur = dir == -1 ? S->Renv[cen].data : S->Lenv[cen].data;
+    double* owned = nullptr;
+    for (int i = cen + dir; i >= 0 && i < S->n && !s; i += dir) {
+      EnvLayout nl;
+      double* nd = nullptr;
+      if ((s = env_step(*S, i - dir, dir, lay, cur, &nl, &nd, st))) break;
+      dfree(owned, st);
+      owned = nd;
+      cur = nd;
+      lay = nl;
+      if (dir == -1) {
+        if (!S->Lenv[i].valid) s = fail(c, DMRG3S_ERR_ARG, "left environment not valid");
+        else s = grad_at(i, S->Lenv[i].lay, S->Lenv[i].data, lay, cur);
+      } else {
+        if (!S->Renv[i].valid) s = fail(c, DMRG3S_ERR_ARG, "right environment not valid");
+        else s = grad_at(i, lay, cur, S->Renv[i].lay, S->Renv[i].data);
+      }
+    }
+    dfree(owned, st);
+  }
+  double nrm = 0.0;
+  if (!s) s = dot_host(c, S->M[cen].data, S->M[cen].data, S->M[cen].lay.size, st, &nrm);
+  std::vector<double> hG(total);
+  if (!s && total > 0)
+    s = cuda_ok(c, cudaMemcpyAsync(hG.data(), dG, (size_t)total * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st), "gradient read-back");
+  dfree(dG, st);
+  if (!s) s = cuda_ok(c, cudaStreamSynchronize(st), "gradient");
+  if (s) return s;
+  if (!(nrm > 0.0)) return fail(c, DMRG3S_ERR_NUMERIC, "zero norm of the centre tensor");
+  if (G) std::memcpy(G, hG.data(), (size_t)total * sizeof(double));
+  if (norm2) *norm2 = nrm;
+  if (dE) {
+    double acc = 0.0;
+    if (dW)
+      for (int64_t k = 0; k < total; ++k) acc += hG[k] * dW[k];
+    *dE = acc / nrm;
+  }
+  return DMRG3S_OK;
 }
 
 }  // extern "C"
