@@ -130,13 +130,14 @@ const char* dmrg3s_last_error(dmrg3s_ctx ctx);
 dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
 
 /* Kernel timing.  While enabled, the context records CUDA events on the
- * launching stream around every grouped-GEMM launch (kernel 0: the block
- * products of stages 1 and 3 of the contraction order of Sec. V, and the
- * S V^dagger product of the truncation) and every MPO combination launch
- * (kernel 1: stage 2), and around the phases of every local update (2:
- * eigensolver, 3: expansion term, 4: gather + SVD + new tensors, 5: S V^dagger
- * into the neighbour, 6: environment update, 7: energy after truncation;
- * flops and bytes are 0 for phases).  dmrg3s_profile(ctx, 1) resets and enables, 0
+ * launching stream around every grouped-GEMM launch of the contractions
+ * (kernel 0: the block products of stages 1 and 3 of the contraction order
+ * of Sec. V) and every MPO combination launch (kernel 1: stage 2), around
+ * the phases of every local update (2: eigensolver, 3: expansion term,
+ * 4: gather + SVD + new tensors, 5: S V^dagger into the neighbour,
+ * 6: environment update, 7: energy after truncation; flops and bytes are 0
+ * for phases), and around the other FP64 grouped GEMMs (kernel 8: the
+ * truncation's S V^dagger products and the MPO-entry gradient).  dmrg3s_profile(ctx, 1) resets and enables, 0
  * disables; dmrg3s_profile_read synchronises on the recorded events and
  * returns, for one kernel, the number of launches, their summed device time
  * and their summed algorithmic flops and bytes (each distinct operand block

@@ -599,6 +599,7 @@ class _KernelStats(ctypes.Structure):
 
 KERNEL_GEMM, KERNEL_COMBINE = 0, 1
 PHASE_EIG, PHASE_EXPAND, PHASE_SVD, PHASE_REMAINDER, PHASE_ENV, PHASE_ENERGY = 2, 3, 4, 5, 6, 7
+KERNEL_AUX_GEMM = 8
 
 
 def dmrg3s_profile(ctx, enable):

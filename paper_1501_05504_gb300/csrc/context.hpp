@@ -48,7 +48,9 @@ enum ProfKind {
   kProfRemainder = 5,   //   S V^dagger (or U S) into the neighbour
   kProfEnv = 6,         //   environment update
   kProfEnergy = 7,      //   energy after truncation
-  kProfKinds = 8
+  kProfAuxGemm = 8,     // FP64 grouped GEMMs outside H_eff/expansion/environment:
+                        //   the remainder of the truncation, the MPO-entry gradient
+  kProfKinds = 9
 };
 struct ProfRec {
   int kind;

@@ -41,7 +41,7 @@ dmrg3s_status gemm_stage(Context* c, const GemmStage& g, const double* A, const 
   if ((s = put(c, g.tiles, &dt, st)) || (s = put(c, g.tasks, &dk, st)) ||
       (s = put(c, g.segs, &ds, st)))
     return s;
-  const int id = c->prof.on ? c->prof.begin(kProfGemm, g.flops, g.bytes, st) : -1;
+  const int id = c->prof.on ? c->prof.begin(kProfAuxGemm, g.flops, g.bytes, st) : -1;
   launch_gemm_f64(g.ta, g.tb, dt, (int)g.tiles.size(), dk, ds, A, B, C, st);
   if (id >= 0) c->prof.end(id, st);
   cudaFreeAsync(dt, st);

@@ -109,7 +109,7 @@ dmrg3s_status run_gemm(Context* c, const GemmStage& g, const double* A, int64_t 
   if ((s = upload(c, g.tiles, &dt, st)) || (s = upload(c, g.tasks, &dk, st)) ||
       (s = upload(c, g.segs, &ds, st)))
     return s;
-  const int id = c->prof.on ? c->prof.begin(kProfGemm, g.flops, g.bytes, st) : -1;
+  const int id = c->prof.on ? c->prof.begin(kProfAuxGemm, g.flops, g.bytes, st) : -1;
   launch_gemm_f64(g.ta, g.tb, dt, (int)g.tiles.size(), dk, ds, A, B, C, st);
   if (id >= 0) c->prof.end(id, st);
   cudaFreeAsync(dt, st);
@@ -253,9 +253,15 @@ struct Sector {
   int64_t offU = 0, offVT = 0, offS = 0;  // U (m x r), VT (r x n), S (r) in the output buffers
   int keep = 0;
   int jbase = -1;                         // old bond sector of the M* part, -1 if none
+  // The kept basis (left vectors for L->R, right vectors for R->L) is the
+  // small side n of the factorised matrix: gesvd then forms VT only (no U),
+  // and the remainder S V^T (or U S) is the projection of X onto the kept
+  // vectors, one GEMM.
+  bool vt_only = false;
 };
 
-// FP64 SVD X_tall = U S VT of every sector (cuSOLVER gesvd, jobs 'S'),
+// FP64 SVD X_tall = U S VT of every sector (cuSOLVER gesvd; U only where
+// the kept basis is the large side),
 // spread over the worker streams, largest sectors first; `st` waits for all.
 dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, double* F,
                           double* Sv, int* info, cudaStream_t st) {
@@ -264,9 +270,10 @@ dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, 
   size_t dmax = 1, hmax = 1;
   for (const Sector& sc : secs) {
     size_t wd = 0, wh = 0;
-    if (cusolverDnXgesvd_bufferSize(S.svd[0].h, S.svd[0].p, 'S', 'S', sc.m, sc.n, CUDA_R_64F, nullptr,
-                                    sc.m, CUDA_R_64F, nullptr, CUDA_R_64F, nullptr, sc.m, CUDA_R_64F,
-                                    nullptr, sc.r, CUDA_R_64F, &wd, &wh) != CUSOLVER_STATUS_SUCCESS)
+    if (cusolverDnXgesvd_bufferSize(S.svd[0].h, S.svd[0].p, sc.vt_only ? 'N' : 'S', 'S', sc.m, sc.n,
+                                    CUDA_R_64F, nullptr, sc.m, CUDA_R_64F, nullptr, CUDA_R_64F,
+                                    nullptr, sc.m, CUDA_R_64F, nullptr, sc.r, CUDA_R_64F, &wd,
+                                    &wh) != CUSOLVER_STATUS_SUCCESS)
       return fail(c, DMRG3S_ERR_CUDA, "gesvd buffer size");
     dmax = std::max(dmax, wd);
     hmax = std::max(hmax, wh);
@@ -305,8 +312,9 @@ dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, 
     cusolverDnSetStream(wk.h, wk.s);
     for (int k : jobs[w]) {
       const Sector& sc = secs[k];
-      if (cusolverDnXgesvd(wk.h, wk.p, 'S', 'S', sc.m, sc.n, CUDA_R_64F, X + sc.off, sc.m,
-                           CUDA_R_64F, Sv + sc.offS, CUDA_R_64F, F + sc.offU, sc.m, CUDA_R_64F,
+      if (cusolverDnXgesvd(wk.h, wk.p, sc.vt_only ? 'N' : 'S', 'S', sc.m, sc.n, CUDA_R_64F,
+                           X + sc.off, sc.m, CUDA_R_64F, Sv + sc.offS, CUDA_R_64F,
+                           sc.vt_only ? nullptr : F + sc.offU, sc.m, CUDA_R_64F,
                            F + sc.offVT, sc.r, CUDA_R_64F, wk.dwork, wk.dbytes, wk.hwork.data(),
                            wk.hwork.size(), info + k) != CUSOLVER_STATUS_SUCCESS)
         bad[w] = 1;
@@ -434,6 +442,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     sc.m = sc.tall ? sc.rows : sc.cols;
     sc.n = sc.tall ? sc.cols : sc.rows;
     sc.r = sc.n;
+    sc.vt_only = dir == 1 ? !sc.tall : sc.tall;
     sc.off = xoff;
     xoff += sc.rows * sc.cols;
     for (auto& pr : parts) {
@@ -484,7 +493,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   int64_t foff = 0, soff = 0;
   for (Sector& sc : secs) {
     sc.offU = foff;
-    foff += sc.m * sc.r;
+    if (!sc.vt_only) foff += sc.m * sc.r;
     sc.offVT = foff;
     foff += sc.r * sc.n;
     sc.offS = soff;
@@ -495,6 +504,16 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if ((s = dalloc(c, &F, foff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
       (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
     return s;
+  // gesvd overwrites its input: the projected remainder reads a copy of X
+  double* X0 = nullptr;
+  bool any_proj = false;
+  for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
+  if (any_proj) {
+    if ((s = dalloc(c, &X0, xoff, st))) return s;
+    if ((s = cuda_ok(c, cudaMemcpyAsync(X0, X, (size_t)xoff * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st), "copy of M~")))
+      return s;
+  }
   if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st))) return s;
   std::vector<double> hs(std::max<int64_t>(soff, 1));
   std::vector<int> hinfo(secs.size() + 1, 0);
@@ -566,6 +585,11 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     return copy_task(sc.offU + col0, sc.m, dst, ldd, nc, na, false, rs, -1);
   };
   std::vector<CopyTask> cp_new, cp_rem;
+  GemmStage proj_lr, proj_rl;   // remainder by projection (vt_only sectors)
+  proj_lr.ta = Trans::T;
+  proj_lr.tb = Trans::N;
+  proj_rl.ta = Trans::T;
+  proj_rl.tb = Trans::N;
   std::vector<int64_t> rem_off(nbnd.nsec(), 0);
   int64_t rem_size = 0;
   for (int kn = 0; kn < nbnd.nsec(); ++kn) {
@@ -589,7 +613,27 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
       }
       o2 += dio;
     }
-    if (sc.base > 0) {
+    if (sc.base > 0 && sc.vt_only) {
+      // L->R (X^T factorised): SV[c, j] = sum_a VT[c, a] X[a, j], X row-major (rows x cols)
+      // R->L (X factorised):   US[i, c] = sum_a X[i, a] VT[c, a], X column-major (rows x cols)
+      // Both read VT[c, a] at offVT + a r + c, i.e. K x nk row-major with ld r.
+      GemmSeg q{};
+      q.scale = 1.0;
+      q.K = (int32_t)sc.n;
+      if (dir == 1) {     // C (nk x base) = VT^T^T . X: A = VT (K x nk, ld r), B = X (K x base, ld cols)
+        q.offA = sc.offVT;
+        q.lda = (int32_t)sc.r;
+        q.offB = sc.off;
+        q.ldb = (int32_t)sc.cols;
+        proj_lr.add(rem_off[kn], (int)sc.base, (int)nk, (int)sc.base, {q});
+      } else {            // C (base x nk) = X^T^T . VT^T: A = X (K x base, ld rows), B = VT (K x nk, ld r)
+        q.offA = sc.off;
+        q.lda = (int32_t)sc.rows;
+        q.offB = sc.offVT;
+        q.ldb = (int32_t)sc.r;
+        proj_rl.add(rem_off[kn], (int)nk, (int)sc.base, (int)nk, {q});
+      }
+    } else if (sc.base > 0) {
       if (dir == 1)     // SV (nk x base) = S[c] V_X[col, c]^T
         cp_rem.push_back(vxt(sc, 0, rem_off[kn], sc.base, nk, sc.base, (int)sc.offS));
       else              // US (base x nk) = U_X[row, c] S[c]
@@ -602,6 +646,12 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if ((s = run_copies(c, cp_new, F, foff, ndata, nl.size, Sv, soff, st)) ||
       (s = run_copies(c, cp_rem, F, foff, rem, rem_size, Sv, soff, st)))
     return s;
+  if (dir == 1) {
+    if ((s = run_gemm(c, proj_lr, F, foff, X0, xoff, rem, rem_size, st))) return s;
+  } else {
+    if ((s = run_gemm(c, proj_rl, X0, xoff, F, foff, rem, rem_size, st))) return s;
+  }
+  dfree(X0, st);
   dfree(F, st);
   dfree(Sv, st);
   done(ph);
