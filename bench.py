@@ -20,6 +20,7 @@ window's tensors in pinned host memory, copied in and out every step.
 workload (H_eff applications, the step's dominant cost) on the host cores.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -152,7 +153,16 @@ def traffic_for(kernel):
     with open(path) as f:
         t = json.load(f)
     ent = t.get(kernel)
-    return ent.get("bytes_per_launch") if ent else None
+    if not ent:
+        return None
+    # counters taken on another version of the kernel's source are not reported
+    src = os.path.join(ROOT, ent.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != ent.get("source_sha256"):
+            return None
+    return ent.get("bytes_per_launch")
 
 
 def run_ours(args):
@@ -279,18 +289,60 @@ def run_ours(args):
             "clocks": clk.summary()}
 
 
+def cylinder_bonds(lx=16, ly=4):
+    """Nearest-neighbour bonds of the lx x ly cylinder (periodic in y) in snake order."""
+    def idx(x, y):
+        return x * ly + (y if x % 2 == 0 else ly - 1 - y)
+    bonds = set()
+    for x in range(lx):
+        for y in range(ly):
+            if x + 1 < lx:
+                bonds.add(tuple(sorted((idx(x, y), idx(x + 1, y)))))
+            if ly > 2 or y + 1 < ly:
+                bonds.add(tuple(sorted((idx(x, y), idx(x, (y + 1) % ly)))))
+    return sorted(bonds)
+
+
+HEFF_WORKLOADS = {
+    # name: (model, sites, params, central site, seed)
+    "hubbard_l64_m1024_u1u1": ("hubbard", 64, (1.0, 8.0), 32, 1003),
+    "cylinder_4x16_m2048_u1": ("cylinder", 64, None, 32, 1004),
+}
+
+
+def heff_problem(b, name):
+    """Central-site H_eff problem of a larger workload: library MPO site, seeded
+    symmetric environments on the workload's bonds and a random site tensor."""
+    model, n, params, site, seed = HEFF_WORKLOADS[name]
+    if model == "hubbard":
+        mpo = b.Mpo(b.MODEL_HUBBARD, n, params)
+    else:
+        bonds = cylinder_bonds()
+        mpo = b.Mpo(b.MODEL_SPIN_BONDS, n, (), bonds=bonds, couplings=[(1.0, 1.0)] * len(bonds))
+    W = mpo.site(site)
+    left, right = si.central_bonds(name)
+    rng = si.rng_for(seed)
+    Le = si.symmetric_env(rng, W.tl, left, identity_channels=(W.tl.shape[0] - 1,))
+    Re = si.symmetric_env(rng, W.tr, right, identity_channels=(0,))
+    M = si.random_site(rng, W.qp, left, right)
+    return W, b.env_from_neutral(Le), b.env_from_neutral(Re), b.site_from_neutral(M)
+
+
 def run_heff_only(args):
-    """Kernel view: repeated H_eff applications on the window's centre site."""
+    """Kernel view: repeated H_eff applications on a workload's central site."""
     import torch
     from paper_1501_05504_gb300 import binding as b
-    ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
-    spec = window_specs(SEED)
-    mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
-    W0, W1 = mpo.site(50), mpo.site(51)
-    gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
-    gM0, gM1 = (b.site_from_neutral(x) for x in spec["M"])
-    gR0 = b.empty_env(W0.tr, gM0.right)                     # right environment of site 50
-    b.dmrg3s_update_env(ctx, -1, gR, W1, gM1, gR0, "fp64")
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), 4 << 30)
+    if args.workload == WORKLOAD:
+        spec = window_specs(SEED)
+        mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
+        W0, W1 = mpo.site(50), mpo.site(51)
+        gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
+        gM0, gM1 = (b.site_from_neutral(x) for x in spec["M"])
+        gR0 = b.empty_env(W0.tr, gM0.right)                     # right environment of site 50
+        b.dmrg3s_update_env(ctx, -1, gR, W1, gM1, gR0, "fp64")
+    else:
+        W0, gL, gR0, gM0 = heff_problem(b, args.workload)
     gH = b.empty_site_like(gM0.qp, gM0.left, gM0.right)
     for _ in range(args.warmup):
         b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, args.precision)
@@ -308,10 +360,20 @@ def run_heff_only(args):
     b.dmrg3s_profile(ctx, False)
     ms = e0.elapsed_time(e1) / args.steps
     flops = (g["flops"] + c["flops"]) / args.steps
-    return {"metric": "H_eff application on the m=512 window (kernel view)", "value": flops / (ms * 1e-3) / 1e12,
-            "unit": "TFLOP/s", "ms_per_heff": ms, "flops_per_heff": flops, "precision": args.precision,
+    peak = peaks()
+    pk = {"fp64": peak["fp64"], "tf32": peak["tf32"], "tf32x3": peak["tf32"] / 3.0}[args.precision]
+    gemm_tf = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else None
+    ctx.close()
+    return {"metric": "H_eff application on the %s central site (kernel view)" % args.workload,
+            "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_heff": ms,
+            "flops_per_heff": flops, "precision": args.precision, "w": int(W0.W.shape[2]),
+            "d": int(W0.W.shape[0]), "sectors": [len(gM0.left.dim), len(gM0.right.dim)],
+            "max_sector_dim": int(max(gM0.left.dim.max(), gM0.right.dim.max())),
             "gemm_ms_per_heff": g["ms"] / args.steps, "combine_ms_per_heff": c["ms"] / args.steps,
-            "gemm_launches": g["launches"], "l2": "not flushed (kernel view)"}
+            "gemm_launches": g["launches"], "gemm_tflops": gemm_tf,
+            "gemm_frac_of_peak": gemm_tf / pk if gemm_tf else None, "peak_tflops": pk,
+            "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (peak["source"], args.precision),
+            "l2": "not flushed (kernel view)"}
 
 
 def cpu_baseline(sample_s=15.0):
@@ -353,6 +415,74 @@ def run_reference(args):
             "wall_s": time.time() - t0}
 
 
+def _sweep_run(b, ctx, L, m_max, ladder, e_ref=None, max_sweeps=24, cap_s=240.0):
+    """Sweeps of the XXZ chain from the Neel state, one dmrg3s_sweep call per sweep.
+
+    ladder: list of (precision, until) pairs; a precision is used until the
+    relative sweep-to-sweep energy change drops below `until` (the last one
+    until convergence at 1e-11).  Returns per-sweep (wall seconds, energy)."""
+    import torch
+    W = b.Mpo(b.MODEL_XXZ, L, (1.0, 1.0)).sites()
+    spec = si.product_state_sites(si.XXZ_QP, [0, 1] * (L // 2))
+    st = b.dmrg3s_state_create(ctx, W, [b.site_from_neutral(x) for x in spec], None, None, L - 1)
+    alpha = ALPHA
+    log = []
+    stage = 0
+    prev = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max_sweeps):
+        prec, until = ladder[stage]
+        rep = b.dmrg3s_sweep(st, b.alpha_rule(alpha), 1, 0.0, b.update_opts(m_max, prec=prec))
+        alpha = rep["alpha"]
+        e = rep["energy"]
+        log.append((time.perf_counter() - t0, e, prec))
+        rel = abs(e - prev) / abs(e) if prev is not None else 1.0
+        prev = e
+        if rel < until:
+            if stage + 1 < len(ladder):
+                stage += 1
+            else:
+                break
+        if time.perf_counter() - t0 > cap_s:
+            break
+    st.close()
+    return log
+
+
+def run_sweep(args):
+    """Sweep-to-1e-9 time on one GB300: a mixed ladder (3xTF32 block products
+    until the energy changes by < 1e-7 per sweep, then FP64) against all-FP64,
+    both timed to the first sweep whose energy is within 1e-9 (relative) of
+    the converged FP64 energy."""
+    import torch
+    from paper_1501_05504_gb300 import binding as b
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
+    L, m_max = args.sweep_sites, args.sweep_m
+    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)])
+    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)])
+    e_ref = min(fp64[-1][1], mixed[-1][1])
+
+    def first(log):
+        for t, e, _ in log:
+            if abs(e - e_ref) <= 1e-9 * abs(e_ref):
+                return t
+        return None
+    t64, tmix = first(fp64), first(mixed)
+    ctx.close()
+    return {"metric": "sweep-to-1e-9 time, mixed vs FP64 (DMRG3S, XXZ chain from the Neel state)",
+            "value": tmix, "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "fp64_s": t64, "speedup_vs_fp64": (t64 / tmix) if (t64 and tmix) else None,
+            "energy_ref": e_ref, "energy_fp64": fp64[-1][1], "energy_mixed": mixed[-1][1],
+            "sweeps_fp64": [[round(t, 3), e, p] for t, e, p in fp64],
+            "sweeps_mixed": [[round(t, 3), e, p] for t, e, p in mixed],
+            "config": {"workload": "xxz_l%d_m%d_u1 full sweeps" % (L, m_max),
+                       "model": "S=1/2 XXZ chain Delta=1, L=%d, d=2, w=5, U(1) S^z" % L,
+                       "m_max": m_max, "alpha0": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
+                       "start": "Neel product state, m=1"},
+            "data": "synthetic"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,10 +495,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--heff-only", action="store_true",
                     help="kernel view: time repeated H_eff applications instead of local updates")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD] + sorted(HEFF_WORKLOADS),
+                    help="central-site problem of the kernel view (--heff-only)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="sweep-to-1e-9 time of full sweeps, mixed ladder vs FP64")
+    ap.add_argument("--sweep-sites", type=int, default=100)
+    ap.add_argument("--sweep-m", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.heff_only:
+    if args.sweep:
+        res = run_sweep(args)
+    elif args.heff_only:
         res = run_heff_only(args)
     else:
         res = run_reference(args) if args.impl == "reference" else run_ours(args)
