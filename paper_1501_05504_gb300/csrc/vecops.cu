@@ -34,33 +34,34 @@ __device__ double block_sum(double v, double* sh) {
   return r;   // valid in thread 0
 }
 
+// h[j] = <V_j, w> for j < k: block (c, j) sums chunk c of vector j (one block
+// reduction per block); multidot_final adds the chunk partials of vector j
+// in chunk order, so the result is deterministic.
 __global__ void __launch_bounds__(kThreads) multidot_partial(const double* __restrict__ V,
-                                                             int64_t ldv, int k,
-                                                             const double* __restrict__ w,
-                                                             int64_t n, double* __restrict__ partial) {
+                                                             int64_t ldv, const double* __restrict__ w,
+                                                             int64_t n, int64_t chunk,
+                                                             double* __restrict__ partial) {
   __shared__ double sh[32];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int j = 0; j < k; ++j) {
-    const double* v = V + (int64_t)j * ldv;
-    double acc = 0.0;
-    for (int64_t e = start; e < n; e += stride) acc = fma(v[e], w[e], acc);
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
-  }
+  const int j = blockIdx.y;
+  const double* v = V + (int64_t)j * ldv;
+  const int64_t e0 = (int64_t)blockIdx.x * chunk;
+  const int64_t e1 = e0 + chunk < n ? e0 + chunk : n;
+  double acc = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc = fma(v[e], w[e], acc);
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void multidot_final(const double* __restrict__ partial, int nblk, int k,
+__global__ void multidot_final(const double* __restrict__ partial, int nchunk, int k,
                                double* __restrict__ h, double* __restrict__ copy_last) {
   __shared__ double sh[32];
-  for (int j = 0; j < k; ++j) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(int64_t)j * nblk + b];
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-      h[j] = s;
-      if (copy_last && j == k - 1) *copy_last = s;
-    }
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nchunk; b += blockDim.x) acc += partial[(int64_t)j * nchunk + b];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    h[j] = s;
+    if (copy_last && j == k - 1) *copy_last = s;
   }
 }
 
@@ -352,9 +353,16 @@ int grid_for(int64_t n) {
 
 void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                      double* partial, double* h, double* copy_last, cudaStream_t st) {
+  if (k <= 0) return;
   count_launch(2);
-  multidot_partial<<<kRedBlocks, kThreads, 0, st>>>(V, ldv, k, w, n, partial);
-  multidot_final<<<1, kThreads, 0, st>>>(partial, kRedBlocks, k, h, copy_last);
+  // chunks of at least 2048 elements, at most kRedBlocks of them per vector
+  int64_t chunk = (n + kRedBlocks - 1) / kRedBlocks;
+  if (chunk < 2048) chunk = 2048;
+  chunk = (chunk + kThreads - 1) / kThreads * kThreads;
+  int nchunk = (int)((n + chunk - 1) / chunk);
+  if (nchunk < 1) nchunk = 1;
+  multidot_partial<<<dim3(nchunk, k), kThreads, 0, st>>>(V, ldv, w, n, chunk, partial);
+  multidot_final<<<k, 128, 0, st>>>(partial, nchunk, k, h, copy_last);
 }
 
 void launch_multi_axpy(const double* V, int64_t ldv, int k, const double* h, double* w, int64_t n,

@@ -7,12 +7,15 @@
 
 namespace dmrg3s {
 
-// Number of CTAs of the reductions (two per SM of the 152-SM GB300).
+// Most chunks a vector is split into by the reductions (two per SM of the
+// 152-SM GB300).
 constexpr int kRedBlocks = 304;
 
 // h[j] = <V_j, w> for j < k with V_j = V + j * ldv.  Deterministic two-pass
-// reduction through `partial` (kRedBlocks * k doubles).  When `copy_last` is
-// non-null, h[k-1] is also stored there (the Lanczos alpha_k).
+// reduction: one CTA per (chunk of >= 2048 elements, vector) writes a partial
+// sum into `partial` (room for kRedBlocks * k doubles), then one CTA per
+// vector adds its partials in chunk order.  When `copy_last` is non-null,
+// h[k-1] is also stored there (the Lanczos alpha_k).
 void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                      double* partial, double* h, double* copy_last, cudaStream_t st);
 
@@ -28,8 +31,9 @@ void launch_combine_vectors(const double* V, int64_t ldv, int k, const double* c
 void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2, cudaStream_t st);
 
 // Smallest eigenpair of the symmetric tridiagonal Lanczos matrix of order k
-// (diagonal alpha, off-diagonal beta[0..k-2]) in one thread: Sturm-sequence
-// bisection for the eigenvalue, inverse iteration for the eigenvector.
+// (diagonal alpha, off-diagonal beta[0..k-2]) in one CTA: Sturm multisection
+// (double-float counts) brackets the eigenvalue, one thread runs inverse
+// iteration for the eigenvector and returns its Rayleigh quotient.
 // beta[k-1] is set to sqrt(*nrm2) (the norm of the new residual vector).
 struct TridiagOut {
   double theta, resid, beta_last, nan_seen;
