@@ -165,6 +165,23 @@ def traffic_for(kernel):
     return ent.get("bytes_per_launch")
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest replica's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(flops_per_step, world, ms_per_step):
+    """Whole-job TFLOP/s of `world` independent replicas, each doing flops_per_step
+    per step, timed by the slowest one (ms_per_step)."""
+    return flops_per_step * world / (ms_per_step * 1e-3) / 1e12
+
+
 def run_ours(args):
     import torch
     rank, world, local = _rank_env()
@@ -218,14 +235,10 @@ def run_ours(args):
               for k, name in enumerate(["eigensolver", "expansion", "svd_truncation", "remainder",
                                         "environment", "energy"], start=2)}
     b.dmrg3s_profile(ctx, False)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), world, "cuda")
     flops_step = (g["flops"] + cmb["flops"]) / args.steps
     ms_step = total_ms / args.steps
-    value = flops_step * world / (ms_step * 1e-3) / 1e12
+    value = replica_value(flops_step, world, ms_step)
     pk = peaks()
     prec = args.precision
     peak = pk["fp64"] if prec == "fp64" else pk["tf32"] / (3.0 if prec == "tf32x3" else 1.0)
@@ -266,7 +279,8 @@ def run_ours(args):
             et.append(e0.elapsed_time(e1))
             st.close()
         ems = statistics.mean(et)
-        e2e = {"value": flops_step * world / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+        ems = max_over_ranks(ems, world, "cuda")
+        e2e = {"value": replica_value(flops_step, world, ems), "unit": "TFLOP/s",
                "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
     state.close()
     if rank != 0:
