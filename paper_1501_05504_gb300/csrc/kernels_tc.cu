@@ -217,11 +217,10 @@ __global__ void __launch_bounds__(TNT, 2)
 
   for (int sgi = 0; sgi < task.nseg && ok; ++sgi) {
     const GemmSeg sg = segs[task.seg0 + sgi];
-    for (int k0 = 0; k0 < sg.K && ok; k0 += TBK, ++it) {
+    for (int k0 = 0; k0 < sg.K; k0 += TBK, ++it) {
       const int st = it & 1;
       // stage st and TMEM buffer st were last used by chunk it - 2
-      if (it >= 2) ok = mbar_wait(&bars[st], (uint32_t)(((it - 2) >> 1) & 1));
-      if (!ok) break;
+      if (it >= 2 && ok) ok = mbar_wait(&bars[st], (uint32_t)(((it - 2) >> 1) & 1));
       unsigned char* base = smem + st * kStage;
       unsigned char* a_hi = base;
       unsigned char* a_lo = base + kStageA;
@@ -234,7 +233,13 @@ __global__ void __launch_bounds__(TNT, 2)
       // make the generic-proxy stores visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
+      // one decision for the whole CTA (a wait that timed out in any thread
+      // stops every thread), so that all threads meet the same barriers; a
+      // stage written after a failed wait is never handed to the tensor core
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sah = smem_u32(a_hi), sal = smem_u32(a_lo);
@@ -262,6 +267,7 @@ __global__ void __launch_bounds__(TNT, 2)
         }
       }
     }
+    ok = __syncthreads_and(ok);
   }
   // the last chunk
   if (ok && it > 0) {
@@ -271,6 +277,7 @@ __global__ void __launch_bounds__(TNT, 2)
       drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), ah, al);
     }
   }
+  ok = __syncthreads_and(ok);
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
   } else {
