@@ -347,6 +347,24 @@ def site_from_neutral(spec, device="cuda"):
     return s
 
 
+def product_state(qp, local_states, device="cuda"):
+    """Site tensors (m = 1) of the product state |s_1 ... s_l>; the bond charges
+    add up the local charges from the left (charge 0 at the left end)."""
+    import torch
+    qp = np.asarray(qp, dtype=np.int64).reshape(len(qp), -1)
+    q = np.zeros(qp.shape[1], dtype=np.int64)
+    sites = []
+    for s in local_states:
+        left = Bond(q.reshape(1, -1).copy(), np.array([1], dtype=np.int64))
+        q = q + qp[s]
+        right = Bond(q.reshape(1, -1).copy(), np.array([1], dtype=np.int64))
+        site = Site(qp, left, right)
+        flat = pack_blocks(site.blocks(), {(int(s), 0, 0): np.ones((1, 1))})
+        site.data = torch.from_numpy(flat).to(device)
+        sites.append(site)
+    return sites
+
+
 def env_from_neutral(spec, device="cuda"):
     import torch
     e = Env(spec["t"], Bond.from_neutral(spec["bond"] if "bond" in spec else spec["ket"]))
