@@ -324,9 +324,10 @@ HEFF_WORKLOADS = {
 }
 
 
-def heff_problem(b, name):
-    """Central-site H_eff problem of a larger workload: library MPO site, seeded
-    symmetric environments on the workload's bonds and a random site tensor."""
+def heff_problem_specs(b, name):
+    """Central-site H_eff problem of a larger workload: the library's MPO site,
+    and seeded symmetric environments and a random site tensor (neutral specs)
+    on the workload's bonds."""
     model, n, params, site, seed = HEFF_WORKLOADS[name]
     if model == "hubbard":
         mpo = b.Mpo(b.MODEL_HUBBARD, n, params)
@@ -339,6 +340,11 @@ def heff_problem(b, name):
     Le = si.symmetric_env(rng, W.tl, left, identity_channels=(W.tl.shape[0] - 1,))
     Re = si.symmetric_env(rng, W.tr, right, identity_channels=(0,))
     M = si.random_site(rng, W.qp, left, right)
+    return W, Le, Re, M
+
+
+def heff_problem(b, name):
+    W, Le, Re, M = heff_problem_specs(b, name)
     return W, b.env_from_neutral(Le), b.env_from_neutral(Re), b.site_from_neutral(M)
 
 

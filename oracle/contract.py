@@ -36,6 +36,16 @@ def apply_heff_literal(L, W, R, M):
     return np.einsum("bXx,Ssbc,sxy,cYy->SXY", L, W, M, R, optimize=False)
 
 
+def apply_heff_rows(L, W, R, M, rows):
+    """HA[:, rows, :]: the definition of apply_heff for the listed left bra
+    indices al' only (the same sum, restricted to those output rows), for
+    sampled checks at sizes where the full product is too slow."""
+    Lr = L[:, rows, :]                                   # (w_l, len(rows), m_l)
+    T1 = np.einsum("bXx,sxy->bsXy", Lr, M)               # L . M
+    T2 = np.einsum("Ssbc,bsXy->cSXy", W, T1)             # . W
+    return np.einsum("cSXy,cYy->SXY", T2, R)             # . R
+
+
 def expansion_term_lr(L, W, M, alpha):
     """P_i = alpha L_{i-1} M_i W_i in (d, m_{i-1}, w_i m_i)  (Eq. subexp-ourt, Sec. IV B).
 

@@ -110,6 +110,19 @@ def _u1_problem(seed, m=24):
     return mpo.W[2], io.env_dense(Le), io.env_dense(Re), left, right
 
 
+def test_heff_rows_equal_the_rows_of_the_unordered_sum():
+    """The row-restricted H_eff equals the matching rows of the literal sum."""
+    rng = np.random.default_rng(7)
+    d, wl, wr, ml, mr = 3, 4, 5, 6, 7
+    L = rng.standard_normal((wl, ml, ml))
+    W = rng.standard_normal((d, d, wl, wr))
+    R = rng.standard_normal((wr, mr, mr))
+    M = rng.standard_normal((d, ml, mr))
+    rows = [5, 0, 3]
+    full = contract.apply_heff_literal(L, W, R, M)
+    assert np.abs(contract.apply_heff_rows(L, W, R, M, rows) - full[:, rows, :]).max() < 1e-12
+
+
 def test_heff_symmetric_on_symmetric_environments():
     W, Le, Re, left, right = _u1_problem(7)
     rng = np.random.default_rng(8)
