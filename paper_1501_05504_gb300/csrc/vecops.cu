@@ -234,41 +234,46 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
   // inverse iteration: solve (T - theta I) z = y with a pivoted tridiagonal LU
   // (partial pivoting keeps the elimination stable at the near-singular shift);
   // an exactly zero pivot is replaced by 1e-15 of the matrix scale, which keeps
-  // the solution finite (of order 1e15 times the scale) before normalisation
+  // the solution finite (of order 1e15 times the scale) before normalisation.
+  // The shift is the same in every sweep, so the matrix is factored once and
+  // the pivots are inverted once; a sweep is then two substitutions without
+  // divisions (FP64 division is the long pole of this one-thread chain).
   const double tiny = 1e-15 * fmax(span, fmax(fabs(lo), fabs(hi)));
   double dl[128], dd[128], du[128], du2[128];
   int piv[128];
-  for (int i = 0; i < kk; ++i) y[i] = 1.0 / sqrt((double)kk);
-  for (int sweep = 0; sweep < 3; ++sweep) {
-    for (int i = 0; i < kk; ++i) {
-      dd[i] = alpha[i] - theta;
-      du[i] = i < kk - 1 ? beta[i] : 0.0;
-      dl[i] = i < kk - 1 ? beta[i] : 0.0;
-      du2[i] = 0.0;
-    }
-    for (int i = 0; i < kk - 1; ++i) {
-      if (fabs(dd[i]) >= fabs(dl[i])) {
-        piv[i] = i;
-        if (dd[i] == 0.0) dd[i] = tiny;
-        const double f = dl[i] / dd[i];
-        dl[i] = f;
-        dd[i + 1] -= f * du[i];
-      } else {
-        piv[i] = i + 1;
-        const double f = dd[i] / dl[i];
-        dd[i] = dl[i];
-        dl[i] = f;
-        const double t = du[i];
-        du[i] = dd[i + 1];
-        dd[i + 1] = t - f * dd[i + 1];
-        if (i < kk - 2) {
-          du2[i] = du[i + 1];
-          du[i + 1] = -f * du[i + 1];
-        }
+  for (int i = 0; i < kk; ++i) {
+    dd[i] = alpha[i] - theta;
+    du[i] = i < kk - 1 ? beta[i] : 0.0;
+    dl[i] = i < kk - 1 ? beta[i] : 0.0;
+    du2[i] = 0.0;
+  }
+  for (int i = 0; i < kk - 1; ++i) {
+    if (fabs(dd[i]) >= fabs(dl[i])) {
+      piv[i] = i;
+      if (dd[i] == 0.0) dd[i] = tiny;
+      const double f = dl[i] / dd[i];
+      dl[i] = f;
+      dd[i + 1] -= f * du[i];
+    } else {
+      piv[i] = i + 1;
+      const double f = dd[i] / dl[i];
+      dd[i] = dl[i];
+      dl[i] = f;
+      const double t = du[i];
+      du[i] = dd[i + 1];
+      dd[i + 1] = t - f * dd[i + 1];
+      if (i < kk - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
       }
     }
-    for (int i = 0; i < kk; ++i)
-      if (dd[i] == 0.0) dd[i] = tiny;
+  }
+  for (int i = 0; i < kk; ++i) {
+    if (dd[i] == 0.0) dd[i] = tiny;
+    dd[i] = 1.0 / dd[i];               // dd now holds the inverted pivots
+  }
+  for (int i = 0; i < kk; ++i) y[i] = 1.0 / sqrt((double)kk);
+  for (int sweep = 0; sweep < 3; ++sweep) {
     // forward: apply row interchanges and L
     for (int i = 0; i < kk - 1; ++i) {
       if (piv[i] == i) {
@@ -279,11 +284,11 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
         y[i + 1] = t - dl[i] * y[i];
       }
     }
-    // back substitution with U (diagonal dd, super du, second super du2)
-    y[kk - 1] /= dd[kk - 1];
-    if (kk > 1) y[kk - 2] = (y[kk - 2] - du[kk - 2] * y[kk - 1]) / dd[kk - 2];
+    // back substitution with U (inverted diagonal dd, super du, second super du2)
+    y[kk - 1] *= dd[kk - 1];
+    if (kk > 1) y[kk - 2] = (y[kk - 2] - du[kk - 2] * y[kk - 1]) * dd[kk - 2];
     for (int i = kk - 3; i >= 0; --i)
-      y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / dd[i];
+      y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * dd[i];
     // normalise: scale by the largest component first (no overflow in the squares)
     double big = 0.0;
     for (int i = 0; i < kk; ++i) big = fmax(big, fabs(y[i]));
