@@ -322,6 +322,14 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
     delete c;
     return DMRG3S_ERR_CUDA;
   }
+  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFreeHost(c->pinned);
+    cudaFree(c->ws);
+    delete c;
+    return DMRG3S_ERR_CUDA;
+  }
   *ctx = reinterpret_cast<dmrg3s_ctx>(c);
   return DMRG3S_OK;
 }
@@ -335,6 +343,9 @@ dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
   if (c->ws) cudaFree(c->ws);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->d_err) cudaFree(c->d_err);
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
   return DMRG3S_OK;
 }

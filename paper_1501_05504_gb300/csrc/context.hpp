@@ -98,6 +98,8 @@ struct Context {
   size_t ws_bytes = 0;
   double* pinned = nullptr;     // small pinned host buffer for scalar read-backs (64 doubles)
   int* d_err = nullptr;         // device error word latched by bounded waits (tensor-core kernel)
+  cudaStream_t aux = nullptr;   // side stream: the Lanczos tridiagonal solve beside the next product
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;
   std::string last_error;
 };

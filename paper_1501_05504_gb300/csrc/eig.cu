@@ -63,33 +63,57 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   if (!(c->pinned[0] > 0.0)) return fail(c, DMRG3S_ERR_BREAKDOWN, "zero start vector");
   launch_normalise(x, V, n, nrm2, st);
 
+  // Iteration k: w = H v_k was enqueued before; orthogonalise, then solve the
+  // tridiagonal problem on the side stream while the main stream already
+  // normalises v_{k+1} and applies H to it.  If iteration k turns out to be
+  // the last, that product is discarded (its flops are not counted).
   int k = 0;
   TridiagOut res{};
+  dmrg3s_status rs = run_plan(c, heff, Ldata, V, ws1, ws2, 1.0, ws2, Rdata, w, st, prec, &hints);
+  if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
   for (;; ++k) {
-    double* vk = V + (int64_t)k * n;
-    dmrg3s_status rs = run_plan(c, heff, Ldata, vk, ws1, ws2, 1.0, ws2, Rdata, w, st, prec, &hints);
-    if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
     launch_multidot(V, n, k + 1, w, n, part, h, alpha + k, st);   // alpha_k = <v_k, H v_k>
     launch_multi_axpy(V, n, k + 1, h, w, n, st);
     launch_multidot(V, n, k + 1, w, n, part, h, nullptr, st);     // second Gram-Schmidt pass
     launch_multi_axpy(V, n, k + 1, h, w, n, st);
     launch_multidot(w, 0, 1, w, n, part, nrm2, nullptr, st);
-    launch_tridiag_smallest(alpha, beta, k + 1, nrm2, y, out, st);
-    cudaMemcpyAsync(c->pinned, out, sizeof(TridiagOut), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(c->pinned + 8, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos step");
+    cudaEventRecord(c->ev_ready, st);
+    cudaStreamWaitEvent(c->aux, c->ev_ready, 0);
+    launch_tridiag_smallest(alpha, beta, k + 1, nrm2, y, out, c->aux);
+    cudaMemcpyAsync(c->pinned, out, sizeof(TridiagOut), cudaMemcpyDeviceToHost, c->aux);
+    cudaMemcpyAsync(c->pinned + 8, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->aux);
+    cudaEventRecord(c->ev_done, c->aux);
+    // speculative: the next basis vector and its product
+    const bool spec = k + 1 < kmax;
+    size_t rec0 = c->prof.recs.size();
+    if (spec) {
+      launch_normalise(w, V + (int64_t)(k + 1) * n, n, nrm2, st);
+      rs = run_plan(c, heff, Ldata, V + (int64_t)(k + 1) * n, ws1, ws2, 1.0, ws2, Rdata, w, st,
+                    prec, &hints);
+      if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
+    }
+    if (cudaEventSynchronize(c->ev_done) != cudaSuccess)
+      return fail(c, DMRG3S_ERR_CUDA, "Lanczos step");
     std::memcpy(&res, c->pinned, sizeof(res));
     int dev_err = 0;
     std::memcpy(&dev_err, c->pinned + 8, sizeof(int));
     if (dev_err) {
+      cudaStreamSynchronize(st);
       cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
       return fail(c, DMRG3S_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
     }
     if (res.nan_seen != 0.0) return fail(c, DMRG3S_ERR_NUMERIC, "NaN in the Lanczos recursion");
     const bool conv = res.resid <= tol * std::fmax(1.0, std::fabs(res.theta));
-    if (conv || res.beta_last < 1e-14 || k + 1 == kmax) break;
-    launch_normalise(w, V + (int64_t)(k + 1) * n, n, nrm2, st);
+    if (conv || res.beta_last < 1e-14 || k + 1 == kmax) {
+      for (size_t r = rec0; r < c->prof.recs.size(); ++r) {   // the discarded product
+        c->prof.recs[r].flops = 0.0;
+        c->prof.recs[r].bytes = 0.0;
+      }
+      break;
+    }
   }
+  // y was written on the side stream
+  cudaStreamWaitEvent(st, c->ev_done, 0);
   // Ritz vector x = V y, normalised
   launch_combine_vectors(V, n, k + 1, y, w, n, st);
   launch_multidot(w, 0, 1, w, n, part, nrm2, nullptr, st);
