@@ -335,7 +335,11 @@ typedef struct dmrg3s_update_info {
  * right_env are the boundary environments L_0 / R_{l+1} (device data, copied);
  * NULL means the trivial 1x1x1 environment equal to 1, which requires bond
  * and MPO bond dimension 1 there.  All environments up to the centre are
- * built on the device.  Synchronous.  Errors: ARG, SHAPE, QN, CUDA, OOM. */
+ * built on the device.  The truncation's per-sector SVDs run on several
+ * streams at once, each with its own cuSOLVER handle and host thread: about
+ * one per four charge sectors, at least four, at most 8 (or the value 1..16
+ * of the environment variable DMRG3S_SVD_STREAMS read here).
+ * Synchronous.  Errors: ARG, SHAPE, QN, CUDA, OOM. */
 dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_mpo_site* W,
                                   const dmrg3s_site* M, const dmrg3s_env* left_env,
                                   const dmrg3s_env* right_env, int32_t centre,

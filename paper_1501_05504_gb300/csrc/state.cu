@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 #include <tuple>
@@ -53,7 +54,19 @@ struct SvdWorker {
   size_t dbytes = 0;
   std::vector<char> hwork;
 };
-constexpr int kSvdWorkers = 4;
+constexpr int kSvdWorkers = 8;      // default number of concurrent SVD lanes
+
+// Lanes of a new state: DMRG3S_SVD_STREAMS (1..16) when set, else the default.
+// A truncation uses about one lane per four charge sectors, at least four
+// (one large sector then runs beside the rest) and at most the state's lanes:
+// measured on GB300, four lanes suit the 14 sectors of an m=512 XXZ update
+// (more add contention), eight the many mid-size sectors of the Hubbard chain.
+int svd_lanes() {
+  const char* e = std::getenv("DMRG3S_SVD_STREAMS");
+  if (!e) return kSvdWorkers;
+  const int v = std::atoi(e);
+  return v < 1 ? 1 : (v > 16 ? 16 : v);
+}
 
 struct State {
   Context* c = nullptr;
@@ -295,7 +308,10 @@ dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, 
   std::sort(order.begin(), order.end(), [&](int a, int b) {
     return (double)secs[a].m * secs[a].n * secs[a].n > (double)secs[b].m * secs[b].n * secs[b].n;
   });
-  const int nw = (int)S.svd.size();
+  const int lanes = (int)S.svd.size();
+  int nw = (int)secs.size() / 4;
+  if (nw < 4) nw = 4;
+  if (nw > lanes) nw = lanes;
   std::vector<std::vector<int>> jobs(nw);
   std::vector<double> load(nw, 0.0);
   for (int k : order) {
@@ -811,7 +827,7 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
     cudaMemcpyAsync(S->M[i].data, M[i].data, (size_t)S->M[i].lay.size * sizeof(double),
                     cudaMemcpyDeviceToDevice, st);
   }
-  S->svd.resize(kSvdWorkers);
+  S->svd.resize(svd_lanes());
   for (SvdWorker& w : S->svd) {
     if (cusolverDnCreate(&w.h) != CUSOLVER_STATUS_SUCCESS ||
         cusolverDnCreateParams(&w.p) != CUSOLVER_STATUS_SUCCESS ||
