@@ -324,7 +324,7 @@ HEFF_WORKLOADS = {
 }
 
 
-def heff_problem_specs(b, name):
+def heff_problem_specs(b, name, m=None):
     """Central-site H_eff problem of a larger workload: the library's MPO site,
     and seeded symmetric environments and a random site tensor (neutral specs)
     on the workload's bonds."""
@@ -335,7 +335,7 @@ def heff_problem_specs(b, name):
         bonds = cylinder_bonds()
         mpo = b.Mpo(b.MODEL_SPIN_BONDS, n, (), bonds=bonds, couplings=[(1.0, 1.0)] * len(bonds))
     W = mpo.site(site)
-    left, right = si.central_bonds(name)
+    left, right = si.central_bonds(name, m)
     rng = si.rng_for(seed)
     Le = si.symmetric_env(rng, W.tl, left, identity_channels=(W.tl.shape[0] - 1,))
     Re = si.symmetric_env(rng, W.tr, right, identity_channels=(0,))
@@ -343,8 +343,8 @@ def heff_problem_specs(b, name):
     return W, Le, Re, M
 
 
-def heff_problem(b, name):
-    W, Le, Re, M = heff_problem_specs(b, name)
+def heff_problem(b, name, m=None):
+    W, Le, Re, M = heff_problem_specs(b, name, m)
     return W, b.env_from_neutral(Le), b.env_from_neutral(Re), b.site_from_neutral(M)
 
 
@@ -352,7 +352,7 @@ def run_heff_only(args):
     """Kernel view: repeated H_eff applications on a workload's central site."""
     import torch
     from paper_1501_05504_gb300 import binding as b
-    ctx = b.dmrg3s_create(torch.cuda.current_device(), 4 << 30)
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), int(args.workspace_gb * (1 << 30)))
     if args.workload == WORKLOAD:
         spec = window_specs(SEED)
         mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
@@ -362,7 +362,7 @@ def run_heff_only(args):
         gR0 = b.empty_env(W0.tr, gM0.right)                     # right environment of site 50
         b.dmrg3s_update_env(ctx, -1, gR, W1, gM1, gR0, "fp64")
     else:
-        W0, gL, gR0, gM0 = heff_problem(b, args.workload)
+        W0, gL, gR0, gM0 = heff_problem(b, args.workload, args.workload_m)
     gH = b.empty_site_like(gM0.qp, gM0.left, gM0.right)
     for _ in range(args.warmup):
         b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, args.precision)
@@ -385,6 +385,7 @@ def run_heff_only(args):
     gemm_tf = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else None
     ctx.close()
     return {"metric": "H_eff application on the %s central site (kernel view)" % args.workload,
+            "m": int(sum(gM0.left.dim)),
             "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_heff": ms,
             "flops_per_heff": flops, "precision": args.precision, "w": int(W0.W.shape[2]),
             "d": int(W0.W.shape[0]), "sectors": [len(gM0.left.dim), len(gM0.right.dim)],
@@ -528,6 +529,10 @@ def main():
                     help="kernel view: time repeated H_eff applications instead of local updates")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD] + sorted(HEFF_WORKLOADS),
                     help="central-site problem of the kernel view (--heff-only)")
+    ap.add_argument("--workload-m", type=int, default=None,
+                    help="bond dimension of the kernel view's problem (default: the workload's)")
+    ap.add_argument("--workspace-gb", type=float, default=4.0,
+                    help="context workspace of the kernel view, GiB")
     ap.add_argument("--sweep", action="store_true",
                     help="sweep-to-1e-9 time of full sweeps, mixed ladder vs FP64")
     ap.add_argument("--sweep-sites", type=int, default=100)
