@@ -132,20 +132,23 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   };
   const SplitHints none;
   const SplitHints& hn = hints ? *hints : none;
+  // the tensor-core stages write double-float pairs (8 bytes per element, in
+  // place of the FP64 intermediates), combined on the FP32 pipe
+  float2* t1p = reinterpret_cast<float2*>(ws1);
   if (!hn.g1A) launch_split(g1A, hi(sl.a1), lo(sl.a1, h.nA1), h.nA1, st);
   if (!hn.g1B) launch_split(g1B, hi(sl.b1), lo(sl.b1, h.nB1), h.nB1, st);
   if (!h.g1.tiles.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
     launch_gemm_tc(passes, h.g1.ta, h.g1.tb, p.g1_tiles_tc, (int)h.g1.tiles_tc.size(), p.g1_tasks,
-                   p.g1_segs, hi(sl.a1), lo(sl.a1, h.nA1), hi(sl.b1), lo(sl.b1, h.nB1), ws1,
+                   p.g1_segs, hi(sl.a1), lo(sl.a1, h.nA1), hi(sl.b1), lo(sl.b1, h.nB1), t1p,
                    c->d_err, st);
     if (id >= 0) pr.end(id, st);
   }
   if (!h.has_g3) {
     if (!h.c2.chunks.empty()) {
       const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
-      launch_combine_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1,
-                         c2out, c2scale, st);
+      launch_combine_pairs_f64(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms,
+                               t1p, c2out, c2scale, st);
       if (id >= 0) pr.end(id, st);
     }
     return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
@@ -153,8 +156,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   // stage 2 writes T2 directly as a split operand of stage 3
   if (!h.c2.chunks.empty()) {
     const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
-    launch_combine_split(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, ws1,
-                         hi(sl.t2s), lo(sl.t2s, h.ws2), c2scale, st);
+    launch_combine_pairs_split(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, t1p,
+                               hi(sl.t2s), lo(sl.t2s, h.ws2), c2scale, st);
     if (id >= 0) pr.end(id, st);
   }
   // stage 3: the operand that is T2 (ws2 in the FP64 layout) uses the split T2;
@@ -181,7 +184,7 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   operand(g3A, sl.a3, h.nA3, hn.g3A, &a3h, &a3l);
   operand(g3B, sl.b3, h.nB3, hn.g3B, &b3h, &b3l);
   // split-K: one CTA per (tile, K-segment) into FP64 partials, then a fixed-order sum
-  double* part = base + sl.p3;
+  float2* part = reinterpret_cast<float2*>(base + sl.p3);
   if (!h.g3s.tiles_tc.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g3s.flops, h.g3s.bytes, st) : -1;
     launch_gemm_tc(passes, h.g3s.ta, h.g3s.tb, p.g3s_tiles, (int)h.g3s.tiles_tc.size(),
@@ -190,8 +193,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   }
   if (!h.c3r.chunks.empty()) {
     const int id = pr.on ? pr.begin(kProfCombine, 0.0, 0.0, st) : -1;
-    launch_combine_f64(p.c3r_chunks, (int)h.c3r.chunks.size(), p.c3r_tasks, p.c3r_terms, part,
-                       g3C, 1.0, st);
+    launch_combine_pairs_f64(p.c3r_chunks, (int)h.c3r.chunks.size(), p.c3r_tasks, p.c3r_terms,
+                             part, g3C, 1.0, st);
     if (id >= 0) pr.end(id, st);
   }
   return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;

@@ -36,8 +36,11 @@ struct CombTask {
 };
 struct CombTerm {
   int64_t offIn;
-  int32_t ldi, pad;
+  int32_t ldi;
+  float chi;        // coef = chi + clo (FP32 pair, filled by the planner)
   double coef;
+  float clo;
+  int32_t pad;
 };
 // Work unit of the combination kernel: up to kCombRows rows of one task.
 struct CombChunk {
@@ -70,21 +73,28 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
 // out = scale * sum_k coef_k in_k for every task.
 // Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32).  The
 // operands are pre-split FP32 arrays (hi = tf32(x), lo = tf32(x - hi)) with
-// the offsets of the FP64 layout; lo may be null when passes == 1.  C is FP64.
+// the offsets of the FP64 layout; lo may be null when passes == 1.  C
+// receives every output element as a double-float pair (hi, lo) at the
+// element offset of the FP64 layout (8 bytes, like the double it stands for).
 // err is a device flag set to 1 when a bounded wait timed out.
 void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
                     const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
-                    const float* Alo, const float* Bhi, const float* Blo, double* C, int* err,
+                    const float* Alo, const float* Bhi, const float* Blo, float2* C, int* err,
                     cudaStream_t st);
 
 // hi[i] = tf32(x[i]), lo[i] = tf32(x[i] - hi[i]) (the 3xTF32 split of an FP64 array).
 void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t st);
 
-// As launch_combine_f64, but the output is written split (hi, lo) for a
-// following tensor-core stage instead of in FP64.
-void launch_combine_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
-                          const CombTerm* terms, const double* in, float* out_hi,
-                          float* out_lo, double scale, cudaStream_t st);
+// Combinations of double-float pair inputs (the tensor-core outputs), in
+// double-float arithmetic on the FP32 pipe: out = scale * sum_k coef_k in_k.
+// _split writes the result as the 3xTF32 split operand (hi, lo; lo may be
+// null) of a following tensor-core stage, _f64 writes FP64.
+void launch_combine_pairs_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                                const CombTerm* terms, const float2* in, float* out_hi,
+                                float* out_lo, double scale, cudaStream_t st);
+void launch_combine_pairs_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                              const CombTerm* terms, const float2* in, double* out,
+                              double scale, cudaStream_t st);
 
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
                         const CombTerm* terms, const double* in, double* out, double scale,

@@ -120,32 +120,75 @@ __global__ void __launch_bounds__(256) combine_f64_kernel(const CombChunk* __res
   }
 }
 
-__global__ void __launch_bounds__(256) combine_split_kernel(const CombChunk* __restrict__ chunks,
-                                                           const CombTask* __restrict__ tasks,
-                                                           const CombTerm* __restrict__ terms,
-                                                           const double* __restrict__ in,
-                                                           float* __restrict__ out_hi,
-                                                           float* __restrict__ out_lo,
-                                                           double scale) {
+// ---- double-float combinations (inputs: tensor-core output pairs) ----
+// Knuth's two-sum and an FMA-based product keep ~48 bits; all on the FP32
+// pipe (the intrinsics also keep the compiler from contracting the sums).
+__device__ __forceinline__ void df_acc(float ch, float cl, float2 x, float& ah, float& al) {
+  const float p = __fmul_rn(ch, x.x);
+  float pe = __fmaf_rn(ch, x.x, -p);
+  pe = __fmaf_rn(ch, x.y, pe);
+  pe = __fmaf_rn(cl, x.x, pe);
+  const float s = __fadd_rn(ah, p);
+  const float bb = __fsub_rn(s, ah);
+  float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  e = __fadd_rn(e, __fadd_rn(al, pe));
+  ah = __fadd_rn(s, e);
+  al = __fsub_rn(e, __fsub_rn(ah, s));
+}
+
+// sum_k coef_k in_k for output element (r, c) of a chunk's task, as a pair
+__device__ __forceinline__ void df_combine(const CombTask& t, const CombTerm* __restrict__ terms,
+                                           const float2* __restrict__ in, int r, int c, float sh,
+                                           float sl, float& ah, float& al) {
+  ah = 0.f;
+  al = 0.f;
+  for (int k = 0; k < t.nt; ++k) {
+    const CombTerm tm = terms[t.t0 + k];
+    df_acc(tm.chi, tm.clo, in[tm.offIn + (int64_t)r * tm.ldi + c], ah, al);
+  }
+  if (sh != 1.f || sl != 0.f) {
+    const float h = ah, l = al;
+    ah = 0.f;
+    al = 0.f;
+    df_acc(sh, sl, make_float2(h, l), ah, al);
+  }
+}
+
+__global__ void __launch_bounds__(256) combine_pairs_split_kernel(
+    const CombChunk* __restrict__ chunks, const CombTask* __restrict__ tasks,
+    const CombTerm* __restrict__ terms, const float2* __restrict__ in, float* __restrict__ out_hi,
+    float* __restrict__ out_lo, float sh, float sl) {
   const CombChunk ch = chunks[blockIdx.x];
   const CombTask t = tasks[ch.task];
   const int n = ch.nrows * t.cols;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int r = ch.row0 + idx / t.cols, c = idx % t.cols;
-    double acc = 0.0;
-    for (int k = 0; k < t.nt; ++k) {
-      const CombTerm tm = terms[t.t0 + k];
-      acc = fma(tm.coef, in[tm.offIn + (int64_t)r * tm.ldi + c], acc);
-    }
-    acc *= scale;
+    float ah, al;
+    df_combine(t, terms, in, r, c, sh, sl, ah, al);
     uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"((float)acc));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(ah));
     const float hf = __uint_as_float(h);
+    // ah - hf is exact (hf is ah rounded to the 10-bit TF32 mantissa)
     uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"((float)(acc - (double)hf)));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fadd_rn(__fsub_rn(ah, hf), al)));
     const int64_t o = t.offOut + (int64_t)r * t.ldo + c;
     out_hi[o] = hf;
     if (out_lo) out_lo[o] = __uint_as_float(l);
+  }
+}
+
+__global__ void __launch_bounds__(256) combine_pairs_f64_kernel(
+    const CombChunk* __restrict__ chunks, const CombTask* __restrict__ tasks,
+    const CombTerm* __restrict__ terms, const float2* __restrict__ in, double* __restrict__ out,
+    float sh, float sl) {
+  const CombChunk ch = chunks[blockIdx.x];
+  const CombTask t = tasks[ch.task];
+  const int n = ch.nrows * t.cols;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int r = ch.row0 + idx / t.cols, c = idx % t.cols;
+    float ah, al;
+    df_combine(t, terms, in, r, c, sh, sl, ah, al);
+    out[t.offOut + (int64_t)r * t.ldo + c] = (double)ah + (double)al;
   }
 }
 
@@ -195,12 +238,23 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
     gemm_f64_kernel<Trans::T, Trans::T><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
 }
 
-void launch_combine_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
-                          const CombTerm* terms, const double* in, float* out_hi,
-                          float* out_lo, double scale, cudaStream_t st) {
+void launch_combine_pairs_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                                const CombTerm* terms, const float2* in, float* out_hi,
+                                float* out_lo, double scale, cudaStream_t st) {
   if (nchunks <= 0) return;
   count_launch();
-  combine_split_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out_hi, out_lo, scale);
+  const float sh = (float)scale, sl = (float)(scale - (double)sh);
+  combine_pairs_split_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out_hi, out_lo, sh,
+                                                      sl);
+}
+
+void launch_combine_pairs_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
+                              const CombTerm* terms, const float2* in, double* out,
+                              double scale, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  count_launch();
+  const float sh = (float)scale, sl = (float)(scale - (double)sh);
+  combine_pairs_f64_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out, sh, sl);
 }
 
 void launch_combine_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,

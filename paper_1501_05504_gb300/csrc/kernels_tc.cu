@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(TNT, 2)
     gemm_tc_kernel(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                    const GemmSeg* __restrict__ segs, const float* __restrict__ Ahi,
                    const float* __restrict__ Alo, const float* __restrict__ Bhi,
-                   const float* __restrict__ Blo, double* __restrict__ C, int* __restrict__ err) {
+                   const float* __restrict__ Blo, float2* __restrict__ C, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr bool kLo = kPasses == 3;
   constexpr int kStage = (kStageA + kStageB) * (kLo ? 2 : 1);
@@ -284,11 +284,11 @@ __global__ void __launch_bounds__(TNT, 2)
     // ---- epilogue: thread (warp, lane) owns accumulator row 32 warp + lane
     const int gm = m0 + warp * 32 + lane;
     if (gm < task.M) {
-      double* crow = C + task.offC + (int64_t)gm * task.ldc + n0;
+      float2* crow = C + task.offC + (int64_t)gm * task.ldc + n0;
       const int nv = task.N - n0 < TBN ? task.N - n0 : TBN;
 #pragma unroll
       for (int j = 0; j < TBN; ++j)
-        if (j < nv) crow[j] = (double)ah[j] + (double)al[j];
+        if (j < nv) crow[j] = make_float2(ah[j], al[j]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -312,7 +312,7 @@ __global__ void split_kernel(const double* __restrict__ x, float* __restrict__ h
 
 template <Trans TA, Trans TB, int P>
 void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const GemmSeg* segs,
-                const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
+                const float* Ah, const float* Al, const float* Bh, const float* Bl, float2* C,
                 int* err, cudaStream_t st) {
   constexpr int kLo = P == 3 ? 1 : 0;
   constexpr int smem = 2 * (kStageA + kStageB) * (1 + kLo);
@@ -337,7 +337,7 @@ void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t
 
 void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
                     const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
-                    const float* Alo, const float* Bhi, const float* Blo, double* C, int* err,
+                    const float* Alo, const float* Bhi, const float* Blo, float2* C, int* err,
                     cudaStream_t st) {
   if (ntiles <= 0) return;
   count_launch();

@@ -59,7 +59,11 @@ void CombStage::add(int64_t offOut, int ldo, int rows, int cols, const std::vect
   task.nt = (int32_t)t.size();
   const int id = (int)tasks.size();
   tasks.push_back(task);
-  terms.insert(terms.end(), t.begin(), t.end());
+  for (CombTerm tm : t) {
+    tm.chi = (float)tm.coef;
+    tm.clo = (float)(tm.coef - (double)tm.chi);
+    terms.push_back(tm);
+  }
   flops += 2.0 * rows * (double)cols * t.size();
   bytes += 8.0 * rows * (double)cols * (1 + t.size());
   for (int r = 0; r < rows; r += kCombRows)
