@@ -11,12 +11,13 @@
 //   kPasses = 3: C = A_hi B_hi + A_hi B_lo + A_lo B_hi          (3xTF32)
 //
 // CTA tile 128 x 64 (M x N), K chunks of 32, two shared-memory stages and two
-// TMEM accumulator buffers.  All 128 threads load and convert; one thread
-// issues tcgen05.mma and commits each stage to an mbarrier; while the tensor
-// core works on chunk k the four warps drain chunk k-1's FP32 accumulator
-// (tcgen05.ld) into FP64 registers.  Every wait on an mbarrier is bounded: on
-// time-out the CTA records an error code, frees its tensor memory and
-// returns.
+// TMEM accumulator buffers.  All 128 threads load the operand tiles; one
+// thread issues tcgen05.mma and commits each stage to an mbarrier; while the
+// tensor core works on chunk k the four warps drain chunk k-1's FP32
+// accumulator (tcgen05.ld) into double-float registers.  Each output element
+// is stored as its (hi, lo) FP32 pair, for the double-float combinations that
+// consume it.  Every wait on an mbarrier is bounded: on time-out the CTA
+// records an error code, frees its tensor memory and returns.
 #include <cstdint>
 
 #include "kernels.hpp"
