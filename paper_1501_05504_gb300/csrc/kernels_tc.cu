@@ -18,6 +18,7 @@
 // is stored as its (hi, lo) FP32 pair, for the double-float combinations that
 // consume it.  Every wait on an mbarrier is bounded: on time-out the CTA
 // records an error code, frees its tensor memory and returns.
+#include <atomic>
 #include <cstdint>
 
 #include "kernels.hpp"
@@ -317,11 +318,15 @@ void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const 
                 int* err, cudaStream_t st) {
   constexpr int kLo = P == 3 ? 1 : 0;
   constexpr int smem = 2 * (kStageA + kStageB) * (1 + kLo);
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory limit is a per-device attribute of the kernel
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (!bit || !(done.load() & bit)) {
     cudaFuncSetAttribute(gemm_tc_kernel<TA, TB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem);
-    attr = true;
+    if (bit) done.fetch_or(bit);
   }
   gemm_tc_kernel<TA, TB, P><<<ntiles, TNT, smem, st>>>(tiles, tasks, segs, Ah, Al, Bh, Bl, C, err);
 }
