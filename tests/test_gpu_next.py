@@ -7,7 +7,8 @@
   ground energy (sparse exact diagonalisation in the S^z = 0 sector).
 * Free fermions at full length: the open XX chain with L = 100 (the XXZ MPO
   at Delta = 0) against the closed-form energy of the filled single-particle
-  levels.
+  levels, and the half-filled U = 0 Hubbard chain (d = 4, U(1)xU(1) blocks,
+  Jordan-Wigner MPO) against its closed form.
 """
 import pytest
 
@@ -59,4 +60,15 @@ def test_xx_chain_l100_closed_form(b, ctx):
     rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 12, 1e-11, b.update_opts(256))
     st.close()
     e0 = exact.xx_chain_energy(L, 1.0)
+    assert abs(rep["energy"] - e0) < 1e-8 * abs(e0)
+
+
+def test_hubbard_u0_closed_form(b, ctx):
+    L = 32
+    W = b.Mpo(b.MODEL_HUBBARD, L, (1.0, 0.0)).sites()
+    st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [2, 1] * (L // 2)), None, None,
+                               L - 1)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 12, 1e-11, b.update_opts(512))
+    st.close()
+    e0 = exact.free_fermion_energy(L, L // 2, L // 2)
     assert abs(rep["energy"] - e0) < 1e-8 * abs(e0)
