@@ -269,9 +269,13 @@ dmrg3s_status dmrg3s_mpo_grad_site(dmrg3s_ctx ctx, const dmrg3s_env* L, const dm
  * Rayleigh quotient of the resulting vector.  M: start vector on input, the
  * normalised Ritz vector on output.  Stops when the Ritz residual
  * |beta_k y_k| <= tol * max(1, |lambda|), when beta_k < 1e-14 or after kmax
- * (<= 128) products.  Synchronises `stream` once per iteration to test the
- * stopping rule.  Errors: as dmrg3s_apply_heff, plus BREAKDOWN (zero start
- * vector) and NUMERIC (NaN). */
+ * (<= 128) products.  The tridiagonal solve of iteration k runs on a side
+ * stream of the context while `stream` already computes the product of the
+ * next basis vector; the host waits once per iteration for the solve's
+ * result.  When iteration k is the last, that product is discarded (the
+ * profiler does not count its flops), so a run issues one product more
+ * than it reports.  Errors: as dmrg3s_apply_heff, plus BREAKDOWN (zero
+ * start vector) and NUMERIC (NaN). */
 dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
                                 const dmrg3s_env* R, dmrg3s_site* M, int32_t kmax, double tol,
                                 dmrg3s_precision prec, double* lambda, int32_t* iters,
