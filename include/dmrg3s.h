@@ -63,11 +63,13 @@ typedef enum dmrg3s_status {
 } dmrg3s_status;
 
 /* Arithmetic of the block products (stages 1 and 3 of the order of Sec. V).
- * The MPO combination (stage 2), the eigensolver's vector algebra, the SVD and
- * all data in memory stay FP64 in every mode.  In the tensor-core modes each
- * FP64 operand element is split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi)
- * while it is staged in shared memory; 3xTF32 sums hi*hi + hi*lo + lo*hi
- * (relative error of a block product ~1e-6), TF32 only hi*hi (~1e-3). */
+ * The eigensolver's vector algebra, the SVD and all data the caller sees stay
+ * FP64 in every mode.  In the tensor-core modes each FP64 operand is split
+ * once into two FP32 arrays, x = hi + lo with hi = tf32(x), lo = tf32(x - hi);
+ * 3xTF32 sums hi*hi + hi*lo + lo*hi (relative error of a block product
+ * ~1e-6), TF32 only hi*hi (~1e-3); the block products leave double-float
+ * (FP32 pair) results, which the MPO combination (stage 2) and the split-K
+ * sum combine in double-float arithmetic (~48 bits). */
 typedef enum dmrg3s_precision {
   DMRG3S_FP64 = 0,    /* double precision on the CUDA cores                          */
   DMRG3S_TF32X3 = 1,  /* 3xTF32 split products on tcgen05 tensor cores, FP32 accum.  */
@@ -137,8 +139,9 @@ dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
  * 4: gather + SVD + new tensors, 5: S V^dagger into the neighbour,
  * 6: environment update, 7: energy after truncation; flops and bytes are 0
  * for phases), and around the other FP64 grouped GEMMs (kernel 8: the
- * truncation's S V^dagger products and the MPO-entry gradient).  dmrg3s_profile(ctx, 1) resets and enables, 0
- * disables; dmrg3s_profile_read synchronises on the recorded events and
+ * truncation's S V^dagger products and the MPO-entry gradient).
+ * dmrg3s_profile(ctx, 1) resets and enables, 0 disables;
+ * dmrg3s_profile_read synchronises on the recorded events and
  * returns, for one kernel, the number of launches, their summed device time
  * and their summed algorithmic flops and bytes (each distinct operand block
  * read once, each output written once). */
