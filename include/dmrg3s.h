@@ -345,12 +345,13 @@ typedef struct dmrg3s_update_info {
  * built on the device.  The truncation's per-sector SVDs run on several
  * streams at once, each with its own cuSOLVER handle and host thread: about
  * one per four charge sectors, at least four, at most 8 (or the value 1..16
- * of the environment variable DMRG3S_SVD_STREAMS read here).
- * Synchronous.  Errors: ARG, SHAPE, QN, CUDA, OOM. */
+ * of the environment variable DMRG3S_SVD_STREAMS read here).  The copies
+ * and environment builds run on `stream` (the inputs must be ready there);
+ * synchronous.  Errors: ARG, SHAPE, QN, CUDA, OOM. */
 dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_mpo_site* W,
                                   const dmrg3s_site* M, const dmrg3s_env* left_env,
                                   const dmrg3s_env* right_env, int32_t centre,
-                                  dmrg3s_state* out);
+                                  dmrg3s_state* out, dmrg3s_stream stream);
 dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state);
 
 /* One DMRG3S local update at the current centre i (Sec. V, steps 1-7), moving
@@ -416,10 +417,10 @@ dmrg3s_status dmrg3s_state_site_info(dmrg3s_state state, int32_t i, int32_t* nse
  * dW (HOST, may be NULL) holds dW_i/dtheta in the same layout, and
  *   *dE = sum_i <G_i, dW_i/dtheta> / <Psi|Psi>
  * (0 when dW is NULL).  len is the summed size (checked when G or dW is
- * given).  *norm2 = <Psi|Psi> = <M_c|M_c>.  Synchronous.
+ * given).  *norm2 = <Psi|Psi> = <M_c|M_c>.  Runs on `stream`; synchronous.
  * Errors: ARG, SHAPE, OOM, CUDA, NUMERIC (zero norm). */
 dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
-                              double* dE, double* norm2);
+                              double* dE, double* norm2, dmrg3s_stream stream);
 
 /* Copies site i (canonical layout, nelem doubles) to dst (device or host). */
 dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,

@@ -73,8 +73,9 @@ class GroundStateSolver:
                 e[k] = 1.0
                 Wk = self._mpo(params + e)
                 grad[k] = sum(float(np.sum(g * (wk.W - w.W))) for g, wk, w in zip(G, Wk, W)) / norm2
-            c, _ = st.centre()
-            self._prev = ([st.site(i) for i in range(self.nsites)], c)
+            if self.warm:
+                c, _ = st.centre()
+                self._prev = ([st.site(i) for i in range(self.nsites)], c)
         finally:
             st.close()
         return energy, grad

@@ -438,7 +438,7 @@ def _setup_state_api(L):
     L.dmrg3s_state_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_MpoSite),
                                       ctypes.POINTER(_Site), ctypes.POINTER(_Env),
                                       ctypes.POINTER(_Env), ctypes.c_int32,
-                                      ctypes.POINTER(ctypes.c_void_p)]
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
     L.dmrg3s_state_destroy.argtypes = [ctypes.c_void_p]
     L.dmrg3s_local_update.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                       ctypes.POINTER(_UpdateOpts), ctypes.POINTER(_UpdateInfo),
@@ -513,7 +513,7 @@ def dmrg3s_mpo_create(model, nsites, params=(), bonds=None, couplings=None):
 class State:
     """Library-owned DMRG3S state (dmrg3s_state_create)."""
 
-    def __init__(self, ctx, W, M, left_env=None, right_env=None, centre=0):
+    def __init__(self, ctx, W, M, left_env=None, right_env=None, centre=0, stream=None):
         n = len(W)
         self.ctx = ctx
         ctx._states.add(self)
@@ -524,7 +524,8 @@ class State:
         ce_r = ctypes.byref(right_env._c()) if right_env is not None else None
         self._keep = (W, M, cw, cm)
         _check(slib().dmrg3s_state_create(ctx.handle, n, cw, cm, ce_l, ce_r, int(centre),
-                                          ctypes.byref(self.handle)), "dmrg3s_state_create", ctx.handle)
+                                          ctypes.byref(self.handle), _stream(stream)),
+               "dmrg3s_state_create", ctx.handle)
         self.nsites = n
         self.qp = M[0].qp
 
@@ -566,8 +567,8 @@ class State:
         return Site(self.qp, Bond(ql, dl), Bond(qr, dr), data)
 
 
-def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0):
-    return State(ctx, W, M, left_env, right_env, centre)
+def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0, stream=None):
+    return State(ctx, W, M, left_env, right_env, centre, stream)
 
 
 def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False):
@@ -662,14 +663,15 @@ def dmrg3s_mpo_grad_site(ctx, L, W, R, M, G, stream=None):
            "dmrg3s_mpo_grad_site", ctx.handle)
 
 
-def dmrg3s_mpo_grad(state, dW=None, shapes=None):
+def dmrg3s_mpo_grad(state, dW=None, shapes=None, stream=None):
     """MPO-entry gradients of <Psi|H|Psi> at every site of the state.
 
     dW: optional list of per-site arrays dW_i/dtheta (shape (d, d, wl, wr)).
     shapes: the per-site (d, d, wl, wr) of the state's MPO (needed to split G).
     Returns (G list, dE/dtheta, <Psi|Psi>)."""
     lb = lib()
-    lb.dmrg3s_mpo_grad.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int64, f64p, f64p]
+    lb.dmrg3s_mpo_grad.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int64, f64p, f64p,
+                                   ctypes.c_void_p]
     sizes = [int(np.prod(s)) for s in shapes]
     total = sum(sizes)
     G = np.zeros(max(total, 1), np.float64)
@@ -681,7 +683,8 @@ def dmrg3s_mpo_grad(state, dW=None, shapes=None):
     dE, n2 = ctypes.c_double(), ctypes.c_double()
     _check(lb.dmrg3s_mpo_grad(state.handle, G.ctypes.data_as(f64p),
                               dw.ctypes.data_as(f64p) if dw is not None else None, total,
-                              ctypes.byref(dE), ctypes.byref(n2)), "dmrg3s_mpo_grad", state.ctx.handle)
+                              ctypes.byref(dE), ctypes.byref(n2), _stream(stream)),
+           "dmrg3s_mpo_grad", state.ctx.handle)
     out, off = [], 0
     for s, n in zip(shapes, sizes):
         out.append(G[off:off + n].reshape(s))

@@ -796,7 +796,7 @@ extern "C" {
 dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_mpo_site* W,
                                   const dmrg3s_site* M, const dmrg3s_env* left_env,
                                   const dmrg3s_env* right_env, int32_t centre,
-                                  dmrg3s_state* out) {
+                                  dmrg3s_state* out, dmrg3s_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !W || !M || !out || nsites < 1) return fail(c, DMRG3S_ERR_ARG, "bad argument");
   if (centre < 0 || centre >= nsites) return fail(c, DMRG3S_ERR_ARG, "centre out of range");
@@ -811,7 +811,7 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
   S->Lenv.resize(nsites);
   S->Renv.resize(nsites);
   std::string err;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   for (int i = 0; i < nsites; ++i) {
     if ((s = make_mpo(&W[i], &S->W[i], &err)) || (s = make_site(&M[i], &S->M[i].lay, &err)) ||
         (s = check_site_mpo(S->M[i].lay, S->W[i], &err)))
@@ -940,7 +940,7 @@ dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,
 }
 
 dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
-                              double* dE, double* norm2) {
+                              double* dE, double* norm2, dmrg3s_stream stream) {
   State* S = reinterpret_cast<State*>(state);
   if (!S) return DMRG3S_ERR_ARG;
   Context* c = S->c;
@@ -954,7 +954,7 @@ dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, i
     return fail(c, DMRG3S_ERR_SHAPE, "len must be the summed d*d*wl*wr over the sites");
   dmrg3s_status s;
   if ((s = use_device(c))) return s;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int cen = S->centre;
   if (!S->Lenv[cen].valid || !S->Renv[cen].valid)
     return fail(c, DMRG3S_ERR_ARG, "environments of the centre are not valid");
