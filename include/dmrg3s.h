@@ -185,6 +185,17 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
 
 /* ---- the hot path -------------------------------------------------------------- */
 
+/* Algorithmic cost of one dmrg3s_apply_heff with these structures, without
+ * touching the device (the data pointers are not read and may be NULL):
+ * *flops = the sum of 2 M N K over the block products of stages 1 and 3
+ * plus 2 rows cols per MPO term of stage 2 (the order of Sec. V); *bytes
+ * (may be NULL) = each distinct operand block read once and each output
+ * block written once, 8 bytes per element, summed over the three stages.
+ * Host function.  Errors: ARG, SHAPE, QN. */
+dmrg3s_status dmrg3s_heff_cost(const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                               const dmrg3s_env* R, const dmrg3s_site* A, double* flops,
+                               double* bytes);
+
 /* HA = L W A R: the left-hand side of the local eigenproblem
  *   L_{i-1} R_{i+1} W_i M_i = lambda M_i           (Eq. es-iter, Sec. V)
  * i.e. HA[s'](al', ar') = sum L[bl](al', al) W[s', s, bl, br] A[s](al, ar) R[br](ar', ar),

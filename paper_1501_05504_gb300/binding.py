@@ -690,3 +690,15 @@ def dmrg3s_mpo_grad(state, dW=None, shapes=None, stream=None):
         out.append(G[off:off + n].reshape(s))
         off += n
     return out, dE.value, n2.value
+
+
+def dmrg3s_heff_cost(L, W, R, A):
+    """(flops, bytes) of one H_eff application with these structures (host only)."""
+    lb = lib()
+    lb.dmrg3s_heff_cost.argtypes = [ctypes.POINTER(_Env), ctypes.POINTER(_MpoSite),
+                                    ctypes.POINTER(_Env), ctypes.POINTER(_Site), f64p, f64p]
+    cL, cW, cR, cA = L._c(), W._c(), R._c(), A._c()
+    fl, by = ctypes.c_double(), ctypes.c_double()
+    _check(lb.dmrg3s_heff_cost(ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR), ctypes.byref(cA),
+                               ctypes.byref(fl), ctypes.byref(by)), "dmrg3s_heff_cost")
+    return fl.value, by.value

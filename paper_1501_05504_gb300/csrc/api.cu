@@ -438,6 +438,28 @@ dmrg3s_status dmrg3s_site_size(const dmrg3s_site* M, int64_t* nelem) {
   return DMRG3S_OK;
 }
 
+dmrg3s_status dmrg3s_heff_cost(const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                               const dmrg3s_env* R, const dmrg3s_site* A, double* flops,
+                               double* bytes) {
+  if (!L || !W || !R || !A || !flops) return DMRG3S_ERR_ARG;
+  std::string err;
+  EnvLayout le, re;
+  MpoLayout w;
+  SiteLayout a;
+  dmrg3s_status st;
+  if ((st = make_env(L, &le, &err)) || (st = make_env(R, &re, &err)) ||
+      (st = make_mpo(W, &w, &err)) || (st = make_site(A, &a, &err)))
+    return st;
+  if ((st = check_site_mpo(a, w, &err)) || (st = check_env(le, a.left, w.wl, w.tl, "L", &err)) ||
+      (st = check_env(re, a.right, w.wr, w.tr, "R", &err)))
+    return st;
+  Plan p;
+  if ((st = plan_heff(le, w, re, a, &p, &err))) return st;
+  *flops = p.flops();
+  if (bytes) *bytes = p.g1.bytes + p.c2.bytes + p.g3.bytes;
+  return DMRG3S_OK;
+}
+
 dmrg3s_status dmrg3s_env_size(const dmrg3s_env* E, int64_t* nelem) {
   if (!nelem) return DMRG3S_ERR_ARG;
   EnvLayout e;
