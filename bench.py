@@ -293,7 +293,7 @@ def run_ours(args):
                                                              "tf32": "tf32"}[prec],
             "data": "synthetic", "impl": "ours",
             "config": {"workload": "xxz_l100_m512_u1 central two-site window, one local update per step",
-                       "model": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z", "m_max": M_MAX,
+                       "hamiltonian": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z", "m_max": M_MAX,
                        "alpha": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "lanczos_iters_mean": statistics.mean(iters), "flops_per_step": flops_step,
                        "phase_ms_per_step": phases,
@@ -508,7 +508,7 @@ def run_sweep(args):
             "sweeps_fp64": [[round(t, 3), e, p] for t, e, p in fp64],
             "sweeps_mixed": [[round(t, 3), e, p] for t, e, p in mixed],
             "config": {"workload": "%s_l%d_m%d full sweeps" % (model, L, m_max),
-                       "model": "%s, L=%d" % (SWEEP_MODELS[model][3], L),
+                       "hamiltonian": "%s, L=%d" % (SWEEP_MODELS[model][3], L),
                        "m_max": m_max, "alpha0": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "start": "product state %s..., m=1" % SWEEP_MODELS[model][2],
                        "cap_s_per_arm": cap},
