@@ -8,7 +8,8 @@ environment update and the energy after truncation.  Workload: the central
 two-site window of the S=1/2 Heisenberg (XXZ, Delta = 1) chain with L = 100,
 d = 2, w = 5, U(1) S^z blocks and m_max = 512; the boundary environments are
 seeded synthetic symmetric block tensors with Gaussian sector dimensions (a
-stand-in for converged environments; see the design doc for the recipe).  Steps
+stand-in for converged environments: seeded_inputs.central_bonds and
+symmetric_env build them).  Steps
 alternate direction (left-to-right, right-to-left) so every step is a full
 update of the same window.
 
