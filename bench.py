@@ -442,6 +442,9 @@ SWEEP_MODELS = {
     "xxz": ("MODEL_XXZ", (1.0, 1.0), [0, 1], "S=1/2 XXZ chain Delta=1, d=2, w=5, U(1) S^z"),
     "hubbard": ("MODEL_HUBBARD", (1.0, 8.0), [2, 1],
                 "Fermi-Hubbard chain t=1, U=8, half filling, d=4, w=6, U(1)xU(1) (N, S^z)"),
+    "cylinder": ("MODEL_SPIN_BONDS", None, [0, 1],
+                 "S=1/2 Heisenberg J1 on the 4 x L/4 cylinder (snake order, periodic in width), "
+                 "d=2, w=14, U(1) S^z"),
 }
 
 
@@ -453,7 +456,11 @@ def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0
     until convergence at 1e-11).  Returns per-sweep (wall seconds, energy)."""
     import torch
     lib_model, params, pattern, _ = SWEEP_MODELS[model]
-    W = b.Mpo(getattr(b, lib_model), L, params).sites()
+    if model == "cylinder":
+        bonds = cylinder_bonds(L // 4, 4)
+        W = b.Mpo(b.MODEL_SPIN_BONDS, L, (), bonds=bonds, couplings=[(1.0, 1.0)] * len(bonds)).sites()
+    else:
+        W = b.Mpo(getattr(b, lib_model), L, params).sites()
     st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, pattern * (L // 2)), None, None,
                                L - 1)
     alpha = ALPHA
@@ -483,7 +490,8 @@ def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0
 
 def run_sweep(args):
     """Sweep-to-1e-9 time on one GB300: a mixed ladder (3xTF32 block products
-    until the energy changes by < 1e-7 per sweep, then FP64) against all-FP64,
+    until the energy changes by < 1e-7 per sweep, then FP64 until < 1e-11)
+    against all-FP64 (until < 1e-11),
     both timed to the first sweep whose energy is within 1e-9 (relative) of
     the converged FP64 energy."""
     import torch
