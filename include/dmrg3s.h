@@ -138,11 +138,17 @@ dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
  * the phases of every local update (2: eigensolver, 3: expansion term,
  * 4: gather + SVD + new tensors, 5: S V^dagger into the neighbour,
  * 6: environment update, 7: energy after truncation; flops and bytes are 0
- * for phases), and around the other FP64 grouped GEMMs (kernel 8: the
- * truncation's S V^dagger products and the MPO-entry gradient).
+ * for phases), around the other FP64 grouped GEMMs (kernel 8: the
+ * truncation's S V^dagger products and the MPO-entry gradient), and around
+ * each sweep of the truncation's Jacobi SVD (kernel 9: one record per sweep
+ * covering its launches, the sweep-counter kernel and one launch per round;
+ * flops 6n per column-pair test and 6n per rotated column pair, bytes 16n
+ * per pair test and 16n per rotated pair, both doubled or tripled with the
+ * left vectors' rotations).
  * dmrg3s_profile(ctx, 1) resets and enables, 0 disables;
  * dmrg3s_profile_read synchronises on the recorded events and
  * returns, for one kernel, the number of launches, their summed device time
+ * (for kernel 9 the time of whole sweeps, gaps between launches included)
  * and their summed algorithmic flops and bytes (each distinct operand block
  * read once, each output written once). */
 typedef struct dmrg3s_kernel_stats {
@@ -184,6 +190,24 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
                                    int32_t* q, int64_t* dim);
 
 /* ---- the hot path -------------------------------------------------------------- */
+
+/* FP64 singular value decomposition of a batch of matrices: the factorisation
+ * of the truncation step (Sec. IV A, Sec. V step 4; DMRG3S_SVD_JACOBI).
+ * Matrix k is A_k (m[k] x n[k], 1 <= n[k] <= m[k], n[k] <= 32768),
+ * column-major with leading dimension m[k], stored back to back in `A`
+ * (device; overwritten).  Each is factorised A = Q R (cuSOLVER Householder
+ * QR) and R^T is orthogonalised by one-sided Jacobi rotations (the parallel
+ * round-robin order over column pairs, one CTA per pair, every matrix in each
+ * launch) until no pair has |<y_a, y_b>| > sqrt(n) 2^-52 |y_a| |y_b|.
+ * Outputs, back to back per matrix (device): S (n[k] singular values,
+ * descending), VT (n[k] x n[k], ld n[k]; row c = right singular vector c,
+ * zero for a zero singular value) and, when U is not NULL, U (m[k] x n[k],
+ * ld m[k]; column c = left singular vector c).  Runs on `stream` and on the
+ * context's own streams; synchronous (one host read per sweep).
+ * Errors: ARG (shapes), CUDA, NOT_CONVERGED (a matrix still rotating after
+ * 40 sweeps; outputs then invalid). */
+dmrg3s_status dmrg3s_svd(dmrg3s_ctx ctx, int32_t nmat, const int64_t* m, const int64_t* n,
+                         double* A, double* S, double* VT, double* U, dmrg3s_stream stream);
 
 /* Algorithmic cost of one dmrg3s_apply_heff with these structures, without
  * touching the device (the data pointers are not read and may be NULL):
@@ -328,6 +352,14 @@ dmrg3s_status dmrg3s_mpo_get_site(dmrg3s_mpo mpo, int32_t i, dmrg3s_mpo_site* si
 
 typedef struct dmrg3s_state_s* dmrg3s_state;
 
+/* Factorisation of the truncation's per-sector SVD (Sec. V step 4); both FP64. */
+typedef enum dmrg3s_svd_method {
+  DMRG3S_SVD_JACOBI = 0,  /* cuSOLVER QR, then one-sided Jacobi on R^T in this
+                             library's kernels, every sector in each launch
+                             (dmrg3s_svd)                                         */
+  DMRG3S_SVD_GESVD = 1    /* cuSOLVER gesvd per sector on concurrent streams      */
+} dmrg3s_svd_method;
+
 typedef struct dmrg3s_update_opts {
   int32_t m_max;            /* bond dimension kept after truncation (Sec. V step 4) */
   int32_t lanczos_kmax;     /* <= 0: 40                                            */
@@ -335,6 +367,7 @@ typedef struct dmrg3s_update_opts {
   double trunc_eps;         /* singular values <= eps * s_max are dropped; <= 0: 1e-12 */
   dmrg3s_precision precision;
   int32_t skip_eigensolver; /* != 0: keep M as is (a pure gauge/expansion move)    */
+  dmrg3s_svd_method svd;    /* factorisation of the truncation                     */
 } dmrg3s_update_opts;
 
 typedef struct dmrg3s_update_info {

@@ -396,7 +396,12 @@ def mpo_from_neutral(spec):
 class _UpdateOpts(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int32), ("lanczos_kmax", ctypes.c_int32),
                 ("lanczos_tol", ctypes.c_double), ("trunc_eps", ctypes.c_double),
-                ("precision", ctypes.c_int), ("skip_eigensolver", ctypes.c_int32)]
+                ("precision", ctypes.c_int), ("skip_eigensolver", ctypes.c_int32),
+                ("svd", ctypes.c_int)]
+
+
+SVD_JACOBI, SVD_GESVD = 0, 1
+_SVD = {"jacobi": SVD_JACOBI, "gesvd": SVD_GESVD}
 
 
 class _UpdateInfo(ctypes.Structure):
@@ -571,8 +576,9 @@ def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0, stre
     return State(ctx, W, M, left_env, right_env, centre, stream)
 
 
-def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False):
-    return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)))
+def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False, svd="jacobi"):
+    return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)),
+                       _SVD[svd] if isinstance(svd, str) else int(svd))
 
 
 def dmrg3s_local_update(state, direction, alpha, opts, stream=None):
@@ -619,6 +625,7 @@ class _KernelStats(ctypes.Structure):
 KERNEL_GEMM, KERNEL_COMBINE = 0, 1
 PHASE_EIG, PHASE_EXPAND, PHASE_SVD, PHASE_REMAINDER, PHASE_ENV, PHASE_ENERGY = 2, 3, 4, 5, 6, 7
 KERNEL_AUX_GEMM = 8
+KERNEL_JACOBI = 9
 
 
 def dmrg3s_profile(ctx, enable):
@@ -702,3 +709,37 @@ def dmrg3s_heff_cost(L, W, R, A):
     _check(lb.dmrg3s_heff_cost(ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR), ctypes.byref(cA),
                                ctypes.byref(fl), ctypes.byref(by)), "dmrg3s_heff_cost")
     return fl.value, by.value
+
+
+def dmrg3s_svd(ctx, mats, want_u=True, stream=None):
+    """FP64 SVD of a batch of matrices (QR, then one-sided Jacobi on R^T).
+
+    mats: list of device float64 tensors A_k of shape (m_k, n_k), 1 <= n_k <= m_k.
+    Returns a list of (U (m_k x n_k) or None, S (n_k,), VT (n_k x n_k)), device tensors."""
+    import torch
+    lb = lib()
+    lb.dmrg3s_svd.argtypes = [ctypes.c_void_p, ctypes.c_int32, i64p, i64p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    ms = np.array([int(a.shape[0]) for a in mats], np.int64)
+    ns = np.array([int(a.shape[1]) for a in mats], np.int64)
+    dev = mats[0].device if mats else torch.device("cuda")
+    # column-major storage: the transpose of each matrix, row-major, back to back
+    A = torch.cat([a.t().contiguous().reshape(-1) for a in mats]) if mats else \
+        torch.zeros(1, dtype=torch.float64, device=dev)
+    S = torch.zeros(max(int(ns.sum()), 1), dtype=torch.float64, device=dev)
+    VT = torch.zeros(max(int((ns * ns).sum()), 1), dtype=torch.float64, device=dev)
+    U = torch.zeros(max(int((ms * ns).sum()), 1), dtype=torch.float64, device=dev) if want_u else None
+    _check(lb.dmrg3s_svd(ctx.handle, len(mats), ms.ctypes.data_as(i64p), ns.ctypes.data_as(i64p),
+                         _ptr(A), _ptr(S), _ptr(VT), _ptr(U) if want_u else None, _stream(stream)),
+           "dmrg3s_svd", ctx.handle)
+    out, oa, os_, ov = [], 0, 0, 0
+    for m, n in zip(ms.tolist(), ns.tolist()):
+        s_k = S[os_:os_ + n]
+        # VT is stored column-major (ld n): element (c, a) at a n + c
+        vt = VT[ov:ov + n * n].reshape(n, n).t()
+        u = U[oa:oa + m * n].reshape(n, m).t() if want_u else None
+        out.append((u, s_k, vt))
+        oa += m * n
+        os_ += n
+        ov += n * n
+    return out

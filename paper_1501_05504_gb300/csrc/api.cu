@@ -414,7 +414,7 @@ dmrg3s_status dmrg3s_profile_read(dmrg3s_ctx ctx, int32_t kernel, dmrg3s_kernel_
     if (cudaEventSynchronize(r.e1) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "profile events");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.e0, r.e1);
-    out->launches += 1;
+    out->launches += r.launches;
     out->ms += ms;
     out->flops += r.flops;
     out->bytes += r.bytes;

@@ -50,12 +50,14 @@ enum ProfKind {
   kProfEnergy = 7,      //   energy after truncation
   kProfAuxGemm = 8,     // FP64 grouped GEMMs outside H_eff/expansion/environment:
                         //   the remainder of the truncation, the MPO-entry gradient
-  kProfKinds = 9
+  kProfJacobi = 9,      // one Jacobi sweep of the truncation's SVD (all its round launches)
+  kProfKinds = 10
 };
 struct ProfRec {
   int kind;
   cudaEvent_t e0, e1;
   double flops, bytes;
+  int64_t launches = 1;   // kernel launches between e0 and e1
 };
 struct Profiler {
   bool on = false;

@@ -8,9 +8,10 @@
 //   3. M~ = [M* P] per charge sector of the expanded right bond; the neighbour
 //      is padded with zero rows (never materialised: the zero rows only meet
 //      the P columns, so step 5 multiplies with the M* part only)
-//   4. FP64 SVD of every sector (cuSOLVER gesvd, sectors concurrently on
-//      several streams) and global truncation to
-//      m_max states: A~ = U
+//   4. FP64 SVD of every sector (QR, then one-sided Jacobi on R^T in this
+//      library's kernels, all sectors in each launch [svd.cu]; or cuSOLVER
+//      gesvd, sectors concurrently on several streams) and global truncation
+//      to m_max states: A~ = U
 //   5. B~_{i+1} = (S V^dagger)[:, M part] . B_{i+1}                     [grouped GEMM]
 //   6. L_i = L_{i-1} A~^dagger W_i A~                                   [plan]
 //   7. E_f = <B~|H_eff(i+1)|B~> / <B~|B~> (Rayleigh quotient after truncation)
@@ -25,6 +26,7 @@
 
 #include "context.hpp"
 #include "dmrg3s.h"
+#include "svd.hpp"
 #include "validate.hpp"
 #include "vecops.hpp"
 
@@ -44,16 +46,7 @@ struct DevEnv {
 
 }  // namespace
 
-// One concurrent SVD lane: its own cuSOLVER handle, stream and workspaces.
-struct SvdWorker {
-  cusolverDnHandle_t h = nullptr;
-  cusolverDnParams_t p = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t ev = nullptr;
-  void* dwork = nullptr;
-  size_t dbytes = 0;
-  std::vector<char> hwork;
-};
+using SvdWorker = SvdLane;
 constexpr int kSvdWorkers = 8;      // default number of concurrent SVD lanes
 
 // Lanes of a new state: DMRG3S_SVD_STREAMS (1..16) when set, else the default.
@@ -249,6 +242,7 @@ struct Opts {
   double eps = 1e-12;
   bool optimise = true;
   dmrg3s_precision prec = DMRG3S_FP64;   // arithmetic of the eigensolver's H_eff products
+  dmrg3s_svd_method svd = DMRG3S_SVD_JACOBI;
 };
 
 struct Info {
@@ -530,13 +524,29 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
                                         cudaMemcpyDeviceToDevice, st), "copy of M~")))
       return s;
   }
-  if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st))) return s;
   std::vector<double> hs(std::max<int64_t>(soff, 1));
   std::vector<int> hinfo(secs.size() + 1, 0);
+  if (o.svd == DMRG3S_SVD_JACOBI) {
+    std::vector<SvdJob> jobs(secs.size());
+    for (size_t k = 0; k < secs.size(); ++k) {
+      const Sector& sc = secs[k];
+      jobs[k].m = sc.m;
+      jobs[k].n = sc.n;
+      jobs[k].offA = sc.off;
+      jobs[k].offS = sc.offS;
+      jobs[k].offVT = sc.offVT;
+      jobs[k].offU = sc.vt_only ? -1 : sc.offU;
+    }
+    int nw = (int)secs.size() / 4;
+    nw = std::min(std::max(nw, 4), (int)S.svd.size());
+    if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st))) return s;
+  } else if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
+             (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
+                                             cudaMemcpyDeviceToHost, st), "SVD info"))) {
+    return s;
+  }
   if ((s = cuda_ok(c, cudaMemcpyAsync(hs.data(), Sv, soff * sizeof(double), cudaMemcpyDeviceToHost, st),
                    "singular values")) ||
-      (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
-                                      cudaMemcpyDeviceToHost, st), "SVD info")) ||
       (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
     return s;
   dfree(X, st);
@@ -828,13 +838,8 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
                     cudaMemcpyDeviceToDevice, st);
   }
   S->svd.resize(svd_lanes());
-  for (SvdWorker& w : S->svd) {
-    if (cusolverDnCreate(&w.h) != CUSOLVER_STATUS_SUCCESS ||
-        cusolverDnCreateParams(&w.p) != CUSOLVER_STATUS_SUCCESS ||
-        cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming) != cudaSuccess)
-      return fail(c, DMRG3S_ERR_CUDA, "SVD worker set-up");
-  }
+  for (SvdWorker& w : S->svd)
+    if ((s = lane_create(c, &w))) return s;
   if (cudaEventCreateWithFlags(&S->svd_in, cudaEventDisableTiming) != cudaSuccess)
     return fail(c, DMRG3S_ERR_CUDA, "SVD event");
   if ((s = boundary_env(*S, left_env, true, st)) || (s = boundary_env(*S, right_env, false, st)))
@@ -857,13 +862,7 @@ dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state) {
   for (auto& m : S->M) cudaFree(m.data);
   for (auto& e : S->Lenv) cudaFree(e.data);
   for (auto& e : S->Renv) cudaFree(e.data);
-  for (SvdWorker& w : S->svd) {
-    if (w.dwork) cudaFree(w.dwork);
-    if (w.p) cusolverDnDestroyParams(w.p);
-    if (w.h) cusolverDnDestroy(w.h);
-    if (w.ev) cudaEventDestroy(w.ev);
-    if (w.s) cudaStreamDestroy(w.s);
-  }
+  for (SvdWorker& w : S->svd) lane_destroy(&w);
   if (S->svd_in) cudaEventDestroy(S->svd_in);
   delete S;
   return DMRG3S_OK;
@@ -880,6 +879,8 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
       opts->precision != DMRG3S_TF32)
     return fail(c, DMRG3S_ERR_ARG, "local update precision");
   if (opts->m_max < 1) return fail(c, DMRG3S_ERR_ARG, "m_max must be >= 1");
+  if (opts->svd != DMRG3S_SVD_JACOBI && opts->svd != DMRG3S_SVD_GESVD)
+    return fail(c, DMRG3S_ERR_ARG, "SVD method");
   dmrg3s_status s;
   if ((s = use_device(c))) return s;
   Opts o;
@@ -889,6 +890,7 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-12;
   o.optimise = opts->skip_eigensolver == 0;
   o.prec = opts->precision;
+  o.svd = opts->svd;
   Info inf;
   s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));
   if (s != DMRG3S_OK) return s;

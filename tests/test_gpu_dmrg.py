@@ -160,7 +160,8 @@ def _cut_gap(orc, direction, alpha, m_max):
 @pytest.mark.parametrize("direction", [1, -1])
 @pytest.mark.parametrize("kind,seed", [("dense", 11), ("u1", 12), ("u1u1", 13), ("u1u1_big", 14)])
 @pytest.mark.parametrize("m_max", [40, 100000])
-def test_local_update_matches_oracle(b, ctx, kind, seed, direction, m_max):
+@pytest.mark.parametrize("svd", ["jacobi", "gesvd"])
+def test_local_update_matches_oracle(b, ctx, kind, seed, direction, m_max, svd):
     """m_max = 100000 keeps every state (no truncation): the state must be reproduced
     exactly.  m_max = 40 truncates: the kept subspace is then defined only up to
     the first-order perturbation eps / gap of the spectrum at the cut, and the
@@ -174,7 +175,7 @@ def test_local_update_matches_oracle(b, ctx, kind, seed, direction, m_max):
     lam_o, ef_o = orc.update_lr(0) if direction == 1 else orc.update_rl(1)
     st = _gpu_window(b, ctx, w, centre)
     info = b.dmrg3s_local_update(st, direction, alpha, b.update_opts(m_max, kmax=80, tol=1e-12,
-                                                                     eps=EPS))
+                                                                     eps=EPS, svd=svd))
     assert abs(info["lambda"] - lam_o) < 1e-9 * max(1.0, abs(lam_o))
     assert abs(info["energy_after"] - ef_o) < 1e-8 * max(1.0, abs(ef_o))
     g0, g1 = st.site(0), st.site(1)
