@@ -198,14 +198,15 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
  * (device; overwritten).  Each is factorised A = Q R (cuSOLVER Householder
  * QR) and R^T is orthogonalised by one-sided Jacobi rotations (the parallel
  * round-robin order over column pairs, one CTA per pair, every matrix in each
- * launch) until no pair has |<y_a, y_b>| > sqrt(n) 2^-52 |y_a| |y_b|.
+ * launch) until no pair has |<y_a, y_b>| > max(sqrt(n), 32) 2^-52 |y_a| |y_b|.
  * Outputs, back to back per matrix (device): S (n[k] singular values,
  * descending), VT (n[k] x n[k], ld n[k]; row c = right singular vector c,
  * zero for a zero singular value) and, when U is not NULL, U (m[k] x n[k],
  * ld m[k]; column c = left singular vector c).  Runs on `stream` and on the
  * context's own streams; synchronous (one host read per sweep).
  * Errors: ARG (shapes), CUDA, NOT_CONVERGED (a matrix still rotating after
- * 40 sweeps; outputs then invalid). */
+ * 40 sweeps, or after the number 1..40 in the environment variable
+ * DMRG3S_JACOBI_SWEEPS; outputs then invalid). */
 dmrg3s_status dmrg3s_svd(dmrg3s_ctx ctx, int32_t nmat, const int64_t* m, const int64_t* n,
                          double* A, double* S, double* VT, double* U, dmrg3s_stream stream);
 
@@ -356,7 +357,9 @@ typedef struct dmrg3s_state_s* dmrg3s_state;
 typedef enum dmrg3s_svd_method {
   DMRG3S_SVD_JACOBI = 0,  /* cuSOLVER QR, then one-sided Jacobi on R^T in this
                              library's kernels, every sector in each launch
-                             (dmrg3s_svd)                                         */
+                             (dmrg3s_svd); an update whose Jacobi sweeps do not
+                             converge redoes its SVD with gesvd
+                             (dmrg3s_update_info.svd_fallback)                    */
   DMRG3S_SVD_GESVD = 1    /* cuSOLVER gesvd per sector on concurrent streams      */
 } dmrg3s_svd_method;
 
@@ -377,6 +380,7 @@ typedef struct dmrg3s_update_info {
   double discarded_weight;  /* sum of the squared discarded singular values        */
   int32_t lanczos_iters;
   int32_t new_bond_dim;
+  int32_t svd_fallback;     /* 1: the Jacobi SVD did not converge and gesvd was used */
 } dmrg3s_update_info;
 
 /* Creates a state for a chain of `nsites` sites: MPO tensors W[0..n-1] (host,
@@ -430,7 +434,8 @@ typedef struct dmrg3s_sweep_opts {
 } dmrg3s_sweep_opts;
 
 typedef struct dmrg3s_sweep_report {
-  int32_t sweeps, converged, lanczos_iters, pad;
+  int32_t sweeps, converged, lanczos_iters;
+  int32_t svd_fallbacks;   /* updates whose Jacobi SVD fell back to gesvd */
   double energy, alpha;
 } dmrg3s_sweep_report;
 

@@ -407,7 +407,8 @@ _SVD = {"jacobi": SVD_JACOBI, "gesvd": SVD_GESVD}
 class _UpdateInfo(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("energy_before", ctypes.c_double),
                 ("energy_after", ctypes.c_double), ("discarded_weight", ctypes.c_double),
-                ("lanczos_iters", ctypes.c_int32), ("new_bond_dim", ctypes.c_int32)]
+                ("lanczos_iters", ctypes.c_int32), ("new_bond_dim", ctypes.c_int32),
+                ("svd_fallback", ctypes.c_int32)]
 
 
 class _AlphaRule(ctypes.Structure):
@@ -423,7 +424,7 @@ class _SweepOpts(ctypes.Structure):
 
 class _SweepReport(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("lanczos_iters", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("lanczos_iters", ctypes.c_int32), ("svd_fallbacks", ctypes.c_int32),
                 ("energy", ctypes.c_double), ("alpha", ctypes.c_double)]
 
 
@@ -588,7 +589,7 @@ def dmrg3s_local_update(state, direction, alpha, opts, stream=None):
            state.ctx.handle)
     return {"lambda": info.lambda_, "energy_before": info.energy_before, "energy_after": info.energy_after,
             "discarded_weight": info.discarded_weight, "lanczos_iters": info.lanczos_iters,
-            "new_bond_dim": info.new_bond_dim}
+            "new_bond_dim": info.new_bond_dim, "svd_fallback": bool(info.svd_fallback)}
 
 
 def alpha_rule(alpha0=1e-2, target=0.3, up=1.25, down=0.8, alpha_min=1e-14, alpha_max=1.0, fixed=False):
@@ -602,7 +603,8 @@ def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, stream=None):
     _check(slib().dmrg3s_sweep(state.handle, ctypes.byref(rule), ctypes.byref(so), en.ctypes.data_as(f64p),
                                ctypes.byref(rep), _stream(stream)), "dmrg3s_sweep", state.ctx.handle)
     return {"energies": en[:rep.sweeps].tolist(), "sweeps": rep.sweeps, "converged": bool(rep.converged),
-            "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters}
+            "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters,
+            "svd_fallbacks": rep.svd_fallbacks}
 
 
 def dmrg3s_apply_heff_noalloc(L, W, R, A, HA, stream=None):

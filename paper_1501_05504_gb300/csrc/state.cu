@@ -248,6 +248,7 @@ struct Opts {
 struct Info {
   double lambda = 0.0, e_f = 0.0, discarded = 0.0;
   int iters = 0, new_dim = 0;
+  bool svd_fallback = false;
 };
 
 // One sector of M~ for the SVD: a (rows x cols) row-major matrix.
@@ -514,9 +515,10 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if ((s = dalloc(c, &F, foff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
       (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
     return s;
-  // gesvd overwrites its input: the projected remainder reads a copy of X
+  // the SVD overwrites its input: the projected remainder reads a copy of X,
+  // which also restores X when the Jacobi sweeps do not converge
   double* X0 = nullptr;
-  bool any_proj = false;
+  bool any_proj = o.svd == DMRG3S_SVD_JACOBI;
   for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
   if (any_proj) {
     if ((s = dalloc(c, &X0, xoff, st))) return s;
@@ -540,6 +542,17 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     int nw = (int)secs.size() / 4;
     nw = std::min(std::max(nw, 4), (int)S.svd.size());
     if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st))) return s;
+    bool conv = true;
+    for (size_t k = 0; k < secs.size(); ++k) conv = conv && hinfo[k] == 0;
+    if (!conv) {   // redo this update's SVD with gesvd on the restored X
+      info->svd_fallback = true;
+      if ((s = cuda_ok(c, cudaMemcpyAsync(X, X0, (size_t)xoff * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, st), "copy of M~")) ||
+          (s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
+          (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
+                                          cudaMemcpyDeviceToHost, st), "SVD info")))
+        return s;
+    }
   } else if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
              (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
                                              cudaMemcpyDeviceToHost, st), "SVD info"))) {
@@ -900,6 +913,7 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   info->discarded_weight = inf.discarded;
   info->lanczos_iters = inf.iters;
   info->new_bond_dim = inf.new_dim;
+  info->svd_fallback = inf.svd_fallback ? 1 : 0;
   S->e_in = inf.e_f;
   return DMRG3S_OK;
 }
@@ -1052,6 +1066,7 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
   report->sweeps = 0;
   report->converged = 0;
   report->lanczos_iters = 0;
+  report->svd_fallbacks = 0;
   double prev = 0.0;
   for (int sw = 0; sw < opts->max_sweeps; ++sw) {
     double e = 0.0;
@@ -1063,6 +1078,7 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
         if (s != DMRG3S_OK) return s;
         alpha = alpha_update(*rule, alpha, inf.energy_before, inf.lambda, inf.energy_after);
         report->lanczos_iters += inf.lanczos_iters;
+        report->svd_fallbacks += inf.svd_fallback;
         e = inf.energy_after;
       }
     }

@@ -9,7 +9,10 @@
 // (beta - alpha) / (2 gamma), and
 //   y_a <- c y_a - s y_b,   y_b <- s y_a + c y_b,   c = 1/sqrt(1+t^2), s = c t,
 // after which <y_a, y_b> = 0 in exact arithmetic.  A pair is rotated only when
-// |gamma| > tol sqrt(alpha beta), tol = sqrt(n) 2^-52 (relative orthogonality).
+// |gamma| > tol sqrt(alpha beta), tol = max(sqrt(n), 32) 2^-52 (relative
+// orthogonality; the floor keeps tol above the rounding error of the computed
+// dot product, which would otherwise restart rotations of pairs with equal
+// norms indefinitely).
 //
 // Working on R^T (A = Q R, Householder QR) instead of A: the singular values
 // of a truncated MPS span many orders of magnitude, and on such matrices the
@@ -28,6 +31,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <thread>
 
@@ -117,7 +121,7 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
   sab = cta_sum(sab, red[2]);
   // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
   if (!(saa > 0.0) || !(sbb > 0.0)) return;
-  const double tol = sqrt((double)n) * DBL_EPSILON;
+  const double tol = fmax(sqrt((double)n), 32.0) * DBL_EPSILON;
   if (!(fabs(sab) > tol * sqrt(saa) * sqrt(sbb))) return;
   const double zeta = (sbb - saa) / (2.0 * sab);
   const double az = fabs(zeta);
@@ -214,9 +218,16 @@ void lane_destroy(SvdLane* w) {
   *w = SvdLane();
 }
 
+int jacobi_max_sweeps() {
+  const char* e = std::getenv("DMRG3S_JACOBI_SWEEPS");
+  if (!e) return kJacobiMaxSweeps;
+  const int v = std::atoi(e);
+  return v < 1 ? 1 : (v > kJacobiMaxSweeps ? kJacobiMaxSweeps : v);
+}
+
 dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
                          const std::vector<SvdJob>& jobs, double* A, double* S, double* VT,
-                         double* U, int* info, cudaStream_t st) {
+                         double* U, int* info, cudaStream_t st, std::string* diag) {
   const int nj = (int)jobs.size();
   if (nj == 0) return DMRG3S_OK;
   if (nlanes < 1 || nlanes > (int)lanes.size()) nlanes = (int)lanes.size();
@@ -392,7 +403,8 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   std::vector<int> hrot(nj), active(nj, 1);
   std::vector<int> conv(nj, 0);
   Profiler& pr = c->prof;
-  for (int sw = 0; !s && sw < kJacobiMaxSweeps; ++sw) {
+  const int max_sweeps = jacobi_max_sweeps();
+  for (int sw = 0; !s && sw < max_sweeps; ++sw) {
     const int id = pr.on ? pr.begin(kProfJacobi, 0.0, 0.0, st) : -1;
     if (gexec) {
       s = cuda_ok(c, cudaGraphLaunch(gexec, st), "Jacobi sweep");
@@ -457,7 +469,13 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
         [&](int k) { return tab[k].offV >= 0; });
     if (!ok) s = fail(c, DMRG3S_ERR_CUDA, "left singular vectors (ormqr)");
   }
-  for (int k = 0; k < nj; ++k) info[k] = conv[k] ? 0 : 1;
+  for (int k = 0; k < nj; ++k) {
+    info[k] = conv[k] ? 0 : 1;
+    if (!conv[k] && diag && diag->empty())
+      *diag = "matrix " + std::to_string(k) + " (" + std::to_string(tab[k].m) + " x " +
+              std::to_string(tab[k].n) + ") still had " + std::to_string(hrot[k]) +
+              " rotations in sweep " + std::to_string(max_sweeps);
+  }
   cudaFreeAsync(dd, st);
   cudaFreeAsync(di, st);
   cudaFreeAsync(dt, st);
@@ -495,14 +513,14 @@ extern "C" dmrg3s_status dmrg3s_svd(dmrg3s_ctx ctx, int32_t nmat, const int64_t*
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::vector<SvdLane> lanes(1);
   std::vector<int> info(nmat, 0);
+  std::string diag;
   if (!(s = lane_create(c, &lanes[0]))) {
-    s = svd_jacobi(c, lanes, 1, jobs, A, S, VT, U, info.data(), st);
+    s = svd_jacobi(c, lanes, 1, jobs, A, S, VT, U, info.data(), st, &diag);
     if (!s && cudaStreamSynchronize(st) != cudaSuccess)
       s = fail(c, DMRG3S_ERR_CUDA, "dmrg3s_svd: stream synchronisation");
   }
   lane_destroy(&lanes[0]);
   for (int k = 0; !s && k < nmat; ++k)
-    if (info[k]) s = fail(c, DMRG3S_ERR_NOT_CONVERGED, "dmrg3s_svd: matrix " + std::to_string(k) +
-                                                           " did not converge");
+    if (info[k]) s = fail(c, DMRG3S_ERR_NOT_CONVERGED, "dmrg3s_svd: " + diag);
   return s;
 }

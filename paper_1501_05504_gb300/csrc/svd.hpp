@@ -13,6 +13,7 @@
 #include <cusolverDn.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "context.hpp"
@@ -42,17 +43,22 @@ struct SvdJob {
   int64_t m = 0, n = 0, offA = 0, offS = 0, offVT = 0, offU = -1;
 };
 
-// Jacobi sweeps allowed before a matrix counts as not converged.
+// Jacobi sweeps allowed before a matrix counts as not converged: at most
+// kJacobiMaxSweeps, fewer when the environment variable DMRG3S_JACOBI_SWEEPS
+// (1 .. kJacobiMaxSweeps) is set.
 constexpr int kJacobiMaxSweeps = 40;
+int jacobi_max_sweeps();
 
-// Factorises every job; A is overwritten.  `lanes[0 .. nlanes)` run the QR
-// factorisations (and Q V1) concurrently after the work already queued on
-// `st`; `st` waits for all results.  info[k] (host) = 0, or 1 when job k did
-// not converge within kJacobiMaxSweeps.  Synchronises `st` once per sweep.
-// Profiling (kind kProfJacobi) records each sweep's rounds with the flops of
-// its pair tests and rotations.
+// Factorises every job; A is overwritten (its upper triangle then holds R).
+// `lanes[0 .. nlanes)` run the QR factorisations (and Q V1) concurrently
+// after the work already queued on `st`; `st` waits for all results.
+// info[k] (host) = 0, or 1 when job k did not converge within the sweep
+// limit (its outputs are then invalid; *diag, when given, names the first
+// such job).  Synchronises `st` once per sweep.  Profiling (kind
+// kProfJacobi) records each sweep's rounds with the flops of its pair tests
+// and rotations.
 dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
                          const std::vector<SvdJob>& jobs, double* A, double* S, double* VT,
-                         double* U, int* info, cudaStream_t st);
+                         double* U, int* info, cudaStream_t st, std::string* diag = nullptr);
 
 }  // namespace dmrg3s

@@ -114,3 +114,38 @@ def test_sweeps_jacobi_vs_gesvd(b, ctx):
     assert abs(eg - ej) < 1e-9 * abs(eg)
     assert ig["new_bond_dim"] == ij["new_bond_dim"]
     assert abs(ig["energy_after"] - ij["energy_after"]) < 1e-9 * abs(ig["energy_after"])
+
+
+def test_sweep_limit_reports_not_converged(b, ctx, monkeypatch):
+    """With the sweep limit at one sweep a graded 30 x 30 matrix is not done:
+    dmrg3s_svd reports NOT_CONVERGED (status 6) instead of a result."""
+    rng = si.rng_for(43)
+    X = _matrix(rng, 30, 30, -8, 30)
+    monkeypatch.setenv("DMRG3S_JACOBI_SWEEPS", "1")
+    with pytest.raises(b.Dmrg3sError) as e:
+        b.dmrg3s_svd(ctx, [torch.from_numpy(X).cuda()])
+    assert e.value.status == 6
+    monkeypatch.delenv("DMRG3S_JACOBI_SWEEPS")
+    _check(X, b.dmrg3s_svd(ctx, [torch.from_numpy(X).cuda()])[0])
+
+
+def test_local_update_falls_back_to_gesvd(b, ctx, monkeypatch):
+    """An update whose Jacobi sweeps stop unconverged (limit forced to one
+    sweep) redoes its SVD with gesvd on the restored matrix: it reports the
+    fallback and matches the gesvd update of the same state."""
+    L = 16
+    W = b.Mpo(b.MODEL_XXZ, L, (1.0, 0.6)).sites()
+    res = {}
+    for method, limit in (("gesvd", None), ("jacobi", "1")):
+        st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [0, 1] * (L // 2)), None, None,
+                                   L - 1)
+        b.dmrg3s_sweep(st, b.alpha_rule(1e-2, fixed=True), 2, 1e-14,
+                       b.update_opts(32, svd="gesvd"))
+        if limit:
+            monkeypatch.setenv("DMRG3S_JACOBI_SWEEPS", limit)
+        res[method] = b.dmrg3s_local_update(st, -1, 1e-2, b.update_opts(32, svd=method))
+        monkeypatch.delenv("DMRG3S_JACOBI_SWEEPS", raising=False)
+        st.close()
+    assert res["jacobi"]["svd_fallback"] and not res["gesvd"]["svd_fallback"]
+    for k in ("energy_after", "discarded_weight", "new_bond_dim", "lambda"):
+        assert res["jacobi"][k] == res["gesvd"][k], k
