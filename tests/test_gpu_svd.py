@@ -141,6 +141,8 @@ def test_local_update_falls_back_to_gesvd(b, ctx, monkeypatch):
                                    L - 1)
         b.dmrg3s_sweep(st, b.alpha_rule(1e-2, fixed=True), 2, 1e-14,
                        b.update_opts(32, svd="gesvd"))
+        for _ in range(L // 2 - 1):   # centre to the middle, where the sectors are largest
+            b.dmrg3s_local_update(st, -1, 1e-2, b.update_opts(32, svd="gesvd"))
         if limit:
             monkeypatch.setenv("DMRG3S_JACOBI_SWEEPS", limit)
         res[method] = b.dmrg3s_local_update(st, -1, 1e-2, b.update_opts(32, svd=method))
