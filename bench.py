@@ -213,7 +213,7 @@ def run_ours(args):
     # ---- device-resident timed region
     b.dmrg3s_profile(ctx, True)
     n0 = b.dmrg3s_launch_count()
-    times, iters = [], []
+    times, iters, sweeps, fallbacks = [], [], [], 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -228,6 +228,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
             iters.append(info["lanczos_iters"])
+            sweeps.append(info["svd_sweeps"])
+            fallbacks += int(info["svd_fallback"])
     torch.cuda.synchronize()
     launches = b.dmrg3s_launch_count() - n0
     g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
@@ -315,7 +317,8 @@ def run_ours(args):
                        "alpha": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "lanczos_iters_mean": statistics.mean(iters), "flops_per_step": flops_step,
                        "phase_ms_per_step": phases,
-                       "precision": prec, "svd": args.svd,
+                       "precision": prec, "svd": args.svd, "svd_jacobi_sweeps": sweeps,
+                       "svd_fallbacks": fallbacks,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

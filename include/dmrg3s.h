@@ -195,8 +195,9 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
  * of the truncation step (Sec. IV A, Sec. V step 4; DMRG3S_SVD_JACOBI).
  * Matrix k is A_k (m[k] x n[k], 1 <= n[k] <= m[k], n[k] <= 32768),
  * column-major with leading dimension m[k], stored back to back in `A`
- * (device; overwritten).  Each is factorised A = Q R (cuSOLVER Householder
- * QR) and R^T is orthogonalised by one-sided Jacobi rotations (the parallel
+ * (device; not modified).  With its columns in descending norm order (A P),
+ * each is factorised A P = Q R (cuSOLVER Householder QR, on a copy) and R^T
+ * is orthogonalised by one-sided Jacobi rotations (the parallel
  * round-robin order over column pairs, one CTA per pair, every matrix in each
  * launch) until no pair has |<y_a, y_b>| > max(sqrt(n), 32) 2^-52 |y_a| |y_b|.
  * Outputs, back to back per matrix (device): S (n[k] singular values,
@@ -381,6 +382,7 @@ typedef struct dmrg3s_update_info {
   int32_t lanczos_iters;
   int32_t new_bond_dim;
   int32_t svd_fallback;     /* 1: the Jacobi SVD did not converge and gesvd was used */
+  int32_t svd_sweeps;       /* Jacobi sweeps of the truncation's SVD (0 with gesvd)  */
 } dmrg3s_update_info;
 
 /* Creates a state for a chain of `nsites` sites: MPO tensors W[0..n-1] (host,

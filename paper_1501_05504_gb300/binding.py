@@ -408,7 +408,7 @@ class _UpdateInfo(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("energy_before", ctypes.c_double),
                 ("energy_after", ctypes.c_double), ("discarded_weight", ctypes.c_double),
                 ("lanczos_iters", ctypes.c_int32), ("new_bond_dim", ctypes.c_int32),
-                ("svd_fallback", ctypes.c_int32)]
+                ("svd_fallback", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32)]
 
 
 class _AlphaRule(ctypes.Structure):
@@ -589,7 +589,8 @@ def dmrg3s_local_update(state, direction, alpha, opts, stream=None):
            state.ctx.handle)
     return {"lambda": info.lambda_, "energy_before": info.energy_before, "energy_after": info.energy_after,
             "discarded_weight": info.discarded_weight, "lanczos_iters": info.lanczos_iters,
-            "new_bond_dim": info.new_bond_dim, "svd_fallback": bool(info.svd_fallback)}
+            "new_bond_dim": info.new_bond_dim, "svd_fallback": bool(info.svd_fallback),
+            "svd_sweeps": info.svd_sweeps}
 
 
 def alpha_rule(alpha0=1e-2, target=0.3, up=1.25, down=0.8, alpha_min=1e-14, alpha_max=1.0, fixed=False):

@@ -249,6 +249,7 @@ struct Info {
   double lambda = 0.0, e_f = 0.0, discarded = 0.0;
   int iters = 0, new_dim = 0;
   bool svd_fallback = false;
+  int svd_sweeps = 0;
 };
 
 // One sector of M~ for the SVD: a (rows x cols) row-major matrix.
@@ -541,7 +542,9 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     }
     int nw = (int)secs.size() / 4;
     nw = std::min(std::max(nw, 4), (int)S.svd.size());
-    if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st))) return s;
+    if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st, nullptr,
+                        &info->svd_sweeps)))
+      return s;
     bool conv = true;
     for (size_t k = 0; k < secs.size(); ++k) conv = conv && hinfo[k] == 0;
     if (!conv) {   // redo this update's SVD with gesvd on the restored X
@@ -914,6 +917,7 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   info->lanczos_iters = inf.iters;
   info->new_bond_dim = inf.new_dim;
   info->svd_fallback = inf.svd_fallback ? 1 : 0;
+  info->svd_sweeps = inf.svd_sweeps;
   S->e_in = inf.e_f;
   return DMRG3S_OK;
 }

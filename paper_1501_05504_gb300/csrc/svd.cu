@@ -14,9 +14,11 @@
 // dot product, which would otherwise restart rotations of pairs with equal
 // norms indefinitely).
 //
-// Working on R^T (A = Q R, Householder QR) instead of A: the singular values
-// of a truncated MPS span many orders of magnitude, and on such matrices the
-// method needs several times fewer sweeps on R^T than on A.
+// Working on R^T (A P = Q R, Householder QR of A with its columns in
+// descending norm order) instead of A: the singular values of a truncated MPS
+// span many orders of magnitude, and on such matrices the method needs several
+// times fewer sweeps on R^T than on A; the norm order cuts the sweeps on the
+// most graded sectors by a further third.
 //
 // Parallel order: the circle (round-robin) schedule.  With n' = n rounded up
 // to even and N = n' - 1, round r (0 <= r < N) pairs column r with N and
@@ -79,16 +81,48 @@ jac_init_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job
   }
 }
 
+// Squared norm of every column of every A (m rows, ld m).  One CTA per column.
+__global__ void __launch_bounds__(kJacThreads)
+jac_anorm_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job,
+                 const double* __restrict__ A, double* __restrict__ nrm) {
+  __shared__ double red[kJacThreads / 32];
+  const JacJob J = jobs[col_job[blockIdx.x]];
+  const int j = blockIdx.x - J.col0;
+  const double* x = A + J.offA + (int64_t)j * J.m;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < J.m; i += kJacThreads) s = fma(x[i], x[i], s);
+  s = cta_sum(s, red);
+  if (threadIdx.x == 0) nrm[blockIdx.x] = s;
+}
+
+// T = A P: column j of T is column perm[j] of A.  One CTA per column.
+__global__ void __launch_bounds__(kJacThreads)
+jac_permute_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job,
+                   const int* __restrict__ perm, const double* __restrict__ A,
+                   double* __restrict__ T) {
+  const JacJob J = jobs[col_job[blockIdx.x]];
+  const int j = blockIdx.x - J.col0;
+  const double* x = A + J.offA + (int64_t)perm[blockIdx.x] * J.m;
+  double* t = T + J.offA + (int64_t)j * J.m;
+  for (int i = threadIdx.x; i < J.m; i += kJacThreads) t[i] = x[i];
+}
+
 // Advances the sweep counter read by the round kernels (first node of a sweep).
 __global__ void jac_next_sweep_kernel(int* sweep) { *sweep += 1; }
 
 // One round r of the current sweep for every matrix: one CTA per pair.
-// rot[s * njobs + job] counts the rotations of sweep s.
+// rot[s * njobs + job] counts the rotations of sweep s.  The first kJacCache
+// elements of each thread's share stay in registers between the dot products
+// and the rotation; the rotation itself (a few FP64 divisions and square
+// roots) is computed once, by thread 0.
+constexpr int kJacCache = 4;
 __global__ void __launch_bounds__(kJacThreads)
 jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_job, int njobs, int r,
                  const int* __restrict__ sweep, int* __restrict__ rot, double* __restrict__ Y,
                  double* __restrict__ V) {
   __shared__ double red[3][kJacThreads / 32];
+  __shared__ double cs_sn[2];
+  __shared__ int go;
   const int sw = *sweep;
   if (sw < 0 || sw >= kJacobiMaxSweeps) return;
   const int jb = cta_job[blockIdx.x];
@@ -109,26 +143,73 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
   if (a >= n || b >= n) return;   // the padding column
   double* ya = Y + J.offY + (int64_t)a * n;
   double* yb = Y + J.offY + (int64_t)b * n;
+  double ua[kJacCache], ub[kJacCache];
   double saa = 0.0, sbb = 0.0, sab = 0.0;
-  for (int i = threadIdx.x; i < n; i += kJacThreads) {
+#pragma unroll
+  for (int e = 0; e < kJacCache; ++e) {
+    const int i = threadIdx.x + e * kJacThreads;
+    ua[e] = i < n ? ya[i] : 0.0;
+    ub[e] = i < n ? yb[i] : 0.0;
+    saa = fma(ua[e], ua[e], saa);
+    sbb = fma(ub[e], ub[e], sbb);
+    sab = fma(ua[e], ub[e], sab);
+  }
+  for (int i = threadIdx.x + kJacCache * kJacThreads; i < n; i += kJacThreads) {
     const double u = ya[i], v = yb[i];
     saa = fma(u, u, saa);
     sbb = fma(v, v, sbb);
     sab = fma(u, v, sab);
   }
-  saa = cta_sum(saa, red[0]);
-  sbb = cta_sum(sbb, red[1]);
-  sab = cta_sum(sab, red[2]);
-  // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
-  if (!(saa > 0.0) || !(sbb > 0.0)) return;
-  const double tol = fmax(sqrt((double)n), 32.0) * DBL_EPSILON;
-  if (!(fabs(sab) > tol * sqrt(saa) * sqrt(sbb))) return;
-  const double zeta = (sbb - saa) / (2.0 * sab);
-  const double az = fabs(zeta);
-  const double t = az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + az * az));
-  const double cs = 1.0 / sqrt(1.0 + t * t);
-  const double sn = cs * t;
-  for (int i = threadIdx.x; i < n; i += kJacThreads) {
+  for (int o = 16; o > 0; o >>= 1) {
+    saa += __shfl_xor_sync(0xffffffffu, saa, o);
+    sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+    sab += __shfl_xor_sync(0xffffffffu, sab, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = saa;
+    red[1][threadIdx.x >> 5] = sbb;
+    red[2][threadIdx.x >> 5] = sab;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    saa = red[0][0];
+    sbb = red[1][0];
+    sab = red[2][0];
+    for (int w = 1; w < kJacThreads / 32; ++w) {
+      saa += red[0][w];
+      sbb += red[1][w];
+      sab += red[2][w];
+    }
+    int g = 0;
+    // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
+    if (saa > 0.0 && sbb > 0.0) {
+      const double tol = fmax(sqrt((double)n), 32.0) * DBL_EPSILON;
+      if (fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
+        const double zeta = (sbb - saa) / (2.0 * sab);
+        const double az = fabs(zeta);
+        const double t =
+            az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + az * az));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        cs_sn[0] = c;
+        cs_sn[1] = c * t;
+        g = 1;
+        atomicAdd(rot + sw * njobs + jb, 1);
+      }
+    }
+    go = g;
+  }
+  __syncthreads();
+  if (!go) return;
+  const double cs = cs_sn[0], sn = cs_sn[1];
+#pragma unroll
+  for (int e = 0; e < kJacCache; ++e) {
+    const int i = threadIdx.x + e * kJacThreads;
+    if (i < n) {
+      ya[i] = cs * ua[e] - sn * ub[e];
+      yb[i] = sn * ua[e] + cs * ub[e];
+    }
+  }
+  for (int i = threadIdx.x + kJacCache * kJacThreads; i < n; i += kJacThreads) {
     const double u = ya[i], v = yb[i];
     ya[i] = cs * u - sn * v;
     yb[i] = sn * u + cs * v;
@@ -142,7 +223,6 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
       vb[i] = sn * u + cs * v;
     }
   }
-  if (threadIdx.x == 0) atomicAdd(rot + sw * njobs + jb, 1);
 }
 
 // sigma of every column of every Y.  One CTA per column.
@@ -163,13 +243,14 @@ jac_norm_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job
 __device__ __forceinline__ double sig_key(double x) { return x != x ? INFINITY : x; }
 
 // Column j of matrix J goes to position c = its rank (descending sigma, ties
-// by index): S[c] = sigma_j, VT row c = y_j / sigma_j, and, when wanted, U
-// column c = (V1 column j; 0), which Q then multiplies.  One CTA per column.
+// by index): S[c] = sigma_j, VT row c = P y_j / sigma_j (P: the column order
+// of the factorised A P), and, when wanted, U column c = (V1 column j; 0),
+// which Q then multiplies.  One CTA per column.
 __global__ void __launch_bounds__(kJacThreads)
 jac_scatter_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job,
-                   const double* __restrict__ Y, const double* __restrict__ V,
-                   const double* __restrict__ sig, double* __restrict__ S, double* __restrict__ VT,
-                   double* __restrict__ U) {
+                   const int* __restrict__ perm, const double* __restrict__ Y,
+                   const double* __restrict__ V, const double* __restrict__ sig,
+                   double* __restrict__ S, double* __restrict__ VT, double* __restrict__ U) {
   __shared__ int red[kJacThreads / 32];
   const JacJob J = jobs[col_job[blockIdx.x]];
   const int j = blockIdx.x - J.col0;
@@ -184,8 +265,9 @@ jac_scatter_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_
   const int c = cta_sum(cnt, red);
   if (threadIdx.x == 0) S[J.offS + c] = s;
   const double* y = Y + J.offY + (int64_t)j * n;
+  const int* pj = perm + J.col0;   // row i of R belongs to column pj[i] of A
   for (int i = threadIdx.x; i < n; i += kJacThreads)
-    VT[J.offVT + c + (int64_t)i * n] = s > 0.0 ? y[i] / s : 0.0;
+    VT[J.offVT + c + (int64_t)pj[i] * n] = s > 0.0 ? y[i] / s : 0.0;
   if (J.offU >= 0) {
     const double* v = V + J.offV + (int64_t)j * n;
     double* u = U + J.offU + (int64_t)c * J.m;
@@ -227,7 +309,8 @@ int jacobi_max_sweeps() {
 
 dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
                          const std::vector<SvdJob>& jobs, double* A, double* S, double* VT,
-                         double* U, int* info, cudaStream_t st, std::string* diag) {
+                         double* U, int* info, cudaStream_t st, std::string* diag,
+                         int* sweeps) {
   const int nj = (int)jobs.size();
   if (nj == 0) return DMRG3S_OK;
   if (nlanes < 1 || nlanes > (int)lanes.size()) nlanes = (int)lanes.size();
@@ -264,9 +347,12 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     maxr = std::max(maxr, t.npad - 1);
   }
   const int ncta = (int)cta_job.size(), ncol = (int)col_job.size();
-  // ---- device buffers: doubles [tau | Y | V1 | sigma], ints [cta_job | col_job | rot | sweep | qinfo]
-  const int64_t nd = ntau + ny + nv + ncol;
-  const int64_t ni = ncta + ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj;
+  int64_t na = 0;   // extent of the A buffer used by the jobs
+  for (const JacJob& t : tab) na = std::max(na, t.offA + (int64_t)t.m * t.n);
+  // ---- device buffers: doubles [tau | Y | V1 | sigma | column norms | T = A P],
+  //      ints [cta_job | col_job | perm | rot | sweep | qinfo]
+  const int64_t nd = ntau + ny + nv + 2 * (int64_t)ncol + na;
+  const int64_t ni = ncta + 2 * (int64_t)ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj;
   double* dd = nullptr;
   int* di = nullptr;
   JacJob* dt = nullptr;
@@ -282,9 +368,12 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   double* Y = tau + ntau;
   double* V1 = Y + ny;
   double* sig = V1 + nv;
+  double* anrm = sig + ncol;
+  double* T = anrm + ncol;
   int* d_cta = di;
   int* d_col = d_cta + ncta;
-  int* rot = d_col + ncol;
+  int* d_perm = d_col + ncol;
+  int* rot = d_perm + ncol;
   int* d_sweep = rot + (int64_t)kJacobiMaxSweeps * nj;
   int* qinfo = d_sweep + 1;
   cudaMemcpyAsync(dt, tab.data(), tab.size() * sizeof(JacJob), cudaMemcpyHostToDevice, st);
@@ -293,12 +382,34 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   cudaMemsetAsync(rot, 0, (size_t)kJacobiMaxSweeps * nj * sizeof(int), st);
   cudaMemsetAsync(d_sweep, 0xff, sizeof(int), st);   // -1: the first sweep advances it to 0
   s = cuda_ok(c, cudaGetLastError(), "SVD tables");
+  // ---- columns in descending norm order, T = A P: the Jacobi sweeps on R^T
+  // of A P need fewer sweeps than on R^T of A when the column norms are graded
+  std::vector<int> perm(ncol);
+  if (!s) {
+    std::vector<double> hn(ncol);
+    jac_anorm_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, A, anrm);
+    count_launch();
+    if (!(s = cuda_ok(c, cudaMemcpyAsync(hn.data(), anrm, ncol * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st), "column norms")) &&
+        !(s = cuda_ok(c, cudaStreamSynchronize(st), "column norms"))) {
+      for (const JacJob& t : tab) {
+        int* pj = perm.data() + t.col0;
+        for (int i = 0; i < t.n; ++i) pj[i] = i;
+        const double* nj_ = hn.data() + t.col0;
+        std::stable_sort(pj, pj + t.n, [&](int x, int y) { return nj_[x] > nj_[y]; });
+      }
+      cudaMemcpyAsync(d_perm, perm.data(), ncol * sizeof(int), cudaMemcpyHostToDevice, st);
+      jac_permute_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, d_perm, A, T);
+      count_launch();
+      s = cuda_ok(c, cudaGetLastError(), "column order");
+    }
+  }
   // ---- lane workspaces (QR, and Q V1 for the left vectors)
   size_t dmax = 1, hmax = 1;
   for (const JacJob& t : tab) {
     if (s) break;
     size_t wd = 0, wh = 0;
-    if (cusolverDnXgeqrf_bufferSize(lanes[0].h, lanes[0].p, t.m, t.n, CUDA_R_64F, A + t.offA, t.m,
+    if (cusolverDnXgeqrf_bufferSize(lanes[0].h, lanes[0].p, t.m, t.n, CUDA_R_64F, T + t.offA, t.m,
                                     CUDA_R_64F, tau + t.offTau, CUDA_R_64F, &wd,
                                     &wh) != CUSOLVER_STATUS_SUCCESS)
       s = fail(c, DMRG3S_ERR_CUDA, "QR buffer size");
@@ -307,7 +418,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     if (!s && t.offU >= 0) {
       int lw = 0;
       if (cusolverDnDormqr_bufferSize(lanes[0].h, CUBLAS_SIDE_LEFT, CUBLAS_OP_N, t.m, t.n, t.n,
-                                      A + t.offA, t.m, tau + t.offTau, U + t.offU, t.m,
+                                      T + t.offA, t.m, tau + t.offTau, U + t.offU, t.m,
                                       &lw) != CUSOLVER_STATUS_SUCCESS)
         s = fail(c, DMRG3S_ERR_CUDA, "ormqr buffer size");
       dmax = std::max(dmax, (size_t)lw * sizeof(double));
@@ -374,7 +485,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   const bool qr_ok = s || on_lanes(
       [&](SvdLane& l, int k) {
         const JacJob& t = tab[k];
-        return cusolverDnXgeqrf(l.h, l.p, t.m, t.n, CUDA_R_64F, A + t.offA, t.m, CUDA_R_64F,
+        return cusolverDnXgeqrf(l.h, l.p, t.m, t.n, CUDA_R_64F, T + t.offA, t.m, CUDA_R_64F,
                                 tau + t.offTau, CUDA_R_64F, l.dwork, l.dbytes, l.hwork.data(),
                                 l.hwork.size(), qinfo + k) == CUSOLVER_STATUS_SUCCESS;
       },
@@ -382,7 +493,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   if (!s && !qr_ok) s = fail(c, DMRG3S_ERR_CUDA, "QR factorisation");
   // ---- 2. Y = R^T, V1 = I
   if (!s) {
-    jac_init_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, A, Y, V1);
+    jac_init_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, T, Y, V1);
     count_launch();
     s = cuda_ok(c, cudaGetLastError(), "Jacobi set-up");
   }
@@ -404,7 +515,9 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   std::vector<int> conv(nj, 0);
   Profiler& pr = c->prof;
   const int max_sweeps = jacobi_max_sweeps();
+  if (sweeps) *sweeps = 0;
   for (int sw = 0; !s && sw < max_sweeps; ++sw) {
+    if (sweeps) *sweeps = sw + 1;
     const int id = pr.on ? pr.begin(kProfJacobi, 0.0, 0.0, st) : -1;
     if (gexec) {
       s = cuda_ok(c, cudaGraphLaunch(gexec, st), "Jacobi sweep");
@@ -452,7 +565,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   // ---- 4. singular values in descending order, VT, (V1; 0) for the left vectors
   if (!s) {
     jac_norm_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, Y, sig);
-    jac_scatter_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, Y, V1, sig, S, VT, U);
+    jac_scatter_kernel<<<ncol, kJacThreads, 0, st>>>(dt, d_col, d_perm, Y, V1, sig, S, VT, U);
     count_launch(2);
     s = cuda_ok(c, cudaGetLastError(), "singular vectors");
   }
@@ -461,7 +574,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     const bool ok = on_lanes(
         [&](SvdLane& l, int k) {
           const JacJob& t = tab[k];
-          return cusolverDnDormqr(l.h, CUBLAS_SIDE_LEFT, CUBLAS_OP_N, t.m, t.n, t.n, A + t.offA,
+          return cusolverDnDormqr(l.h, CUBLAS_SIDE_LEFT, CUBLAS_OP_N, t.m, t.n, t.n, T + t.offA,
                                   t.m, tau + t.offTau, U + t.offU, t.m, (double*)l.dwork,
                                   (int)(l.dbytes / sizeof(double)),
                                   qinfo + k) == CUSOLVER_STATUS_SUCCESS;
