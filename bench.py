@@ -553,7 +553,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "tf32"])
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--svd", default="jacobi", choices=["jacobi", "gesvd"],
+    ap.add_argument("--svd", default="gesvd", choices=["gesvd", "jacobi"],
                     help="factorisation of the truncation's per-sector SVD")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

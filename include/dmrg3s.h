@@ -356,12 +356,12 @@ typedef struct dmrg3s_state_s* dmrg3s_state;
 
 /* Factorisation of the truncation's per-sector SVD (Sec. V step 4); both FP64. */
 typedef enum dmrg3s_svd_method {
-  DMRG3S_SVD_JACOBI = 0,  /* cuSOLVER QR, then one-sided Jacobi on R^T in this
+  DMRG3S_SVD_GESVD = 0,   /* cuSOLVER gesvd per sector on concurrent streams      */
+  DMRG3S_SVD_JACOBI = 1   /* cuSOLVER QR, then one-sided Jacobi on R^T in this
                              library's kernels, every sector in each launch
                              (dmrg3s_svd); an update whose Jacobi sweeps do not
                              converge redoes its SVD with gesvd
                              (dmrg3s_update_info.svd_fallback)                    */
-  DMRG3S_SVD_GESVD = 1    /* cuSOLVER gesvd per sector on concurrent streams      */
 } dmrg3s_svd_method;
 
 typedef struct dmrg3s_update_opts {

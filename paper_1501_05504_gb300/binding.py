@@ -400,7 +400,7 @@ class _UpdateOpts(ctypes.Structure):
                 ("svd", ctypes.c_int)]
 
 
-SVD_JACOBI, SVD_GESVD = 0, 1
+SVD_GESVD, SVD_JACOBI = 0, 1
 _SVD = {"jacobi": SVD_JACOBI, "gesvd": SVD_GESVD}
 
 
@@ -577,7 +577,7 @@ def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0, stre
     return State(ctx, W, M, left_env, right_env, centre, stream)
 
 
-def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False, svd="jacobi"):
+def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False, svd="gesvd"):
     return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)),
                        _SVD[svd] if isinstance(svd, str) else int(svd))
 

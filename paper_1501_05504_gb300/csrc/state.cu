@@ -242,7 +242,7 @@ struct Opts {
   double eps = 1e-12;
   bool optimise = true;
   dmrg3s_precision prec = DMRG3S_FP64;   // arithmetic of the eigensolver's H_eff products
-  dmrg3s_svd_method svd = DMRG3S_SVD_JACOBI;
+  dmrg3s_svd_method svd = DMRG3S_SVD_GESVD;
 };
 
 struct Info {

@@ -53,15 +53,18 @@ def test_stuck_spins_l20(b, ctx):
     assert abs(rep["energy"] - e0) < 1e-9 * abs(e0)
 
 
-def test_xx_chain_l100_closed_form(b, ctx):
+@pytest.mark.parametrize("svd", ["gesvd", "jacobi"])
+def test_xx_chain_l100_closed_form(b, ctx, svd):
+    """(Free fermions: Schmidt spectra with many equal singular values, the
+    hardest case met for the Jacobi SVD.)"""
     L = 100
     W = b.Mpo(b.MODEL_XXZ, L, (1.0, 0.0)).sites()
     st = _neel(b, ctx, W, L)
-    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 12, 1e-11, b.update_opts(256))
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 12, 1e-11, b.update_opts(256, svd=svd))
     st.close()
     e0 = exact.xx_chain_energy(L, 1.0)
-    print("XX chain L=100: %d updates of %d fell back to gesvd" % (
-        rep["svd_fallbacks"], 2 * (L - 1) * rep["sweeps"]))
+    print("XX chain L=100 (%s): %d updates of %d fell back to gesvd" % (
+        svd, rep["svd_fallbacks"], 2 * (L - 1) * rep["sweeps"]))
     assert abs(rep["energy"] - e0) < 1e-8 * abs(e0)
 
 
