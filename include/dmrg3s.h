@@ -140,11 +140,11 @@ dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
  * 6: environment update, 7: energy after truncation; flops and bytes are 0
  * for phases), around the other FP64 grouped GEMMs (kernel 8: the
  * truncation's S V^dagger products and the MPO-entry gradient), and around
- * each sweep of the truncation's Jacobi SVD (kernel 9: one record per sweep
- * covering its launches, the sweep-counter kernel and one launch per round;
- * flops 6n per column-pair test and 6n per rotated column pair, bytes 16n
- * per pair test and 16n per rotated pair, both doubled or tripled with the
- * left vectors' rotations).
+ * each sweep of the truncation's Jacobi SVD (kernel 9: one record per sweep,
+ * counting its launches: the sweep-counter kernel and one launch per round;
+ * flops: 6n per column-pair test plus, per rotation, 6n (12n when the left
+ * vectors' rotations are accumulated too); bytes: 16n per pair test plus,
+ * per rotation, 16n (48n with the left vectors)).
  * dmrg3s_profile(ctx, 1) resets and enables, 0 disables;
  * dmrg3s_profile_read synchronises on the recorded events and
  * returns, for one kernel, the number of launches, their summed device time
