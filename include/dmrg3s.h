@@ -332,9 +332,12 @@ dmrg3s_status dmrg3s_eigensolve(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
  *  HUBBARD  params {t, U}: -t sum_{i,s} (c+_{i,s} c_{i+1,s} + h.c.) + U sum_i n_up n_dn,
  *           Jordan-Wigner string, w = 6, d = 4 (index 2 n_up + n_dn), charges (N, 2 S^z).
  *  SPIN_BONDS: sum over `nbonds` pairs bonds[2k] < bonds[2k+1] of
- *           couplings[2k]/2 (S+ S- + S- S+) + couplings[2k+1] Sz Sz (d = 2), e.g.
- *           the snake-ordered cylinder; channels (S+, S-, Sz) per open site.
- * Open boundary conditions.  Host-only. */
+ *           couplings[2k]/2 (S+ S- + S- S+) + couplings[2k+1] Sz Sz, e.g. the
+ *           snake-ordered cylinder or a ring (the S = 1 chain of Sec. VII B 1
+ *           with its periodic link (0, l-1)); channels (S+, S-, Sz) per open
+ *           site.  params NULL: spin 1/2; else params[0] = 2S (1..8): d = 2S+1,
+ *           basis m = S, S-1, ..., -S, charge 2m.
+ * XXZ and HUBBARD have open boundary conditions.  Host-only. */
 typedef enum dmrg3s_model {
   DMRG3S_MODEL_XXZ = 0,
   DMRG3S_MODEL_HUBBARD = 1,

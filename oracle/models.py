@@ -15,6 +15,7 @@ Two independent routes are kept on purpose:
   routes can be compared entry by entry.
 
 Spin-1/2 local basis: index 0 = up, 1 = down, charge 2*S^z in {+1, -1}.
+Spin-S local basis (``two_s`` = 2S): index k holds m = S - k, charge 2m.
 Fermion (Hubbard) local basis: index 2*n_up + n_dn, i.e. 0=|0>, 1=|dn>,
 2=|up>, 3=|up dn>; charges (N, 2*S^z).  Mode order for the Jordan-Wigner
 string: site-major, spin-up before spin-down.
@@ -38,6 +39,19 @@ N_UP = A_UP.T @ A_UP
 N_DN = A_DN.T @ A_DN
 I4 = np.eye(4)
 HUB_Q = np.array([[0, 0], [1, -1], [1, 1], [2, 0]])   # (N, 2Sz) of 0,dn,up,updn
+
+
+def spin_ops(two_s):
+    """(S+, S-, Sz, identity, charges) of spin S = two_s / 2 in the basis
+    m = S, S-1, ..., -S: <m+1|S+|m> = sqrt(S(S+1) - m(m+1)), charge 2m."""
+    d = two_s + 1
+    S = two_s / 2.0
+    m = S - np.arange(d)
+    sp = np.zeros((d, d))
+    for k in range(1, d):          # |m = S - k> -> |m + 1> (index k - 1)
+        sp[k - 1, k] = np.sqrt(S * (S + 1) - m[k] * (m[k] + 1))
+    q = (two_s - 2 * np.arange(d)).reshape(d, 1)
+    return sp, sp.T.copy(), np.diag(m), np.eye(d), q
 
 
 class MPO:
@@ -118,8 +132,8 @@ def mpo_hubbard(L, t_hop=1.0, U=0.0):
     return MPO(Ws, HUB_Q.copy(), ts)
 
 
-def mpo_spin_bonds(L, bonds):
-    """Spin-1/2 Heisenberg-type MPO for arbitrary two-site couplings.
+def mpo_spin_bonds(L, bonds, two_s=1):
+    """Spin-S Heisenberg-type MPO (S = two_s / 2) for arbitrary two-site couplings.
 
     ``bonds`` is a list of ``(i, j, Jxy, Jz)`` with 0 <= i < j < L meaning
     ``Jxy/2 (S+_i S-_j + S-_i S+_j) + Jz Sz_i Sz_j``.  Finite-state layout: at
@@ -129,6 +143,8 @@ def mpo_spin_bonds(L, bonds):
     suite; for nearest-neighbour bonds it reproduces ``mpo_xxz``'s w = 5.
     """
     partners = {}
+    sp, sm, sz, eye, qphys = spin_ops(two_s)
+    d = two_s + 1
     for (i, j, jxy, jz) in bonds:
         assert 0 <= i < j < L
         partners.setdefault(i, []).append((j, jxy, jz))
@@ -144,7 +160,7 @@ def mpo_spin_bonds(L, bonds):
     chans[0] = [("start",)]
     chans[L] = [("done",)]
     qmap = {"S+": 2, "S-": -2, "Sz": 0}
-    opmap = {"S+": SP, "S-": SM, "Sz": SZ}
+    opmap = {"S+": sp, "S-": sm, "Sz": sz}
     close = {"S+": ("S-", 0.5), "S-": ("S+", 0.5), "Sz": ("Sz", None)}
     Ws, ts = [], []
     for k in range(L + 1):
@@ -153,11 +169,11 @@ def mpo_spin_bonds(L, bonds):
         cl, cr = chans[site], chans[site + 1]
         ixl = {c: n for n, c in enumerate(cl)}
         ixr = {c: n for n, c in enumerate(cr)}
-        Wi = np.zeros((2, 2, len(cl), len(cr)))
+        Wi = np.zeros((d, d, len(cl), len(cr)))
         if ("done",) in ixl and ("done",) in ixr:
-            Wi[:, :, ixl[("done",)], ixr[("done",)]] += I2
+            Wi[:, :, ixl[("done",)], ixr[("done",)]] += eye
         if ("start",) in ixl and ("start",) in ixr:
-            Wi[:, :, ixl[("start",)], ixr[("start",)]] += I2
+            Wi[:, :, ixl[("start",)], ixr[("start",)]] += eye
         # open new channels at this site
         if ("start",) in ixl:
             for op in ("S+", "S-", "Sz"):
@@ -169,14 +185,14 @@ def mpo_spin_bonds(L, bonds):
                 continue
             src, op = c
             if c in ixr:
-                Wi[:, :, ixl[c], ixr[c]] += I2
+                Wi[:, :, ixl[c], ixr[c]] += eye
             for (j, jxy, jz) in partners.get(src, []):
                 if j == site:
                     cop, half = close[op]
                     coef = jxy * half if half is not None else jz
                     Wi[:, :, ixl[c], ixr[("done",)]] += coef * opmap[cop]
         Ws.append(Wi)
-    return MPO(Ws, SPIN_HALF_Q.copy(), ts)
+    return MPO(Ws, qphys, ts)
 
 
 def cylinder_bonds(Lx, Ly, J=1.0):
@@ -251,16 +267,26 @@ def _two_site_op(op_i, i, op_j, j, L, d):
     return out
 
 
-def dense_spin_bonds(L, bonds):
-    """Dense spin-1/2 Hamiltonian sum Jxy (SxSx + SySy) + Jz SzSz over ``bonds``."""
-    sx = 0.5 * (SP + SM)
-    sy_im = 0.5 * (SP - SM)          # S^y = -i * sy_im ; S^y S^y = -(sy_im x sy_im)
-    H = np.zeros((2 ** L, 2 ** L))
+def dense_spin_bonds(L, bonds, two_s=1):
+    """Dense spin-S Hamiltonian sum Jxy (SxSx + SySy) + Jz SzSz over ``bonds``."""
+    if two_s == 1:
+        sp, sm, sz, d = SP, SM, SZ, 2
+    else:
+        sp, sm, sz, _, _ = spin_ops(two_s)
+        d = two_s + 1
+    sx = 0.5 * (sp + sm)
+    sy_im = 0.5 * (sp - sm)          # S^y = -i * sy_im ; S^y S^y = -(sy_im x sy_im)
+    H = np.zeros((d ** L, d ** L))
     for (i, j, jxy, jz) in bonds:
-        H += jxy * _two_site_op(sx, i, sx, j, L, 2)
-        H -= jxy * _two_site_op(sy_im, i, sy_im, j, L, 2)
-        H += jz * _two_site_op(SZ, i, SZ, j, L, 2)
+        H += jxy * _two_site_op(sx, i, sx, j, L, d)
+        H -= jxy * _two_site_op(sy_im, i, sy_im, j, L, d)
+        H += jz * _two_site_op(sz, i, sz, j, L, d)
     return H
+
+
+def ring_bonds(L, J=1.0):
+    """Heisenberg ring: nearest neighbours plus the link (0, L-1) closing it."""
+    return [(i, i + 1, J, J) for i in range(L - 1)] + [(0, L - 1, J, J)]
 
 
 def dense_xxz(L, J=1.0, Delta=1.0):

@@ -13,10 +13,13 @@
 //      with the Jordan-Wigner string (modes site-major, up before down):
 //      c+_i c_{i+1} = (a+ F)_i (a)_{i+1}, c+_{i+1} c_i = (F a)_i (a+)_{i+1}.
 //      Local basis index 2 n_up + n_dn, charges (N, 2 S^z).
-//  Spin bonds (general two-site couplings, e.g. the snake-ordered cylinder):
-//      channels at each MPO bond: done, then (S+, S-, Sz) held for every site
-//      left of the bond with a partner right of it, then start.
+//  Spin bonds (general two-site couplings, e.g. the snake-ordered cylinder or
+//      a ring): channels at each MPO bond: done, then (S+, S-, Sz) held for
+//      every site left of the bond with a partner right of it, then start.
+//      Spin S = two_s / 2, local basis m = S, S-1, ..., -S, charge 2m, with
+//      <m+1|S+|m> = sqrt(S(S+1) - m(m+1)).
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <memory>
 #include <set>
@@ -135,9 +138,21 @@ void build_hubbard(int L, double t, double U, Mpo* out) {
                   {0, 0, 1, 1, -1, -1, 1, -1, -1, 1, 0, 0}, out);
 }
 
-// bonds: nb entries (i, j) with i < j, couplings (Jxy, Jz)
-dmrg3s_status build_spin_bonds(int L, int nb, const int32_t* ij, const double* J, Mpo* out) {
-  const Mat I = {1, 0, 0, 1}, Sp = {0, 1, 0, 0}, Sm = {0, 0, 1, 0}, Sz = {0.5, 0, 0, -0.5};
+// bonds: nb entries (i, j) with i < j, couplings (Jxy, Jz); spin two_s / 2
+dmrg3s_status build_spin_bonds(int L, int nb, const int32_t* ij, const double* J, int two_s,
+                               Mpo* out) {
+  const int d = two_s + 1;
+  const double S = 0.5 * two_s;
+  Mat I((size_t)d * d, 0.0), Sp((size_t)d * d, 0.0), Sz((size_t)d * d, 0.0);
+  std::vector<int32_t> qp(d);
+  for (int k = 0; k < d; ++k) {
+    const double m = S - k;
+    I[(size_t)k * d + k] = 1.0;
+    Sz[(size_t)k * d + k] = m;
+    qp[k] = two_s - 2 * k;
+    if (k > 0) Sp[(size_t)(k - 1) * d + k] = std::sqrt(S * (S + 1.0) - m * (m + 1.0));
+  }
+  const Mat Sm = transpose(Sp, d);
   std::map<int, std::vector<std::pair<int, std::pair<double, double>>>> partners;
   for (int k = 0; k < nb; ++k) {
     const int i = ij[2 * k], j = ij[2 * k + 1];
@@ -176,12 +191,12 @@ dmrg3s_status build_spin_bonds(int L, int nb, const int32_t* ij, const double* J
   out->sites.resize(L);
   for (int i = 0; i < L; ++i) {
     SiteT& s = out->sites[i];
-    s.d = 2;
+    s.d = d;
     s.nsym = 1;
     s.wl = (int)chans[i].size();
     s.wr = (int)chans[i + 1].size();
-    s.W.assign((size_t)4 * s.wl * s.wr, 0.0);
-    s.qp = {1, -1};
+    s.W.assign((size_t)d * d * s.wl * s.wr, 0.0);
+    s.qp = qp;
     for (const Ch& c : chans[i]) s.tl.push_back(c.kind == 1 ? charge[c.op] : 0);
     for (const Ch& c : chans[i + 1]) s.tr.push_back(c.kind == 1 ? charge[c.op] : 0);
     const int dl = index(i, 0, 0, 0), dr = index(i + 1, 0, 0, 0);
@@ -235,7 +250,13 @@ dmrg3s_status dmrg3s_mpo_create(int32_t model, int32_t nsites, const double* par
       break;
     case DMRG3S_MODEL_SPIN_BONDS: {
       if (nbonds < 1 || !bonds || !couplings) return DMRG3S_ERR_ARG;
-      dmrg3s_status s = build_spin_bonds(nsites, nbonds, bonds, couplings, &h->m);
+      int two_s = 1;
+      if (params) {
+        if (!(params[0] >= 1.0 && params[0] <= 8.0) || params[0] != (double)(int)params[0])
+          return DMRG3S_ERR_ARG;
+        two_s = (int)params[0];
+      }
+      dmrg3s_status s = build_spin_bonds(nsites, nbonds, bonds, couplings, two_s, &h->m);
       if (s != DMRG3S_OK) return s;
       break;
     }
