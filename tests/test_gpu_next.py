@@ -77,3 +77,22 @@ def test_hubbard_u0_closed_form(b, ctx):
     st.close()
     e0 = exact.free_fermion_energy(L, L // 2, L // 2)
     assert abs(rep["energy"] - e0) < 1e-8 * abs(e0)
+
+
+def test_spin1_ring_l6_matches_ed(b, ctx):
+    """S = 1 Heisenberg ring (Sec. VII B 1 at L = 6; d = 3, periodic link
+    (0, 5), w = 8): sweeps reach the exact ground energy of the S^z = 0 sector."""
+    from oracle import models
+    L = 6
+    bonds = models.ring_bonds(L)
+    ij = [[i, j] for (i, j, _, _) in bonds]
+    cp = [[jx, jz] for (_, _, jx, jz) in bonds]
+    W = b.Mpo(b.MODEL_SPIN_BONDS, L, (2.0,), ij, cp).sites()
+    st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [0, 2] * (L // 2)), None, None,
+                               L - 1)
+    rep = b.dmrg3s_sweep(st, b.alpha_rule(1e-2), 12, 1e-13, b.update_opts(64, tol=1e-12))
+    st.close()
+    mpo = models.mpo_spin_bonds(L, bonds, 2)
+    e0 = exact.ed_ground_energy(models.dense_spin_bonds(L, bonds, 2),
+                                models.dense_charges(mpo.qphys, L), [0])
+    assert abs(rep["energy"] - e0) < 1e-9 * abs(e0)
