@@ -8,9 +8,9 @@
 //   3. M~ = [M* P] per charge sector of the expanded right bond; the neighbour
 //      is padded with zero rows (never materialised: the zero rows only meet
 //      the P columns, so step 5 multiplies with the M* part only)
-//   4. FP64 SVD of every sector (QR, then one-sided Jacobi on R^T in this
-//      library's kernels, all sectors in each launch [svd.cu]; or cuSOLVER
-//      gesvd, sectors concurrently on several streams) and global truncation
+//   4. FP64 SVD of every sector (cuSOLVER gesvd, sectors concurrently on
+//      several streams; or QR, then one-sided Jacobi on R^T in this library's
+//      kernels, all sectors in each launch [svd.cu]) and global truncation
 //      to m_max states: A~ = U
 //   5. B~_{i+1} = (S V^dagger)[:, M part] . B_{i+1}                     [grouped GEMM]
 //   6. L_i = L_{i-1} A~^dagger W_i A~                                   [plan]
@@ -499,9 +499,10 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   if ((s = run_copies(c, gather_m, m.data, m.lay.size, X, xoff, nullptr, 0, st))) return s;
   if (expand && (s = run_copies(c, gather_p, P, pl.size, X, xoff, nullptr, 0, st))) return s;
   dfree(P, st);
-  // ---- 4. SVD per sector (FP64, cuSOLVER gesvd on the tall orientation):
-  // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n.  The
-  // sectors are independent and run concurrently on the workers' streams.
+  // ---- 4. SVD per sector (FP64, on the tall orientation):
+  // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n.  cuSOLVER
+  // gesvd runs the independent sectors concurrently on the workers' streams;
+  // the Jacobi SVD (svd.cu) runs every sector in each of its launches.
   int64_t foff = 0, soff = 0;
   for (Sector& sc : secs) {
     sc.offU = foff;
