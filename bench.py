@@ -469,7 +469,7 @@ SWEEP_MODELS = {
 }
 
 
-def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0):
+def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0, svd="gesvd"):
     """Sweeps from a product state (Neel / alternating up-down), one dmrg3s_sweep call per sweep.
 
     ladder: list of (precision, until) pairs; a precision is used until the
@@ -492,7 +492,7 @@ def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0
     t0 = time.perf_counter()
     for _ in range(max_sweeps):
         prec, until = ladder[stage]
-        rep = b.dmrg3s_sweep(st, b.alpha_rule(alpha), 1, 0.0, b.update_opts(m_max, prec=prec))
+        rep = b.dmrg3s_sweep(st, b.alpha_rule(alpha), 1, 0.0, b.update_opts(m_max, prec=prec, svd=svd))
         alpha = rep["alpha"]
         e = rep["energy"]
         log.append((time.perf_counter() - t0, e, prec))
@@ -520,8 +520,9 @@ def run_sweep(args):
     ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
     L, m_max, model = args.sweep_sites, args.sweep_m, args.sweep_model
     cap = args.sweep_cap_s
-    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, cap_s=cap)
-    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, cap_s=cap)
+    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, cap_s=cap, svd=args.svd)
+    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, cap_s=cap,
+                       svd=args.svd)
     e_ref = min(fp64[-1][1], mixed[-1][1])
 
     def first(log):
@@ -541,7 +542,7 @@ def run_sweep(args):
                        "hamiltonian": "%s, L=%d" % (SWEEP_MODELS[model][3], L),
                        "m_max": m_max, "alpha0": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "start": "product state %s..., m=1" % SWEEP_MODELS[model][2],
-                       "cap_s_per_arm": cap},
+                       "svd": args.svd, "cap_s_per_arm": cap},
             "data": "synthetic"}
 
 
