@@ -203,8 +203,9 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
  * Outputs, back to back per matrix (device): S (n[k] singular values,
  * descending), VT (n[k] x n[k], ld n[k]; row c = right singular vector c,
  * zero for a zero singular value) and, when U is not NULL, U (m[k] x n[k],
- * ld m[k]; column c = left singular vector c).  Runs on `stream` and on the
- * context's own streams; synchronous (one host read per sweep).
+ * ld m[k]; column c = left singular vector c).  Runs on `stream` and on a
+ * cuSOLVER handle and stream created for the call (the local update reuses
+ * its state's); synchronous (one host read per sweep).
  * Errors: ARG (shapes), CUDA, NOT_CONVERGED (a matrix still rotating after
  * 40 sweeps, or after the number 1..40 in the environment variable
  * DMRG3S_JACOBI_SWEEPS; outputs then invalid). */
