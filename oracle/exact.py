@@ -66,3 +66,41 @@ def ed_sparse_spin(L, bonds, two_sz=0):
     H = sp.csr_matrix((vals, (rows, cols)), shape=(n, n)) + sp.diags(diag)
     w = sla.eigsh(H, k=1, which="SA", tol=1e-13, maxiter=100000)[0]
     return float(w[0])
+
+
+def ed_sparse_spin_s(L, bonds, two_s, two_sz=0):
+    """Ground energy of a spin-S bond Hamiltonian (S = two_s / 2) in the
+    2 S^z_total = two_sz sector: sum over bonds (i, j, Jxy, Jz) of
+    Jxy/2 (S+_i S-_j + S-_i S+_j) + Jz Sz_i Sz_j.  Basis states are integers in
+    base d = two_s + 1 (site 0 the most significant digit, digit k meaning
+    m = S - k), the order of the Kronecker-product Hamiltonians."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    d = two_s + 1
+    S = two_s / 2.0
+    allidx = np.arange(d ** L, dtype=np.int64)
+    digits = np.stack([(allidx // d ** (L - 1 - i)) % d for i in range(L)])   # (L, d^L)
+    keep = digits.sum(0) * 2 == L * two_s - two_sz
+    states, dig = allidx[keep], digits[:, keep]
+    m = S - dig                                                             # (L, n)
+    n = len(states)
+    diag = np.zeros(n)
+    rows, cols, vals = [], [], []
+    for (i, j, jxy, jz) in bonds:
+        diag += jz * m[i] * m[j]
+        # S+_i S-_j: m_i -> m_i + 1 (digit k_i - 1), m_j -> m_j - 1 (digit k_j + 1)
+        ok = (dig[i] >= 1) & (dig[j] <= two_s - 1)
+        src = np.nonzero(ok)[0]
+        amp = np.sqrt(S * (S + 1) - m[i, src] * (m[i, src] + 1)) * \
+            np.sqrt(S * (S + 1) - m[j, src] * (m[j, src] - 1))
+        dst_state = states[src] - d ** (L - 1 - i) + d ** (L - 1 - j)
+        dst = np.searchsorted(states, dst_state)
+        rows += [dst, src]
+        cols += [src, dst]
+        vals += [0.5 * jxy * amp, 0.5 * jxy * amp]
+    H = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n)) + sp.diags(diag)
+    if n <= 64:
+        return float(np.linalg.eigvalsh(H.toarray())[0])
+    w = sla.eigsh(H, k=1, which="SA", tol=1e-13, maxiter=100000)[0]
+    return float(w[0])

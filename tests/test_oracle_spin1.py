@@ -97,3 +97,22 @@ def test_dmrg3s_spin1_ring_reaches_ed():
     H = models.dense_spin_bonds(L, bonds, 2)
     e0 = exact.ed_ground_energy(H, models.dense_charges(mpo.qphys, L), [0])
     assert abs(log.energies[-1] - e0) < 1e-9 * abs(e0)
+
+
+@pytest.mark.parametrize("two_s,L", [(1, 8), (2, 6), (3, 4)])
+def test_sparse_ed_matches_dense(two_s, L):
+    bonds = models.ring_bonds(L)
+    H = models.dense_spin_bonds(L, bonds, two_s)
+    _, _, _, _, q = models.spin_ops(two_s)
+    e_dense = exact.ed_ground_energy(H, models.dense_charges(q, L), [0 if (L * two_s) % 2 == 0 else 1])
+    tz = 0 if (L * two_s) % 2 == 0 else 1
+    assert abs(exact.ed_sparse_spin_s(L, bonds, two_s, tz) - e_dense) < 1e-10 * abs(e_dense)
+
+
+def test_sparse_ed_closed_forms():
+    # four-site rings: -2S(2S+1); spin-1/2 chains: the existing spin-1/2 routine
+    for two_s in (1, 2, 3):
+        S = two_s / 2.0
+        assert abs(exact.ed_sparse_spin_s(4, models.ring_bonds(4), two_s) + 2 * S * (2 * S + 1)) < 1e-10
+    bonds = [(i, i + 1, 1.0, 0.6) for i in range(11)]
+    assert abs(exact.ed_sparse_spin_s(12, bonds, 1) - exact.ed_sparse_spin(12, bonds)) < 1e-10
