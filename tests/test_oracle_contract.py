@@ -284,6 +284,60 @@ def test_expansion_rl_leaves_state_unchanged():
     assert np.abs(dmrg3s.mps_to_dense(mps2) - psi_before).max() < 1e-13
 
 
+def expansion_rl_mirror_error(expand_rl, seed=7):
+    """Largest deviation of the right-to-left expansion term from the mirror
+    image of the left-to-right one (Sec. IV B).
+
+    Reflecting the chain swaps the two MPS bonds of M, the two MPO bonds of W
+    and the roles of L and R.  The R->L term on the chain is then the L->R
+    term on the reflected chain with its two bond indices exchanged:
+      P_rl[s', (bl, al), ar'] = P_lr^mirror[s', ar', (bl, al)],
+      P_lr^mirror = expansion_term_lr(R, W with (bl, br) swapped, M with (al, ar) swapped).
+    The L->R term is pinned by the printed two-spin example (Sec. IV C).
+    Checked on random unsymmetric tensors of unequal bond dimensions (so a
+    transposed operand or a swapped index cannot cancel) and on the XXZ MPO
+    of a warm U(1) state."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    d, wl, wr, ml, mr = 3, 4, 5, 6, 7
+    cases.append((rng.standard_normal((wr, mr, mr)), rng.standard_normal((d, d, wl, wr)),
+                  rng.standard_normal((d, ml, mr))))
+    mpo, drv = _warm_u1_state()
+    i = mpo.L - 2      # the right environment of site L-2, built from the last site
+    Re = contract.right_env(drv.Renv[i + 1], mpo.W[i + 1], drv.mps.M[i + 1])
+    cases.append((Re, mpo.W[i], drv.mps.M[i]))
+    err = 0.0
+    for R, W, M in cases:
+        got = expand_rl(R, W, M, 0.43)
+        mirror = contract.expansion_term_lr(R, np.transpose(W, (0, 1, 3, 2)),
+                                            np.transpose(M, (0, 2, 1)), 0.43)
+        ref = np.transpose(mirror, (0, 2, 1))
+        if got.shape != ref.shape:
+            return np.inf
+        err = max(err, float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)))
+    return err
+
+
+def test_expansion_rl_is_the_mirror_of_expansion_lr():
+    assert expansion_rl_mirror_error(contract.expansion_term_rl) < 1e-14
+
+
+def test_expansion_rl_basis_carries_the_expansion_term():
+    """After [M; P] and the SVD the kept right basis still holds all of M~ (no
+    truncation), P included (the mirror of the L->R check)."""
+    mpo, drv = _warm_u1_state()
+    mps = drv.mps
+    i = mps.L - 1
+    M = mps.M[i]
+    P = contract.expansion_term_rl(drv.Renv[i], mpo.W[i], M, 0.29)
+    assert np.linalg.norm(P) > 1e-3 * np.linalg.norm(M)
+    Mt = np.concatenate([M, P], axis=1)
+    ql_t = np.concatenate([mps.q[i], labels.combine(mpo.t[i], mps.q[i])], axis=0)
+    B, US, _ = dmrg3s.truncate_rl(Mt, mps.qphys, ql_t, mps.q[i + 1], 10 ** 6)
+    rebuilt = np.einsum("yk,skx->syx", US, B)
+    assert np.abs(rebuilt - Mt).max() < 1e-13 * np.abs(Mt).max()
+
+
 def test_truncation_error_is_discarded_weight():
     rng = np.random.default_rng(4)
     nos = np.zeros((2, 0), dtype=np.int64)

@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 from oracle import contract, models
-from test_oracle_contract import (_mixed_canonical, expansion_lr_errors, heff_projection_error,
-                                  two_spin_errors)
+from test_oracle_contract import (_mixed_canonical, expansion_lr_errors, expansion_rl_mirror_error,
+                                  heff_projection_error, two_spin_errors)
 
 
 def _heff_R_transposed(L, W, R, M):
@@ -74,3 +74,42 @@ def test_u1_expansion_pin_catches_fused_index_order():
     assert max(two_spin_errors(_expand_fused_index_wrong_order, 0.3, 0.6).values()) < 1e-14
     errs = expansion_lr_errors(_expand_fused_index_wrong_order)
     assert errs["after_svd"] > 1e-6 or errs["p_kept"] > 1e-6
+
+
+# ---- right-to-left expansion term: planted slips must break the mirror identity
+
+def _expand_rl_R_transposed(R, W, M, alpha):
+    return contract.expansion_term_rl(np.transpose(R, (0, 2, 1)), W, M, alpha)
+
+
+def _expand_rl_W_phys_swapped(R, W, M, alpha):
+    return contract.expansion_term_rl(R, np.transpose(W, (1, 0, 2, 3)), M, alpha)
+
+
+def _expand_rl_fused_index_wrong_order(R, W, M, alpha):
+    # (al, bl) with al the slower index instead of (bl, al)
+    U1 = np.einsum("sxy,cYy->csxY", M, R)
+    U2 = np.einsum("Ssbc,csxY->SxbY", W, U1)
+    P = alpha * U2
+    return P.reshape(P.shape[0], -1, P.shape[3])
+
+
+def _expand_rl_W_mpo_swapped(R, W, M, alpha):
+    # contracts R with the left MPO bond of W (only shape-compatible when wl == wr)
+    if W.shape[2] != W.shape[3]:
+        return contract.expansion_term_rl(R, W, M, alpha) * 1.5
+    return contract.expansion_term_rl(R, np.transpose(W, (0, 1, 3, 2)), M, alpha)
+
+
+def _expand_rl_dropped_channel(R, W, M, alpha):
+    W2 = W.copy()
+    W2[:, :, :, 0] = 0.0
+    return contract.expansion_term_rl(R, W2, M, alpha)
+
+
+@pytest.mark.parametrize("bad", [_expand_rl_R_transposed, _expand_rl_W_phys_swapped,
+                                 _expand_rl_fused_index_wrong_order, _expand_rl_W_mpo_swapped,
+                                 _expand_rl_dropped_channel])
+def test_rl_mirror_pin_catches(bad):
+    assert expansion_rl_mirror_error(contract.expansion_term_rl) < 1e-14
+    assert expansion_rl_mirror_error(bad) > 1e-3
