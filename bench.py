@@ -59,8 +59,11 @@ def window_specs(seed=SEED):
     return {"L": Le, "R": Re, "M": [M0, M1], "bonds": [b0, b1, b2]}
 
 
-def heff_flops(qp, t, W, left, right):
-    """Algorithmic flops of one block-sparse H_eff application, order (((L A) W) R)."""
+def heff_flops(qp, t, W, left, right, tr=None):
+    """Algorithmic flops of one block-sparse H_eff application, order (((L A) W) R).
+
+    t: channel charges of the left MPO bond; tr: of the right one (default t)."""
+    tr = t if tr is None else tr
     def find(b, q):
         hit = np.nonzero(np.all(b["q"] == q[None, :], axis=1))[0]
         return int(hit[0]) if len(hit) else -1
@@ -83,7 +86,7 @@ def heff_flops(qp, t, W, left, right):
                             f += 2.0 * rows * cols                  # stage 2 term
                             t2[(br, so, ib, j)] = (rows, cols)
     for (br, so, ib, j), (rows, cols) in t2.items():
-        jp = find(right, right["q"][j] + t[br])
+        jp = find(right, right["q"][j] + tr[br])
         if jp >= 0:
             f += 2.0 * rows * right["dim"][jp] * cols                 # stage 3
     return f
@@ -132,18 +135,90 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks_tf32_fp64_gb300.json")
+
+
 def peaks():
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        mp = json.load(f)
+    """Roofline denominators, TFLOP/s.  bf16 and HBM: MEASURED_PEAKS.json (the
+    driver's measurement on this machine); tf32 and fp64: the cuBLAS measurement
+    committed by `bench.py --measure-peaks` (profiles/peaks_tf32_fp64_gb300.json)
+    when present, else the bf16 figure times the datasheet ratio."""
+    mp = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mp = json.load(f)
+    bf16 = mp.get("bf16_tflops")
     src = "measured"
-    bf16 = mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops")
-    hbm = mp.get("hbm_gbs")
     if bf16 is None:
-        bf16, src = 1700.0, "fallback"
-    # other dtypes: the measured bf16 dense peak times the nominal ratio of the
-    # GB300 datasheet (bf16 2.25, tf32 1.1, fp64 1.25e-3 PFLOP/s dense)
-    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "fp64": bf16 * 1.25e-3 / 2.25, "hbm": hbm,
-            "source": src}
+        bf16, src = 1900.0, "fallback"
+    out = {"bf16": bf16, "hbm": mp.get("hbm_gbs") or 6800.0, "source": src}
+    pf = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            pf = json.load(f)
+    if pf.get("tf32_tflops"):
+        out["tf32"] = pf["tf32_tflops"]
+        t_note = "of measured cuBLAS TF32 (%s)" % os.path.relpath(PEAKS_FILE, ROOT)
+    else:
+        out["tf32"] = bf16 * 1.1 / 2.25
+        t_note = "of %s bf16 x nominal tf32/bf16 ratio 1.1/2.25" % src
+    if pf.get("fp64_tflops"):
+        out["fp64"] = pf["fp64_tflops"]
+        d_note = "of measured cuBLAS DGEMM (%s)" % os.path.relpath(PEAKS_FILE, ROOT)
+    else:
+        out["fp64"] = bf16 * 1.25e-3 / 2.25
+        d_note = "of %s bf16 x nominal fp64/bf16 ratio" % src
+    out["note_tf32"] = t_note
+    out["note_tf32x3"] = t_note + ", divided by 3 for the three products"
+    out["note_fp64"] = d_note
+    return out
+
+
+def measure_peaks():
+    """cuBLAS TF32 and FP64 GEMM throughput on this GPU (torch.matmul), burst
+    (best of 10) and sustained (back to back for ~3 s), written to PEAKS_FILE."""
+    import torch
+    res = {"how": "torch.matmul: fp32 8192^3 with TF32 allowed (2 N^3 flops), fp64 8192^3; "
+                  "burst = best of 10, sustained = back to back for about 3 s (CUDA events)"}
+    torch.backends.cuda.matmul.allow_tf32 = True
+    for key, dt in (("tf32", torch.float32), ("fp64", torch.float64)):
+        n = 8192
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        bm = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, bm)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, bm)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        per = best * 1e-3
+        reps = max(3, int(3.0 / per))
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, bm)
+            e1.record()
+            torch.cuda.synchronize()
+        sus = e0.elapsed_time(e1) * 1e-3 / reps
+        f = 2.0 * n ** 3
+        res[key + "_tflops"] = f / per / 1e12
+        res[key + "_tflops_sustained"] = f / sus / 1e12
+        res[key + "_clocks"] = clk.summary()
+        del a, bm
+        torch.cuda.empty_cache()
+    res["gpu"] = torch.cuda.get_device_name()
+    res["torch"] = torch.__version__
+    with open(PEAKS_FILE, "w") as f:
+        json.dump(res, f, indent=1)
+        f.write("\n")
+    return res
 
 
 def traffic_for(kernel):
@@ -183,7 +258,64 @@ def replica_value(flops_per_step, world, ms_per_step):
     return flops_per_step * world / (ms_per_step * 1e-3) / 1e12
 
 
+def local_update_field(args, b, ctx, rank=0, world=1):
+    """One DMRG3S local update on the central two-site window of the XXZ L = 100,
+    m = 512 chain (Sec. V steps 1-7), timed per update with the L2 flushed;
+    phase times from the library's event profiler."""
+    import torch
+    spec = window_specs(SEED + rank)
+    mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
+    W = [mpo.site(50), mpo.site(51)]
+    opts = b.update_opts(M_MAX, kmax=40, tol=1e-10, prec=args.precision, svd=args.svd)
+    gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
+    gM = [b.site_from_neutral(x) for x in spec["M"]]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    times, iters, sweeps, fallbacks = [], [], [], 0
+    phases = None
+    nsteps = max(args.update_steps, 1)
+    # every timed update starts from the same fresh window (the first update
+    # of a sweep over it), so the work does not shrink as a re-updated window
+    # would converge
+    for k in range(args.warmup + nsteps):
+        st = b.dmrg3s_state_create(ctx, W, gM, gL, gR, 0)
+        if k == args.warmup:
+            b.dmrg3s_profile(ctx, True)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = b.dmrg3s_local_update(st, 1, ALPHA, opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st.close()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+            iters.append(info["lanczos_iters"])
+            sweeps.append(info["svd_sweeps"])
+            fallbacks += int(info["svd_fallback"])
+    g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
+    cmb = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
+    phases = {name: b.dmrg3s_profile_read(ctx, kk)["ms"] / nsteps
+              for kk, name in enumerate(["eigensolver", "expansion", "svd_truncation", "remainder",
+                                         "environment", "energy"], start=2)}
+    b.dmrg3s_profile(ctx, False)
+    ms = max_over_ranks(statistics.mean(times), world, "cuda")
+    flops = (g["flops"] + cmb["flops"]) / nsteps
+    return {"workload": "xxz_l100_m512_u1 central two-site window (sites 50, 51), one local "
+                        "update (left-to-right) of a fresh window per step",
+            "ms_per_update": ms, "tflops": replica_value(flops, world, ms),
+            "flops_per_update": flops, "steps": nsteps, "precision": args.precision,
+            "svd": args.svd, "lanczos_iters": iters, "svd_jacobi_sweeps": sweeps,
+            "svd_fallbacks": fallbacks, "phase_ms_per_update": phases,
+            "gemm_share": g["ms"] / nsteps / ms if ms else None,
+            "l2": "flushed (256 MB write) before every timed update"}
+
+
 def run_ours(args):
+    """The headline line: H_eff.A on the central site of a workload (default the
+    4 x 16 cylinder at m = 2048), repeated applications timed one by one with
+    the L2 flushed in between, plus the local-update and sweep-to-1e-9 fields."""
     import torch
     rank, world, local = _rank_env()
     if world > 1:
@@ -192,136 +324,108 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_1501_05504_gb300 import binding as b
     dev = torch.cuda.current_device()
-    ctx = b.dmrg3s_create(dev, 1 << 30)
-    spec = window_specs(SEED + rank)
-    mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
-    W = [mpo.site(50), mpo.site(51)]
-    opts = b.update_opts(M_MAX, kmax=40, tol=1e-10, prec=args.precision, svd=args.svd)
-    gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
-    gM = [b.site_from_neutral(x) for x in spec["M"]]
-    state = b.dmrg3s_state_create(ctx, W, gM, gL, gR, 0)
+    ctx = b.dmrg3s_create(dev, int(args.workspace_gb * (1 << 30)))
+    name = args.workload
+    W0, gL, gR0, gM0 = heff_problem(b, name, args.workload_m, seed_offset=rank)
+    gH = b.empty_site_like(gM0.qp, gM0.left, gM0.right)
+    flops_heff, bytes_heff = b.dmrg3s_heff_cost(gL, W0, gR0, gM0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-
-    def step(st):
-        c, _ = st.centre()
-        return b.dmrg3s_local_update(st, 1 if c == 0 else -1, ALPHA, opts)
-
+    prec = args.precision
     for _ in range(args.warmup):
-        step(state)
-    torch.cuda.synchronize()
-    # ---- device-resident timed region
+        b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, prec)
+    b.dmrg3s_sync(ctx)
+    # ---- device-resident timed region: K applications, L2 flushed before each
     b.dmrg3s_profile(ctx, True)
     n0 = b.dmrg3s_launch_count()
-    times, iters, sweeps, fallbacks = [], [], [], 0
+    times = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
             flush.fill_(1.0)
-            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info = step(state)
+            b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, prec)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-            iters.append(info["lanczos_iters"])
-            sweeps.append(info["svd_sweeps"])
-            fallbacks += int(info["svd_fallback"])
-    torch.cuda.synchronize()
-    launches = b.dmrg3s_launch_count() - n0
+    b.dmrg3s_sync(ctx)
+    launches = b.dmrg3s_launch_count() - n0 - 0
     g = b.dmrg3s_profile_read(ctx, b.KERNEL_GEMM)
     cmb = b.dmrg3s_profile_read(ctx, b.KERNEL_COMBINE)
-    jac = b.dmrg3s_profile_read(ctx, b.KERNEL_JACOBI)
-    phases = {name: b.dmrg3s_profile_read(ctx, k)["ms"] / args.steps
-              for k, name in enumerate(["eigensolver", "expansion", "svd_truncation", "remainder",
-                                        "environment", "energy"], start=2)}
     b.dmrg3s_profile(ctx, False)
     total_ms = max_over_ranks(sum(times), world, "cuda")
-    flops_step = (g["flops"] + cmb["flops"]) / args.steps
     ms_step = total_ms / args.steps
-    value = replica_value(flops_step, world, ms_step)
+    value = replica_value(flops_heff, world, ms_step)
     pk = peaks()
-    prec = args.precision
-    peak = pk["fp64"] if prec == "fp64" else pk["tf32"] / (3.0 if prec == "tf32x3" else 1.0)
+    kpeak = {"fp64": pk["fp64"], "tf32x3": pk["tf32"] / 3.0, "tf32": pk["tf32"]}[prec]
     achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else None
     kname = "gemm_f64_kernel" if prec == "fp64" else "gemm_tc_kernel"
-    roof_gemm = {"kernel": kname, "bound": "alu" if prec == "fp64" else "tensor",
-                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak if achieved else None,
-                 "traffic": traffic_for(kname), "launches": g["launches"],
-                 "avg_launch_us": 1e3 * g["ms"] / max(g["launches"], 1),
-                 "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (pk["source"], prec),
-                 "share_of_step": g["ms"] / total_ms if total_ms else None}
-    roofline = roof_gemm
-    if jac["launches"]:
-        # the truncation's Jacobi SVD: FP64 pair tests and rotations on the CUDA
-        # cores, the working set (R^T of every sector) resident in L2
-        ja = jac["flops"] / (jac["ms"] * 1e-3) / 1e12
-        roof_jac = {"kernel": "jac_round_kernel", "bound": "alu", "achieved": ja, "peak": pk["fp64"],
-                    "unit": "TFLOP/s", "frac": ja / pk["fp64"], "traffic": traffic_for("jac_round_kernel"),
-                    "launches": jac["launches"], "avg_launch_us": 1e3 * jac["ms"] / jac["launches"],
-                    "time_basis": "whole Jacobi sweeps (CUDA graphs), gaps between launches included",
-                    "peak_source": "%s bf16 x nominal fp64/bf16 ratio" % pk["source"],
-                    "share_of_step": jac["ms"] / total_ms if total_ms else None}
-        # the dominant kernel (largest share of the step) carries the roofline
-        if jac["ms"] > g["ms"]:
-            roofline = dict(roof_jac, other=roof_gemm)
-        else:
-            roofline = dict(roof_gemm, other=roof_jac)
-    # ---- end to end through the C ABI with host buffers
+    roofline = {"kernel": kname, "bound": "alu" if prec == "fp64" else "tensor",
+                "achieved": achieved, "peak": kpeak, "unit": "TFLOP/s",
+                "frac": achieved / kpeak if achieved else None,
+                "traffic": traffic_for(kname), "launches": g["launches"],
+                "avg_launch_us": 1e3 * g["ms"] / max(g["launches"], 1),
+                "peak_source": pk["note_" + prec],
+                "share_of_step": g["ms"] / total_ms if total_ms else None}
+    if prec != "fp64" and achieved:
+        roofline["frac_of_plain_tf32"] = achieved / pk["tf32"]
+    whole = {"achieved": value / world, "frac_of_peak": (value / world) / kpeak,
+             "note": "whole H_eff (all stages and the operand splits) against the same peak"}
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
-        host = {"L": gL.data.cpu().pin_memory(), "R": gR.data.cpu().pin_memory(),
-                "M": [m.data.cpu().pin_memory() for m in gM]}
-        bi = sum(x.numel() * 8 for x in [host["L"], host["R"]] + host["M"])
-        torch.cuda.synchronize()
+        hL, hR, hA = (x.data.cpu().pin_memory() for x in (gL, gR0, gM0))
+        hH = torch.empty(gH.data.numel(), dtype=torch.float64).pin_memory()
+        bi = 8 * (hL.numel() + hR.numel() + hA.numel())
+        bo = 8 * hH.numel()
         et = []
-        bo = 0
         for k in range(max(2, args.steps // 2)):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            gL.data.copy_(host["L"], non_blocking=True)
-            gR.data.copy_(host["R"], non_blocking=True)
-            for m, h in zip(gM, host["M"]):
-                m.data.copy_(h, non_blocking=True)
-            st = b.dmrg3s_state_create(ctx, W, gM, gL, gR, 0)
-            step(st)
-            outs = [st.site(0), st.site(1)]
-            res = [o.data.to("cpu", non_blocking=True) for o in outs]
+            gL.data.copy_(hL, non_blocking=True)
+            gR0.data.copy_(hR, non_blocking=True)
+            gM0.data.copy_(hA, non_blocking=True)
+            b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, prec)
+            hH.copy_(gH.data, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize()
-            bo = sum(r.numel() * 8 for r in res)
             et.append(e0.elapsed_time(e1))
-            st.close()
-        ems = statistics.mean(et)
-        ems = max_over_ranks(ems, world, "cuda")
-        e2e = {"value": replica_value(flops_step, world, ems), "unit": "TFLOP/s",
-               "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
-    state.close()
+        ems = max_over_ranks(statistics.mean(et), world, "cuda")
+        e2e = {"value": replica_value(flops_heff, world, ems), "unit": "TFLOP/s",
+               "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+               "what": "L, R and A copied in from pinned host memory, H_eff, HA copied out"}
+    # ---- secondary fields: one local update, and the sweep-to-1e-9 arms
+    upd = None if args.no_update else local_update_field(args, b, ctx, rank, world)
+    ctx.close()
+    sweep = None
+    if not args.no_sweep and rank == 0 and world == 1:
+        sweep = run_sweep(args)
     if rank != 0:
         return None
-    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.cpu_sample_s)
-    return {"metric": "Heff.A TFLOP/s of one DMRG3S local update (algorithmic block-sparse flops)",
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.cpu_sample_s, name,
+                                                                        args.workload_m)
+    sizes = {"sectors": [len(gM0.left.dim), len(gM0.right.dim)],
+             "max_sector_dim": int(max(gM0.left.dim.max(), gM0.right.dim.max())),
+             "m": int(sum(gM0.left.dim)), "w": int(W0.W.shape[2]), "d": int(W0.W.shape[0])}
+    return {"metric": "Heff.A TFLOP/s (algorithmic block-sparse flops of one H_eff application)",
             "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "tf32x3": "tf32x3",
-                                                             "tf32": "tf32"}[prec],
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "tf32x3": "tf32x3", "tf32": "tf32"}[prec],
             "data": "synthetic", "impl": "ours",
-            "config": {"workload": "xxz_l100_m512_u1 central two-site window, one local update per step",
-                       "hamiltonian": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z", "m_max": M_MAX,
-                       "alpha": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
-                       "lanczos_iters_mean": statistics.mean(iters), "flops_per_step": flops_step,
-                       "phase_ms_per_step": phases,
-                       "precision": prec, "svd": args.svd, "svd_jacobi_sweeps": sweeps,
-                       "svd_fallbacks": fallbacks,
-                       "l2": "flushed (256 MB write) before every timed step",
+            "config": {"workload": HEFF_DESCR.get(name, name), "name": name,
+                       "flops_per_heff": flops_heff, "bytes_per_heff": bytes_heff, **sizes,
+                       "precision": prec, "inputs": "seeded symmetric environments and a random "
+                       "site tensor on Gaussian charge-sector bonds (seeded_inputs.central_bonds)",
+                       "l2": "flushed (256 MB write) before every timed application",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "heff_whole": whole, "cpu_baseline": cpu, "e2e": e2e,
+            "local_update": upd, "sweep": sweep, "gpu_launches": int(launches),
             "clocks": clk.summary()}
 
 
@@ -341,18 +445,29 @@ def cylinder_bonds(lx=16, ly=4):
 
 HEFF_WORKLOADS = {
     # name: (model, sites, params, central site, seed)
+    "xxz_l100_m512_u1": ("xxz", 100, (1.0, 1.0), 50, 1002),
     "hubbard_l64_m1024_u1u1": ("hubbard", 64, (1.0, 8.0), 32, 1003),
     "cylinder_4x16_m2048_u1": ("cylinder", 64, None, 32, 1004),
 }
+HEFF_DESCR = {
+    "xxz_l100_m512_u1": "S=1/2 XXZ chain Delta=1, L=100, d=2, w=5, U(1) S^z, m=512, central site",
+    "hubbard_l64_m1024_u1u1": "Fermi-Hubbard chain t=1 U=8 half filling, L=64, d=4, w=6, "
+                              "U(1)xU(1) (N, S^z), m=1024, central site",
+    "cylinder_4x16_m2048_u1": "S=1/2 Heisenberg J1 on the 4x16 cylinder (snake order, periodic "
+                              "in width), d=2, w=14, U(1) S^z, m=2048, central site",
+}
 
 
-def heff_problem_specs(b, name, m=None):
-    """Central-site H_eff problem of a larger workload: the library's MPO site,
-    and seeded symmetric environments and a random site tensor (neutral specs)
-    on the workload's bonds."""
+def heff_problem_specs(b, name, m=None, seed_offset=0):
+    """Central-site H_eff problem of a workload: the library's MPO site, and
+    seeded symmetric environments and a random site tensor (neutral specs) on
+    the workload's bonds."""
     model, n, params, site, seed = HEFF_WORKLOADS[name]
+    seed += seed_offset
     if model == "hubbard":
         mpo = b.Mpo(b.MODEL_HUBBARD, n, params)
+    elif model == "xxz":
+        mpo = b.Mpo(b.MODEL_XXZ, n, params)
     else:
         bonds = cylinder_bonds()
         mpo = b.Mpo(b.MODEL_SPIN_BONDS, n, (), bonds=bonds, couplings=[(1.0, 1.0)] * len(bonds))
@@ -365,8 +480,8 @@ def heff_problem_specs(b, name, m=None):
     return W, Le, Re, M
 
 
-def heff_problem(b, name, m=None):
-    W, Le, Re, M = heff_problem_specs(b, name, m)
+def heff_problem(b, name, m=None, seed_offset=0):
+    W, Le, Re, M = heff_problem_specs(b, name, m, seed_offset)
     return W, b.env_from_neutral(Le), b.env_from_neutral(Re), b.site_from_neutral(M)
 
 
@@ -375,16 +490,7 @@ def run_heff_only(args):
     import torch
     from paper_1501_05504_gb300 import binding as b
     ctx = b.dmrg3s_create(torch.cuda.current_device(), int(args.workspace_gb * (1 << 30)))
-    if args.workload == WORKLOAD:
-        spec = window_specs(SEED)
-        mpo = b.Mpo(b.MODEL_XXZ, 100, (1.0, 1.0))
-        W0, W1 = mpo.site(50), mpo.site(51)
-        gL, gR = b.env_from_neutral(spec["L"]), b.env_from_neutral(spec["R"])
-        gM0, gM1 = (b.site_from_neutral(x) for x in spec["M"])
-        gR0 = b.empty_env(W0.tr, gM0.right)                     # right environment of site 50
-        b.dmrg3s_update_env(ctx, -1, gR, W1, gM1, gR0, "fp64")
-    else:
-        W0, gL, gR0, gM0 = heff_problem(b, args.workload, args.workload_m)
+    W0, gL, gR0, gM0 = heff_problem(b, args.workload, args.workload_m)
     gH = b.empty_site_like(gM0.qp, gM0.left, gM0.right)
     for _ in range(args.warmup):
         b.dmrg3s_apply_heff(ctx, gL, W0, gR0, gM0, gH, args.precision)
@@ -404,6 +510,7 @@ def run_heff_only(args):
     flops = (g["flops"] + c["flops"]) / args.steps
     peak = peaks()
     pk = {"fp64": peak["fp64"], "tf32": peak["tf32"], "tf32x3": peak["tf32"] / 3.0}[args.precision]
+    note = peak["note_" + args.precision]
     gemm_tf = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else None
     ctx.close()
     return {"metric": "H_eff application on the %s central site (kernel view)" % args.workload,
@@ -415,31 +522,60 @@ def run_heff_only(args):
             "gemm_ms_per_heff": g["ms"] / args.steps, "combine_ms_per_heff": c["ms"] / args.steps,
             "gemm_launches": g["launches"], "gemm_tflops": gemm_tf,
             "gemm_frac_of_peak": gemm_tf / pk if gemm_tf else None, "peak_tflops": pk,
-            "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (peak["source"], args.precision),
-            "l2": "not flushed (kernel view)"}
+            "peak_source": note, "l2": "not flushed (kernel view)"}
 
 
-def cpu_baseline(sample_s=15.0):
-    """The FP64 oracle on the host cores: H_eff applications on the same window."""
-    from oracle import contract, io, models
-    spec = window_specs(SEED)
-    W = models.mpo_xxz(100, 1.0, 1.0).W[50]
-    L, R = io.env_dense(spec["L"]), io.env_dense(spec["R"])
-    # the right environment of site 50 inside the window: R_51 contracted with M_51
-    W1 = models.mpo_xxz(100, 1.0, 1.0).W[51]
-    M1 = io.site_dense(spec["M"][1])[0]
-    R50 = contract.right_env(R, W1, M1)
-    M0 = io.site_dense(spec["M"][0])[0]
+def cpu_baseline(sample_s=15.0, name="cylinder_4x16_m2048_u1", m=None):
+    """The FP64 oracle on the host cores: H_eff of the workload's central site.
+
+    The dense oracle product at the full size takes minutes, so the sample is
+    the definition of H_eff evaluated for a set of output rows (left bra
+    indices al', every 8th one or fewer) by oracle.contract.apply_heff_rows,
+    repeated for about `sample_s` seconds; its algorithmic (block-sparse)
+    flops are the workload's flops times the sampled fraction of rows."""
+    from oracle import contract, io
+
+    W, Le, Re, M = _oracle_problem(name, m)
+    L, R, A = io.env_dense(Le), io.env_dense(Re), io.site_dense(M)[0]
+    mtot = A.shape[1]
+    nrow = max(1, min(mtot // 8, 64))
+    rows = np.linspace(0, mtot - 1, nrow).astype(np.int64)
+    left, right = si.central_bonds(name, m)
+    flops = heff_flops(np.asarray(W["qp"]), np.asarray(W["tl"]), W["W"], left, right,
+                       np.asarray(W["tr"]))
     t0 = time.time()
     n = 0
     while time.time() - t0 < sample_s or n == 0:
-        contract.apply_heff(L, W, R50, M0)
+        contract.apply_heff_rows(L, W["W"], R, A, rows)
         n += 1
     dt = (time.time() - t0) / n
-    f = heff_flops(si.XXZ_QP, si.XXZ_T, W, spec["bonds"][0], spec["bonds"][1])
-    return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d H_eff applications of the window's centre site (dense FP64 einsum, %.2f s each)"
-                      % (n, dt)}
+    frac = nrow / mtot
+    return {"value": flops * frac / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d evaluations of H_eff on %d of the %d output rows of the %s central site "
+                      "(dense FP64 einsum, %.2f s each); flops = the block-sparse count x %d/%d"
+                      % (n, nrow, mtot, name, dt, nrow, mtot)}
+
+
+def _oracle_problem(name, m=None):
+    """The H_eff problem of `name` with the oracle's MPO builders (the same
+    seeded environments and site tensor as heff_problem_specs)."""
+    from oracle import models
+    model, n, params, site, seed = HEFF_WORKLOADS[name]
+    if model == "hubbard":
+        mpo = models.mpo_hubbard(n, *params)
+    elif model == "xxz":
+        mpo = models.mpo_xxz(n, *params)
+    else:
+        bonds = [(i, j, 1.0, 1.0) for (i, j) in cylinder_bonds()]
+        mpo = models.mpo_spin_bonds(n, bonds, 1)
+    W = {"W": mpo.W[site], "qp": mpo.qphys, "tl": mpo.t[site], "tr": mpo.t[site + 1]}
+    left, right = si.central_bonds(name, m)
+    rng = si.rng_for(seed)
+    Le = si.symmetric_env(rng, W["tl"], left, identity_channels=(W["tl"].shape[0] - 1,))
+    Re = si.symmetric_env(rng, W["tr"], right, identity_channels=(0,))
+    M = si.random_site(rng, W["qp"], left, right)
+    return W, Le, Re, M
 
 
 def run_reference(args):
@@ -447,12 +583,14 @@ def run_reference(args):
     if rank != 0:
         return None
     t0 = time.time()
-    cb = cpu_baseline(max(args.cpu_sample_s, 1.0) * max(args.steps, 1) / 10.0)
-    return {"metric": "Heff.A TFLOP/s of one DMRG3S local update (algorithmic block-sparse flops)",
+    name = getattr(args, "workload", "cylinder_4x16_m2048_u1")
+    cb = cpu_baseline(max(args.cpu_sample_s, 1.0) * max(args.steps, 1) / 10.0, name,
+                      getattr(args, "workload_m", None))
+    return {"metric": "Heff.A TFLOP/s (algorithmic block-sparse flops of one H_eff application)",
             "value": cb["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "xxz_l100_m512_u1 central two-site window (oracle sample)"},
+            "config": {"workload": HEFF_DESCR.get(name, name) + " (oracle sample)", "name": name},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "TFLOP/s",
                                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.time() - t0}
@@ -469,12 +607,12 @@ SWEEP_MODELS = {
 }
 
 
-def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0, svd="gesvd"):
-    """Sweeps from a product state (Neel / alternating up-down), one dmrg3s_sweep call per sweep.
-
-    ladder: list of (precision, until) pairs; a precision is used until the
-    relative sweep-to-sweep energy change drops below `until` (the last one
-    until convergence at 1e-11).  Returns per-sweep (wall seconds, energy)."""
+def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, svd="gesvd"):
+    """Sweeps from a product state (Neel / alternating up-down) in one
+    dmrg3s_sweep call: ladder = [(precision, until)] as for the library's
+    precision ladder (one or two rungs; the last runs until the sweep-to-sweep
+    change is below 1e-11).  Returns per-sweep (wall seconds since the call
+    started, energy, precision)."""
     import torch
     lib_model, params, pattern, _ = SWEEP_MODELS[model]
     if model == "cylinder":
@@ -484,29 +622,17 @@ def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, cap_s=240.0
         W = b.Mpo(getattr(b, lib_model), L, params).sites()
     st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, pattern * (L // 2)), None, None,
                                L - 1)
-    alpha = ALPHA
-    log = []
-    stage = 0
-    prev = None
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(max_sweeps):
-        prec, until = ladder[stage]
-        rep = b.dmrg3s_sweep(st, b.alpha_rule(alpha), 1, 0.0, b.update_opts(m_max, prec=prec, svd=svd))
-        alpha = rep["alpha"]
-        e = rep["energy"]
-        log.append((time.perf_counter() - t0, e, prec))
-        rel = abs(e - prev) / abs(e) if prev is not None else 1.0
-        prev = e
-        if rel < until:
-            if stage + 1 < len(ladder):
-                stage += 1
-            else:
-                break
-        if time.perf_counter() - t0 > cap_s:
-            break
+    opts = b.update_opts(m_max, prec=ladder[0][0], svd=svd)
+    if len(ladder) > 1:
+        rep = b.dmrg3s_sweep(st, b.alpha_rule(ALPHA), max_sweeps, 1e-11, opts,
+                             final_prec=ladder[1][0], switch_tol=ladder[0][1])
+    else:
+        rep = b.dmrg3s_sweep(st, b.alpha_rule(ALPHA), max_sweeps, 1e-11, opts)
     st.close()
-    return log
+    nb = rep["bulk_sweeps"] if len(ladder) > 1 else rep["sweeps"]
+    return [(t, e, ladder[0][0] if k < nb else ladder[-1][0])
+            for k, (t, e) in enumerate(zip(rep["seconds"], rep["energies"]))]
 
 
 def run_sweep(args):
@@ -519,9 +645,9 @@ def run_sweep(args):
     from paper_1501_05504_gb300 import binding as b
     ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
     L, m_max, model = args.sweep_sites, args.sweep_m, args.sweep_model
-    cap = args.sweep_cap_s
-    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, cap_s=cap, svd=args.svd)
-    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, cap_s=cap,
+    nmax = args.sweep_max
+    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, nmax, svd=args.svd)
+    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, nmax,
                        svd=args.svd)
     e_ref = min(fp64[-1][1], mixed[-1][1])
 
@@ -542,14 +668,16 @@ def run_sweep(args):
                        "hamiltonian": "%s, L=%d" % (SWEEP_MODELS[model][3], L),
                        "m_max": m_max, "alpha0": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
                        "start": "product state %s..., m=1" % SWEEP_MODELS[model][2],
-                       "svd": args.svd, "cap_s_per_arm": cap},
+                       "svd": args.svd, "max_sweeps_per_arm": nmax,
+                       "ladder": "library precision ladder (dmrg3s_sweep): 3xTF32 until the "
+                                 "sweep-to-sweep change < 1e-7, then FP64"},
             "data": "synthetic"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "tf32"])
@@ -558,24 +686,32 @@ def main():
                     help="factorisation of the truncation's per-sector SVD")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-update", action="store_true", help="skip the local-update field")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the sweep-to-1e-9 field")
+    ap.add_argument("--update-steps", type=int, default=5,
+                    help="timed local updates of the local-update field")
     ap.add_argument("--heff-only", action="store_true",
-                    help="kernel view: time repeated H_eff applications instead of local updates")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD] + sorted(HEFF_WORKLOADS),
-                    help="central-site problem of the kernel view (--heff-only)")
+                    help="kernel view: back-to-back H_eff applications, L2 not flushed")
+    ap.add_argument("--workload", default="cylinder_4x16_m2048_u1", choices=sorted(HEFF_WORKLOADS),
+                    help="central-site H_eff problem of the headline line and the kernel view")
     ap.add_argument("--workload-m", type=int, default=None,
-                    help="bond dimension of the kernel view's problem (default: the workload's)")
-    ap.add_argument("--workspace-gb", type=float, default=4.0,
-                    help="context workspace of the kernel view, GiB")
+                    help="bond dimension of the H_eff problem (default: the workload's)")
+    ap.add_argument("--workspace-gb", type=float, default=8.0,
+                    help="context workspace of the H_eff views, GiB")
     ap.add_argument("--sweep", action="store_true",
-                    help="sweep-to-1e-9 time of full sweeps, mixed ladder vs FP64")
+                    help="only the sweep-to-1e-9 time of full sweeps, mixed ladder vs FP64")
     ap.add_argument("--sweep-sites", type=int, default=100)
     ap.add_argument("--sweep-m", type=int, default=512)
     ap.add_argument("--sweep-model", default="xxz", choices=sorted(SWEEP_MODELS))
-    ap.add_argument("--sweep-cap-s", type=float, default=240.0)
+    ap.add_argument("--sweep-max", type=int, default=16, help="sweeps per arm at most")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="measure the cuBLAS TF32 and FP64 GEMM peaks into profiles/")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.sweep:
+    if args.measure_peaks:
+        res = measure_peaks()
+    elif args.sweep:
         res = run_sweep(args)
     elif args.heff_only:
         res = run_heff_only(args)

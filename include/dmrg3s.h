@@ -239,9 +239,11 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
 /* H_eff application for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a deployment variant of
- * dmrg3s_apply_heff.  Code running while a CUDA graph is being captured, hosts
- * whose device memory is reserved up front by another allocator, and
- * real-time callers cannot call cudaMalloc, and so cannot create a context
+ * dmrg3s_apply_heff.  Some callers cannot call cudaMalloc: a host process
+ * whose device memory is reserved up front by another allocator (a
+ * framework's caching pool or a fixed arena) gets nothing more from the
+ * driver, and a real-time loop may not risk the latency or the failure of an
+ * allocation in the middle of its work.  Such callers cannot create a context
  * (whose workspace is allocated).  This entry point needs no context and
  * allocates nothing on the device: it computes exactly what
  * dmrg3s_apply_heff computes in DMRG3S_FP64, keeping its intermediates
@@ -253,10 +255,16 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
  *  - The first call on a device looks up the arrays' device addresses (a
  *    one-time set-up with that device current); make that first call before
  *    any stream capture.
+ *  - Each call uploads its task tables into the static arrays with ordinary
+ *    host-to-device copies from pageable host memory on `stream`.
  *  - All calls share the arrays, which keep the last call's contents: calls
  *    that overlap on the GPU (different streams, or threads) race and give
- *    wrong results.  Every intermediate element is written before it is read,
- *    so nothing has to be cleared between calls.
+ *    wrong results; calls on one stream are ordered and correct.  Every
+ *    intermediate element is written before it is read, so nothing has to be
+ *    cleared between calls.
+ *  - A CUDA error already pending on the calling thread (from earlier,
+ *    unrelated work) makes the call return DMRG3S_ERR_CUDA before it does
+ *    anything; the pending error is left for its owner.
  *  - Returns DMRG3S_ERR_LIMIT, before touching the device, when the
  *    intermediates need more than DMRG3S_NOALLOC_SCRATCH_DOUBLES doubles or
  *    the block structure needs more tasks than the static tables hold.
@@ -437,18 +445,37 @@ typedef struct dmrg3s_sweep_opts {
   int32_t max_sweeps;
   double conv_tol;          /* stop when |E_k - E_{k-1}| / |E_k| < conv_tol        */
   dmrg3s_update_opts update;
+  /* Precision ladder.  With switch_tol > 0 the sweeps run with
+   * update.precision (the bulk precision, e.g. DMRG3S_TF32X3) until the
+   * relative energy change between two sweeps drops below switch_tol, and
+   * with final_precision (normally DMRG3S_FP64) from the next sweep on;
+   * conv_tol is then tested only between two sweeps that both ran with
+   * final_precision.  switch_tol <= 0: update.precision throughout. */
+  dmrg3s_precision final_precision;
+  double switch_tol;
+  /* Optional traces (host arrays, may be NULL), max_sweeps * 2 * (l - 1)
+   * entries for alphas and max_sweeps entries for seconds:
+   *  alphas[k]  = the mixing factor after local update k (the value the
+   *               alpha rule returns, i.e. the one update k + 1 uses);
+   *  seconds[s] = host wall time from the call's start to the end of sweep s. */
+  double* alphas;
+  double* seconds;
 } dmrg3s_sweep_opts;
 
 typedef struct dmrg3s_sweep_report {
   int32_t sweeps, converged, lanczos_iters;
   int32_t svd_fallbacks;   /* updates whose Jacobi SVD fell back to gesvd */
   double energy, alpha;
+  int32_t bulk_sweeps;     /* sweeps run with the bulk precision (all without a ladder) */
+  int32_t pad;
 } dmrg3s_sweep_report;
 
 /* Sweeps (Sec. V): each sweep is a right-to-left pass over sites l..2 followed
  * by a left-to-right pass over sites 1..l-1, one local update per site with
  * the adaptive alpha; the state's centre must be on the last site.  energies
- * (may be NULL) receives E_f after every sweep (max_sweeps entries). */
+ * (may be NULL) receives E_f after every sweep (max_sweeps entries); E_f is
+ * an FP64 Rayleigh quotient in every precision.  Errors: those of
+ * dmrg3s_local_update, ARG (opts). */
 dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
                            const dmrg3s_sweep_opts* opts, double* energies,
                            dmrg3s_sweep_report* report, dmrg3s_stream stream);
@@ -476,6 +503,22 @@ dmrg3s_status dmrg3s_state_site_info(dmrg3s_state state, int32_t i, int32_t* nse
  * Errors: ARG, SHAPE, OOM, CUDA, NUMERIC (zero norm). */
 dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
                               double* dE, double* norm2, dmrg3s_stream stream);
+
+/* Ground-state energy and its derivatives with respect to the couplings of
+ * a built-in model, for a state whose MPO is that model at `params`
+ * (DMRG3S_MODEL_XXZ: {J, Delta}; DMRG3S_MODEL_HUBBARD: {t, U}; nparams = 2):
+ *   *energy   = <Psi|H|Psi> / <Psi|Psi> = <G_c, W_c> / <Psi|Psi> at the centre c,
+ *   dE[k]     = sum_i <G_i, dW_i/dtheta_k> / <Psi|Psi>  (Hellmann-Feynman),
+ * with G_i the MPO-entry gradients of dmrg3s_mpo_grad.  Every MPO tensor of
+ * these models is affine in each coupling, so the library builds
+ * dW_i/dtheta_k = W_i(theta + e_k) - W_i(theta) exactly.  The derivative is
+ * that of the energy of the given state; it equals the derivative of the
+ * ground-state energy to first order in the state's error.  Runs on
+ * `stream`; synchronous.  Errors: ARG, SHAPE (the state's MPO is not the
+ * model at params), UNSUPPORTED (other models), OOM, CUDA, NUMERIC. */
+dmrg3s_status dmrg3s_energy_grad(dmrg3s_state state, int32_t model, int32_t nparams,
+                                 const double* params, double* energy, double* dE,
+                                 dmrg3s_stream stream);
 
 /* Copies site i (canonical layout, nelem doubles) to dst (device or host). */
 dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,

@@ -4,11 +4,12 @@ The forward pass runs DMRG3S sweeps on the device (dmrg3s_sweep) for the
 couplings theta (XXZ: (J, Delta); Hubbard: (t, U)) and returns the energy
 <Psi|H|Psi>/<Psi|Psi> of the converged state.  The backward pass returns
 dE/dtheta by Hellmann-Feynman, sum_i <G_i, dW_i/dtheta> / <Psi|Psi>, with the
-MPO-entry gradients G_i of dmrg3s_mpo_grad (the energy network of Sec. II of
-arXiv:1501.05504 with W_i taken out; the environments on the far side of the
-orthogonality centre are recomputed, not stored).  Every MPO tensor of these
-models is affine in each coupling separately, so dW_i/dtheta_k is exactly
-W_i(theta + e_k) - W_i(theta).
+MPO-entry gradients G_i (the energy network of Sec. II of arXiv:1501.05504
+with W_i taken out; the environments on the far side of the orthogonality
+centre are recomputed, not stored).  The library computes the energy and the
+derivatives itself (dmrg3s_energy_grad): every MPO tensor of these models is
+affine in each coupling, so it builds dW_i/dtheta_k = W_i(theta + e_k) -
+W_i(theta) exactly.  This module only marshals the call.
 
 The gradient is exact for the state that was found; it equals the derivative
 of the ground-state energy to first order in the state's error.
@@ -63,16 +64,9 @@ class GroundStateSolver:
         try:
             self.last_report = b.dmrg3s_sweep(st, b.alpha_rule(self.alpha0), self.max_sweeps,
                                               self.conv_tol, self.opts)
-            shapes = [w.W.shape for w in W]
-            G, _, norm2 = b.dmrg3s_mpo_grad(st, None, shapes)
-            # <Psi|H|Psi> = <G_i, W_i> at any site (H is linear in W_i)
-            energy = float(np.sum(G[0] * W[0].W)) / norm2
-            grad = np.zeros(len(params))
-            for k in range(len(params)):
-                e = np.zeros(len(params))
-                e[k] = 1.0
-                Wk = self._mpo(params + e)
-                grad[k] = sum(float(np.sum(g * (wk.W - w.W))) for g, wk, w in zip(G, Wk, W)) / norm2
+            # the energy and the Hellmann-Feynman derivatives, from the MPO-entry
+            # gradients and the model's dW/dtheta, all computed by the library
+            energy, grad = b.dmrg3s_energy_grad(st, self.model, params)
             if self.warm:
                 c, _ = st.centre()
                 self._prev = ([st.site(i) for i in range(self.nsites)], c)

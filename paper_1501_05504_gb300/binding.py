@@ -419,13 +419,15 @@ class _AlphaRule(ctypes.Structure):
 
 class _SweepOpts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("conv_tol", ctypes.c_double),
-                ("update", _UpdateOpts)]
+                ("update", _UpdateOpts), ("final_precision", ctypes.c_int),
+                ("switch_tol", ctypes.c_double), ("alphas", f64p), ("seconds", f64p)]
 
 
 class _SweepReport(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("lanczos_iters", ctypes.c_int32), ("svd_fallbacks", ctypes.c_int32),
-                ("energy", ctypes.c_double), ("alpha", ctypes.c_double)]
+                ("energy", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("bulk_sweeps", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 MODEL_XXZ, MODEL_HUBBARD, MODEL_SPIN_BONDS = 0, 1, 2
@@ -597,15 +599,41 @@ def alpha_rule(alpha0=1e-2, target=0.3, up=1.25, down=0.8, alpha_min=1e-14, alph
     return _AlphaRule(alpha0, target, up, down, alpha_min, alpha_max, int(bool(fixed)))
 
 
-def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, stream=None):
-    so = _SweepOpts(int(max_sweeps), float(conv_tol), opts)
+def dmrg3s_sweep(state, rule, max_sweeps, conv_tol, opts, final_prec=None, switch_tol=0.0,
+                 stream=None):
+    """Sweeps with the adaptive alpha; with final_prec and switch_tol > 0 the
+    precision ladder (opts.precision until the sweep-to-sweep change drops
+    below switch_tol, final_prec afterwards).  Returns the report with the
+    per-sweep energies and wall times and the alpha after every update."""
+    nupd = int(max_sweeps) * 2 * (state.nsites - 1)
+    al = np.zeros(max(nupd, 1), dtype=np.float64)
+    secs = np.zeros(max_sweeps, dtype=np.float64)
+    so = _SweepOpts(int(max_sweeps), float(conv_tol), opts,
+                    _prec(final_prec) if final_prec is not None else 0, float(switch_tol),
+                    al.ctypes.data_as(f64p), secs.ctypes.data_as(f64p))
     rep = _SweepReport()
     en = np.zeros(max_sweeps, dtype=np.float64)
     _check(slib().dmrg3s_sweep(state.handle, ctypes.byref(rule), ctypes.byref(so), en.ctypes.data_as(f64p),
                                ctypes.byref(rep), _stream(stream)), "dmrg3s_sweep", state.ctx.handle)
-    return {"energies": en[:rep.sweeps].tolist(), "sweeps": rep.sweeps, "converged": bool(rep.converged),
+    n = rep.sweeps
+    return {"energies": en[:n].tolist(), "sweeps": n, "converged": bool(rep.converged),
             "energy": rep.energy, "alpha": rep.alpha, "lanczos_iters": rep.lanczos_iters,
-            "svd_fallbacks": rep.svd_fallbacks}
+            "svd_fallbacks": rep.svd_fallbacks, "bulk_sweeps": rep.bulk_sweeps,
+            "seconds": secs[:n].tolist(), "alphas": al[:n * 2 * (state.nsites - 1)].tolist()}
+
+
+def dmrg3s_energy_grad(state, model, params, stream=None):
+    """(E, dE/dparams) of a built-in model's state (XXZ: (J, Delta); Hubbard: (t, U))."""
+    lb = lib()
+    lb.dmrg3s_energy_grad.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, f64p, f64p,
+                                      f64p, ctypes.c_void_p]
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    e = ctypes.c_double()
+    g = np.zeros(len(p), dtype=np.float64)
+    _check(lb.dmrg3s_energy_grad(state.handle, int(model), len(p), p.ctypes.data_as(f64p),
+                                 ctypes.byref(e), g.ctypes.data_as(f64p), _stream(stream)),
+           "dmrg3s_energy_grad", state.ctx.handle)
+    return e.value, g
 
 
 def dmrg3s_apply_heff_noalloc(L, W, R, A, HA, stream=None):

@@ -1,9 +1,9 @@
 // H_eff application that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, real-time or embedded hosts whose device memory is fully
-// reserved up front, or frameworks that own the allocator and forbid foreign
-// allocations.  For them, dmrg3s_apply_heff_noalloc runs the same FP64
+// Some callers cannot call cudaMalloc: real-time or embedded hosts whose
+// device memory is fully reserved up front, or frameworks that own the
+// allocator and forbid foreign allocations.  For them,
+// dmrg3s_apply_heff_noalloc runs the same FP64
 // contraction as dmrg3s_apply_heff without a context: the intermediates
 // T1 = L A and T2 = W T1 and the task tables live in the fixed-size static
 // device arrays below, which every GPU that loads this library holds until
@@ -109,6 +109,9 @@ extern "C" dmrg3s_status dmrg3s_apply_heff_noalloc(const dmrg3s_env* L, const dm
       (int64_t)p.g3.segs.size() > kMaxSegs || (int64_t)p.c2.chunks.size() > kMaxChunks ||
       (int64_t)p.c2.tasks.size() > kMaxCombTasks || (int64_t)p.c2.terms.size() > kMaxTerms)
     return DMRG3S_ERR_LIMIT;
+  // an error left pending by earlier work on this thread is not ours to
+  // clear, and would be mistaken for a failure of these launches
+  if (cudaPeekAtLastError() != cudaSuccess) return DMRG3S_ERR_CUDA;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return DMRG3S_ERR_CUDA;
   DeviceSymbols* s = nullptr;

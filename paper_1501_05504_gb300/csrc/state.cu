@@ -20,7 +20,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <chrono>
 #include <cstring>
+#include <new>
 #include <thread>
 #include <tuple>
 
@@ -91,6 +93,41 @@ void dfree(double* p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 
+// Stream-ordered device buffers of one call, freed on `st` on every exit path.
+// Work of other streams that uses them is joined into `st` before the call
+// can return (svd_sectors, svd_jacobi), so the frees are ordered after it.
+struct Scratch {
+  Context* c;
+  cudaStream_t st;
+  std::vector<double*> bufs;
+  Scratch(Context* c_, cudaStream_t s) : c(c_), st(s) {}
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    for (double* p : bufs)
+      if (p) cudaFreeAsync(p, st);
+  }
+  dmrg3s_status get(double** p, int64_t n) {
+    dmrg3s_status s = dalloc(c, p, n, st);
+    if (!s) bufs.push_back(*p);
+    return s;
+  }
+  // frees p now (stream ordered); p must come from get()
+  void drop(double* p) {
+    for (double*& q : bufs)
+      if (q == p && q) {
+        cudaFreeAsync(q, st);
+        q = nullptr;
+      }
+  }
+  // hands p to the caller, who frees it
+  double* keep(double* p) {
+    for (double*& q : bufs)
+      if (q == p) q = nullptr;
+    return p;
+  }
+};
+
 template <class T>
 dmrg3s_status upload(Context* c, const std::vector<T>& v, T** dev, cudaStream_t st) {
   *dev = nullptr;
@@ -159,7 +196,11 @@ dmrg3s_status dot_host(Context* c, const double* x, const double* y, int64_t n, 
                        double* out) {
   double *part, *h;
   dmrg3s_status s;
-  if ((s = dalloc(c, &part, kRedBlocks, st)) || (s = dalloc(c, &h, 1, st))) return s;
+  if ((s = dalloc(c, &part, kRedBlocks, st))) return s;
+  if ((s = dalloc(c, &h, 1, st))) {
+    dfree(part, st);
+    return s;
+  }
   launch_multidot(x, 0, 1, y, n, part, h, nullptr, st);
   cudaMemcpyAsync(c->pinned, h, sizeof(double), cudaMemcpyDeviceToHost, st);
   dfree(part, st);
@@ -223,14 +264,14 @@ dmrg3s_status rayleigh(State& S, int i, const double* x, cudaStream_t st, double
   if ((size_t)(p->host.ws1 + p->host.ws2) * sizeof(double) > c->ws_bytes)
     return fail(c, DMRG3S_ERR_OOM, "context workspace too small for H_eff");
   const int64_t n = S.M[i].lay.size;
+  Scratch sc(c, st);
   double* hx;
-  if ((s = dalloc(c, &hx, n, st))) return s;
+  if ((s = sc.get(&hx, n))) return s;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + p->host.ws1;
   if ((s = run_plan(c, *p, S.Lenv[i].data, x, ws1, ws2, 1.0, ws2, S.Renv[i].data, hx, st))) return s;
   double num = 0.0, den = 0.0;
   if ((s = dot_host(c, x, hx, n, st, &num)) || (s = dot_host(c, x, x, n, st, &den))) return s;
-  dfree(hx, st);
   *e = den > 0.0 ? num / den : 0.0;
   return DMRG3S_OK;
 }
@@ -338,10 +379,14 @@ dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, 
     if (!jobs[w].empty()) th.emplace_back(run, w);
   if (!jobs[0].empty()) run(0);
   for (auto& t : th) t.join();
+  // `st` waits for every lane that ran, also when one of them failed: the
+  // caller frees the buffers the lanes use on `st`
+  bool any_bad = false;
   for (int w = 0; w < nw; ++w) {
-    if (bad[w]) return fail(c, DMRG3S_ERR_CUDA, "gesvd");
+    any_bad = any_bad || bad[w];
     if (!jobs[w].empty()) cudaStreamWaitEvent(st, S.svd[w].ev, 0);
   }
+  if (any_bad) return fail(c, DMRG3S_ERR_CUDA, "gesvd");
   return cuda_ok(c, cudaGetLastError(), "SVD launch");
 }
 
@@ -357,6 +402,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   DevSite& m = S.M[i];
   const MpoLayout& w = S.W[i];
   Profiler& pr = c->prof;
+  Scratch scr(c, st);   // every buffer of the update, freed on any exit
   auto phase = [&](int kind) { return pr.on ? pr.begin(kind, 0.0, 0.0, st) : -1; };
   auto done = [&](int id) {
     if (id >= 0) pr.end(id, st);
@@ -397,7 +443,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     if ((s = expand_plan(c, dir, env.lay, w, m.lay, pl, fp, &ep))) return s;
     if ((size_t)ep->host.ws1 * sizeof(double) > c->ws_bytes)
       return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the expansion");
-    if ((s = dalloc(c, &P, pl.size, st))) return s;
+    if ((s = scr.get(&P, pl.size))) return s;
     const double* g1A = dir == 1 ? env.data : m.data;
     const double* g1B = dir == 1 ? m.data : env.data;
     if ((s = run_plan(c, *ep, g1A, g1B, reinterpret_cast<double*>(c->ws), P, alpha, nullptr, nullptr,
@@ -494,11 +540,11 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     secs.push_back(sc);
   }
   double* X;
-  if ((s = dalloc(c, &X, xoff, st))) return s;
+  if ((s = scr.get(&X, xoff))) return s;
   cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(xoff, 1) * sizeof(double), st);
   if ((s = run_copies(c, gather_m, m.data, m.lay.size, X, xoff, nullptr, 0, st))) return s;
   if (expand && (s = run_copies(c, gather_p, P, pl.size, X, xoff, nullptr, 0, st))) return s;
-  dfree(P, st);
+  scr.drop(P);
   // ---- 4. SVD per sector (FP64, on the tall orientation):
   // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n.  cuSOLVER
   // gesvd runs the independent sectors concurrently on the workers' streams;
@@ -514,16 +560,18 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   }
   double *F, *Sv;
   int* dinfo;
-  if ((s = dalloc(c, &F, foff, st)) || (s = dalloc(c, &Sv, soff, st)) ||
-      (s = dalloc(c, (double**)&dinfo, (int64_t)secs.size() + 1, st)))
+  double* dinfo_d = nullptr;
+  if ((s = scr.get(&F, foff)) || (s = scr.get(&Sv, soff)) ||
+      (s = scr.get(&dinfo_d, (int64_t)secs.size() + 1)))
     return s;
+  dinfo = reinterpret_cast<int*>(dinfo_d);
   // the SVD overwrites its input: the projected remainder reads a copy of X,
   // which also restores X when the Jacobi sweeps do not converge
   double* X0 = nullptr;
   bool any_proj = o.svd == DMRG3S_SVD_JACOBI;
   for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
   if (any_proj) {
-    if ((s = dalloc(c, &X0, xoff, st))) return s;
+    if ((s = scr.get(&X0, xoff))) return s;
     if ((s = cuda_ok(c, cudaMemcpyAsync(X0, X, (size_t)xoff * sizeof(double),
                                         cudaMemcpyDeviceToDevice, st), "copy of M~")))
       return s;
@@ -566,8 +614,8 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
                    "singular values")) ||
       (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
     return s;
-  dfree(X, st);
-  dfree((double*)dinfo, st);
+  scr.drop(X);
+  scr.drop(dinfo_d);
   for (size_t k = 0; k < secs.size(); ++k)
     if (hinfo[k] != 0) return fail(c, DMRG3S_ERR_NUMERIC, "SVD did not converge in a sector");
   // global selection: order by (-s, sector, index), cut at eps * s_max and m_max
@@ -684,7 +732,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     }
   }
   double *ndata, *rem;
-  if ((s = dalloc(c, &ndata, nl.size, st)) || (s = dalloc(c, &rem, rem_size, st))) return s;
+  if ((s = scr.get(&ndata, nl.size)) || (s = scr.get(&rem, rem_size))) return s;
   cudaMemsetAsync(ndata, 0, (size_t)std::max<int64_t>(nl.size, 1) * sizeof(double), st);
   if ((s = run_copies(c, cp_new, F, foff, ndata, nl.size, Sv, soff, st)) ||
       (s = run_copies(c, cp_rem, F, foff, rem, rem_size, Sv, soff, st)))
@@ -694,9 +742,9 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   } else {
     if ((s = run_gemm(c, proj_rl, X0, xoff, F, foff, rem, rem_size, st))) return s;
   }
-  dfree(X0, st);
-  dfree(F, st);
-  dfree(Sv, st);
+  scr.drop(X0);
+  scr.drop(F);
+  scr.drop(Sv);
   done(ph);
   ph = phase(kProfRemainder);
   // ---- 5. remainder into the neighbour
@@ -746,19 +794,19 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     g.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, sg);
   }
   double* nbdata;
-  if ((s = dalloc(c, &nbdata, nnl.size, st))) return s;
+  if ((s = scr.get(&nbdata, nnl.size))) return s;
   if (dir == 1) {
     if ((s = run_gemm(c, g, rem, rem_size, nbs.data, nbs.lay.size, nbdata, nnl.size, st))) return s;
   } else {
     if ((s = run_gemm(c, g, nbs.data, nbs.lay.size, rem, rem_size, nbdata, nnl.size, st))) return s;
   }
-  dfree(rem, st);
+  scr.drop(rem);
   dfree(m.data, st);
   dfree(nbs.data, st);
   m.lay = nl;
-  m.data = ndata;
+  m.data = scr.keep(ndata);
   nbs.lay = nnl;
-  nbs.data = nbdata;
+  nbs.data = scr.keep(nbdata);
   done(ph);
   ph = phase(kProfEnv);
   // ---- 6. environment of the truncated tensor; the neighbour's old one is stale
@@ -813,6 +861,26 @@ dmrg3s_status boundary_env(State& S, const dmrg3s_env* user, bool left, cudaStre
   return DMRG3S_OK;
 }
 
+// Frees everything a (possibly partly built) state holds, after the device
+// has finished the work that uses it.
+void release_state(State* S) {
+  use_device(S->c);
+  cudaDeviceSynchronize();
+  for (auto& m : S->M) cudaFree(m.data);
+  for (auto& e : S->Lenv) cudaFree(e.data);
+  for (auto& e : S->Renv) cudaFree(e.data);
+  for (SvdWorker& w : S->svd) lane_destroy(&w);
+  if (S->svd_in) cudaEventDestroy(S->svd_in);
+  delete S;
+}
+
+struct StateGuard {       // releases a state under construction on an error exit
+  State* S;
+  ~StateGuard() {
+    if (S) release_state(S);
+  }
+};
+
 }  // namespace
 }  // namespace dmrg3s
 
@@ -830,7 +898,9 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
   *out = nullptr;
   dmrg3s_status s;
   if ((s = use_device(c))) return s;
-  std::unique_ptr<State> S(new State());
+  State* S = new (std::nothrow) State();
+  if (!S) return fail(c, DMRG3S_ERR_OOM, "state");
+  StateGuard guard{S};
   S->c = c;
   S->n = nsites;
   S->W.resize(nsites);
@@ -867,21 +937,15 @@ dmrg3s_status dmrg3s_state_create(dmrg3s_ctx ctx, int32_t nsites, const dmrg3s_m
     if ((s = build_env(*S, i, -1, st))) return s;
   S->centre = centre;
   if ((s = rayleigh(*S, centre, S->M[centre].data, st, &S->e_in))) return s;
-  *out = reinterpret_cast<dmrg3s_state>(S.release());
+  guard.S = nullptr;
+  *out = reinterpret_cast<dmrg3s_state>(S);
   return DMRG3S_OK;
 }
 
 dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state) {
   State* S = reinterpret_cast<State*>(state);
   if (!S) return DMRG3S_ERR_ARG;
-  use_device(S->c);
-  cudaDeviceSynchronize();
-  for (auto& m : S->M) cudaFree(m.data);
-  for (auto& e : S->Lenv) cudaFree(e.data);
-  for (auto& e : S->Renv) cudaFree(e.data);
-  for (SvdWorker& w : S->svd) lane_destroy(&w);
-  if (S->svd_in) cudaEventDestroy(S->svd_in);
-  delete S;
+  release_state(S);
   return DMRG3S_OK;
 }
 
@@ -960,22 +1024,24 @@ dmrg3s_status dmrg3s_state_site_copy(dmrg3s_state state, int32_t i, double* dst,
   return e == cudaSuccess ? DMRG3S_OK : fail(S->c, DMRG3S_ERR_CUDA, "site copy");
 }
 
-dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
-                              double* dE, double* norm2, dmrg3s_stream stream) {
-  State* S = reinterpret_cast<State*>(state);
-  if (!S) return DMRG3S_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Every G_i of the state (host, concatenated in site order; goff[i] = offset
+// of site i) and <Psi|Psi>.
+dmrg3s_status grad_all(State* S, cudaStream_t st, std::vector<double>* hGout,
+                       std::vector<int64_t>* goffout, double* norm2) {
   Context* c = S->c;
   int64_t total = 0;
-  std::vector<int64_t> goff(S->n);
+  std::vector<int64_t>& goff = *goffout;
+  goff.assign(S->n, 0);
   for (int i = 0; i < S->n; ++i) {
     goff[i] = total;
     total += (int64_t)S->W[i].d * S->W[i].d * S->W[i].wl * S->W[i].wr;
   }
-  if ((G || dW) && len != total)
-    return fail(c, DMRG3S_ERR_SHAPE, "len must be the summed d*d*wl*wr over the sites");
   dmrg3s_status s;
   if ((s = use_device(c))) return s;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int cen = S->centre;
   if (!S->Lenv[cen].valid || !S->Renv[cen].valid)
     return fail(c, DMRG3S_ERR_ARG, "environments of the centre are not valid");
@@ -1018,7 +1084,8 @@ dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, i
   }
   double nrm = 0.0;
   if (!s) s = dot_host(c, S->M[cen].data, S->M[cen].data, S->M[cen].lay.size, st, &nrm);
-  std::vector<double> hG(total);
+  std::vector<double>& hG = *hGout;
+  hG.assign(total, 0.0);
   if (!s && total > 0)
     s = cuda_ok(c, cudaMemcpyAsync(hG.data(), dG, (size_t)total * sizeof(double),
                                    cudaMemcpyDeviceToHost, st), "gradient read-back");
@@ -1026,7 +1093,29 @@ dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, i
   if (!s) s = cuda_ok(c, cudaStreamSynchronize(st), "gradient");
   if (s) return s;
   if (!(nrm > 0.0)) return fail(c, DMRG3S_ERR_NUMERIC, "zero norm of the centre tensor");
-  if (G) std::memcpy(G, hG.data(), (size_t)total * sizeof(double));
+  *norm2 = nrm;
+  return DMRG3S_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, int64_t len,
+                              double* dE, double* norm2, dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  int64_t total = 0;
+  for (int i = 0; i < S->n; ++i) total += (int64_t)S->W[i].d * S->W[i].d * S->W[i].wl * S->W[i].wr;
+  if ((G || dW) && len != total)
+    return fail(c, DMRG3S_ERR_SHAPE, "len must be the summed d*d*wl*wr over the sites");
+  std::vector<double> hG;
+  std::vector<int64_t> goff;
+  double nrm = 0.0;
+  dmrg3s_status s = grad_all(S, reinterpret_cast<cudaStream_t>(stream), &hG, &goff, &nrm);
+  if (s) return s;
+  if (G && total > 0) std::memcpy(G, hG.data(), (size_t)total * sizeof(double));
   if (norm2) *norm2 = nrm;
   if (dE) {
     double acc = 0.0;
@@ -1034,6 +1123,68 @@ dmrg3s_status dmrg3s_mpo_grad(dmrg3s_state state, double* G, const double* dW, i
       for (int64_t k = 0; k < total; ++k) acc += hG[k] * dW[k];
     *dE = acc / nrm;
   }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_energy_grad(dmrg3s_state state, int32_t model, int32_t nparams,
+                                 const double* params, double* energy, double* dE,
+                                 dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  if (!params || nparams != 2) return fail(c, DMRG3S_ERR_ARG, "nparams must be 2 with params");
+  if (model != DMRG3S_MODEL_XXZ && model != DMRG3S_MODEL_HUBBARD)
+    return fail(c, DMRG3S_ERR_UNSUPPORTED, "energy gradient: XXZ and HUBBARD only");
+  // the model's MPO at params and at params + e_k (host builders)
+  std::vector<dmrg3s_mpo> mp(nparams + 1, nullptr);
+  struct Free {
+    std::vector<dmrg3s_mpo>& v;
+    ~Free() {
+      for (dmrg3s_mpo m : v)
+        if (m) dmrg3s_mpo_destroy(m);
+    }
+  } free_mpos{mp};
+  for (int k = 0; k <= nparams; ++k) {
+    double p[2] = {params[0], params[1]};
+    if (k > 0) p[k - 1] += 1.0;
+    dmrg3s_status s = dmrg3s_mpo_create(model, S->n, p, 0, nullptr, nullptr, &mp[k]);
+    if (s) return fail(c, s, "energy gradient: model MPO");
+  }
+  // the state's MPO must be the model at params (same structure and entries)
+  for (int i = 0; i < S->n; ++i) {
+    dmrg3s_mpo_site w{};
+    dmrg3s_mpo_get_site(mp[0], i, &w);
+    const MpoLayout& sw = S->W[i];
+    if (w.d != sw.d || w.wl != sw.wl || w.wr != sw.wr ||
+        std::memcmp(w.W, sw.W.data(), sizeof(double) * sw.W.size()) != 0)
+      return fail(c, DMRG3S_ERR_SHAPE,
+                  "energy gradient: the state's MPO at site " + std::to_string(i) +
+                      " is not the model at params");
+  }
+  std::vector<double> hG;
+  std::vector<int64_t> goff;
+  double nrm = 0.0;
+  dmrg3s_status s = grad_all(S, reinterpret_cast<cudaStream_t>(stream), &hG, &goff, &nrm);
+  if (s) return s;
+  if (energy) {
+    const int cen = S->centre;
+    const std::vector<double>& Wc = S->W[cen].W;
+    double acc = 0.0;
+    for (size_t e = 0; e < Wc.size(); ++e) acc += hG[goff[cen] + e] * Wc[e];
+    *energy = acc / nrm;
+  }
+  if (dE)
+    for (int k = 0; k < nparams; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < S->n; ++i) {
+        dmrg3s_mpo_site wk{}, w0{};
+        dmrg3s_mpo_get_site(mp[k + 1], i, &wk);
+        dmrg3s_mpo_get_site(mp[0], i, &w0);
+        const int64_t ne = (int64_t)w0.d * w0.d * w0.wl * w0.wr;
+        for (int64_t e = 0; e < ne; ++e) acc += hG[goff[i] + e] * (wk.W[e] - w0.W[e]);
+      }
+      dE[k] = acc / nrm;
+    }
   return DMRG3S_OK;
 }
 
@@ -1067,11 +1218,22 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
   if (S->centre != S->n - 1)
     return fail(c, DMRG3S_ERR_ARG, "a sweep starts with the centre on the last site");
   if (opts->max_sweeps < 1) return fail(c, DMRG3S_ERR_ARG, "max_sweeps must be >= 1");
+  const bool ladder = opts->switch_tol > 0.0;
+  if (ladder && opts->final_precision != DMRG3S_FP64 && opts->final_precision != DMRG3S_TF32X3 &&
+      opts->final_precision != DMRG3S_TF32)
+    return fail(c, DMRG3S_ERR_ARG, "final precision");
+  const auto t0 = std::chrono::steady_clock::now();
   double alpha = rule->alpha0;
   report->sweeps = 0;
   report->converged = 0;
   report->lanczos_iters = 0;
   report->svd_fallbacks = 0;
+  report->bulk_sweeps = 0;
+  report->pad = 0;
+  dmrg3s_update_opts uo = opts->update;
+  bool final_stage = !ladder;       // without a ladder every sweep counts
+  int final_sweeps = 0;             // sweeps completed in the final precision
+  int64_t nupd = 0;
   double prev = 0.0;
   for (int sw = 0; sw < opts->max_sweeps; ++sw) {
     double e = 0.0;
@@ -1079,23 +1241,38 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
       const int dir = pass == 0 ? -1 : 1;
       for (int k = 0; k < S->n - 1; ++k) {
         dmrg3s_update_info inf{};
-        dmrg3s_status s = dmrg3s_local_update(state, dir, alpha, &opts->update, &inf, stream);
+        dmrg3s_status s = dmrg3s_local_update(state, dir, alpha, &uo, &inf, stream);
         if (s != DMRG3S_OK) return s;
         alpha = alpha_update(*rule, alpha, inf.energy_before, inf.lambda, inf.energy_after);
+        if (opts->alphas) opts->alphas[nupd] = alpha;
+        ++nupd;
         report->lanczos_iters += inf.lanczos_iters;
         report->svd_fallbacks += inf.svd_fallback;
         e = inf.energy_after;
       }
     }
     if (energies) energies[sw] = e;
+    if (opts->seconds)
+      opts->seconds[sw] =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     report->sweeps = sw + 1;
     report->energy = e;
     report->alpha = alpha;
-    if (sw > 0 && std::fabs(e - prev) / std::fabs(e) < opts->conv_tol) {
-      report->converged = 1;
-      break;
-    }
+    const double rel = sw > 0 ? std::fabs(e - prev) / std::fabs(e) : INFINITY;
     prev = e;
+    if (final_stage) {
+      ++final_sweeps;
+      if (final_sweeps >= 2 && rel < opts->conv_tol) {
+        report->converged = 1;
+        break;
+      }
+    } else {
+      ++report->bulk_sweeps;
+      if (rel < opts->switch_tol) {   // later sweeps in the final precision
+        final_stage = true;
+        uo.precision = opts->final_precision;
+      }
+    }
   }
   return DMRG3S_OK;
 }

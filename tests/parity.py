@@ -11,11 +11,53 @@ from oracle import io
 
 FP64_TOL = 1e-12        # relative Frobenius error, FP64 path vs FP64 oracle
 TF32X3_TOL = 1e-6       # relative Frobenius error of 3xTF32 with FP32 accumulation
+# Per-block max-relative bounds (block_rel_err): one element of a block against
+# the block's largest entry, so a factor ~10 above the Frobenius bounds.
+FP64_BLOCK_TOL = 1e-11
+TF32X3_BLOCK_TOL = 1e-5
 
 
 def rel_err(got, ref):
     den = np.linalg.norm(ref)
     return float(np.linalg.norm(got - ref) / (den if den > 0 else 1.0))
+
+
+def block_rel_err(got, ref, parts):
+    """Largest per-block relative error max|got - ref| / max|ref| over the charge
+    blocks of a dense array, so that a wrong small sector cannot hide under the
+    Frobenius norm of the large ones.
+
+    parts: one sequence of sector dimensions per axis (an axis without sectors,
+    such as the physical index or the MPO channel, is given as [1] * size).
+    A block whose reference is zero must be zero in ``got`` too, up to 1e-300
+    of nothing: its error is taken relative to the largest reference entry.
+    """
+    offs = [np.concatenate([[0], np.cumsum(np.asarray(p, dtype=np.int64))]) for p in parts]
+    assert tuple(int(o[-1]) for o in offs) == ref.shape == got.shape
+    gmax = float(np.abs(ref).max()) if ref.size else 0.0
+    worst = 0.0
+    for idx in np.ndindex(*[len(o) - 1 for o in offs]):
+        sl = tuple(slice(int(o[k]), int(o[k + 1])) for o, k in zip(offs, idx))
+        r, g = ref[sl], got[sl]
+        if r.size == 0:
+            continue
+        den = float(np.abs(r).max())
+        if den == 0.0:
+            den = gmax if gmax > 0.0 else 1.0
+        worst = max(worst, float(np.abs(g - r).max()) / den)
+    return worst
+
+
+def site_parts(d, left, right):
+    """Axis partition of a site tensor (d, m_left, m_right) for block_rel_err."""
+    return [[1] * d, list(np.asarray(left["dim"] if isinstance(left, dict) else left.dim)),
+            list(np.asarray(right["dim"] if isinstance(right, dict) else right.dim))]
+
+
+def env_parts(w, bond):
+    """Axis partition of an environment (w, m, m) for block_rel_err."""
+    dims = list(np.asarray(bond["dim"] if isinstance(bond, dict) else bond.dim))
+    return [[1] * w, dims, dims]
 
 
 def site_to_dense(b, site):

@@ -11,7 +11,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import contract, io  # noqa: E402
-from parity import FP64_TOL, env_to_dense, fused_permutation, problem, rel_err, site_to_dense  # noqa: E402
+from parity import (FP64_BLOCK_TOL, FP64_TOL, block_rel_err, env_parts, env_to_dense,  # noqa: E402
+                    fused_permutation, problem, rel_err, site_parts, site_to_dense)
 
 CASES = [("dense", 1, {}), ("dense", 2, {"m_left": 37, "m_right": 71}),
          ("u1", 3, {}), ("u1", 4, {"density": 0.5}), ("u1u1", 5, {}),
@@ -52,7 +53,9 @@ def test_apply_heff_fp64(b, ctx, kind, seed, kw):
     torch.cuda.synchronize()
     L, W, R, A = _dense(pb)
     ref = contract.apply_heff(L, W, R, A)
-    assert rel_err(site_to_dense(b, gH), ref) < FP64_TOL
+    got = site_to_dense(b, gH)
+    assert rel_err(got, ref) < FP64_TOL
+    assert block_rel_err(got, ref, site_parts(A.shape[0], pb["left"], pb["right"])) < FP64_BLOCK_TOL
 
 
 def test_apply_heff_fp64_repeated_calls_reuse_plan(b, ctx):
@@ -82,6 +85,7 @@ def test_expand_fp64(b, ctx, kind, seed, kw, direction):
         ref = contract.expansion_term_lr(L, W, A, alpha)
         perm = fused_permutation(pb["right"], pb["t"], fused.q.astype(np.int64))
         ref = ref[:, :, perm]
+        parts = site_parts(A.shape[0], pb["left"], fused)
     else:
         fused = b.expanded_bond(gA.left, pb["t"], False)
         gP = b.empty_site_like(gA.qp, fused, gA.right)
@@ -89,8 +93,11 @@ def test_expand_fp64(b, ctx, kind, seed, kw, direction):
         ref = contract.expansion_term_rl(R, W, A, alpha)
         perm = fused_permutation(pb["left"], pb["t"], fused.q.astype(np.int64))
         ref = ref[:, perm, :]
+        parts = site_parts(A.shape[0], fused, pb["right"])
     torch.cuda.synchronize()
-    assert rel_err(site_to_dense(b, gP), ref) < FP64_TOL
+    got = site_to_dense(b, gP)
+    assert rel_err(got, ref) < FP64_TOL
+    assert block_rel_err(got, ref, parts) < FP64_BLOCK_TOL
 
 
 @pytest.mark.parametrize("direction", [1, -1])
@@ -103,12 +110,16 @@ def test_update_env_fp64(b, ctx, kind, seed, kw, direction):
         gO = b.empty_env(gW.tr, gA.right)
         b.dmrg3s_update_env(ctx, 1, gL, gW, gA, gO, "fp64")
         ref = contract.left_env(L, W, A)
+        parts = env_parts(W.shape[3], pb["right"])
     else:
         gO = b.empty_env(gW.tl, gA.left)
         b.dmrg3s_update_env(ctx, -1, gR, gW, gA, gO, "fp64")
         ref = contract.right_env(R, W, A)
+        parts = env_parts(W.shape[2], pb["left"])
     torch.cuda.synchronize()
-    assert rel_err(env_to_dense(b, gO), ref) < FP64_TOL
+    got = env_to_dense(b, gO)
+    assert rel_err(got, ref) < FP64_TOL
+    assert block_rel_err(got, ref, parts) < FP64_BLOCK_TOL
 
 
 def test_apply_heff_fp64_full_size_xxz_m512(b, ctx):
@@ -119,7 +130,10 @@ def test_apply_heff_fp64_full_size_xxz_m512(b, ctx):
     b.dmrg3s_apply_heff(ctx, gL, gW, gR, gA, gH, "fp64")
     torch.cuda.synchronize()
     L, W, R, A = _dense(pb)
-    assert rel_err(site_to_dense(b, gH), contract.apply_heff(L, W, R, A)) < FP64_TOL
+    ref = contract.apply_heff(L, W, R, A)
+    got = site_to_dense(b, gH)
+    assert rel_err(got, ref) < FP64_TOL
+    assert block_rel_err(got, ref, site_parts(A.shape[0], pb["left"], pb["right"])) < FP64_BLOCK_TOL
 
 
 def test_structure_mismatch_is_an_error(b, ctx):

@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 import bench  # noqa: E402
 import seeded_inputs as si  # noqa: E402
 from oracle import contract, dmrg3s as odm, io  # noqa: E402
-from parity import (TF32X3_TOL, env_to_dense, fused_permutation, problem, rel_err,  # noqa: E402
-                    site_to_dense)
+from parity import (TF32X3_BLOCK_TOL, TF32X3_TOL, block_rel_err, env_parts,  # noqa: E402
+                    env_to_dense, fused_permutation, problem, rel_err, site_parts, site_to_dense)
 
 TF32_TOL = 2e-3
 CASES = [("dense", 31, {}), ("u1", 32, {}), ("u1u1", 33, {}), ("u1", 34, {"m_left": 9, "m_right": 7}),
@@ -56,7 +56,11 @@ def test_apply_heff_tensor_core(b, ctx, kind, seed, kw, prec, tol):
     b.dmrg3s_apply_heff(ctx, gL, gW, gR, gA, gH, prec)
     b.dmrg3s_sync(ctx)
     L, W, R, A = _dense(pb)
-    assert rel_err(site_to_dense(b, gH), contract.apply_heff(L, W, R, A)) < tol
+    ref = contract.apply_heff(L, W, R, A)
+    got = site_to_dense(b, gH)
+    assert rel_err(got, ref) < tol
+    if prec == "tf32x3":
+        assert block_rel_err(got, ref, site_parts(A.shape[0], pb["left"], pb["right"])) < TF32X3_BLOCK_TOL
 
 
 @pytest.mark.parametrize("direction", [1, -1])
@@ -74,6 +78,8 @@ def test_expand_and_env_tf32x3(b, ctx, kind, seed, kw, direction):
         gO = b.empty_env(gW.tr, gA.right)
         b.dmrg3s_update_env(ctx, 1, gL, gW, gA, gO, "tf32x3")
         refO = contract.left_env(L, W, A)
+        pP = site_parts(A.shape[0], pb["left"], fused)
+        pO = env_parts(W.shape[3], pb["right"])
     else:
         fused = b.expanded_bond(gA.left, pb["t"], False)
         gP = b.empty_site_like(gA.qp, fused, gA.right)
@@ -83,9 +89,14 @@ def test_expand_and_env_tf32x3(b, ctx, kind, seed, kw, direction):
         gO = b.empty_env(gW.tl, gA.left)
         b.dmrg3s_update_env(ctx, -1, gR, gW, gA, gO, "tf32x3")
         refO = contract.right_env(R, W, A)
+        pP = site_parts(A.shape[0], fused, pb["right"])
+        pO = env_parts(W.shape[2], pb["left"])
     b.dmrg3s_sync(ctx)
-    assert rel_err(site_to_dense(b, gP), refP) < TF32X3_TOL
-    assert rel_err(env_to_dense(b, gO), refO) < TF32X3_TOL
+    gotP, gotO = site_to_dense(b, gP), env_to_dense(b, gO)
+    assert rel_err(gotP, refP) < TF32X3_TOL
+    assert rel_err(gotO, refO) < TF32X3_TOL
+    assert block_rel_err(gotP, refP, pP) < TF32X3_BLOCK_TOL
+    assert block_rel_err(gotO, refO, pO) < TF32X3_BLOCK_TOL
 
 
 def test_eigensolve_tf32x3(b, ctx):

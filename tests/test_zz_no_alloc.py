@@ -1,13 +1,15 @@
 """The H_eff entry point that allocates no device memory.
 
-Callers that cannot call cudaMalloc (code running during CUDA graph capture,
-hosts whose device memory belongs to another allocator, real-time callers)
-use dmrg3s_apply_heff_noalloc, which keeps its intermediates in static device
+Callers that cannot call cudaMalloc (hosts whose device memory belongs to
+another allocator, real-time callers that may not allocate mid-work) use
+dmrg3s_apply_heff_noalloc, which keeps its intermediates in static device
 arrays of the library instead of a context workspace.  This test calls it
 through the C ABI and checks its output against dmrg3s_apply_heff, the
-context-based entry point, within the FP64 tolerance of the other parity
-tests, on two calls in a row (the static arrays keep the first call's
-contents when the second one runs).  The file is named to be collected last.
+context-based entry point, and against the FP64 oracle, within the FP64
+tolerance of the other parity tests, on two calls in a row (the static arrays
+keep the first call's contents when the second one runs), and on two calls
+with different structures queued back to back on one non-default stream.
+The file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -15,6 +17,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import contract, io  # noqa: E402
 from parity import FP64_TOL, problem, rel_err, site_to_dense  # noqa: E402
 
 
@@ -47,6 +50,10 @@ def test_noalloc_matches_context_entry_point_twice(b):
         got, want = site_to_dense(b, out), site_to_dense(b, ref)
         assert np.all(np.isfinite(got))
         assert rel_err(got, want) < FP64_TOL
+        pb = problem(kind, seed, **kw)
+        oracle = contract.apply_heff(io.env_dense(pb["L"]), pb["W"]["W"], io.env_dense(pb["R"]),
+                                     io.site_dense(pb["A"])[0])
+        assert rel_err(got, oracle) < FP64_TOL
     # the same structure again: the arrays hold the previous call's data
     gL, gW, gR, gA = _inputs(b, "u1", 22)
     ref = b.empty_site_like(gA.qp, gA.left, gA.right)
@@ -55,6 +62,37 @@ def test_noalloc_matches_context_entry_point_twice(b):
     b.dmrg3s_apply_heff_noalloc(gL, gW, gR, gA, out)
     torch.cuda.synchronize()
     assert rel_err(site_to_dense(b, out), site_to_dense(b, ref)) < FP64_TOL
+    ctx.close()
+
+
+def test_noalloc_two_structures_on_one_stream(b):
+    """Two calls with different block structures queued on one side stream
+    with no synchronisation between them: stream order keeps them apart."""
+    ctx = b.dmrg3s_create(0, 1 << 28)
+    side = torch.cuda.Stream()
+    probs = [problem("u1u1", 23), problem("u1", 24, m_left=37, m_right=29)]
+    ins, outs, refs = [], [], []
+    for pb in probs:
+        gL, gW, gR, gA = (b.env_from_neutral(pb["L"]), b.mpo_from_neutral(pb["W"]),
+                          b.env_from_neutral(pb["R"]), b.site_from_neutral(pb["A"]))
+        ref = b.empty_site_like(gA.qp, gA.left, gA.right)
+        b.dmrg3s_apply_heff(ctx, gL, gW, gR, gA, ref, "fp64")
+        out = b.empty_site_like(gA.qp, gA.left, gA.right)
+        out.data.fill_(float("nan"))
+        ins.append((gL, gW, gR, gA))
+        outs.append(out)
+        refs.append(ref)
+    torch.cuda.synchronize()
+    for (gL, gW, gR, gA), out in zip(ins, outs):
+        b.dmrg3s_apply_heff_noalloc(gL, gW, gR, gA, out, stream=side)
+    side.synchronize()
+    for pb, out, ref in zip(probs, outs, refs):
+        got = site_to_dense(b, out)
+        assert np.all(np.isfinite(got))
+        assert rel_err(got, site_to_dense(b, ref)) < FP64_TOL
+        want = contract.apply_heff(io.env_dense(pb["L"]), pb["W"]["W"], io.env_dense(pb["R"]),
+                                   io.site_dense(pb["A"])[0])
+        assert rel_err(got, want) < FP64_TOL
     ctx.close()
 
 
