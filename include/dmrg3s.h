@@ -131,6 +131,16 @@ const char* dmrg3s_last_error(dmrg3s_ctx ctx);
  * The latch is cleared.  Errors: ARG, CUDA, TIMEOUT. */
 dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream);
 
+/* Limit of every bounded wait inside this library's kernels (the tensor-core
+ * kernel's waits for bulk copies, products and drains), in seconds of
+ * elapsed device time (%globaltimer); default 1.0.  A wait that runs out makes
+ * its CTA stop (after the copies and products already in flight have
+ * finished), latches DMRG3S_ERR_TIMEOUT for dmrg3s_sync and the eigensolver,
+ * and leaves the context usable; the results of that launch are invalid.
+ * seconds = 0 makes every wait that does not succeed at once run out (for
+ * testing the error path).  Errors: ARG (negative or not finite). */
+dmrg3s_status dmrg3s_set_wait_limit(dmrg3s_ctx ctx, double seconds);
+
 /* Kernel timing.  While enabled, the context records CUDA events on the
  * launching stream around every grouped-GEMM launch of the contractions
  * (kernel 0: the block products of stages 1 and 3 of the contraction order

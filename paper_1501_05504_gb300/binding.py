@@ -674,6 +674,13 @@ def dmrg3s_profile_read(ctx, kernel):
     return {"launches": st.launches, "ms": st.ms, "flops": st.flops, "bytes": st.bytes}
 
 
+def dmrg3s_set_wait_limit(ctx, seconds):
+    """Limit (seconds of device time) of the bounded waits in the tensor-core kernel."""
+    L = lib()
+    L.dmrg3s_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    _check(L.dmrg3s_set_wait_limit(ctx.handle, float(seconds)), "dmrg3s_set_wait_limit", ctx.handle)
+
+
 def dmrg3s_sync(ctx, stream=None):
     """Synchronise and surface a latched device-side error (DMRG3S_ERR_TIMEOUT)."""
     L = lib()

@@ -64,9 +64,11 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   size_t total = bytes_of(h.g1.tiles) + bytes_of(h.g1.tasks) + bytes_of(h.g1.segs) +
                  bytes_of(h.c2.chunks) + bytes_of(h.c2.tasks) + bytes_of(h.c2.terms) +
                  bytes_of(h.g3.tiles) + bytes_of(h.g3.tasks) + bytes_of(h.g3.segs) +
-                 bytes_of(h.g1.tiles_tc) + bytes_of(h.g3.tiles_tc) + bytes_of(h.g3s.tiles_tc) +
-                 bytes_of(h.g3s.tasks) + bytes_of(h.g3s.segs) + bytes_of(h.c3r.chunks) +
-                 bytes_of(h.c3r.tasks) + bytes_of(h.c3r.terms);
+                 bytes_of(h.g3s.tasks) + bytes_of(h.c3r.chunks) + bytes_of(h.c3r.tasks) +
+                 bytes_of(h.c3r.terms) + bytes_of(h.g1.tc.units) + bytes_of(h.g1.tc.segs) +
+                 bytes_of(h.g1.tc.packA) + bytes_of(h.g1.tc.packB) + bytes_of(h.g3s.tc.units) +
+                 bytes_of(h.g3s.tc.segs) + bytes_of(h.g3s.tc.packA) + bytes_of(h.g3s.tc.packB) +
+                 bytes_of(h.c2pack);
   if (total == 0) total = 256;
   if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
   std::vector<char> staging(total, 0);
@@ -81,11 +83,16 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   dp->g3_tiles = place(base, &off, h.g3.tiles, &staging);
   dp->g3_tasks = place(base, &off, h.g3.tasks, &staging);
   dp->g3_segs = place(base, &off, h.g3.segs, &staging);
-  dp->g1_tiles_tc = place(base, &off, h.g1.tiles_tc, &staging);
-  dp->g3_tiles_tc = place(base, &off, h.g3.tiles_tc, &staging);
-  dp->g3s_tiles = place(base, &off, h.g3s.tiles_tc, &staging);
   dp->g3s_tasks = place(base, &off, h.g3s.tasks, &staging);
-  dp->g3s_segs = place(base, &off, h.g3s.segs, &staging);
+  dp->g1_units = place(base, &off, h.g1.tc.units, &staging);
+  dp->g1_tsegs = place(base, &off, h.g1.tc.segs, &staging);
+  dp->g1_packA = place(base, &off, h.g1.tc.packA, &staging);
+  dp->g1_packB = place(base, &off, h.g1.tc.packB, &staging);
+  dp->g3s_units = place(base, &off, h.g3s.tc.units, &staging);
+  dp->g3s_tsegs = place(base, &off, h.g3s.tc.segs, &staging);
+  dp->g3s_packA = place(base, &off, h.g3s.tc.packA, &staging);
+  dp->g3s_packB = place(base, &off, h.g3s.tc.packB, &staging);
+  dp->c2_pack = place(base, &off, h.c2pack, &staging);
   dp->c3r_chunks = place(base, &off, h.c3r.chunks, &staging);
   dp->c3r_tasks = place(base, &off, h.c3r.tasks, &staging);
   dp->c3r_terms = place(base, &off, h.c3r.terms, &staging);
@@ -123,7 +130,7 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
     }
     return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
   }
-  // ---- tensor-core mode: split the operands into FP32 (hi, lo) pairs
+  // ---- tensor-core mode: packed (hi, lo) operands
   const TcSlots sl = tc_slots(h);
   double* base = reinterpret_cast<double*>(c->ws);
   auto hi = [&](int64_t slot) { return reinterpret_cast<float*>(base + slot); };
@@ -135,13 +142,15 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   // the tensor-core stages write double-float pairs (8 bytes per element, in
   // place of the FP64 intermediates), combined on the FP32 pipe
   float2* t1p = reinterpret_cast<float2*>(ws1);
-  if (!hn.g1A) launch_split(g1A, hi(sl.a1), lo(sl.a1, h.nA1), h.nA1, st);
-  if (!hn.g1B) launch_split(g1B, hi(sl.b1), lo(sl.b1, h.nB1), h.nB1, st);
-  if (!h.g1.tiles.empty()) {
+  const TcStage& t1 = h.g1.tc;
+  if (!hn.g1A) launch_pack(p.g1_packA, (int)t1.packA.size(), t1.tilesA, g1A, hi(sl.a1),
+                           lo(sl.a1, t1.nA), st);
+  if (!hn.g1B) launch_pack(p.g1_packB, (int)t1.packB.size(), t1.tilesB, g1B, hi(sl.b1),
+                           lo(sl.b1, t1.nB), st);
+  if (!t1.units.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
-    launch_gemm_tc(passes, h.g1.ta, h.g1.tb, p.g1_tiles_tc, (int)h.g1.tiles_tc.size(), p.g1_tasks,
-                   p.g1_segs, hi(sl.a1), lo(sl.a1, h.nA1), hi(sl.b1), lo(sl.b1, h.nB1), t1p,
-                   c->d_err, st);
+    launch_gemm_tc(passes, p.g1_units, (int)t1.units.size(), p.g1_tasks, p.g1_tsegs, hi(sl.a1),
+                   lo(sl.a1, t1.nA), hi(sl.b1), lo(sl.b1, t1.nB), t1p, c->d_err, c->wait_ns, st);
     if (id >= 0) pr.end(id, st);
   }
   if (!h.has_g3) {
@@ -153,42 +162,40 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
     }
     return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
   }
-  // stage 2 writes T2 directly as a split operand of stage 3
-  if (!h.c2.chunks.empty()) {
+  // stage 2 writes T2 packed as the stage-3 operand it feeds
+  if (!h.c2pack.empty()) {
     const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
-    launch_combine_pairs_split(p.c2_chunks, (int)h.c2.chunks.size(), p.c2_tasks, p.c2_terms, t1p,
-                               hi(sl.t2s), lo(sl.t2s, h.ws2), c2scale, st);
+    launch_combine_pairs_pack(p.c2_pack, (int)h.c2pack.size(), h.tilesT2, p.c2_tasks, p.c2_terms,
+                              t1p, hi(sl.t2p), lo(sl.t2p, h.nT2p), c2scale, st);
     if (id >= 0) pr.end(id, st);
   }
-  // stage 3: the operand that is T2 (ws2 in the FP64 layout) uses the split T2;
-  // an operand equal to a stage-1 operand reuses that split
-  const double* ws2 = ws1 + h.ws1;
-  auto operand = [&](const double* x, int64_t slot, int64_t n, bool hinted, const float** ph,
-                     const float** pl) {
-    if (x == ws2) {
-      *ph = hi(sl.t2s);
-      *pl = lo(sl.t2s, h.ws2);
-    } else if (x == g1A) {
-      *ph = hi(sl.a1);
-      *pl = lo(sl.a1, h.nA1);
-    } else if (x == g1B) {
-      *ph = hi(sl.b1);
-      *pl = lo(sl.b1, h.nB1);
-    } else {
-      if (!hinted) launch_split(x, hi(slot), lo(slot, n), n, st);
-      *ph = hi(slot);
-      *pl = lo(slot, n);
-    }
-  };
+  // stage 3: T2 is A for H_eff, B for the environment updates; the other
+  // operand is packed into slot x3 (unless the caller already did)
+  const TcStage& t3 = h.g3s.tc;
+  const bool t2_is_a = h.kind == Kind::Heff;
   const float *a3h, *a3l, *b3h, *b3l;
-  operand(g3A, sl.a3, h.nA3, hn.g3A, &a3h, &a3l);
-  operand(g3B, sl.b3, h.nB3, hn.g3B, &b3h, &b3l);
-  // split-K: one CTA per (tile, K-segment) into FP64 partials, then a fixed-order sum
+  if (t2_is_a) {
+    a3h = hi(sl.t2p);
+    a3l = lo(sl.t2p, h.nT2p);
+    if (!hn.g3B) launch_pack(p.g3s_packB, (int)t3.packB.size(), t3.tilesB, g3B, hi(sl.x3),
+                             lo(sl.x3, t3.nB), st);
+    b3h = hi(sl.x3);
+    b3l = lo(sl.x3, t3.nB);
+  } else {
+    if (!hn.g3A) launch_pack(p.g3s_packA, (int)t3.packA.size(), t3.tilesA, g3A, hi(sl.x3),
+                             lo(sl.x3, t3.nA), st);
+    a3h = hi(sl.x3);
+    a3l = lo(sl.x3, t3.nA);
+    b3h = hi(sl.t2p);
+    b3l = lo(sl.t2p, h.nT2p);
+  }
+  // split-K: one unit per (tile, K-segment) into double-float partials, then
+  // a fixed-order sum
   float2* part = reinterpret_cast<float2*>(base + sl.p3);
-  if (!h.g3s.tiles_tc.empty()) {
+  if (!t3.units.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g3s.flops, h.g3s.bytes, st) : -1;
-    launch_gemm_tc(passes, h.g3s.ta, h.g3s.tb, p.g3s_tiles, (int)h.g3s.tiles_tc.size(),
-                   p.g3s_tasks, p.g3s_segs, a3h, a3l, b3h, b3l, part, c->d_err, st);
+    launch_gemm_tc(passes, p.g3s_units, (int)t3.units.size(), p.g3s_tasks, p.g3s_tsegs, a3h, a3l,
+                   b3h, b3l, part, c->d_err, c->wait_ns, st);
     if (id >= 0) pr.end(id, st);
   }
   if (!h.c3r.chunks.empty()) {
@@ -393,6 +400,14 @@ dmrg3s_status dmrg3s_sync(dmrg3s_ctx ctx, dmrg3s_stream stream) {
     cudaStreamSynchronize(s);
     return fail(c, DMRG3S_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
   }
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_set_wait_limit(dmrg3s_ctx ctx, double seconds) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c) return DMRG3S_ERR_ARG;
+  if (!(seconds >= 0.0) || seconds > 1e6) return fail(c, DMRG3S_ERR_ARG, "wait limit");
+  c->wait_ns = (uint64_t)(seconds * 1e9);
   return DMRG3S_OK;
 }
 

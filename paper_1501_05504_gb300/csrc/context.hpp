@@ -18,17 +18,24 @@ struct DevicePlan {
   Plan host;
   void* mem = nullptr;      // one allocation holding every table
   GemmTile* g1_tiles = nullptr;
-  GemmTile* g1_tiles_tc = nullptr;
   GemmTask* g1_tasks = nullptr;
   GemmSeg* g1_segs = nullptr;
   CombChunk* c2_chunks = nullptr;
   CombTask* c2_tasks = nullptr;
   CombTerm* c2_terms = nullptr;
   GemmTile* g3_tiles = nullptr;
-  GemmTile* g3_tiles_tc = nullptr;
-  GemmTile* g3s_tiles = nullptr;     // split-K stage 3 (tensor-core tiles)
-  GemmTask* g3s_tasks = nullptr;
-  GemmSeg* g3s_segs = nullptr;
+  GemmTask* g3s_tasks = nullptr;     // split-K stage 3 (tensor-core form)
+  // tensor-core tables: units, segments and operand packs of stages 1 and 3,
+  // and the packed outputs of stage 2
+  TcUnit* g1_units = nullptr;
+  TcSeg* g1_tsegs = nullptr;
+  PackBlock* g1_packA = nullptr;
+  PackBlock* g1_packB = nullptr;
+  TcUnit* g3s_units = nullptr;
+  TcSeg* g3s_tsegs = nullptr;
+  PackBlock* g3s_packA = nullptr;
+  PackBlock* g3s_packB = nullptr;
+  PackOut* c2_pack = nullptr;
   CombChunk* c3r_chunks = nullptr;
   CombTask* c3r_tasks = nullptr;
   CombTerm* c3r_terms = nullptr;
@@ -100,6 +107,7 @@ struct Context {
   size_t ws_bytes = 0;
   double* pinned = nullptr;     // small pinned host buffer for scalar read-backs (64 doubles)
   int* d_err = nullptr;         // device error word latched by bounded waits (tensor-core kernel)
+  uint64_t wait_ns = 1000000000ull;   // limit of every bounded device wait (dmrg3s_set_wait_limit)
   cudaStream_t aux = nullptr;   // side stream: the Lanczos tridiagonal solve beside the next product
   cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;
@@ -176,28 +184,30 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 
 // Enqueue the stages of a plan.  Bases as documented for each plan Kind.
-// Tensor-core mode: the operands of stages 1 and 3 are split into FP32
-// (hi, lo) arrays in the workspace, laid out after the FP64 intermediates:
-//   [T1: ws1][T2: ws2][T2 split: ws2][g1A split][g1B split][g3A split][g3B split]
-//   [stage-3 partial products: ws3]
-// (in units of doubles; a split of n elements takes n doubles of space).  A
-// caller that has already split an operand into its slot passes a hint and
-// run_plan skips that split (the Lanczos loop splits L and R once).
+// Tensor-core mode: the stage-1 and stage-3 operands are packed (hi, lo
+// parts, tile layout of kernels.hpp) into the workspace:
+//   [T1 pairs: ws1][packed T2 (stage-2 output)][g1 A packed][g1 B packed]
+//   [g3 A or B packed (the operand that is not T2)][stage-3 partial pairs: ws3]
+// (offsets in doubles, each slot 1 KB aligned; a packed operand of n floats
+// per part takes n doubles: hi then lo).  A caller that has already packed an
+// operand into its slot passes a hint and run_plan skips that pack (the
+// Lanczos loop packs L and R once per run).
 struct SplitHints {
   bool g1A = false, g1B = false, g3A = false, g3B = false;
 };
 struct TcSlots {
-  int64_t t2s, a1, b1, a3, b3, p3, end;    // offsets in doubles from the workspace start
+  int64_t t2p, a1, b1, x3, p3, end;   // offsets in doubles from the workspace start
 };
+inline int64_t slot_round(int64_t d) { return (d + 127) / 128 * 128; }   // 1 KB
 inline TcSlots tc_slots(const Plan& p) {
   TcSlots s;
-  s.t2s = p.ws1 + p.ws2;
-  s.a1 = s.t2s + p.ws2;
-  s.b1 = s.a1 + p.nA1;
-  s.a3 = s.b1 + p.nB1;
-  s.b3 = s.a3 + p.nA3;
-  s.p3 = s.b3 + p.nB3;
-  s.end = s.p3 + p.ws3;
+  s.t2p = slot_round(p.ws1);
+  s.a1 = s.t2p + slot_round(p.nT2p);
+  s.b1 = s.a1 + slot_round(p.g1.tc.nA);
+  s.x3 = s.b1 + slot_round(p.g1.tc.nB);
+  const int64_t n3 = p.kind == Kind::Heff ? p.g3s.tc.nB : p.g3s.tc.nA;
+  s.p3 = s.x3 + slot_round(p.has_g3 ? n3 : 0);
+  s.end = s.p3 + slot_round(p.ws3);
   return s;
 }
 // Workspace (in doubles) a plan needs in the given precision.

@@ -43,15 +43,19 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   TridiagOut* out = (TridiagOut*)pout;
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + heff.host.ws1;
-  // tensor-core products: split the environments once for the whole run
+  // tensor-core products: pack the environments once for the whole run
   SplitHints hints;
   if (prec != DMRG3S_FP64) {
-    const TcSlots sl = tc_slots(heff.host);
-    const int64_t nL = heff.host.nA1, nR = heff.host.nB3;
-    float* Ls = reinterpret_cast<float*>(ws1 + sl.a1);
-    float* Rs = reinterpret_cast<float*>(ws1 + sl.b3);
-    launch_split(Ldata, Ls, prec == DMRG3S_TF32X3 ? Ls + nL : nullptr, nL, st);
-    launch_split(Rdata, Rs, prec == DMRG3S_TF32X3 ? Rs + nR : nullptr, nR, st);
+    const Plan& hp = heff.host;
+    const TcSlots sl = tc_slots(hp);
+    const TcStage& t1 = hp.g1.tc;
+    const TcStage& t3 = hp.g3s.tc;
+    float* Lp = reinterpret_cast<float*>(ws1 + sl.a1);
+    float* Rp = reinterpret_cast<float*>(ws1 + sl.x3);
+    launch_pack(heff.g1_packA, (int)t1.packA.size(), t1.tilesA, Ldata, Lp,
+                prec == DMRG3S_TF32X3 ? Lp + t1.nA : nullptr, st);
+    launch_pack(heff.g3s_packB, (int)t3.packB.size(), t3.tilesB, Rdata, Rp,
+                prec == DMRG3S_TF32X3 ? Rp + t3.nB : nullptr, st);
     hints.g1A = true;
     hints.g3B = true;
   }

@@ -50,6 +50,37 @@ constexpr int kCombRows = 16;
 
 enum class Trans { N, T };
 
+// ---- tensor-core operands: packed tiles ----
+// A packed matrix (R x K) is stored in tiles of 8 rows x 32 k, tile (g, c) at
+// float offset (c * R8 + g) * 256 (R8 = ceil(R / 8) row groups, KC =
+// ceil(K / 32) k-chunks), each tile in the K-major core-matrix order of the
+// tcgen05 shared-memory descriptors: element (r, k) at ((k % 32) / 4) * 32 +
+// (r % 8) * 4 + k % 4.  Entries beyond R or K are zero.  A 128-row slab of one
+// k-chunk is therefore contiguous (16 KB) and moves into shared memory with
+// one bulk copy.  Every operand has a hi and a lo part (the 3xTF32 split) at
+// the same offsets of two arrays.
+constexpr int kPackTile = 256;             // floats per 8 x 32 tile
+struct PackBlock {
+  // element (r, k) of the packed matrix is src[off + r * ld + k] (trans = 0)
+  // or src[off + k * ld + r] (trans = 1)
+  int64_t src, dst;                        // dst: float offset of tile (0, 0)
+  int32_t ld, R, K, trans, R8, KC, tile0, pad;   // tile0: first tile in the launch numbering
+};
+// One K-segment of a tensor-core task: packed A (rows M) and B (rows N).
+struct TcSeg {
+  int64_t pa, pb;
+  int32_t ra8, rb8, kc, pad;
+};
+// One 128 x 128 output tile: the task's K-segments in order, nchunks k-chunks in all.
+struct TcUnit {
+  int32_t task, tm, tn, nchunks;
+};
+// A combination task whose output is written packed (the stage-3 operand).
+struct PackOut {
+  int64_t dst;
+  int32_t R8, KC, trans, tile0;
+};
+
 // Blockwise inner products: out[task.out] = sum over the task's segments of
 // <A[offA .. offA+len), B[offB .. offB+len)> (FP64, fixed summation order).
 struct DotSeg {
@@ -71,27 +102,29 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
                      cudaStream_t st);
 
 // out = scale * sum_k coef_k in_k for every task.
-// Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32).  The
-// operands are pre-split FP32 arrays (hi = tf32(x), lo = tf32(x - hi)) with
-// the offsets of the FP64 layout; lo may be null when passes == 1.  C
-// receives every output element as a double-float pair (hi, lo) at the
-// element offset of the FP64 layout (8 bytes, like the double it stands for).
-// err is a device flag set to 1 when a bounded wait timed out.
-void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
-                    const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
-                    const float* Alo, const float* Bhi, const float* Blo, float2* C, int* err,
-                    cudaStream_t st);
+// Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32) over
+// packed operands (hi, lo parts; lo unused when passes == 1), persistent CTAs
+// over the units.  C receives every output element as a double-float pair
+// (hi, lo) at the element offset of the FP64 layout (8 bytes, like the double
+// it stands for).  err is a device flag set to 1 when a wait gave up after
+// wait_ns nanoseconds.
+void launch_gemm_tc(int passes, const TcUnit* units, int nunits, const GemmTask* tasks,
+                    const TcSeg* segs, const float* Ahi, const float* Alo, const float* Bhi,
+                    const float* Blo, float2* C, int* err, uint64_t wait_ns, cudaStream_t st);
 
-// hi[i] = tf32(x[i]), lo[i] = tf32(x[i] - hi[i]) (the 3xTF32 split of an FP64 array).
-void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t st);
+// Packs FP64 blocks into tensor-core operands: hi = tf32(x), lo = tf32(x - hi)
+// (lo may be null), in the tile layout above.
+void launch_pack(const PackBlock* blocks, int nblocks, int ntiles, const double* src, float* hi,
+                 float* lo, cudaStream_t st);
 
 // Combinations of double-float pair inputs (the tensor-core outputs), in
 // double-float arithmetic on the FP32 pipe: out = scale * sum_k coef_k in_k.
-// _split writes the result as the 3xTF32 split operand (hi, lo; lo may be
-// null) of a following tensor-core stage, _f64 writes FP64.
-void launch_combine_pairs_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
-                                const CombTerm* terms, const float2* in, float* out_hi,
-                                float* out_lo, double scale, cudaStream_t st);
+// _pack writes the result as the packed 3xTF32 operand (hi, lo; lo may be
+// null) of a following tensor-core stage (one PackOut per task), _f64 writes
+// FP64.
+void launch_combine_pairs_pack(const PackOut* outs, int ntasks, int ntiles, const CombTask* tasks,
+                               const CombTerm* terms, const float2* in, float* out_hi,
+                               float* out_lo, double scale, cudaStream_t st);
 void launch_combine_pairs_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,
                               const CombTerm* terms, const float2* in, double* out,
                               double scale, cudaStream_t st);

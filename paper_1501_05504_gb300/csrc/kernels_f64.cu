@@ -154,29 +154,6 @@ __device__ __forceinline__ void df_combine(const CombTask& t, const CombTerm* __
   }
 }
 
-__global__ void __launch_bounds__(256) combine_pairs_split_kernel(
-    const CombChunk* __restrict__ chunks, const CombTask* __restrict__ tasks,
-    const CombTerm* __restrict__ terms, const float2* __restrict__ in, float* __restrict__ out_hi,
-    float* __restrict__ out_lo, float sh, float sl) {
-  const CombChunk ch = chunks[blockIdx.x];
-  const CombTask t = tasks[ch.task];
-  const int n = ch.nrows * t.cols;
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int r = ch.row0 + idx / t.cols, c = idx % t.cols;
-    float ah, al;
-    df_combine(t, terms, in, r, c, sh, sl, ah, al);
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(ah));
-    const float hf = __uint_as_float(h);
-    // ah - hf is exact (hf is ah rounded to the 10-bit TF32 mantissa)
-    uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fadd_rn(__fsub_rn(ah, hf), al)));
-    const int64_t o = t.offOut + (int64_t)r * t.ldo + c;
-    out_hi[o] = hf;
-    if (out_lo) out_lo[o] = __uint_as_float(l);
-  }
-}
-
 __global__ void __launch_bounds__(256) combine_pairs_f64_kernel(
     const CombChunk* __restrict__ chunks, const CombTask* __restrict__ tasks,
     const CombTerm* __restrict__ terms, const float2* __restrict__ in, double* __restrict__ out,
@@ -236,16 +213,6 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
     gemm_f64_kernel<Trans::T, Trans::N><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
   else
     gemm_f64_kernel<Trans::T, Trans::T><<<grid, block, 0, st>>>(tiles, tasks, segs, A, B, C);
-}
-
-void launch_combine_pairs_split(const CombChunk* chunks, int nchunks, const CombTask* tasks,
-                                const CombTerm* terms, const float2* in, float* out_hi,
-                                float* out_lo, double scale, cudaStream_t st) {
-  if (nchunks <= 0) return;
-  count_launch();
-  const float sh = (float)scale, sl = (float)(scale - (double)sh);
-  combine_pairs_split_kernel<<<nchunks, 256, 0, st>>>(chunks, tasks, terms, in, out_hi, out_lo, sh,
-                                                      sl);
 }
 
 void launch_combine_pairs_f64(const CombChunk* chunks, int nchunks, const CombTask* tasks,

@@ -1,23 +1,46 @@
-// Tensor-core grouped GEMM for sm_103a (tcgen05, TMEM accumulators).
+// Tensor-core grouped GEMM for sm_103a (tcgen05, TMEM accumulators, bulk
+// asynchronous copies), and the kernels that pack its operands.
 //
-// Same task tables as the FP64 kernel (one output block per task, K-segments
-// summed), computed on the 5th-generation tensor cores in TF32 with FP32
-// accumulation per 32-wide K chunk and double-float accumulation across
-// chunks.  Operands are FP64 tensors pre-split into x = hi + lo with
-// hi = tf32(x), lo = tf32(x - hi) (Ootomo and Yokota's split, 2022) by
-// split_kernel or by the MPO combination, so the GEMM itself does no FP64
-// arithmetic (GB300's FP64 rate is ~1/1000 of its TF32 rate):
-//   kPasses = 1: C = A_hi B_hi                                  (TF32)
-//   kPasses = 3: C = A_hi B_hi + A_hi B_lo + A_lo B_hi          (3xTF32)
+// Operands are FP64 tensors split into x = hi + lo with hi = tf32(x),
+// lo = tf32(x - hi) (Ootomo and Yokota's split, 2022) and packed in tiles of
+// 8 rows x 32 k in the K-major core-matrix order of the shared-memory matrix
+// descriptors (kernels.hpp).  A 128-row slab of one 32-wide k-chunk is then a
+// contiguous 16 KB run, so each operand slab reaches shared memory with one
+// bulk copy (cp.async.bulk, completion counted in bytes on an mbarrier); no
+// thread touches operand data on its way to the tensor core.
 //
-// CTA tile 128 x 64 (M x N), K chunks of 32, two shared-memory stages and two
-// TMEM accumulator buffers.  All 128 threads load the operand tiles; one
-// thread issues tcgen05.mma and commits each stage to an mbarrier; while the
-// tensor core works on chunk k the four warps drain chunk k-1's FP32
-// accumulator (tcgen05.ld) into double-float registers.  Each output element
-// is stored as its (hi, lo) FP32 pair, for the double-float combinations that
-// consume it.  Every wait on an mbarrier is bounded: on time-out the CTA
-// records an error code, frees its tensor memory and returns.
+// Products per k-chunk of one 128 x 128 output tile:
+//   kPasses = 1: D_main += A_hi B_hi                                (TF32)
+//   kPasses = 3: D_main += A_hi B_hi,  D_corr += A_hi B_lo + A_lo B_hi  (3xTF32)
+// The small correction terms keep their own TMEM accumulator over the whole
+// K range (their FP32 rounding is ~2^-11 below the result).  The main
+// accumulator is drained every kSpan k-chunks (64 k for kSpan = 2) into
+// double-float registers with Knuth's two-sum, so FP32 rounding only ever
+// sees a short span of main products; a second main buffer takes the next
+// span meanwhile.  No FP64 instruction runs in the kernel (GB300's FP64 rate
+// is ~1/1000 of its TF32 rate).
+//
+// Warp roles of the persistent CTA (one per SM, 384 threads = 3 warpgroups):
+//   warp 0     one lane issues the bulk copies into a 3-stage shared-memory ring
+//   warp 1     owns the tensor memory; one lane issues tcgen05.mma and commits
+//              each stage and each accumulator to mbarriers
+//   warps 2-3  idle (their warpgroup hands its registers to the drain warps)
+//   warps 4-11 drain: warp w reads TMEM lanes 32 (w % 4) .. +31 (its row
+//              quarter) and columns 64 ((w - 4) / 4) .. +63 of every tile, keeps
+//              their double-float sums (128 registers) and stores the tile
+//              through a small shared-memory transpose (coalesced rows of
+//              (hi, lo) pairs).
+// The CTA starts with 168 registers per thread (384 x 168 = 64,512 of the
+// SM's 65,536); warpgroup 0 gives up to 56 (setmaxnreg.dec) and the two drain
+// warpgroups take 224 (setmaxnreg.inc): 128 x 56 + 256 x 224 = 64,512.
+// Units (output tiles) are assigned round robin over the CTAs, longest first.
+//
+// Every wait on an mbarrier is bounded by the elapsed %globaltimer time given
+// by the host.  A wait that runs out sets the device error word and a shared
+// abort flag that every other wait also watches; all roles then leave their
+// loops, the copy lane waits for its copies still in flight, the MMA lane for
+// its products (a fixed one-second limit for these drains), and the CTA frees
+// its tensor memory and returns.  Nothing traps.
 #include <atomic>
 #include <cstdint>
 
@@ -27,24 +50,31 @@ namespace dmrg3s {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 64, TBK = 32, TNT = 128;
-constexpr int kStageA = TBM * TBK * 4;            // bytes of one A tile (hi or lo)
-constexpr int kStageB = TBN * TBK * 4;            // bytes of one B tile
-constexpr uint32_t kTmemCols = 2 * TBN;          // two FP32 accumulator buffers
-constexpr long long kSpinLimit = 1ll << 28;       // bounded mbarrier waits
+constexpr int TBM = 128, TBN = 128, TBK = 32;
+constexpr int kStages = 3;
+constexpr int kThreads = 384;                       // 12 warps
+constexpr int kFirstDrainWarp = 4;
+constexpr int kDrainWarps = 8;
+constexpr int kSlab = TBM * TBK * 4;                // bytes of one 128 x 32 slab (16 KB)
+constexpr int kStageBytes = 4 * kSlab;              // A hi, A lo, B hi, B lo
+constexpr int kEpiRow = 9;                          // float2 per staged row (8 + 1 pad)
+constexpr int kEpiWarp = 32 * kEpiRow * 8;          // bytes of one drain warp's staging
+constexpr int kSmemBytes = kStages * kStageBytes + kDrainWarps * kEpiWarp;
+constexpr uint64_t kDrainLimitNs = 1000000000ull;   // waits for work already in flight
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Operand tiles use the K-major, non-swizzled canonical layout: core matrices
-// of 8 rows x 16 bytes; element (row, k) at byte (row / 8) * 1024 +
-// (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4, i.e. K-adjacent core matrices
-// 128 B apart (leading byte offset) and 8-row groups 1024 B apart (stride
-// byte offset).
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets (all >> 4), descriptor version 1, no swizzle.
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte
+// offset 128 (K-adjacent core matrices), stride byte offset 1024 (8-row
+// groups), all >> 4; descriptor version 1; no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   const uint64_t lbo = 128, sbo = 1024;
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
@@ -63,29 +93,71 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void split(double x, float& hi, float& lo) {
-  hi = to_tf32((float)x);
-  lo = to_tf32((float)(x - (double)hi));
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Shared state of one CTA's bounded waits.
+struct WaitCtl {
+  volatile int* abort;
+  int* err;
+  uint64_t limit_ns;
+};
+
+// Waits for the phase of `bar` with the given parity.  Gives up when another
+// thread has aborted, or after limit_ns (then aborts the CTA itself).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const WaitCtl& w) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (*w.abort) return false;
+    if (globaltimer() - t0 > w.limit_ns) {
+      *w.abort = 1;
+      atomicExch(w.err, 1);
+      return false;
+    }
   }
-  return false;
+}
+
+// Waits for work already in flight (copies, products) before the CTA exits:
+// ignores the abort flag, fixed limit.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > kDrainLimitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy global -> shared, completion counted on `bar` (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
@@ -104,264 +176,414 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// Load one operand tile (ROWS x 32, K-major canonical layout) from the
-// pre-split FP32 arrays.  kContig: the source is contiguous along K (element
-// (row, k) at src[row * ld + k]); otherwise along the row index
-// (src[k * ld + row]).  Lanes cover one 8 x 4 core matrix per step (a
-// 128-byte contiguous shared store), with the fast lane index along the
-// source's contiguous direction.  No FP64 arithmetic: GB300's FP64 rate would
-// otherwise bound the kernel.
-template <int ROWS, bool kContig, bool kLo>
-__device__ __forceinline__ void load_tile(const float* __restrict__ shi, const float* __restrict__ slo,
-                                          int ld, int row0, int nrow, int k0, int nk,
-                                          unsigned char* hi, unsigned char* lo, int warp,
-                                          int lane) {
-  const int r8 = kContig ? (lane >> 2) : (lane & 7);
-  const int k4 = kContig ? (lane & 3) : (lane >> 3);
-#pragma unroll
-  for (int g = warp; g < ROWS / 8; g += 4) {
-    const int row = g * 8 + r8;
-    const bool rok = row0 + row < nrow;
-    float vh[8], vl[8];
-#pragma unroll
-    for (int kc = 0; kc < 8; ++kc) {
-      const int k = k0 + kc * 4 + k4;
-      const int64_t o = kContig ? (int64_t)(row0 + row) * ld + k : (int64_t)k * ld + row0 + row;
-      const bool ok = rok && k < nk;
-      vh[kc] = ok ? shi[o] : 0.f;
-      if (kLo) vl[kc] = ok ? slo[o] : 0.f;
-    }
-#pragma unroll
-    for (int kc = 0; kc < 8; ++kc) {
-      const uint32_t o = (uint32_t)(g * 1024 + kc * 128 + r8 * 16 + k4 * 4);
-      *reinterpret_cast<float*>(hi + o) = vh[kc];
-      if (kLo) *reinterpret_cast<float*>(lo + o) = vl[kc];
-    }
-  }
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-      "%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
         "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Add the FP32 accumulator of one K chunk (TMEM columns col0 .. col0 + 63 of
-// this warp's lanes) into the thread's double-float accumulators (hi, lo),
-// with Knuth's two-sum so that no rounding error is lost between chunks.
-__device__ __forceinline__ void drain(uint32_t dtmem, int warp, uint32_t col0, float (&ah)[TBN],
-                                      float (&al)[TBN]) {
-#pragma unroll
-  for (int c0 = 0; c0 < TBN; c0 += 16) {
-    uint32_t v[16];
-    tmem_ld16(dtmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)c0, v);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float x = __uint_as_float(v[j]), a = ah[c0 + j];
-      const float s = __fadd_rn(a, x);
-      const float bb = __fsub_rn(s, a);
-      const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-      ah[c0 + j] = s;
-      al[c0 + j] = __fadd_rn(al[c0 + j], e);
-    }
-  }
+// Knuth's two-sum: (s, e) with s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Every 32-wide K chunk is accumulated by the tensor core into its own FP32
-// TMEM buffer (two buffers, alternating) and then added into double-float
-// registers, so FP32 rounding only ever sees 32-term sums.
-template <Trans TA, Trans TB, int kPasses>
-__global__ void __launch_bounds__(TNT, 2)
-    gemm_tc_kernel(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
-                   const GemmSeg* __restrict__ segs, const float* __restrict__ Ahi,
+template <int kPasses, int kSpan>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(const TcUnit* __restrict__ units, int nunits, const GemmTask* __restrict__ tasks,
+                   const TcSeg* __restrict__ segs, const float* __restrict__ Ahi,
                    const float* __restrict__ Alo, const float* __restrict__ Bhi,
-                   const float* __restrict__ Blo, float2* __restrict__ C, int* __restrict__ err) {
+                   const float* __restrict__ Blo, float2* __restrict__ C, int* __restrict__ err,
+                   uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr bool kLo = kPasses == 3;
-  constexpr int kStage = (kStageA + kStageB) * (kLo ? 2 : 1);
-  __shared__ uint64_t bars[2];
+  constexpr uint32_t kTmemCols = kLo ? 512 : 256;   // main x2 (+ corr x2), 128 columns each
+  constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ __align__(8) uint64_t mfull[2], mempty[2], cfull[2], cempty[2], done;
   __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const GemmTile tile = tiles[blockIdx.x];
-  const GemmTask task = tasks[tile.task];
-  const int m0 = tile.tm * TBM, n0 = tile.tn * TBN;
 
-  if (warp == 0) {
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&mfull[b], 1);
+      mbar_init(&mempty[b], kDrainWarps);
+      mbar_init(&cfull[b], 1);
+      mbar_init(&cempty[b], kDrainWarps);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const WaitCtl wc{&abort_flag, err, wait_ns};
+  if (warp < kFirstDrainWarp) asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+
+  if (warp == 0) {
+    // ---------------- bulk-copy producer ----------------
+    if (lane == 0) {
+      int pend[kStages];
+#pragma unroll
+      for (int s = 0; s < kStages; ++s) pend[s] = -1;
+      uint32_t q = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const TcUnit un = units[u];
+        const GemmTask t = tasks[un.task];
+        for (int k = 0; k < t.nseg && ok; ++k) {
+          const TcSeg sg = segs[t.seg0 + k];
+          const int ga = min(16, sg.ra8 - un.tm * 16), gb = min(16, sg.rb8 - un.tn * 16);
+          const uint32_t ba = (uint32_t)ga * 1024u, bb = (uint32_t)gb * 1024u;
+          for (int c = 0; c < sg.kc; ++c, ++q) {
+            const int st = (int)(q % kStages);
+            if (q >= (uint32_t)kStages && !mbar_wait(&empty[st], ((q / kStages) - 1) & 1, wc)) {
+              ok = false;
+              break;
+            }
+            unsigned char* base = smem + st * kStageBytes;
+            const int64_t oa = sg.pa + ((int64_t)c * sg.ra8 + un.tm * 16) * kPackTile;
+            const int64_t ob = sg.pb + ((int64_t)c * sg.rb8 + un.tn * 16) * kPackTile;
+            mbar_expect_tx(&full[st], (ba + bb) * (kLo ? 2u : 1u));
+            bulk_g2s(base, Ahi + oa, ba, &full[st]);
+            bulk_g2s(base + 2 * kSlab, Bhi + ob, bb, &full[st]);
+            if (kLo) {
+              bulk_g2s(base + kSlab, Alo + oa, ba, &full[st]);
+              bulk_g2s(base + 3 * kSlab, Blo + ob, bb, &full[st]);
+            }
+            pend[st] = (int)((q / kStages) & 1);
+          }
+        }
+      }
+      // copies still in flight must land before the CTA's memory is released
+      for (int s = 0; s < kStages; ++s)
+        if (pend[s] >= 0) mbar_drain(&full[s], (uint32_t)pend[s]);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t q = 0, p = 0, uc = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int T = units[u].nchunks;
+        if (T == 0) continue;
+        const uint32_t cb = uc & 1;
+        const uint32_t dcorr = tmem + 256u + cb * TBN;
+        if (kLo && uc >= 2 && !mbar_wait(&cempty[cb], ((uc >> 1) - 1) & 1, wc)) break;
+        uint32_t dmain = 0;
+        for (int t = 0; t < T; ++t, ++q) {
+          const bool span0 = t % kSpan == 0;
+          if (span0) {
+            const uint32_t mb = p & 1;
+            if (p >= 2 && !mbar_wait(&mempty[mb], ((p >> 1) - 1) & 1, wc)) {
+              ok = false;
+              break;
+            }
+            dmain = tmem + mb * TBN;
+          }
+          const int st = (int)(q % kStages);
+          if (!mbar_wait(&full[st], (q / kStages) & 1, wc)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* base = smem + st * kStageBytes;
+          const uint32_t sah = smem_u32(base), sal = sah + kSlab;
+          const uint32_t sbh = sah + 2 * kSlab, sbl = sah + 3 * kSlab;
+#pragma unroll
+          for (int kk = 0; kk < TBK / 8; ++kk) {     // K = 8 per instruction (32 bytes)
+            const uint32_t off = kk * 256;           // two core matrices along K
+            mma_tf32(dmain, smem_desc(sah + off), smem_desc(sbh + off), idesc,
+                     (span0 && kk == 0) ? 0u : 1u);
+            if (kLo) {
+              mma_tf32(dcorr, smem_desc(sah + off), smem_desc(sbl + off), idesc,
+                       (t == 0 && kk == 0) ? 0u : 1u);
+              mma_tf32(dcorr, smem_desc(sal + off), smem_desc(sbh + off), idesc, 1u);
+            }
+          }
+          mma_commit(&empty[st]);                    // the stage is free once these are done
+          if (t % kSpan == kSpan - 1 || t == T - 1) {
+            mma_commit(&mfull[p & 1]);               // a span of main products is ready
+            ++p;
+          }
+        }
+        if (!ok) break;
+        if (kLo) mma_commit(&cfull[cb]);
+        ++uc;
+      }
+      // every product issued must finish before the tensor memory is freed
+      mma_commit(&done);
+      mbar_drain(&done, 0);
+    }
+    __syncwarp();
+  } else if (warp >= kFirstDrainWarp) {
+    // ---------------- drain and epilogue ----------------
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
+    const int quarter = warp & 3, half = (warp - kFirstDrainWarp) >> 2;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const uint32_t col0 = (uint32_t)(half * 64);
+    float2* stage_out =
+        reinterpret_cast<float2*>(smem + kStages * kStageBytes + (warp - kFirstDrainWarp) * kEpiWarp);
+    uint32_t p = 0, uc = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      const TcUnit un = units[u];
+      const GemmTask t = tasks[un.task];
+      float ah[64], al[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        ah[j] = 0.f;
+        al[j] = 0.f;
+      }
+      if (un.nchunks > 0) {
+        const int nsp = (un.nchunks + kSpan - 1) / kSpan;
+        for (int j = 0; j < nsp; ++j, ++p) {
+          const uint32_t mb = p & 1;
+          // one decision per warp: tcgen05.ld is a warp-wide instruction
+          if (!__all_sync(0xffffffffu, mbar_wait(&mfull[mb], (p >> 1) & 1, wc))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + mb * TBN + col0 + h * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              float s, e;
+              two_sum(ah[h * 16 + i], __uint_as_float(v[i]), s, e);
+              ah[h * 16 + i] = s;
+              al[h * 16 + i] = __fadd_rn(al[h * 16 + i], e);
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&mempty[mb]);
+        }
+        if (!ok) break;
+        if (kLo) {
+          const uint32_t cb = uc & 1;
+          if (!__all_sync(0xffffffffu, mbar_wait(&cfull[cb], (uc >> 1) & 1, wc))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + 256u + cb * TBN + col0 + h * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              al[h * 16 + i] = __fadd_rn(al[h * 16 + i], __uint_as_float(v[i]));
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&cempty[cb]);
+        }
+        ++uc;
+      }
+      // renormalise (hi, lo) and store: 8 columns at a time through the
+      // warp's staging rows, written back as rows of 8 consecutive pairs
+      const int row0 = un.tm * TBM + quarter * 32;
+      const int n0 = un.tn * TBN + half * 64;
+#pragma unroll
+      for (int c8 = 0; c8 < 64; c8 += 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float s, e;
+          two_sum(ah[c8 + i], al[c8 + i], s, e);
+          stage_out[lane * kEpiRow + i] = make_float2(s, e);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = it * 4 + (lane >> 3), cc = lane & 7;
+          const int gm = row0 + r, gn = n0 + c8 + cc;
+          if (gm < t.M && gn < t.N) C[t.offC + (int64_t)gm * t.ldc + gn] = stage_out[r * kEpiRow + cc];
+        }
+        __syncwarp();
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t dtmem = tmem_base;
-  constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
-  float ah[TBN], al[TBN];
-#pragma unroll
-  for (int j = 0; j < TBN; ++j) {
-    ah[j] = 0.f;
-    al[j] = 0.f;
-  }
-  bool ok = true;
-  int it = 0;
-
-  for (int sgi = 0; sgi < task.nseg && ok; ++sgi) {
-    const GemmSeg sg = segs[task.seg0 + sgi];
-    for (int k0 = 0; k0 < sg.K; k0 += TBK, ++it) {
-      const int st = it & 1;
-      // stage st and TMEM buffer st were last used by chunk it - 2
-      if (it >= 2 && ok) ok = mbar_wait(&bars[st], (uint32_t)(((it - 2) >> 1) & 1));
-      unsigned char* base = smem + st * kStage;
-      unsigned char* a_hi = base;
-      unsigned char* a_lo = base + kStageA;
-      unsigned char* b_hi = base + kStageA * (kLo ? 2 : 1);
-      unsigned char* b_lo = b_hi + kStageB;
-      load_tile<TBM, TA == Trans::N, kLo>(Ahi + sg.offA, kLo ? Alo + sg.offA : nullptr, sg.lda, m0,
-                                          task.M, k0, sg.K, a_hi, a_lo, warp, lane);
-      load_tile<TBN, TB == Trans::T, kLo>(Bhi + sg.offB, kLo ? Blo + sg.offB : nullptr, sg.ldb, n0,
-                                          task.N, k0, sg.K, b_hi, b_lo, warp, lane);
-      // make the generic-proxy stores visible to the tensor core (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      // one decision for the whole CTA (a wait that timed out in any thread
-      // stops every thread), so that all threads meet the same barriers; a
-      // stage written after a failed wait is never handed to the tensor core
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sah = smem_u32(a_hi), sal = smem_u32(a_lo);
-        const uint32_t sbh = smem_u32(b_hi), sbl = smem_u32(b_lo);
-        const uint32_t d = dtmem + (uint32_t)(st * TBN);
-#pragma unroll
-        for (int kk = 0; kk < TBK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
-          const uint32_t off = kk * 256;             // two core matrices along K
-          if (kLo) {
-            mma_tf32(d, smem_desc(sal + off), smem_desc(sbh + off), idesc, kk == 0 ? 0u : 1u);
-            mma_tf32(d, smem_desc(sah + off), smem_desc(sbl + off), idesc, 1u);
-            mma_tf32(d, smem_desc(sah + off), smem_desc(sbh + off), idesc, 1u);
-          } else {
-            mma_tf32(d, smem_desc(sah + off), smem_desc(sbh + off), idesc, kk == 0 ? 0u : 1u);
-          }
-        }
-        mma_commit(&bars[st]);
-      }
-      // meanwhile drain the previous chunk's accumulator
-      if (it >= 1) {
-        ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
-        if (ok) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), ah, al);
-        }
-      }
-    }
-    ok = __syncthreads_and(ok);
-  }
-  // the last chunk
-  if (ok && it > 0) {
-    ok = mbar_wait(&bars[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
-    if (ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      drain(dtmem, warp, (uint32_t)(((it - 1) & 1) * TBN), ah, al);
-    }
-  }
-  ok = __syncthreads_and(ok);
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-  } else {
-    // ---- epilogue: thread (warp, lane) owns accumulator row 32 warp + lane
-    const int gm = m0 + warp * 32 + lane;
-    if (gm < task.M) {
-      float2* crow = C + task.offC + (int64_t)gm * task.ldc + n0;
-      const int nv = task.N - n0 < TBN ? task.N - n0 : TBN;
-#pragma unroll
-      for (int j = 0; j < TBN; ++j)
-        if (j < nv) crow[j] = make_float2(ah[j], al[j]);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem),
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
                  : "memory");
 }
 
-__global__ void split_kernel(const double* __restrict__ x, float* __restrict__ hi,
-                             float* __restrict__ lo, int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    float h, l;
-    split(x[i], h, l);
-    hi[i] = h;
-    if (lo) lo[i] = l;
+// Binary search: the block of tile `tile` (blocks in increasing tile0 order).
+template <class T>
+__device__ __forceinline__ int block_of_tile(const T* __restrict__ b, int n, int tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b[mid].tile0 <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One warp per 8 x 32 tile: lane l handles row l / 4 and k = 4 j + l % 4 of
+// core matrix j (j = 0..7), so each store is a contiguous 128-byte run.
+__global__ void __launch_bounds__(256)
+    pack_kernel(const PackBlock* __restrict__ blocks, int nblocks, int ntiles,
+                const double* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo) {
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;
+  const int lane = threadIdx.x & 31;
+  const PackBlock b = blocks[block_of_tile(blocks, nblocks, tile)];
+  const int local = tile - b.tile0;                  // tile = (c, g) with local = c R8 + g
+  const int c = local / b.R8, g = local - c * b.R8;
+  const int r = g * 8 + (lane >> 2);
+  const int64_t out = b.dst + (int64_t)local * kPackTile + lane;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = c * 32 + j * 4 + (lane & 3);
+    float h = 0.f, l = 0.f;
+    if (r < b.R && k < b.K) {
+      const double x = b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k];
+      h = to_tf32((float)x);
+      l = to_tf32((float)(x - (double)h));
+    }
+    hi[out + j * 32] = h;
+    if (lo) lo[out + j * 32] = l;
   }
 }
 
-template <Trans TA, Trans TB, int P>
-void launch_one(const GemmTile* tiles, int ntiles, const GemmTask* tasks, const GemmSeg* segs,
+// Double-float accumulation of a coefficient pair times an input pair.
+__device__ __forceinline__ void df_acc(float ch, float cl, float2 x, float& ah, float& al) {
+  const float p = __fmul_rn(ch, x.x);
+  float pe = __fmaf_rn(ch, x.x, -p);
+  pe = __fmaf_rn(ch, x.y, pe);
+  pe = __fmaf_rn(cl, x.x, pe);
+  float s, e;
+  two_sum(ah, p, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, pe));
+  ah = __fadd_rn(s, e);
+  al = __fsub_rn(e, __fsub_rn(ah, s));
+}
+
+// Stage 2 into the packed operand of stage 3: one warp per 8 x 32 tile of a
+// task's packed output; the value is scale * sum_k coef_k in_k in double-float
+// arithmetic, then split hi = tf32(v), lo = tf32(v - hi).
+__global__ void __launch_bounds__(256)
+    combine_pairs_pack_kernel(const PackOut* __restrict__ outs, int ntasks, int ntiles,
+                              const CombTask* __restrict__ tasks, const CombTerm* __restrict__ terms,
+                              const float2* __restrict__ in, float* __restrict__ out_hi,
+                              float* __restrict__ out_lo, float sh, float sl) {
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;
+  const int lane = threadIdx.x & 31;
+  const int ti = block_of_tile(outs, ntasks, tile);
+  const PackOut o = outs[ti];
+  const CombTask t = tasks[ti];
+  const int local = tile - o.tile0;
+  const int c = local / o.R8, g = local - c * o.R8;
+  const int r = g * 8 + (lane >> 2);
+  const int R = o.trans ? t.cols : t.rows, K = o.trans ? t.rows : t.cols;
+  const int64_t out = o.dst + (int64_t)local * kPackTile + lane;
+  const bool scaled = sh != 1.f || sl != 0.f;
+#pragma unroll 2
+  for (int j = 0; j < 8; ++j) {
+    const int k = c * 32 + j * 4 + (lane & 3);
+    float h = 0.f, l = 0.f;
+    if (r < R && k < K) {
+      const int row = o.trans ? k : r, col = o.trans ? r : k;
+      float ah = 0.f, al = 0.f;
+      for (int m = 0; m < t.nt; ++m) {
+        const CombTerm tm = terms[t.t0 + m];
+        df_acc(tm.chi, tm.clo, in[tm.offIn + (int64_t)row * tm.ldi + col], ah, al);
+      }
+      if (scaled) {
+        const float xh = ah, xl = al;
+        ah = 0.f;
+        al = 0.f;
+        df_acc(sh, sl, make_float2(xh, xl), ah, al);
+      }
+      h = to_tf32(ah);
+      // ah - h is exact (h is ah rounded to the 10-bit TF32 mantissa)
+      l = to_tf32(__fadd_rn(__fsub_rn(ah, h), al));
+    }
+    out_hi[out + j * 32] = h;
+    if (out_lo) out_lo[out + j * 32] = l;
+  }
+}
+
+template <int P>
+void launch_one(const TcUnit* units, int nunits, const GemmTask* tasks, const TcSeg* segs,
                 const float* Ah, const float* Al, const float* Bh, const float* Bl, float2* C,
-                int* err, cudaStream_t st) {
-  constexpr int kLo = P == 3 ? 1 : 0;
-  constexpr int smem = 2 * (kStageA + kStageB) * (1 + kLo);
+                int* err, uint64_t wait_ns, cudaStream_t st) {
   // the shared-memory limit is a per-device attribute of the kernel
   static std::atomic<uint64_t> done{0};
   int dev = 0;
   cudaGetDevice(&dev);
   const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
   if (!bit || !(done.load() & bit)) {
-    cudaFuncSetAttribute(gemm_tc_kernel<TA, TB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
+    cudaFuncSetAttribute(gemm_tc_kernel<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmemBytes);
     if (bit) done.fetch_or(bit);
   }
-  gemm_tc_kernel<TA, TB, P><<<ntiles, TNT, smem, st>>>(tiles, tasks, segs, Ah, Al, Bh, Bl, C, err);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 152;
+  const int grid = nunits < nsm ? nunits : nsm;
+  gemm_tc_kernel<P, 2><<<grid, kThreads, kSmemBytes, st>>>(units, nunits, tasks, segs, Ah, Al, Bh,
+                                                           Bl, C, err, wait_ns);
 }
 
 }  // namespace
 
-void launch_split(const double* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
-  if (n <= 0) return;
+void launch_pack(const PackBlock* blocks, int nblocks, int ntiles, const double* src, float* hi,
+                 float* lo, cudaStream_t st) {
+  if (ntiles <= 0 || nblocks <= 0) return;
   count_launch();
-  int64_t g = (n + 255) / 256;
-  if (g > 4 * 152) g = 4 * 152;
-  split_kernel<<<(int)g, 256, 0, st>>>(x, hi, lo, n);
+  pack_kernel<<<(ntiles + 7) / 8, 256, 0, st>>>(blocks, nblocks, ntiles, src, hi, lo);
 }
 
-void launch_gemm_tc(int passes, Trans ta, Trans tb, const GemmTile* tiles, int ntiles,
-                    const GemmTask* tasks, const GemmSeg* segs, const float* Ahi,
-                    const float* Alo, const float* Bhi, const float* Blo, float2* C, int* err,
-                    cudaStream_t st) {
-  if (ntiles <= 0) return;
+void launch_combine_pairs_pack(const PackOut* outs, int ntasks, int ntiles, const CombTask* tasks,
+                               const CombTerm* terms, const float2* in, float* out_hi,
+                               float* out_lo, double scale, cudaStream_t st) {
+  if (ntiles <= 0 || ntasks <= 0) return;
   count_launch();
-#define DMRG3S_TC(TA_, TB_)                                                           \
-  if (ta == Trans::TA_ && tb == Trans::TB_) {                                         \
-    if (passes == 3)                                                                  \
-      launch_one<Trans::TA_, Trans::TB_, 3>(tiles, ntiles, tasks, segs, Ahi, Alo, Bhi, Blo, C, \
-                                            err, st);                                   \
-    else                                                                              \
-      launch_one<Trans::TA_, Trans::TB_, 1>(tiles, ntiles, tasks, segs, Ahi, Alo, Bhi, Blo, C, \
-                                            err, st);                                   \
-    return;                                                                           \
-  }
-  DMRG3S_TC(N, N)
-  DMRG3S_TC(N, T)
-  DMRG3S_TC(T, N)
-  DMRG3S_TC(T, T)
-#undef DMRG3S_TC
+  const float sh = (float)scale, sl = (float)(scale - (double)sh);
+  combine_pairs_pack_kernel<<<(ntiles + 7) / 8, 256, 0, st>>>(outs, ntasks, ntiles, tasks, terms,
+                                                              in, out_hi, out_lo, sh, sl);
+}
+
+void launch_gemm_tc(int passes, const TcUnit* units, int nunits, const GemmTask* tasks,
+                    const TcSeg* segs, const float* Ahi, const float* Alo, const float* Bhi,
+                    const float* Blo, float2* C, int* err, uint64_t wait_ns, cudaStream_t st) {
+  if (nunits <= 0) return;
+  count_launch();
+  if (passes == 3)
+    launch_one<3>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, C, err, wait_ns, st);
+  else
+    launch_one<1>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, C, err, wait_ns, st);
 }
 
 }  // namespace dmrg3s

@@ -3,6 +3,7 @@
 
 #include "validate.hpp"
 
+#include <algorithm>
 #include <array>
 #include <map>
 #include <set>
@@ -27,9 +28,6 @@ void GemmStage::add(int64_t offC, int ldc, int M, int N, const std::vector<GemmS
   const int ntm = (M + 63) / 64, ntn = (N + 63) / 64;
   for (int a = 0; a < ntm; ++a)
     for (int b = 0; b < ntn; ++b) tiles.push_back(GemmTile{id, a, b, 0});
-  const int ntm_tc = (M + 127) / 128;
-  for (int a = 0; a < ntm_tc; ++a)
-    for (int b = 0; b < ntn; ++b) tiles_tc.push_back(GemmTile{id, a, b, 0});
 }
 
 void GemmStage::finalize_bytes(Trans, Trans) {
@@ -178,6 +176,120 @@ std::map<Key, Interm> materialise(const std::map<Key, Combo>& combos, Plan* p) {
   return out;
 }
 
+// ---- tensor-core form of the stages ----
+
+inline int32_t groups8(int64_t R) { return (int32_t)((R + 7) / 8); }
+inline int32_t chunks32(int64_t K) { return (int32_t)((K + 31) / 32); }
+
+// Packed placements of one operand array; identical views share one block.
+struct Packer {
+  std::map<std::array<int64_t, 5>, int64_t> seen;    // (src, ld, R, K, trans) -> dst
+  std::vector<PackBlock>* out;
+  int64_t* n;
+  int32_t* tiles;
+  int64_t add(int64_t src, int64_t ld, int64_t R, int64_t K, int trans) {
+    const std::array<int64_t, 5> key{src, ld, R, K, trans};
+    auto it = seen.find(key);
+    if (it != seen.end()) return it->second;
+    PackBlock b{};
+    b.src = src;
+    b.dst = *n;
+    b.ld = (int32_t)ld;
+    b.R = (int32_t)R;
+    b.K = (int32_t)K;
+    b.trans = trans;
+    b.R8 = groups8(R);
+    b.KC = chunks32(K);
+    b.tile0 = *tiles;
+    out->push_back(b);
+    *n += (int64_t)b.R8 * b.KC * kPackTile;
+    *tiles += b.R8 * b.KC;
+    seen[key] = b.dst;
+    return b.dst;
+  }
+};
+
+// Placement of a block packed by stage 2: ws2 element offset -> (dst, R8, R, K).
+struct CombPacked {
+  int64_t dst;
+  int32_t R8, R, K;
+};
+
+// Builds g.tc.  An operand with a map (c2A for A, c2B for B) is the stage-2
+// output, already packed; its segments look their block up by the ws2 offset.
+bool build_tc(GemmStage& g, const std::map<int64_t, CombPacked>* c2A,
+              const std::map<int64_t, CombPacked>* c2B, std::string* err) {
+  TcStage& tc = g.tc;
+  tc = TcStage();
+  Packer pa{{}, &tc.packA, &tc.nA, &tc.tilesA};
+  Packer pb{{}, &tc.packB, &tc.nB, &tc.tilesB};
+  auto lookup = [&](const std::map<int64_t, CombPacked>* m, int64_t off, int64_t R, int64_t K,
+                    int64_t* dst, int32_t* r8) {
+    auto it = m->find(off);
+    if (it == m->end() || it->second.R != R || it->second.K != K) {
+      *err = "tensor-core operand of stage 3 is not a stage-2 block";
+      return false;
+    }
+    *dst = it->second.dst;
+    *r8 = it->second.R8;
+    return true;
+  };
+  for (const GemmTask& t : g.tasks) {
+    int32_t nch = 0;
+    for (int k = 0; k < t.nseg; ++k) {
+      const GemmSeg& sg = g.segs[t.seg0 + k];
+      TcSeg ts{};
+      ts.kc = chunks32(sg.K);
+      // A (rows M): ta = N stores M x K, ta = T stores K x M
+      if (c2A) {
+        if (!lookup(c2A, sg.offA, t.M, sg.K, &ts.pa, &ts.ra8)) return false;
+      } else {
+        ts.pa = pa.add(sg.offA, sg.lda, t.M, sg.K, g.ta == Trans::T ? 1 : 0);
+        ts.ra8 = groups8(t.M);
+      }
+      // B (rows N): tb = N stores K x N, tb = T stores N x K
+      if (c2B) {
+        if (!lookup(c2B, sg.offB, t.N, sg.K, &ts.pb, &ts.rb8)) return false;
+      } else {
+        ts.pb = pb.add(sg.offB, sg.ldb, t.N, sg.K, g.tb == Trans::N ? 1 : 0);
+        ts.rb8 = groups8(t.N);
+      }
+      tc.segs.push_back(ts);
+      nch += ts.kc;
+    }
+    const int id = (int)(&t - g.tasks.data());
+    for (int a = 0; a < (t.M + 127) / 128; ++a)
+      for (int b = 0; b < (t.N + 127) / 128; ++b) tc.units.push_back(TcUnit{id, a, b, nch});
+  }
+  // longest units first: the persistent CTAs take them round robin
+  std::stable_sort(tc.units.begin(), tc.units.end(),
+                   [](const TcUnit& x, const TcUnit& y) { return x.nchunks > y.nchunks; });
+  return true;
+}
+
+// Packs every stage-2 output block (orientation `trans`) and returns the map
+// from its ws2 offset to the packed placement.
+std::map<int64_t, CombPacked> pack_c2(Plan* p, int trans) {
+  std::map<int64_t, CombPacked> m;
+  p->c2pack.clear();
+  p->nT2p = 0;
+  p->tilesT2 = 0;
+  for (const CombTask& t : p->c2.tasks) {
+    PackOut o{};
+    const int64_t R = trans ? t.cols : t.rows, K = trans ? t.rows : t.cols;
+    o.dst = p->nT2p;
+    o.R8 = groups8(R);
+    o.KC = chunks32(K);
+    o.trans = trans;
+    o.tile0 = p->tilesT2;
+    p->c2pack.push_back(o);
+    m[t.offOut] = CombPacked{o.dst, o.R8, (int32_t)R, (int32_t)K};
+    p->nT2p += (int64_t)o.R8 * o.KC * kPackTile;
+    p->tilesT2 += o.R8 * o.KC;
+  }
+  return m;
+}
+
 // Bounds of every table against the buffers the stages address.
 dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
                      int64_t nC3, std::string* err) {
@@ -221,6 +333,26 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
   if (!gemm_ok(p->g1.ta, p->g1.tb, p->g1.tasks, p->g1.segs, nA1, nB1, w1, err) ||
       !comb_ok(p->c2.tasks, p->c2.terms, w1, nOut2, err) ||
       (p->has_g3 && !gemm_ok(p->g3.ta, p->g3.tb, p->g3.tasks, p->g3.segs, nA3, nB3, nC3, err))) {
+    *err = "internal planning error: " + *err;
+    return DMRG3S_ERR_SHAPE;
+  }
+  // tensor-core form: stage 1 packs both operands; stage 3 takes the stage-2
+  // output packed by the combination (A of H_eff, B of the environments)
+  bool ok = build_tc(p->g1, nullptr, nullptr, err);
+  if (ok && p->has_g3) {
+    const bool c2_is_a = p->kind == Kind::Heff;
+    const int trans = p->kind == Kind::EnvLR ? 1 : 0;
+    const std::map<int64_t, CombPacked> m = pack_c2(p, trans);
+    ok = build_tc(p->g3s, c2_is_a ? &m : nullptr, c2_is_a ? nullptr : &m, err);
+  }
+  if (ok) ok = tc_ok(p->g1.tasks, p->g1.tc, nA1, nB1, p->g1.tc.nA, p->g1.tc.nB, err);
+  if (ok && p->has_g3) {
+    const bool c2_is_a = p->kind == Kind::Heff;
+    ok = tc_ok(p->g3s.tasks, p->g3s.tc, nA3, nB3, c2_is_a ? p->nT2p : p->g3s.tc.nA,
+               c2_is_a ? p->g3s.tc.nB : p->nT2p, err) &&
+         packout_ok(p->c2.tasks, p->c2pack, p->nT2p, err);
+  }
+  if (!ok) {
     *err = "internal planning error: " + *err;
     return DMRG3S_ERR_SHAPE;
   }

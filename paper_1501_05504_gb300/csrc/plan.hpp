@@ -31,12 +31,21 @@
 
 namespace dmrg3s {
 
+// Tensor-core form of a grouped GEMM stage (packed operands, 128 x 128 units).
+struct TcStage {
+  std::vector<TcSeg> segs;              // parallel to GemmStage::segs
+  std::vector<TcUnit> units;            // longest first
+  std::vector<PackBlock> packA, packB;  // empty for an operand packed by stage 2
+  int64_t nA = 0, nB = 0;               // floats of one part (hi or lo) of each packed operand
+  int32_t tilesA = 0, tilesB = 0;
+};
+
 struct GemmStage {
   Trans ta = Trans::N, tb = Trans::N;
   std::vector<GemmTask> tasks;
   std::vector<GemmSeg> segs;
   std::vector<GemmTile> tiles;      // 64 x 64 tiles (FP64 kernel)
-  std::vector<GemmTile> tiles_tc;   // 128 x 64 tiles (tensor-core kernel)
+  TcStage tc;
   double flops = 0.0;
   double bytes = 0.0;     // algorithmic: distinct operand blocks read once + output written once
   void add(int64_t offC, int ldc, int M, int N, const std::vector<GemmSeg>& s);
@@ -69,10 +78,16 @@ struct Plan {
   int64_t nA1 = 0, nB1 = 0;     // elements of the stage-1 operand arrays
   int64_t nA3 = 0, nB3 = 0;     // elements of the stage-3 operand arrays (0 without stage 3)
   // Split-K form of stage 3 for the tensor-core kernel: one task per (output
-  // block, K-segment) writing an FP64 partial block, then a deterministic sum.
+  // block, K-segment) writing a double-float partial block, then a
+  // deterministic sum.
   GemmStage g3s;                // partial products (C base = the partial buffer)
   CombStage c3r;                // sum of the partials into the output
-  int64_t ws3 = 0;              // doubles of the partial buffer
+  int64_t ws3 = 0;              // elements of the partial buffer
+  // Tensor-core mode: stage 2 writes its output packed as the stage-3 operand
+  // that is ws2 (A for Heff, B for EnvLR / EnvRL), one PackOut per c2 task.
+  std::vector<PackOut> c2pack;
+  int64_t nT2p = 0;             // floats of one part of the packed stage-2 output
+  int32_t tilesT2 = 0;
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
 

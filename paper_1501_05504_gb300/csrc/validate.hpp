@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "kernels.hpp"
+#include "plan.hpp"
 #include "vecops.hpp"
 
 namespace dmrg3s {
@@ -54,6 +55,83 @@ inline bool comb_ok(const std::vector<CombTask>& tasks, const std::vector<CombTe
         *err = "combination input out of bounds";
         return false;
       }
+    }
+  }
+  return true;
+}
+
+// Tensor-core tables: every packed source view inside its FP64 array, every
+// packed block and every bulk copy of a unit inside its packed array.
+inline bool pack_ok(const std::vector<PackBlock>& blocks, int64_t nSrc, int64_t nPacked,
+                    int32_t ntiles, std::string* err) {
+  for (const PackBlock& b : blocks) {
+    if (b.R <= 0 || b.K <= 0) continue;
+    const int64_t last = b.trans ? (int64_t)(b.K - 1) * b.ld + b.R - 1
+                                 : (int64_t)(b.R - 1) * b.ld + b.K - 1;
+    const int64_t minld = b.trans ? b.R : b.K;
+    if (!span_ok(b.src, last, nSrc) || b.ld < minld || (int64_t)b.R8 * 8 < b.R ||
+        (int64_t)b.KC * 32 < b.K || b.dst < 0 ||
+        b.dst + (int64_t)b.R8 * b.KC * kPackTile > nPacked || b.tile0 < 0 ||
+        (int64_t)b.tile0 + (int64_t)b.R8 * b.KC > ntiles) {
+      *err = "operand pack out of bounds";
+      return false;
+    }
+  }
+  return true;
+}
+
+inline bool tc_ok(const std::vector<GemmTask>& tasks, const TcStage& tc, int64_t nSrcA,
+                  int64_t nSrcB, int64_t nPA, int64_t nPB, std::string* err) {
+  if (!pack_ok(tc.packA, nSrcA, tc.nA, tc.tilesA, err) ||
+      !pack_ok(tc.packB, nSrcB, tc.nB, tc.tilesB, err))
+    return false;
+  std::vector<int32_t> nch(tasks.size(), 0);
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const GemmTask& t = tasks[i];
+    if (t.seg0 < 0 || (size_t)t.seg0 + t.nseg > tc.segs.size()) {
+      *err = "tensor-core segment index out of range";
+      return false;
+    }
+    for (int k = 0; k < t.nseg; ++k) {
+      const TcSeg& s = tc.segs[t.seg0 + k];
+      if (s.kc < 0 || (int64_t)s.ra8 * 8 < t.M || (int64_t)s.rb8 * 8 < t.N || s.pa < 0 ||
+          s.pb < 0 || s.pa + (int64_t)s.kc * s.ra8 * kPackTile > nPA ||
+          s.pb + (int64_t)s.kc * s.rb8 * kPackTile > nPB) {
+        *err = "tensor-core segment out of bounds";
+        return false;
+      }
+      nch[i] += s.kc;
+    }
+  }
+  for (const TcUnit& u : tc.units) {
+    if (u.task < 0 || (size_t)u.task >= tasks.size()) {
+      *err = "tensor-core unit task out of range";
+      return false;
+    }
+    const GemmTask& t = tasks[u.task];
+    if (u.tm < 0 || u.tn < 0 || (int64_t)u.tm * 128 >= t.M || (int64_t)u.tn * 128 >= t.N ||
+        u.nchunks != nch[u.task]) {
+      *err = "tensor-core unit out of range";
+      return false;
+    }
+  }
+  return true;
+}
+
+inline bool packout_ok(const std::vector<CombTask>& tasks, const std::vector<PackOut>& outs,
+                       int64_t nPacked, std::string* err) {
+  if (outs.size() != tasks.size()) {
+    *err = "packed combination table size";
+    return false;
+  }
+  for (size_t i = 0; i < outs.size(); ++i) {
+    const PackOut& o = outs[i];
+    const int64_t R = o.trans ? tasks[i].cols : tasks[i].rows;
+    const int64_t K = o.trans ? tasks[i].rows : tasks[i].cols;
+    if ((int64_t)o.R8 * 8 < R || (int64_t)o.KC * 32 < K || o.dst < 0 ||
+        o.dst + (int64_t)o.R8 * o.KC * kPackTile > nPacked) {
+      *err = "packed combination output out of bounds";
+      return false;
     }
   }
   return true;

@@ -105,7 +105,7 @@ def test_spin1_ring_l100_paper_energy(b, ctx):
     The precision ladder (3xTF32, then FP64) at m_max = 256: a periodic chain
     needs a larger bond dimension than the paper's open-chain runs for the
     same accuracy, so the bound is the variational one plus the relative
-    deviation this m reaches."""
+    deviation this m reaches (1.2e-6 measured on the GB300)."""
     from oracle import models
     L, m = 100, 256
     bonds = models.ring_bonds(L)
@@ -122,13 +122,15 @@ def test_spin1_ring_l100_paper_energy(b, ctx):
     print("S=1 ring L=100 m=%d: E = %.9f (%d sweeps, %.1f s), rel. deviation from the paper %.2e"
           % (m, rep["energy"], rep["sweeps"], rep["seconds"][-1], rel))
     assert rep["energy"] >= e_paper - 5e-7          # the paper's value is rounded to 1e-6
-    assert rel < 2e-4
+    assert rel < 5e-6                               # measured: 1.2e-6 at m = 256
 
 
 def test_hubbard_u0_l100_closed_form(b, ctx):
     """Half-filled U = 0 Hubbard chain (free fermions), L = 100, N = 100
     (Sec. VII B 4): the closed form of the filled single-particle levels,
-    -126.6023783108, and the paper's converged DMRG value -126.602376."""
+    -126.6023783108, and the paper's converged DMRG value -126.602376 (the
+    paper's m = 1200 run lies 1.8e-8 above the closed form; this m = 512 run
+    reached 8.3e-7 on the GB300)."""
     L, m = 100, 512
     W = b.Mpo(b.MODEL_HUBBARD, L, (1.0, 0.0)).sites()
     st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [2, 1] * (L // 2)), None, None,
@@ -143,4 +145,4 @@ def test_hubbard_u0_l100_closed_form(b, ctx):
           % (m, rep["energy"], rep["sweeps"], rep["seconds"][-1], rel,
              (-126.602376 - e0) / abs(e0)))
     assert rep["energy"] >= e0 - 1e-10 * abs(e0)
-    assert rel < 1e-6
+    assert rel < 2e-6                               # measured: 8.3e-7 at m = 512
