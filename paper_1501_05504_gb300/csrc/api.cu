@@ -68,7 +68,8 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
                  bytes_of(h.c3r.terms) + bytes_of(h.g1.tc.units) + bytes_of(h.g1.tc.segs) +
                  bytes_of(h.g1.tc.packA) + bytes_of(h.g1.tc.packB) + bytes_of(h.g3s.tc.units) +
                  bytes_of(h.g3s.tc.segs) + bytes_of(h.g3s.tc.packA) + bytes_of(h.g3s.tc.packB) +
-                 bytes_of(h.c2pack);
+                 bytes_of(h.c2pack) + bytes_of(h.g12.tasks) + bytes_of(h.g12.tc.units) +
+                 bytes_of(h.g12.tc.segs) + bytes_of(h.g12.tc.packA) + bytes_of(h.g12.tc.packB);
   if (total == 0) total = 256;
   if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
   std::vector<char> staging(total, 0);
@@ -93,6 +94,11 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   dp->g3s_packA = place(base, &off, h.g3s.tc.packA, &staging);
   dp->g3s_packB = place(base, &off, h.g3s.tc.packB, &staging);
   dp->c2_pack = place(base, &off, h.c2pack, &staging);
+  dp->g12_tasks = place(base, &off, h.g12.tasks, &staging);
+  dp->g12_units = place(base, &off, h.g12.tc.units, &staging);
+  dp->g12_tsegs = place(base, &off, h.g12.tc.segs, &staging);
+  dp->g12_packA = place(base, &off, h.g12.tc.packA, &staging);
+  dp->g12_packB = place(base, &off, h.g12.tc.packB, &staging);
   dp->c3r_chunks = place(base, &off, h.c3r.chunks, &staging);
   dp->c3r_tasks = place(base, &off, h.c3r.tasks, &staging);
   dp->c3r_terms = place(base, &off, h.c3r.terms, &staging);
@@ -142,16 +148,34 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   // the tensor-core stages write double-float pairs (8 bytes per element, in
   // place of the FP64 intermediates), combined on the FP32 pipe
   float2* t1p = reinterpret_cast<float2*>(ws1);
-  const TcStage& t1 = h.g1.tc;
-  if (!hn.g1A) launch_pack(p.g1_packA, (int)t1.packA.size(), t1.tilesA, g1A, hi(sl.a1),
-                           lo(sl.a1, t1.nA), st);
-  if (!hn.g1B) launch_pack(p.g1_packB, (int)t1.packB.size(), t1.tilesB, g1B, hi(sl.b1),
-                           lo(sl.b1, t1.nB), st);
-  if (!t1.units.empty()) {
-    const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
-    launch_gemm_tc(passes, p.g1_units, (int)t1.units.size(), p.g1_tasks, p.g1_tsegs, hi(sl.a1),
-                   lo(sl.a1, t1.nA), hi(sl.b1), lo(sl.b1, t1.nB), t1p, c->d_err, c->wait_ns, st);
-    if (id >= 0) pr.end(id, st);
+  if (h.fused) {
+    // H_eff: stages 1 and 2 in one grouped GEMM over the MPO terms, writing T2
+    // packed as the stage-3 operand (T1 is never formed)
+    const TcStage& t12 = h.g12.tc;
+    if (!hn.g1A) launch_pack(p.g12_packA, (int)t12.packA.size(), t12.tilesA, g1A, hi(sl.a1),
+                             lo(sl.a1, t12.nA), st);
+    if (!hn.g1B) launch_pack(p.g12_packB, (int)t12.packB.size(), t12.tilesB, g1B, hi(sl.b1),
+                             lo(sl.b1, t12.nB), st);
+    if (!t12.units.empty()) {
+      const int id = pr.on ? pr.begin(kProfGemm, h.g12.flops, h.g12.bytes, st) : -1;
+      launch_gemm_tc(passes, true, p.g12_units, (int)t12.units.size(), p.g12_tasks, p.g12_tsegs,
+                     hi(sl.a1), lo(sl.a1, t12.nA), hi(sl.b1), lo(sl.b1, t12.nB), hi(sl.t2p),
+                     lo(sl.t2p, h.nT2p), c->d_err, c->wait_ns, st);
+      if (id >= 0) pr.end(id, st);
+    }
+  } else {
+    const TcStage& t1 = h.g1.tc;
+    if (!hn.g1A) launch_pack(p.g1_packA, (int)t1.packA.size(), t1.tilesA, g1A, hi(sl.a1),
+                             lo(sl.a1, t1.nA), st);
+    if (!hn.g1B) launch_pack(p.g1_packB, (int)t1.packB.size(), t1.tilesB, g1B, hi(sl.b1),
+                             lo(sl.b1, t1.nB), st);
+    if (!t1.units.empty()) {
+      const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
+      launch_gemm_tc(passes, false, p.g1_units, (int)t1.units.size(), p.g1_tasks, p.g1_tsegs,
+                     hi(sl.a1), lo(sl.a1, t1.nA), hi(sl.b1), lo(sl.b1, t1.nB),
+                     reinterpret_cast<float*>(t1p), nullptr, c->d_err, c->wait_ns, st);
+      if (id >= 0) pr.end(id, st);
+    }
   }
   if (!h.has_g3) {
     if (!h.c2.chunks.empty()) {
@@ -163,7 +187,7 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
     return cudaGetLastError() == cudaSuccess ? DMRG3S_OK : DMRG3S_ERR_CUDA;
   }
   // stage 2 writes T2 packed as the stage-3 operand it feeds
-  if (!h.c2pack.empty()) {
+  if (!h.fused && !h.c2pack.empty()) {
     const int id = pr.on ? pr.begin(kProfCombine, h.c2.flops, h.c2.bytes, st) : -1;
     launch_combine_pairs_pack(p.c2_pack, (int)h.c2pack.size(), h.tilesT2, p.c2_tasks, p.c2_terms,
                               t1p, hi(sl.t2p), lo(sl.t2p, h.nT2p), c2scale, st);
@@ -194,8 +218,9 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   float2* part = reinterpret_cast<float2*>(base + sl.p3);
   if (!t3.units.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g3s.flops, h.g3s.bytes, st) : -1;
-    launch_gemm_tc(passes, p.g3s_units, (int)t3.units.size(), p.g3s_tasks, p.g3s_tsegs, a3h, a3l,
-                   b3h, b3l, part, c->d_err, c->wait_ns, st);
+    launch_gemm_tc(passes, false, p.g3s_units, (int)t3.units.size(), p.g3s_tasks, p.g3s_tsegs,
+                   a3h, a3l, b3h, b3l, reinterpret_cast<float*>(part), nullptr, c->d_err,
+                   c->wait_ns, st);
     if (id >= 0) pr.end(id, st);
   }
   if (!h.c3r.chunks.empty()) {

@@ -36,6 +36,11 @@ struct DevicePlan {
   PackBlock* g3s_packA = nullptr;
   PackBlock* g3s_packB = nullptr;
   PackOut* c2_pack = nullptr;
+  GemmTask* g12_tasks = nullptr;     // fused stages 1 + 2 of the tensor-core H_eff
+  TcUnit* g12_units = nullptr;
+  TcSeg* g12_tsegs = nullptr;
+  PackBlock* g12_packA = nullptr;
+  PackBlock* g12_packB = nullptr;
   CombChunk* c3r_chunks = nullptr;
   CombTask* c3r_tasks = nullptr;
   CombTerm* c3r_terms = nullptr;
@@ -188,6 +193,8 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 // parts, tile layout of kernels.hpp) into the workspace:
 //   [T1 pairs: ws1][packed T2 (stage-2 output)][g1 A packed][g1 B packed]
 //   [g3 A or B packed (the operand that is not T2)][stage-3 partial pairs: ws3]
+// (the fused H_eff has no T1 slot, and its stage-1 operands are g12's: the
+// coefficient-scaled L blocks and the site tensor)
 // (offsets in doubles, each slot 1 KB aligned; a packed operand of n floats
 // per part takes n doubles: hi then lo).  A caller that has already packed an
 // operand into its slot passes a hint and run_plan skips that pack (the
@@ -200,11 +207,13 @@ struct TcSlots {
 };
 inline int64_t slot_round(int64_t d) { return (d + 127) / 128 * 128; }   // 1 KB
 inline TcSlots tc_slots(const Plan& p) {
+  // the fused H_eff never forms T1; its stage-1 operands are g12's
+  const TcStage& s1 = p.fused ? p.g12.tc : p.g1.tc;
   TcSlots s;
-  s.t2p = slot_round(p.ws1);
+  s.t2p = p.fused ? 0 : slot_round(p.ws1);
   s.a1 = s.t2p + slot_round(p.nT2p);
-  s.b1 = s.a1 + slot_round(p.g1.tc.nA);
-  s.x3 = s.b1 + slot_round(p.g1.tc.nB);
+  s.b1 = s.a1 + slot_round(s1.nA);
+  s.x3 = s.b1 + slot_round(s1.nB);
   const int64_t n3 = p.kind == Kind::Heff ? p.g3s.tc.nB : p.g3s.tc.nA;
   s.p3 = s.x3 + slot_round(p.has_g3 ? n3 : 0);
   s.end = s.p3 + slot_round(p.ws3);

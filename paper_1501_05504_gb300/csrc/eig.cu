@@ -48,11 +48,11 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
   if (prec != DMRG3S_FP64) {
     const Plan& hp = heff.host;
     const TcSlots sl = tc_slots(hp);
-    const TcStage& t1 = hp.g1.tc;
+    const TcStage& t1 = hp.g12.tc;      // the fused H_eff: coefficient-scaled L blocks
     const TcStage& t3 = hp.g3s.tc;
     float* Lp = reinterpret_cast<float*>(ws1 + sl.a1);
     float* Rp = reinterpret_cast<float*>(ws1 + sl.x3);
-    launch_pack(heff.g1_packA, (int)t1.packA.size(), t1.tilesA, Ldata, Lp,
+    launch_pack(heff.g12_packA, (int)t1.packA.size(), t1.tilesA, Ldata, Lp,
                 prec == DMRG3S_TF32X3 ? Lp + t1.nA : nullptr, st);
     launch_pack(heff.g3s_packB, (int)t3.packB.size(), t3.tilesB, Rdata, Rp,
                 prec == DMRG3S_TF32X3 ? Rp + t3.nB : nullptr, st);

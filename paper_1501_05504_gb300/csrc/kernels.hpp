@@ -61,9 +61,10 @@ enum class Trans { N, T };
 // the same offsets of two arrays.
 constexpr int kPackTile = 256;             // floats per 8 x 32 tile
 struct PackBlock {
-  // element (r, k) of the packed matrix is src[off + r * ld + k] (trans = 0)
-  // or src[off + k * ld + r] (trans = 1)
+  // element (r, k) of the packed matrix is scale * src[off + r * ld + k]
+  // (trans = 0) or scale * src[off + k * ld + r] (trans = 1)
   int64_t src, dst;                        // dst: float offset of tile (0, 0)
+  double scale;
   int32_t ld, R, K, trans, R8, KC, tile0, pad;   // tile0: first tile in the launch numbering
 };
 // One K-segment of a tensor-core task: packed A (rows M) and B (rows N).
@@ -104,13 +105,20 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
 // out = scale * sum_k coef_k in_k for every task.
 // Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32) over
 // packed operands (hi, lo parts; lo unused when passes == 1), persistent CTAs
-// over the units.  C receives every output element as a double-float pair
-// (hi, lo) at the element offset of the FP64 layout (8 bytes, like the double
-// it stands for).  err is a device flag set to 1 when a wait gave up after
-// wait_ns nanoseconds.
-void launch_gemm_tc(int passes, const TcUnit* units, int nunits, const GemmTask* tasks,
-                    const TcSeg* segs, const float* Ahi, const float* Alo, const float* Bhi,
-                    const float* Blo, float2* C, int* err, uint64_t wait_ns, cudaStream_t st);
+// over the units.  Two output forms:
+//  - packed = false: every output element as a double-float pair (hi, lo) at
+//    (float2*)Chi + offC + m ldc + n (8 bytes per element, like the double it
+//    stands for); Clo unused;
+//  - packed = true: the output block packed as the A operand of a following
+//    tensor-core stage (R = M rows, K = N, tile layout above, hi at Chi, lo at
+//    Clo, lo only with passes == 3), with offC = its float offset and ldc =
+//    its R8; entries beyond N in the last k-chunk and rows M .. 8 R8 - 1 are
+//    written as zero.
+// err is a device flag set to 1 when a wait gave up after wait_ns nanoseconds.
+void launch_gemm_tc(int passes, bool packed, const TcUnit* units, int nunits,
+                    const GemmTask* tasks, const TcSeg* segs, const float* Ahi, const float* Alo,
+                    const float* Bhi, const float* Blo, float* Chi, float* Clo, int* err,
+                    uint64_t wait_ns, cudaStream_t st);
 
 // Packs FP64 blocks into tensor-core operands: hi = tf32(x), lo = tf32(x - hi)
 // (lo may be null), in the tile layout above.

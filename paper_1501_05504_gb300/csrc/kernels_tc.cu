@@ -194,13 +194,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-template <int kPasses, int kSpan>
+template <int kPasses, int kSpan, bool kPackedOut>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const TcUnit* __restrict__ units, int nunits, const GemmTask* __restrict__ tasks,
                    const TcSeg* __restrict__ segs, const float* __restrict__ Ahi,
                    const float* __restrict__ Alo, const float* __restrict__ Bhi,
-                   const float* __restrict__ Blo, float2* __restrict__ C, int* __restrict__ err,
-                   uint64_t wait_ns) {
+                   const float* __restrict__ Blo, float* __restrict__ Chi,
+                   float* __restrict__ Clo, int* __restrict__ err, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr bool kLo = kPasses == 3;
   constexpr uint32_t kTmemCols = kLo ? 512 : 256;   // main x2 (+ corr x2), 128 columns each
@@ -404,26 +404,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++uc;
       }
-      // renormalise (hi, lo) and store: 8 columns at a time through the
-      // warp's staging rows, written back as rows of 8 consecutive pairs
       const int row0 = un.tm * TBM + quarter * 32;
       const int n0 = un.tn * TBN + half * 64;
+      if (kPackedOut) {
+        // packed split operand of the next stage: the thread's row r and 4
+        // consecutive k form one 16-byte run of a core matrix; the 8 rows of
+        // a core matrix are neighbouring lanes, so a warp writes 128-byte runs
+        const int r = row0 + lane, R8 = t.ldc;
+        const int KC32 = (t.N + 31) / 32 * 32;
+        if (r < R8 * 8) {
 #pragma unroll
-      for (int c8 = 0; c8 < 64; c8 += 8) {
+          for (int q = 0; q < 16; ++q) {
+            const int k = n0 + 4 * q;
+            if (k >= KC32) break;
+            float hv[4], lv[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float s, e;
-          two_sum(ah[c8 + i], al[c8 + i], s, e);
-          stage_out[lane * kEpiRow + i] = make_float2(s, e);
+            for (int i = 0; i < 4; ++i) {
+              float sh = 0.f, sl = 0.f;
+              if (r < t.M && k + i < t.N) {
+                float s, e;
+                two_sum(ah[4 * q + i], al[4 * q + i], s, e);
+                sh = to_tf32(s);
+                // s - sh is exact (sh is s rounded to the 10-bit TF32 mantissa)
+                sl = to_tf32(__fadd_rn(__fsub_rn(s, sh), e));
+              }
+              hv[i] = sh;
+              lv[i] = sl;
+            }
+            const int64_t o = t.offC + ((int64_t)(k >> 5) * R8 + (r >> 3)) * kPackTile +
+                              ((k & 31) >> 2) * 32 + (r & 7) * 4;
+            *reinterpret_cast<float4*>(Chi + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            if (kLo) *reinterpret_cast<float4*>(Clo + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+          }
         }
-        __syncwarp();
+      } else {
+        // renormalise (hi, lo) and store: 8 columns at a time through the
+        // warp's staging rows, written back as rows of 8 consecutive pairs
+        float2* C = reinterpret_cast<float2*>(Chi);
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int r = it * 4 + (lane >> 3), cc = lane & 7;
-          const int gm = row0 + r, gn = n0 + c8 + cc;
-          if (gm < t.M && gn < t.N) C[t.offC + (int64_t)gm * t.ldc + gn] = stage_out[r * kEpiRow + cc];
+        for (int c8 = 0; c8 < 64; c8 += 8) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float s, e;
+            two_sum(ah[c8 + i], al[c8 + i], s, e);
+            stage_out[lane * kEpiRow + i] = make_float2(s, e);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int r = it * 4 + (lane >> 3), cc = lane & 7;
+            const int gm = row0 + r, gn = n0 + c8 + cc;
+            if (gm < t.M && gn < t.N)
+              C[t.offC + (int64_t)gm * t.ldc + gn] = stage_out[r * kEpiRow + cc];
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
   }
@@ -466,7 +501,8 @@ __global__ void __launch_bounds__(256)
     const int k = c * 32 + j * 4 + (lane & 3);
     float h = 0.f, l = 0.f;
     if (r < b.R && k < b.K) {
-      const double x = b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k];
+      const double x =
+          b.scale * (b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k]);
       h = to_tf32((float)x);
       l = to_tf32((float)(x - (double)h));
     }
@@ -534,17 +570,17 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int P>
+template <int P, bool kPacked>
 void launch_one(const TcUnit* units, int nunits, const GemmTask* tasks, const TcSeg* segs,
-                const float* Ah, const float* Al, const float* Bh, const float* Bl, float2* C,
-                int* err, uint64_t wait_ns, cudaStream_t st) {
+                const float* Ah, const float* Al, const float* Bh, const float* Bl, float* Chi,
+                float* Clo, int* err, uint64_t wait_ns, cudaStream_t st) {
   // the shared-memory limit is a per-device attribute of the kernel
   static std::atomic<uint64_t> done{0};
   int dev = 0;
   cudaGetDevice(&dev);
   const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
   if (!bit || !(done.load() & bit)) {
-    cudaFuncSetAttribute(gemm_tc_kernel<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(gemm_tc_kernel<P, 2, kPacked>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSmemBytes);
     if (bit) done.fetch_or(bit);
   }
@@ -552,8 +588,9 @@ void launch_one(const TcUnit* units, int nunits, const GemmTask* tasks, const Tc
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm <= 0) nsm = 152;
   const int grid = nunits < nsm ? nunits : nsm;
-  gemm_tc_kernel<P, 2><<<grid, kThreads, kSmemBytes, st>>>(units, nunits, tasks, segs, Ah, Al, Bh,
-                                                           Bl, C, err, wait_ns);
+  gemm_tc_kernel<P, 2, kPacked><<<grid, kThreads, kSmemBytes, st>>>(units, nunits, tasks, segs, Ah,
+                                                                    Al, Bh, Bl, Chi, Clo, err,
+                                                                    wait_ns);
 }
 
 }  // namespace
@@ -575,15 +612,25 @@ void launch_combine_pairs_pack(const PackOut* outs, int ntasks, int ntiles, cons
                                                               in, out_hi, out_lo, sh, sl);
 }
 
-void launch_gemm_tc(int passes, const TcUnit* units, int nunits, const GemmTask* tasks,
-                    const TcSeg* segs, const float* Ahi, const float* Alo, const float* Bhi,
-                    const float* Blo, float2* C, int* err, uint64_t wait_ns, cudaStream_t st) {
+void launch_gemm_tc(int passes, bool packed, const TcUnit* units, int nunits,
+                    const GemmTask* tasks, const TcSeg* segs, const float* Ahi, const float* Alo,
+                    const float* Bhi, const float* Blo, float* Chi, float* Clo, int* err,
+                    uint64_t wait_ns, cudaStream_t st) {
   if (nunits <= 0) return;
   count_launch();
-  if (passes == 3)
-    launch_one<3>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, C, err, wait_ns, st);
-  else
-    launch_one<1>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, C, err, wait_ns, st);
+  if (passes == 3) {
+    if (packed)
+      launch_one<3, true>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err, wait_ns, st);
+    else
+      launch_one<3, false>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr, err, wait_ns,
+                           st);
+  } else {
+    if (packed)
+      launch_one<1, true>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err, wait_ns, st);
+    else
+      launch_one<1, false>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr, err, wait_ns,
+                           st);
+  }
 }
 
 }  // namespace dmrg3s

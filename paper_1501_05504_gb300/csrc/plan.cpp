@@ -183,16 +183,17 @@ inline int32_t chunks32(int64_t K) { return (int32_t)((K + 31) / 32); }
 
 // Packed placements of one operand array; identical views share one block.
 struct Packer {
-  std::map<std::array<int64_t, 5>, int64_t> seen;    // (src, ld, R, K, trans) -> dst
+  std::map<std::pair<std::array<int64_t, 5>, double>, int64_t> seen;   // (view, scale) -> dst
   std::vector<PackBlock>* out;
   int64_t* n;
   int32_t* tiles;
-  int64_t add(int64_t src, int64_t ld, int64_t R, int64_t K, int trans) {
-    const std::array<int64_t, 5> key{src, ld, R, K, trans};
+  int64_t add(int64_t src, int64_t ld, int64_t R, int64_t K, int trans, double scale = 1.0) {
+    const auto key = std::make_pair(std::array<int64_t, 5>{src, ld, R, K, trans}, scale);
     auto it = seen.find(key);
     if (it != seen.end()) return it->second;
     PackBlock b{};
     b.src = src;
+    b.scale = scale;
     b.dst = *n;
     b.ld = (int32_t)ld;
     b.R = (int32_t)R;
@@ -290,6 +291,73 @@ std::map<int64_t, CombPacked> pack_c2(Plan* p, int trans) {
   return m;
 }
 
+// Units per GPU the split-K grouping of stage 3 aims at (two per SM of a GB300).
+constexpr int64_t kTargetUnits = 2 * 152;
+
+// The fused stages 1 + 2 of H_eff: one task per stage-2 block T2 (packed
+// output at its c2pack placement), one K-segment per MPO term of that block:
+// A = coef * L[bl] (the stage-1 A operand of the term's T1 block), B = M[s].
+bool build_fused(Plan* p, const std::map<int64_t, CombPacked>& c2p, std::string* err) {
+  std::map<int64_t, int> t1_task;      // T1 element offset -> stage-1 task
+  for (size_t i = 0; i < p->g1.tasks.size(); ++i) t1_task[p->g1.tasks[i].offC] = (int)i;
+  GemmStage& g = p->g12;
+  g = GemmStage();
+  g.ta = p->g1.ta;
+  g.tb = p->g1.tb;
+  TcStage& tc = g.tc;
+  Packer pa{{}, &tc.packA, &tc.nA, &tc.tilesA};
+  Packer pb{{}, &tc.packB, &tc.nB, &tc.tilesB};
+  for (const CombTask& ct : p->c2.tasks) {
+    auto it = c2p.find(ct.offOut);
+    if (it == c2p.end()) {
+      *err = "fused stage: stage-2 block without a packed placement";
+      return false;
+    }
+    GemmTask t{};
+    t.offC = it->second.dst;
+    t.ldc = it->second.R8;
+    t.M = ct.rows;
+    t.N = ct.cols;
+    t.seg0 = (int32_t)g.segs.size();
+    t.nseg = ct.nt;
+    int32_t nch = 0;
+    for (int k = 0; k < ct.nt; ++k) {
+      const CombTerm& tm = p->c2.terms[ct.t0 + k];
+      auto jt = t1_task.find(tm.offIn);
+      if (jt == t1_task.end()) {
+        *err = "fused stage: MPO term without a stage-1 block";
+        return false;
+      }
+      const GemmTask& t1 = p->g1.tasks[jt->second];
+      if (t1.nseg != 1 || t1.M != ct.rows || t1.N != ct.cols) {
+        *err = "fused stage: stage-1 block shape";
+        return false;
+      }
+      const GemmSeg& s1 = p->g1.segs[t1.seg0];
+      g.segs.push_back(s1);
+      TcSeg ts{};
+      ts.kc = chunks32(s1.K);
+      ts.pa = pa.add(s1.offA, s1.lda, t.M, s1.K, g.ta == Trans::T ? 1 : 0, tm.coef);
+      ts.ra8 = groups8(t.M);
+      ts.pb = pb.add(s1.offB, s1.ldb, t.N, s1.K, g.tb == Trans::N ? 1 : 0);
+      ts.rb8 = groups8(t.N);
+      tc.segs.push_back(ts);
+      nch += ts.kc;
+    }
+    const int id = (int)g.tasks.size();
+    g.tasks.push_back(t);
+    for (int a = 0; a < (t.M + 127) / 128; ++a)
+      for (int b = 0; b < (t.N + 127) / 128; ++b) tc.units.push_back(TcUnit{id, a, b, nch});
+  }
+  std::stable_sort(tc.units.begin(), tc.units.end(),
+                   [](const TcUnit& x, const TcUnit& y) { return x.nchunks > y.nchunks; });
+  // algorithmic work: that of stages 1 and 2, which this stage replaces
+  g.flops = p->g1.flops + p->c2.flops;
+  g.bytes = p->g1.bytes + p->c2.bytes;
+  p->fused = true;
+  return true;
+}
+
 // Bounds of every table against the buffers the stages address.
 dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
                      int64_t nC3, std::string* err) {
@@ -300,14 +368,28 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
   p->g1.finalize_bytes(p->g1.ta, p->g1.tb);
   if (p->has_g3) p->g3.finalize_bytes(p->g3.ta, p->g3.tb);
   if (p->has_g3) {
-    // split-K form of stage 3: every (task, segment) becomes its own task
+    // split-K form of stage 3: the K-segments of every output block in G
+    // consecutive groups, G chosen so that the units fill the GPU about twice
+    // (kTargetUnits); each group writes a partial block, then a fixed-order sum
+    int64_t units1 = 0;
+    int maxseg = 1;
+    for (const GemmTask& t : p->g3.tasks) {
+      units1 += (int64_t)((t.M + 127) / 128) * ((t.N + 127) / 128);
+      maxseg = std::max(maxseg, (int)t.nseg);
+    }
+    int G = units1 > 0 ? (int)((kTargetUnits + units1 - 1) / units1) : 1;
+    G = std::max(1, std::min(G, maxseg));
     p->g3s.ta = p->g3.ta;
     p->g3s.tb = p->g3.tb;
     int64_t poff = 0;
     for (const GemmTask& t : p->g3.tasks) {
       std::vector<CombTerm> terms;
-      for (int k = 0; k < t.nseg; ++k) {
-        p->g3s.add(poff, t.N, t.M, t.N, {p->g3.segs[t.seg0 + k]});
+      const int ng = std::min<int>(G, std::max(1, (int)t.nseg));
+      for (int gi = 0; gi < ng; ++gi) {
+        const int k0 = (int)((int64_t)t.nseg * gi / ng), k1 = (int)((int64_t)t.nseg * (gi + 1) / ng);
+        std::vector<GemmSeg> sg(p->g3.segs.begin() + t.seg0 + k0, p->g3.segs.begin() + t.seg0 + k1);
+        if (sg.empty() && t.nseg > 0) continue;
+        p->g3s.add(poff, t.N, t.M, t.N, sg);
         CombTerm tm{};
         tm.offIn = poff;
         tm.ldi = t.N;
@@ -336,16 +418,24 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
     *err = "internal planning error: " + *err;
     return DMRG3S_ERR_SHAPE;
   }
-  // tensor-core form: stage 1 packs both operands; stage 3 takes the stage-2
-  // output packed by the combination (A of H_eff, B of the environments)
-  bool ok = build_tc(p->g1, nullptr, nullptr, err);
-  if (ok && p->has_g3) {
-    const bool c2_is_a = p->kind == Kind::Heff;
-    const int trans = p->kind == Kind::EnvLR ? 1 : 0;
-    const std::map<int64_t, CombPacked> m = pack_c2(p, trans);
-    ok = build_tc(p->g3s, c2_is_a ? &m : nullptr, c2_is_a ? nullptr : &m, err);
+  // tensor-core form.  H_eff: stages 1 and 2 fused (g12) writing T2 packed
+  // for stage 3.  The others: stage 1 packs both operands, and stage 3 takes
+  // the stage-2 output packed by the combination (B of the environments).
+  bool ok = true;
+  if (p->kind == Kind::Heff) {
+    const std::map<int64_t, CombPacked> m = pack_c2(p, 0);
+    ok = build_fused(p, m, err) && build_tc(p->g3s, &m, nullptr, err) &&
+         tc_ok(p->g12.tasks, p->g12.tc, nA1, nB1, p->g12.tc.nA, p->g12.tc.nB, err) &&
+         packed_tasks_ok(p->g12.tasks, p->nT2p, err);
+  } else {
+    ok = build_tc(p->g1, nullptr, nullptr, err);
+    if (ok && p->has_g3) {
+      const int trans = p->kind == Kind::EnvLR ? 1 : 0;
+      const std::map<int64_t, CombPacked> m = pack_c2(p, trans);
+      ok = build_tc(p->g3s, nullptr, &m, err);
+    }
+    if (ok) ok = tc_ok(p->g1.tasks, p->g1.tc, nA1, nB1, p->g1.tc.nA, p->g1.tc.nB, err);
   }
-  if (ok) ok = tc_ok(p->g1.tasks, p->g1.tc, nA1, nB1, p->g1.tc.nA, p->g1.tc.nB, err);
   if (ok && p->has_g3) {
     const bool c2_is_a = p->kind == Kind::Heff;
     ok = tc_ok(p->g3s.tasks, p->g3s.tc, nA3, nB3, c2_is_a ? p->nT2p : p->g3s.tc.nA,

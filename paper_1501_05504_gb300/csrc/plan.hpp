@@ -88,6 +88,13 @@ struct Plan {
   std::vector<PackOut> c2pack;
   int64_t nT2p = 0;             // floats of one part of the packed stage-2 output
   int32_t tilesT2 = 0;
+  // Tensor-core H_eff (fused = true): stages 1 and 2 in one grouped GEMM g12
+  // whose tasks are the T2 blocks and whose K-segments are the MPO terms,
+  //   T2[br, s'] = sum_{(bl, s): W != 0} (W[s', s, bl, br] L[bl]) . M[s],
+  // written packed (the c2pack placements) as the A operand of stage 3; T1 is
+  // never formed.  g12's A operand is the coefficient-scaled L blocks.
+  GemmStage g12;
+  bool fused = false;
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
 

@@ -118,6 +118,19 @@ inline bool tc_ok(const std::vector<GemmTask>& tasks, const TcStage& tc, int64_t
   return true;
 }
 
+// Tasks whose output is a packed operand (offC = float offset, ldc = R8).
+inline bool packed_tasks_ok(const std::vector<GemmTask>& tasks, int64_t nPacked, std::string* err) {
+  for (const GemmTask& t : tasks) {
+    if (t.M <= 0 || t.N <= 0) continue;
+    const int64_t kc = (t.N + 31) / 32;
+    if ((int64_t)t.ldc * 8 < t.M || t.offC < 0 || t.offC + kc * t.ldc * kPackTile > nPacked) {
+      *err = "packed GEMM output out of bounds";
+      return false;
+    }
+  }
+  return true;
+}
+
 inline bool packout_ok(const std::vector<CombTask>& tasks, const std::vector<PackOut>& outs,
                        int64_t nPacked, std::string* err) {
   if (outs.size() != tasks.size()) {

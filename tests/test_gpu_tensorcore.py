@@ -135,5 +135,5 @@ def test_profiler_flops_match_the_benchmark_count(b, ctx):
     b.dmrg3s_profile(ctx, False)
     want = bench.heff_flops(si.XXZ_QP, si.XXZ_T, W.W, b0, b1)
     assert abs(g["flops"] + c["flops"] - want) <= 1e-9 * want
-    # stage 1, stage 3 (split-K partial products); stage 2 and the partial sum
-    assert g["launches"] == 2 and c["launches"] == 2
+    # stages 1 + 2 fused, stage 3 (split-K partial products); the partial sum
+    assert g["launches"] == 2 and c["launches"] == 1
