@@ -69,7 +69,9 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
                  bytes_of(h.g1.tc.packA) + bytes_of(h.g1.tc.packB) + bytes_of(h.g3s.tc.units) +
                  bytes_of(h.g3s.tc.segs) + bytes_of(h.g3s.tc.packA) + bytes_of(h.g3s.tc.packB) +
                  bytes_of(h.c2pack) + bytes_of(h.g12.tasks) + bytes_of(h.g12.tc.units) +
-                 bytes_of(h.g12.tc.segs) + bytes_of(h.g12.tc.packA) + bytes_of(h.g12.tc.packB);
+                 bytes_of(h.g12.tc.segs) + bytes_of(h.g12.tc.packA) + bytes_of(h.g12.tc.packB) +
+                 bytes_of(h.g1.tc.cta_start) + bytes_of(h.g3s.tc.cta_start) +
+                 bytes_of(h.g12.tc.cta_start);
   if (total == 0) total = 256;
   if (cudaMalloc(&dp->mem, total) != cudaSuccess) return DMRG3S_ERR_CUDA;
   std::vector<char> staging(total, 0);
@@ -99,6 +101,9 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out) {
   dp->g12_tsegs = place(base, &off, h.g12.tc.segs, &staging);
   dp->g12_packA = place(base, &off, h.g12.tc.packA, &staging);
   dp->g12_packB = place(base, &off, h.g12.tc.packB, &staging);
+  dp->g1_cta = place(base, &off, h.g1.tc.cta_start, &staging);
+  dp->g3s_cta = place(base, &off, h.g3s.tc.cta_start, &staging);
+  dp->g12_cta = place(base, &off, h.g12.tc.cta_start, &staging);
   dp->c3r_chunks = place(base, &off, h.c3r.chunks, &staging);
   dp->c3r_tasks = place(base, &off, h.c3r.tasks, &staging);
   dp->c3r_terms = place(base, &off, h.c3r.terms, &staging);
@@ -158,7 +163,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
                              lo(sl.b1, t12.nB), st);
     if (!t12.units.empty()) {
       const int id = pr.on ? pr.begin(kProfGemm, h.g12.flops, h.g12.bytes, st) : -1;
-      launch_gemm_tc(passes, true, p.g12_units, (int)t12.units.size(), p.g12_tasks, p.g12_tsegs,
+      launch_gemm_tc(passes, true, p.g12_units, p.g12_cta, (int)t12.cta_start.size() - 1,
+                     p.g12_tasks, p.g12_tsegs,
                      hi(sl.a1), lo(sl.a1, t12.nA), hi(sl.b1), lo(sl.b1, t12.nB), hi(sl.t2p),
                      lo(sl.t2p, h.nT2p), c->d_err, c->wait_ns, st);
       if (id >= 0) pr.end(id, st);
@@ -171,7 +177,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
                              lo(sl.b1, t1.nB), st);
     if (!t1.units.empty()) {
       const int id = pr.on ? pr.begin(kProfGemm, h.g1.flops, h.g1.bytes, st) : -1;
-      launch_gemm_tc(passes, false, p.g1_units, (int)t1.units.size(), p.g1_tasks, p.g1_tsegs,
+      launch_gemm_tc(passes, false, p.g1_units, p.g1_cta, (int)t1.cta_start.size() - 1,
+                     p.g1_tasks, p.g1_tsegs,
                      hi(sl.a1), lo(sl.a1, t1.nA), hi(sl.b1), lo(sl.b1, t1.nB),
                      reinterpret_cast<float*>(t1p), nullptr, c->d_err, c->wait_ns, st);
       if (id >= 0) pr.end(id, st);
@@ -218,7 +225,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
   float2* part = reinterpret_cast<float2*>(base + sl.p3);
   if (!t3.units.empty()) {
     const int id = pr.on ? pr.begin(kProfGemm, h.g3s.flops, h.g3s.bytes, st) : -1;
-    launch_gemm_tc(passes, false, p.g3s_units, (int)t3.units.size(), p.g3s_tasks, p.g3s_tsegs,
+    launch_gemm_tc(passes, false, p.g3s_units, p.g3s_cta, (int)t3.cta_start.size() - 1,
+                   p.g3s_tasks, p.g3s_tsegs,
                    a3h, a3l, b3h, b3l, reinterpret_cast<float*>(part), nullptr, c->d_err,
                    c->wait_ns, st);
     if (id >= 0) pr.end(id, st);
@@ -336,6 +344,9 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
     return DMRG3S_ERR_CUDA;
   }
   c->ws_bytes = workspace_bytes ? workspace_bytes : (size_t)256 << 20;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) == cudaSuccess)
+    set_plan_ctas(nsm);
   if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
     delete c;
     return DMRG3S_ERR_CUDA;

@@ -28,16 +28,19 @@ struct DevicePlan {
   // tensor-core tables: units, segments and operand packs of stages 1 and 3,
   // and the packed outputs of stage 2
   TcUnit* g1_units = nullptr;
+  int32_t* g1_cta = nullptr;
   TcSeg* g1_tsegs = nullptr;
   PackBlock* g1_packA = nullptr;
   PackBlock* g1_packB = nullptr;
   TcUnit* g3s_units = nullptr;
+  int32_t* g3s_cta = nullptr;
   TcSeg* g3s_tsegs = nullptr;
   PackBlock* g3s_packA = nullptr;
   PackBlock* g3s_packB = nullptr;
   PackOut* c2_pack = nullptr;
   GemmTask* g12_tasks = nullptr;     // fused stages 1 + 2 of the tensor-core H_eff
   TcUnit* g12_units = nullptr;
+  int32_t* g12_cta = nullptr;
   TcSeg* g12_tsegs = nullptr;
   PackBlock* g12_packA = nullptr;
   PackBlock* g12_packB = nullptr;

@@ -53,12 +53,16 @@ enum class Trans { N, T };
 // ---- tensor-core operands: packed tiles ----
 // A packed matrix (R x K) is stored in tiles of 8 rows x 32 k, tile (g, c) at
 // float offset (c * R8 + g) * 256 (R8 = ceil(R / 8) row groups, KC =
-// ceil(K / 32) k-chunks), each tile in the K-major core-matrix order of the
-// tcgen05 shared-memory descriptors: element (r, k) at ((k % 32) / 4) * 32 +
-// (r % 8) * 4 + k % 4.  Entries beyond R or K are zero.  A 128-row slab of one
-// k-chunk is therefore contiguous (16 KB) and moves into shared memory with
-// one bulk copy.  Every operand has a hi and a lo part (the 3xTF32 split) at
-// the same offsets of two arrays.
+// ceil(K / 32) k-chunks).  A tile is one 1 KB atom of the K-major 128-byte
+// swizzled layout of the tcgen05 shared-memory descriptors: row r % 8 is a
+// 128-byte line (32 k), and its 16-byte chunk j = (k % 32) / 4 sits at chunk
+// position j ^ (r % 8), i.e. element (r, k) at float offset (r % 8) * 32 +
+// (((k % 32) / 4) ^ (r % 8)) * 4 + k % 4 (the swizzle spreads the eight rows
+// the tensor core reads together over all shared-memory banks).  Entries
+// beyond R or K are zero.  A 128-row slab of one k-chunk is therefore
+// contiguous (16 KB) and moves into shared memory with one bulk copy.  Every
+// operand has a hi and a lo part (the 3xTF32 split) at the same offsets of
+// two arrays.
 constexpr int kPackTile = 256;             // floats per 8 x 32 tile
 struct PackBlock {
   // element (r, k) of the packed matrix is scale * src[off + r * ld + k]
@@ -105,7 +109,7 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
 // out = scale * sum_k coef_k in_k for every task.
 // Tensor-core grouped GEMM (tcgen05): passes = 1 (TF32) or 3 (3xTF32) over
 // packed operands (hi, lo parts; lo unused when passes == 1), persistent CTAs
-// over the units.  Two output forms:
+// over the units (a static schedule: one unit list per CTA).  Two output forms:
 //  - packed = false: every output element as a double-float pair (hi, lo) at
 //    (float2*)Chi + offC + m ldc + n (8 bytes per element, like the double it
 //    stands for); Clo unused;
@@ -115,10 +119,11 @@ void launch_gemm_f64(Trans ta, Trans tb, const GemmTile* tiles, int ntiles, cons
 //    its R8; entries beyond N in the last k-chunk and rows M .. 8 R8 - 1 are
 //    written as zero.
 // err is a device flag set to 1 when a wait gave up after wait_ns nanoseconds.
-void launch_gemm_tc(int passes, bool packed, const TcUnit* units, int nunits,
-                    const GemmTask* tasks, const TcSeg* segs, const float* Ahi, const float* Alo,
-                    const float* Bhi, const float* Blo, float* Chi, float* Clo, int* err,
-                    uint64_t wait_ns, cudaStream_t st);
+// One CTA per unit list: CTA b runs units [cta_start[b], cta_start[b + 1]).
+void launch_gemm_tc(int passes, bool packed, const TcUnit* units, const int32_t* cta_start,
+                    int ncta, const GemmTask* tasks, const TcSeg* segs, const float* Ahi,
+                    const float* Alo, const float* Bhi, const float* Blo, float* Chi, float* Clo,
+                    int* err, uint64_t wait_ns, cudaStream_t st);
 
 // Packs FP64 blocks into tensor-core operands: hi = tf32(x), lo = tf32(x - hi)
 // (lo may be null), in the tile layout above.

@@ -14,11 +14,15 @@
 //   kPasses = 3: D_main += A_hi B_hi,  D_corr += A_hi B_lo + A_lo B_hi  (3xTF32)
 // The small correction terms keep their own TMEM accumulator over the whole
 // K range (their FP32 rounding is ~2^-11 below the result).  The main
-// accumulator is drained every kSpan k-chunks (64 k for kSpan = 2) into
-// double-float registers with Knuth's two-sum, so FP32 rounding only ever
-// sees a short span of main products; a second main buffer takes the next
-// span meanwhile.  No FP64 instruction runs in the kernel (GB300's FP64 rate
-// is ~1/1000 of its TF32 rate).
+// accumulator is drained every kSpan k-chunks (128 k for kSpan = 4: 16
+// accumulations of hi * hi products) into double-float registers with
+// Knuth's two-sum, so FP32 rounding only ever sees a short span of main
+// products.  The 512 TMEM columns hold two main and two correction buffers
+// (four main buffers for TF32), so the tensor core can start the next tile
+// while the drain warps still finish and store the previous one.  The last N
+// tile of a block issues the narrowest MMA width (a multiple of 16) that
+// covers it.  No FP64 instruction runs in the kernel (GB300's FP64 rate is
+// ~1/1000 of its TF32 rate).
 //
 // Warp roles of the persistent CTA (one per SM, 384 threads = 3 warpgroups):
 //   warp 0     one lane issues the bulk copies into a 3-stage shared-memory ring
@@ -33,7 +37,7 @@
 // The CTA starts with 168 registers per thread (384 x 168 = 64,512 of the
 // SM's 65,536); warpgroup 0 gives up to 56 (setmaxnreg.dec) and the two drain
 // warpgroups take 224 (setmaxnreg.inc): 128 x 56 + 256 x 224 = 64,512.
-// Units (output tiles) are assigned round robin over the CTAs, longest first.
+// Units (output tiles) come in one list per CTA, balanced by the planner.
 //
 // Every wait on an mbarrier is bounded by the elapsed %globaltimer time given
 // by the host.  A wait that runs out sets the device error word and a shared
@@ -58,9 +62,10 @@ constexpr int kDrainWarps = 8;
 constexpr int kSlab = TBM * TBK * 4;                // bytes of one 128 x 32 slab (16 KB)
 constexpr int kStageBytes = 4 * kSlab;              // A hi, A lo, B hi, B lo
 constexpr int kEpiRow = 9;                          // float2 per staged row (8 + 1 pad)
-constexpr int kEpiWarp = 32 * kEpiRow * 8;          // bytes of one drain warp's staging
+constexpr int kEpiWarp = 4096;                      // bytes of one drain warp's staging (4 atoms)
 constexpr int kSmemBytes = kStages * kStageBytes + kDrainWarps * kEpiWarp;
 constexpr uint64_t kDrainLimitNs = 1000000000ull;   // waits for work already in flight
+constexpr int kSpanChunks = 4;                      // k-chunks per drain of the main accumulator
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,13 +77,16 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-// Shared-memory matrix descriptor (tcgen05): start address, leading byte
-// offset 128 (K-adjacent core matrices), stride byte offset 1024 (8-row
-// groups), all >> 4; descriptor version 1; no swizzle.
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand in the
+// 128-byte swizzled layout: start address >> 4, leading byte offset 16 (not
+// used by swizzled K-major layouts), stride byte offset 1024 (8-row atoms),
+// descriptor version 1, swizzle mode 2 (128 bytes) in bits 61-63.  The atoms
+// must start on 1 KB boundaries; a K step inside the 128-byte line advances
+// the start address (the hardware applies the swizzle to the full address).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  const uint64_t lbo = 128, sbo = 1024;
+  const uint64_t lbo = 16, sbo = 1024;
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
 }
 
 // Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
@@ -160,6 +168,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Bulk copy shared -> global (bulk-group completion), and its waits.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                          uint32_t acc) {
   asm volatile(
@@ -196,17 +218,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 template <int kPasses, int kSpan, bool kPackedOut>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(const TcUnit* __restrict__ units, int nunits, const GemmTask* __restrict__ tasks,
+    gemm_tc_kernel(const TcUnit* __restrict__ units, const int32_t* __restrict__ cta_start,
+                   const GemmTask* __restrict__ tasks,
                    const TcSeg* __restrict__ segs, const float* __restrict__ Ahi,
                    const float* __restrict__ Alo, const float* __restrict__ Bhi,
                    const float* __restrict__ Blo, float* __restrict__ Chi,
                    float* __restrict__ Clo, int* __restrict__ err, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr bool kLo = kPasses == 3;
-  constexpr uint32_t kTmemCols = kLo ? 512 : 256;   // main x2 (+ corr x2), 128 columns each
-  constexpr uint32_t idesc = idesc_tf32(TBM, TBN);
+  constexpr uint32_t kTmemCols = 512;
+  constexpr int kMain = kLo ? 2 : 4;                 // main buffers of 128 columns
+  constexpr uint32_t kCorrCol = kMain * TBN;         // two correction buffers (3xTF32)
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  __shared__ __align__(8) uint64_t mfull[2], mempty[2], cfull[2], cempty[2], done;
+  __shared__ __align__(8) uint64_t mfull[kMain], mempty[kMain], cfull[2], cempty[2], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -216,9 +240,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kMain; ++b) {
       mbar_init(&mfull[b], 1);
       mbar_init(&mempty[b], kDrainWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&cfull[b], 1);
       mbar_init(&cempty[b], kDrainWarps);
     }
@@ -238,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const WaitCtl wc{&abort_flag, err, wait_ns};
+  const int u_begin = cta_start[blockIdx.x], u_end = cta_start[blockIdx.x + 1];
   if (warp < kFirstDrainWarp) asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
 
   if (warp == 0) {
@@ -248,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kStages; ++s) pend[s] = -1;
       uint32_t q = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      for (int u = u_begin; u < u_end && ok; ++u) {
         const TcUnit un = units[u];
         const GemmTask t = tasks[un.task];
         for (int k = 0; k < t.nseg && ok; ++k) {
@@ -285,18 +312,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t q = 0, p = 0, uc = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-        const int T = units[u].nchunks;
+      for (int u = u_begin; u < u_end && ok; ++u) {
+        const TcUnit un = units[u];
+        const int T = un.nchunks;
         if (T == 0) continue;
+        // MMA width: the columns of this tile, rounded up to a multiple of 16
+        const int nrem = min(TBN, tasks[un.task].N - un.tn * TBN);
+        const uint32_t idesc = idesc_tf32(TBM, (nrem + 15) & ~15);
         const uint32_t cb = uc & 1;
-        const uint32_t dcorr = tmem + 256u + cb * TBN;
+        const uint32_t dcorr = tmem + kCorrCol + cb * TBN;
         if (kLo && uc >= 2 && !mbar_wait(&cempty[cb], ((uc >> 1) - 1) & 1, wc)) break;
         uint32_t dmain = 0;
         for (int t = 0; t < T; ++t, ++q) {
           const bool span0 = t % kSpan == 0;
           if (span0) {
-            const uint32_t mb = p & 1;
-            if (p >= 2 && !mbar_wait(&mempty[mb], ((p >> 1) - 1) & 1, wc)) {
+            const uint32_t mb = p % kMain;
+            if (p >= (uint32_t)kMain && !mbar_wait(&mempty[mb], ((p / kMain) - 1) & 1, wc)) {
               ok = false;
               break;
             }
@@ -313,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sbh = sah + 2 * kSlab, sbl = sah + 3 * kSlab;
 #pragma unroll
           for (int kk = 0; kk < TBK / 8; ++kk) {     // K = 8 per instruction (32 bytes)
-            const uint32_t off = kk * 256;           // two core matrices along K
+            const uint32_t off = kk * 32;            // 8 k = 32 bytes of the 128-byte line
             mma_tf32(dmain, smem_desc(sah + off), smem_desc(sbh + off), idesc,
                      (span0 && kk == 0) ? 0u : 1u);
             if (kLo) {
@@ -324,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mma_commit(&empty[st]);                    // the stage is free once these are done
           if (t % kSpan == kSpan - 1 || t == T - 1) {
-            mma_commit(&mfull[p & 1]);               // a span of main products is ready
+            mma_commit(&mfull[p % kMain]);           // a span of main products is ready
             ++p;
           }
         }
@@ -347,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         reinterpret_cast<float2*>(smem + kStages * kStageBytes + (warp - kFirstDrainWarp) * kEpiWarp);
     uint32_t p = 0, uc = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+    for (int u = u_begin; u < u_end && ok; ++u) {
       const TcUnit un = units[u];
       const GemmTask t = tasks[un.task];
       float ah[64], al[64];
@@ -356,18 +387,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         ah[j] = 0.f;
         al[j] = 0.f;
       }
+      // columns the MMA writes (its width; the rest of the buffer is stale)
+      const int nmma = (min(TBN, t.N - un.tn * TBN) + 15) & ~15;
       if (un.nchunks > 0) {
         const int nsp = (un.nchunks + kSpan - 1) / kSpan;
         for (int j = 0; j < nsp; ++j, ++p) {
-          const uint32_t mb = p & 1;
+          const uint32_t mb = p % kMain;
           // one decision per warp: tcgen05.ld is a warp-wide instruction
-          if (!__all_sync(0xffffffffu, mbar_wait(&mfull[mb], (p >> 1) & 1, wc))) {
+          if (!__all_sync(0xffffffffu, mbar_wait(&mfull[mb], (p / kMain) & 1, wc))) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
+            if ((int)col0 + h * 16 >= nmma) break;
             uint32_t v[16];
             tmem_ld16(tmem + lane_off + mb * TBN + col0 + h * 16, v);
 #pragma unroll
@@ -392,8 +426,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
+            if ((int)col0 + h * 16 >= nmma) break;
             uint32_t v[16];
-            tmem_ld16(tmem + lane_off + 256u + cb * TBN + col0 + h * 16, v);
+            tmem_ld16(tmem + lane_off + kCorrCol + cb * TBN + col0 + h * 16, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i)
               al[h * 16 + i] = __fadd_rn(al[h * 16 + i], __uint_as_float(v[i]));
@@ -407,34 +442,45 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row0 = un.tm * TBM + quarter * 32;
       const int n0 = un.tn * TBN + half * 64;
       if (kPackedOut) {
-        // packed split operand of the next stage: the thread's row r and 4
-        // consecutive k form one 16-byte run of a core matrix; the 8 rows of
-        // a core matrix are neighbouring lanes, so a warp writes 128-byte runs
-        const int r = row0 + lane, R8 = t.ldc;
-        const int KC32 = (t.N + 31) / 32 * 32;
-        if (r < R8 * 8) {
+        // packed split operand of the next stage: the warp's 32 rows are 4
+        // whole 8-row atoms of each 32-wide k-chunk, contiguous in global
+        // memory; they are staged in shared memory in the swizzled order
+        // (lane = row) and written with one bulk copy per chunk and part
+        const int R8 = t.ldc, KC32 = (t.N + 31) / 32 * 32;
+        const int g0 = row0 >> 3, ng = min(4, R8 - g0);
+        const int r = row0 + lane, rr = lane & 7;
+        unsigned char* stg = reinterpret_cast<unsigned char*>(stage_out);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int k = n0 + 4 * q;
-            if (k >= KC32) break;
-            float hv[4], lv[4];
+        for (int h = 0; h < 2; ++h) {
+          const int k0 = n0 + 32 * h;
+          if (k0 >= KC32 || ng <= 0) break;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              float sh = 0.f, sl = 0.f;
-              if (r < t.M && k + i < t.N) {
-                float s, e;
-                two_sum(ah[4 * q + i], al[4 * q + i], s, e);
-                sh = to_tf32(s);
-                // s - sh is exact (sh is s rounded to the 10-bit TF32 mantissa)
-                sl = to_tf32(__fadd_rn(__fsub_rn(s, sh), e));
+          for (int part = 0; part < (kLo ? 2 : 1); ++part) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float v[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int kk = 32 * h + 4 * j + i;
+                float x = 0.f;
+                if (r < t.M && k0 + 4 * j + i < t.N) {
+                  const float a = ah[kk], hv = to_tf32(a);
+                  // a - hv is exact (hv is a rounded to the 10-bit TF32 mantissa)
+                  x = part == 0 ? hv : to_tf32(__fadd_rn(__fsub_rn(a, hv), al[kk]));
+                }
+                v[i] = x;
               }
-              hv[i] = sh;
-              lv[i] = sl;
+              *reinterpret_cast<float4*>(stg + (lane >> 3) * 1024 + rr * 128 + ((j ^ rr) << 4)) =
+                  make_float4(v[0], v[1], v[2], v[3]);
             }
-            const int64_t o = t.offC + ((int64_t)(k >> 5) * R8 + (r >> 3)) * kPackTile +
-                              ((k & 31) >> 2) * 32 + (r & 7) * 4;
-            *reinterpret_cast<float4*>(Chi + o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-            if (kLo) *reinterpret_cast<float4*>(Clo + o) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              float* dst = (part == 0 ? Chi : Clo) + t.offC + ((int64_t)(k0 >> 5) * R8 + g0) * kPackTile;
+              bulk_s2g(dst, stg, (uint32_t)ng * 1024u);
+              bulk_wait_read();            // the staging buffer is reused next
+            }
+            __syncwarp();
           }
         }
       } else {
@@ -461,6 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    if (kPackedOut && lane == 0) bulk_wait_all();   // the tile stores are complete
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -484,7 +532,7 @@ __device__ __forceinline__ int block_of_tile(const T* __restrict__ b, int n, int
 }
 
 // One warp per 8 x 32 tile: lane l handles row l / 4 and k = 4 j + l % 4 of
-// core matrix j (j = 0..7), so each store is a contiguous 128-byte run.
+// 16-byte chunk j (j = 0..7), stored at its swizzled position.
 __global__ void __launch_bounds__(256)
     pack_kernel(const PackBlock* __restrict__ blocks, int nblocks, int ntiles,
                 const double* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo) {
@@ -494,20 +542,21 @@ __global__ void __launch_bounds__(256)
   const PackBlock b = blocks[block_of_tile(blocks, nblocks, tile)];
   const int local = tile - b.tile0;                  // tile = (c, g) with local = c R8 + g
   const int c = local / b.R8, g = local - c * b.R8;
-  const int r = g * 8 + (lane >> 2);
-  const int64_t out = b.dst + (int64_t)local * kPackTile + lane;
+  const int rr = lane >> 2, r = g * 8 + rr;
+  const int64_t out = b.dst + (int64_t)local * kPackTile + rr * 32 + (lane & 3);
+  const bool scaled = b.scale != 1.0;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int k = c * 32 + j * 4 + (lane & 3);
     float h = 0.f, l = 0.f;
     if (r < b.R && k < b.K) {
-      const double x =
-          b.scale * (b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k]);
+      double x = b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k];
+      if (scaled) x *= b.scale;
       h = to_tf32((float)x);
       l = to_tf32((float)(x - (double)h));
     }
-    hi[out + j * 32] = h;
-    if (lo) lo[out + j * 32] = l;
+    hi[out + ((j ^ rr) << 2)] = h;
+    if (lo) lo[out + ((j ^ rr) << 2)] = l;
   }
 }
 
@@ -540,9 +589,9 @@ __global__ void __launch_bounds__(256)
   const CombTask t = tasks[ti];
   const int local = tile - o.tile0;
   const int c = local / o.R8, g = local - c * o.R8;
-  const int r = g * 8 + (lane >> 2);
+  const int rr = lane >> 2, r = g * 8 + rr;
   const int R = o.trans ? t.cols : t.rows, K = o.trans ? t.rows : t.cols;
-  const int64_t out = o.dst + (int64_t)local * kPackTile + lane;
+  const int64_t out = o.dst + (int64_t)local * kPackTile + rr * 32 + (lane & 3);
   const bool scaled = sh != 1.f || sl != 0.f;
 #pragma unroll 2
   for (int j = 0; j < 8; ++j) {
@@ -565,32 +614,28 @@ __global__ void __launch_bounds__(256)
       // ah - h is exact (h is ah rounded to the 10-bit TF32 mantissa)
       l = to_tf32(__fadd_rn(__fsub_rn(ah, h), al));
     }
-    out_hi[out + j * 32] = h;
-    if (out_lo) out_lo[out + j * 32] = l;
+    out_hi[out + ((j ^ rr) << 2)] = h;
+    if (out_lo) out_lo[out + ((j ^ rr) << 2)] = l;
   }
 }
 
 template <int P, bool kPacked>
-void launch_one(const TcUnit* units, int nunits, const GemmTask* tasks, const TcSeg* segs,
-                const float* Ah, const float* Al, const float* Bh, const float* Bl, float* Chi,
-                float* Clo, int* err, uint64_t wait_ns, cudaStream_t st) {
+void launch_one(const TcUnit* units, const int32_t* cta_start, int ncta, const GemmTask* tasks,
+                const TcSeg* segs, const float* Ah, const float* Al, const float* Bh,
+                const float* Bl, float* Chi, float* Clo, int* err, uint64_t wait_ns,
+                cudaStream_t st) {
   // the shared-memory limit is a per-device attribute of the kernel
   static std::atomic<uint64_t> done{0};
   int dev = 0;
   cudaGetDevice(&dev);
   const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
   if (!bit || !(done.load() & bit)) {
-    cudaFuncSetAttribute(gemm_tc_kernel<P, 2, kPacked>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSmemBytes);
+    cudaFuncSetAttribute(gemm_tc_kernel<P, kSpanChunks, kPacked>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (bit) done.fetch_or(bit);
   }
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (nsm <= 0) nsm = 152;
-  const int grid = nunits < nsm ? nunits : nsm;
-  gemm_tc_kernel<P, 2, kPacked><<<grid, kThreads, kSmemBytes, st>>>(units, nunits, tasks, segs, Ah,
-                                                                    Al, Bh, Bl, Chi, Clo, err,
-                                                                    wait_ns);
+  gemm_tc_kernel<P, kSpanChunks, kPacked><<<ncta, kThreads, kSmemBytes, st>>>(
+      units, cta_start, tasks, segs, Ah, Al, Bh, Bl, Chi, Clo, err, wait_ns);
 }
 
 }  // namespace
@@ -612,24 +657,26 @@ void launch_combine_pairs_pack(const PackOut* outs, int ntasks, int ntiles, cons
                                                               in, out_hi, out_lo, sh, sl);
 }
 
-void launch_gemm_tc(int passes, bool packed, const TcUnit* units, int nunits,
-                    const GemmTask* tasks, const TcSeg* segs, const float* Ahi, const float* Alo,
-                    const float* Bhi, const float* Blo, float* Chi, float* Clo, int* err,
-                    uint64_t wait_ns, cudaStream_t st) {
-  if (nunits <= 0) return;
+void launch_gemm_tc(int passes, bool packed, const TcUnit* units, const int32_t* cta_start,
+                    int ncta, const GemmTask* tasks, const TcSeg* segs, const float* Ahi,
+                    const float* Alo, const float* Bhi, const float* Blo, float* Chi, float* Clo,
+                    int* err, uint64_t wait_ns, cudaStream_t st) {
+  if (ncta <= 0) return;
   count_launch();
   if (passes == 3) {
     if (packed)
-      launch_one<3, true>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err, wait_ns, st);
+      launch_one<3, true>(units, cta_start, ncta, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err,
+                          wait_ns, st);
     else
-      launch_one<3, false>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr, err, wait_ns,
-                           st);
+      launch_one<3, false>(units, cta_start, ncta, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr,
+                           err, wait_ns, st);
   } else {
     if (packed)
-      launch_one<1, true>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err, wait_ns, st);
+      launch_one<1, true>(units, cta_start, ncta, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, Clo, err,
+                          wait_ns, st);
     else
-      launch_one<1, false>(units, nunits, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr, err, wait_ns,
-                           st);
+      launch_one<1, false>(units, cta_start, ncta, tasks, segs, Ahi, Alo, Bhi, Blo, Chi, nullptr,
+                           err, wait_ns, st);
   }
 }
 

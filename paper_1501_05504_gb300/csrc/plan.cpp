@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <map>
 #include <set>
 
@@ -69,6 +70,48 @@ void CombStage::add(int64_t offOut, int ldo, int rows, int cols, const std::vect
 }
 
 namespace {
+std::atomic<int> g_plan_ctas{152};
+}  // namespace
+
+void set_plan_ctas(int n) {
+  if (n > 0 && n <= 4096) g_plan_ctas.store(n);
+}
+int plan_ctas() { return g_plan_ctas.load(); }
+
+namespace {
+
+// Static schedule of a stage's units over the persistent CTAs: longest
+// processing time first onto the least loaded CTA, with a unit's cost its
+// k-chunks times its MMA width plus a fixed share for its drain and store.
+void schedule_units(TcStage& tc, const std::vector<GemmTask>& tasks) {
+  const int n = (int)tc.units.size();
+  const int nc = std::max(1, std::min(plan_ctas(), n));
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
+    const TcUnit& u = tc.units[i];
+    const int nrem = std::min(128, tasks[u.task].N - u.tn * 128);
+    cost[i] = u.nchunks * (double)((nrem + 15) / 16 * 16) / 128.0 + 4.0;
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> lists(nc);
+  std::vector<double> load(nc, 0.0);
+  for (int i : order) {
+    const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lists[c].push_back(i);
+    load[c] += cost[i];
+  }
+  std::vector<TcUnit> out;
+  out.reserve(n);
+  tc.cta_start.assign(nc + 1, 0);
+  for (int c = 0; c < nc; ++c) {
+    tc.cta_start[c] = (int32_t)out.size();
+    for (int i : lists[c]) out.push_back(tc.units[i]);
+  }
+  tc.cta_start[nc] = (int32_t)out.size();
+  tc.units.swap(out);
+}
 
 using Key = std::array<int, 4>;
 struct Interm {
@@ -262,9 +305,7 @@ bool build_tc(GemmStage& g, const std::map<int64_t, CombPacked>* c2A,
     for (int a = 0; a < (t.M + 127) / 128; ++a)
       for (int b = 0; b < (t.N + 127) / 128; ++b) tc.units.push_back(TcUnit{id, a, b, nch});
   }
-  // longest units first: the persistent CTAs take them round robin
-  std::stable_sort(tc.units.begin(), tc.units.end(),
-                   [](const TcUnit& x, const TcUnit& y) { return x.nchunks > y.nchunks; });
+  schedule_units(tc, g.tasks);
   return true;
 }
 
@@ -349,8 +390,7 @@ bool build_fused(Plan* p, const std::map<int64_t, CombPacked>& c2p, std::string*
     for (int a = 0; a < (t.M + 127) / 128; ++a)
       for (int b = 0; b < (t.N + 127) / 128; ++b) tc.units.push_back(TcUnit{id, a, b, nch});
   }
-  std::stable_sort(tc.units.begin(), tc.units.end(),
-                   [](const TcUnit& x, const TcUnit& y) { return x.nchunks > y.nchunks; });
+  schedule_units(tc, g.tasks);
   // algorithmic work: that of stages 1 and 2, which this stage replaces
   g.flops = p->g1.flops + p->c2.flops;
   g.bytes = p->g1.bytes + p->c2.bytes;

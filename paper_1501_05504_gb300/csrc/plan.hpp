@@ -34,7 +34,8 @@ namespace dmrg3s {
 // Tensor-core form of a grouped GEMM stage (packed operands, 128 x 128 units).
 struct TcStage {
   std::vector<TcSeg> segs;              // parallel to GemmStage::segs
-  std::vector<TcUnit> units;            // longest first
+  std::vector<TcUnit> units;            // grouped by CTA: CTA b runs units [cta_start[b], cta_start[b+1])
+  std::vector<int32_t> cta_start;       // one entry per CTA of the persistent launch, plus one
   std::vector<PackBlock> packA, packB;  // empty for an operand packed by stage 2
   int64_t nA = 0, nB = 0;               // floats of one part (hi or lo) of each packed operand
   int32_t tilesA = 0, tilesB = 0;
@@ -97,6 +98,11 @@ struct Plan {
   bool fused = false;
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
+
+// Number of CTAs of the persistent tensor-core launches (the SM count of the
+// device; set when a context is created, 152 for a GB300).
+void set_plan_ctas(int n);
+int plan_ctas();
 
 // Left-side plans.  `mps` is the site tensor M (or A); `le` its left
 // environment (on mps.left, channels W.tl); `re` the right environment (on

@@ -103,6 +103,15 @@ inline bool tc_ok(const std::vector<GemmTask>& tasks, const TcStage& tc, int64_t
       nch[i] += s.kc;
     }
   }
+  if (!tc.units.empty()) {
+    bool ok = tc.cta_start.size() >= 2 && tc.cta_start.front() == 0 &&
+              tc.cta_start.back() == (int32_t)tc.units.size();
+    for (size_t i = 1; ok && i < tc.cta_start.size(); ++i) ok = tc.cta_start[i] >= tc.cta_start[i - 1];
+    if (!ok) {
+      *err = "tensor-core unit schedule";
+      return false;
+    }
+  }
   for (const TcUnit& u : tc.units) {
     if (u.task < 0 || (size_t)u.task >= tasks.size()) {
       *err = "tensor-core unit task out of range";
