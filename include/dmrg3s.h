@@ -246,6 +246,27 @@ dmrg3s_status dmrg3s_apply_heff(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3
                                 const dmrg3s_env* R, const dmrg3s_site* A, dmrg3s_site* HA,
                                 dmrg3s_precision prec, dmrg3s_stream stream);
 
+/* Prepared H_eff operator for repeated application with fixed environments,
+ * as in the Lanczos iteration of Sec. V step 1 (H_eff = L_{i-1} W_i . R_{i+1}
+ * of Eq. es-iter, contracted as dmrg3s_apply_heff does).  dmrg3s_heff_create
+ * plans the contraction for the structures of L, W, R and A (A->data is not
+ * read) and, in the tensor-core modes, packs L and R once into device memory
+ * owned by the handle (on `stream`); dmrg3s_heff_apply then computes
+ * HA = H_eff A for a vector A (device, canonical layout of A's structure, and
+ * HA likewise; both caller-owned) on `stream`, using the context's workspace.
+ * In DMRG3S_FP64 the handle reads L->data and R->data at every application:
+ * they must stay allocated and unchanged while the handle is used.  The
+ * handle must not outlive its context; one host thread at a time.
+ * Errors: as dmrg3s_apply_heff. */
+typedef struct dmrg3s_heff_s* dmrg3s_heff;
+dmrg3s_status dmrg3s_heff_create(dmrg3s_ctx ctx, const dmrg3s_env* L, const dmrg3s_mpo_site* W,
+                                 const dmrg3s_env* R, const dmrg3s_site* A,
+                                 dmrg3s_precision prec, dmrg3s_heff* out, dmrg3s_stream stream);
+dmrg3s_status dmrg3s_heff_apply(dmrg3s_heff op, const double* A, double* HA,
+                                dmrg3s_stream stream);
+/* Synchronises the device, then frees the handle. */
+dmrg3s_status dmrg3s_heff_destroy(dmrg3s_heff op);
+
 /* H_eff application for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a deployment variant of

@@ -636,6 +636,41 @@ def dmrg3s_energy_grad(state, model, params, stream=None):
     return e.value, g
 
 
+class HeffOp:
+    """Prepared H_eff operator (dmrg3s_heff_create): apply(A, HA) computes
+    HA = H_eff A for device vectors in the canonical layout of A's structure."""
+
+    def __init__(self, ctx, L, W, R, A, prec="fp64", stream=None):
+        lb = lib()
+        lb.dmrg3s_heff_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Env), ctypes.POINTER(_MpoSite),
+                                          ctypes.POINTER(_Env), ctypes.POINTER(_Site), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+        lb.dmrg3s_heff_apply.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lb.dmrg3s_heff_destroy.argtypes = [ctypes.c_void_p]
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p()
+        cL, cW, cR, cA = L._c(), W._c(), R._c(), A._c()
+        self._keep = (L, W, R)
+        _check(lb.dmrg3s_heff_create(ctx.handle, ctypes.byref(cL), ctypes.byref(cW), ctypes.byref(cR),
+                                     ctypes.byref(cA), _prec(prec), ctypes.byref(self.handle),
+                                     _stream(stream)), "dmrg3s_heff_create", ctx.handle)
+
+    def apply(self, A, HA, stream=None):
+        _check(lib().dmrg3s_heff_apply(self.handle, _ptr(A.data), _ptr(HA.data), _stream(stream)),
+               "dmrg3s_heff_apply", self.ctx.handle)
+
+    def close(self):
+        if self.handle:
+            lib().dmrg3s_heff_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dmrg3s_apply_heff_noalloc(L, W, R, A, HA, stream=None):
     """H_eff application without a context and without device allocation (static scratch)."""
     lb = lib()

@@ -161,11 +161,12 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
                              lo(sl.a1, t12.nA), st);
     if (!hn.g1B) launch_pack(p.g12_packB, (int)t12.packB.size(), t12.tilesB, g1B, hi(sl.b1),
                              lo(sl.b1, t12.nB), st);
+    const float* aH = hn.g1A_hi ? hn.g1A_hi : hi(sl.a1);
+    const float* aL = hn.g1A_hi ? hn.g1A_lo : lo(sl.a1, t12.nA);
     if (!t12.units.empty()) {
       const int id = pr.on ? pr.begin(kProfGemm, h.g12.flops, h.g12.bytes, st) : -1;
       launch_gemm_tc(passes, true, p.g12_units, p.g12_cta, (int)t12.cta_start.size() - 1,
-                     p.g12_tasks, p.g12_tsegs,
-                     hi(sl.a1), lo(sl.a1, t12.nA), hi(sl.b1), lo(sl.b1, t12.nB), hi(sl.t2p),
+                     p.g12_tasks, p.g12_tsegs, aH, aL, hi(sl.b1), lo(sl.b1, t12.nB), hi(sl.t2p),
                      lo(sl.t2p, h.nT2p), c->d_err, c->wait_ns, st);
       if (id >= 0) pr.end(id, st);
     }
@@ -210,8 +211,8 @@ dmrg3s_status run_plan(Context* c, const DevicePlan& p, const double* g1A, const
     a3l = lo(sl.t2p, h.nT2p);
     if (!hn.g3B) launch_pack(p.g3s_packB, (int)t3.packB.size(), t3.tilesB, g3B, hi(sl.x3),
                              lo(sl.x3, t3.nB), st);
-    b3h = hi(sl.x3);
-    b3l = lo(sl.x3, t3.nB);
+    b3h = hn.g3B_hi ? hn.g3B_hi : hi(sl.x3);
+    b3l = hn.g3B_hi ? hn.g3B_lo : lo(sl.x3, t3.nB);
   } else {
     if (!hn.g3A) launch_pack(p.g3s_packA, (int)t3.packA.size(), t3.tilesA, g3A, hi(sl.x3),
                              lo(sl.x3, t3.nA), st);

@@ -204,6 +204,9 @@ dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);
 // Lanczos loop packs L and R once per run).
 struct SplitHints {
   bool g1A = false, g1B = false, g3A = false, g3B = false;
+  // H_eff only: packed L (stage-1 A) and R (stage-3 B) held outside the
+  // workspace (a prepared operator); when set they replace those slots
+  const float *g1A_hi = nullptr, *g1A_lo = nullptr, *g3B_hi = nullptr, *g3B_lo = nullptr;
 };
 struct TcSlots {
   int64_t t2p, a1, b1, x3, p3, end;   // offsets in doubles from the workspace start

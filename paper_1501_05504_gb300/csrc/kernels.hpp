@@ -69,7 +69,9 @@ struct PackBlock {
   // (trans = 0) or scale * src[off + k * ld + r] (trans = 1)
   int64_t src, dst;                        // dst: float offset of tile (0, 0)
   double scale;
-  int32_t ld, R, K, trans, R8, KC, tile0, pad;   // tile0: first tile in the launch numbering
+  int32_t ld, R, K, trans, R8, KC, tile0;  // tile0: first tile in the launch numbering
+  float pow2;                              // scale when it is a power of two (applied to the
+                                           // FP32 parts, exactly), else 0
 };
 // One K-segment of a tensor-core task: packed A (rows M) and B (rows N).
 struct TcSeg {

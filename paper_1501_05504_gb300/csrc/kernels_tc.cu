@@ -519,6 +519,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
 }
 
+// hi + lo split of a double without FP64 arithmetic (GB300's FP64 pipe would
+// bound the packing): hi = x rounded to 11 significant bits (to nearest, ties
+// away from zero, from the integer significand), lo = tf32(x - hi) with the
+// exact remainder formed from the significand bits.  Returns false for
+// values outside the FP32 normal range and for Inf/NaN, which the caller
+// splits the plain way.
+__device__ __forceinline__ bool split_bits(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const int e = (int)((hw >> 20) & 0x7FF);
+  const uint32_t sign = hw & 0x80000000u;
+  if (e == 0) {                       // zero or an FP64 subnormal (below the FP32 range)
+    hi = __uint_as_float(sign);
+    lo = 0.f;
+    return true;
+  }
+  const int ef = e - 1023 + 127;
+  if (e == 0x7FF || ef <= 0 || ef >= 254) return false;
+  const int hm = (int)((hw & 0xFFFFFu) | 0x100000u);      // top 21 significand bits
+  const int r = (hm >> 10) + ((hm >> 9) & 1);              // 11 bits, rounded half away
+  hi = __uint_as_float(sign | (((uint32_t)ef << 23) + ((uint32_t)(r - 1024) << 13)));
+  const int dh = hm - (r << 10);                           // |dh| <= 512
+  // (x - hi) / 2^(e - 1075) = dh 2^32 + lw, rounded once to FP32 by the sum
+  const float rem = __fadd_rn(__fmul_rn((float)dh, 4294967296.f), __uint2float_rn(lw));
+  const float v = ldexpf(rem, e - 1075);
+  lo = to_tf32(sign ? -v : v);
+  return true;
+}
+
 // Binary search: the block of tile `tile` (blocks in increasing tile0 order).
 template <class T>
 __device__ __forceinline__ int block_of_tile(const T* __restrict__ b, int n, int tile) {
@@ -544,16 +573,23 @@ __global__ void __launch_bounds__(256)
   const int c = local / b.R8, g = local - c * b.R8;
   const int rr = lane >> 2, r = g * 8 + rr;
   const int64_t out = b.dst + (int64_t)local * kPackTile + rr * 32 + (lane & 3);
-  const bool scaled = b.scale != 1.0;
+  // a power-of-two scale multiplies the FP32 parts exactly; any other one is
+  // applied in FP64 before the split
+  const bool f64scale = b.scale != 1.0 && b.pow2 == 0.f;
+  const float fs = b.pow2 != 0.f ? b.pow2 : 1.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int k = c * 32 + j * 4 + (lane & 3);
     float h = 0.f, l = 0.f;
     if (r < b.R && k < b.K) {
       double x = b.trans ? src[b.src + (int64_t)k * b.ld + r] : src[b.src + (int64_t)r * b.ld + k];
-      if (scaled) x *= b.scale;
-      h = to_tf32((float)x);
-      l = to_tf32((float)(x - (double)h));
+      if (f64scale) x *= b.scale;
+      if (!split_bits(x, h, l)) {
+        h = to_tf32((float)x);
+        l = to_tf32((float)(x - (double)h));
+      }
+      h *= fs;
+      l *= fs;
     }
     hi[out + ((j ^ rr) << 2)] = h;
     if (lo) lo[out + ((j ^ rr) << 2)] = l;

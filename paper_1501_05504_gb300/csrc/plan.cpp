@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <set>
 
@@ -237,6 +238,10 @@ struct Packer {
     PackBlock b{};
     b.src = src;
     b.scale = scale;
+    int ex = 0;
+    b.pow2 = (std::frexp(scale, &ex) == 0.5 || std::frexp(scale, &ex) == -0.5) && ex > -100 && ex < 100
+                 ? (float)scale
+                 : 0.f;
     b.dst = *n;
     b.ld = (int32_t)ld;
     b.R = (int32_t)R;

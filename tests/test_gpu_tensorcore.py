@@ -137,3 +137,23 @@ def test_profiler_flops_match_the_benchmark_count(b, ctx):
     assert abs(g["flops"] + c["flops"] - want) <= 1e-9 * want
     # stages 1 + 2 fused, stage 3 (split-K partial products); the partial sum
     assert g["launches"] == 2 and c["launches"] == 1
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", TF32X3_TOL)])
+@pytest.mark.parametrize("kind,seed,kw", [("u1", 51, {}), ("u1u1", 52, {}), ("dense", 53, {"m_left": 70})])
+def test_prepared_operator_matches_oracle(b, ctx, kind, seed, kw, prec, tol):
+    """dmrg3s_heff_create once, dmrg3s_heff_apply on two different vectors."""
+    pb = problem(kind, seed, **kw)
+    gL, gW, gR, gA = _gpu(b, pb)
+    op = b.HeffOp(ctx, gL, gW, gR, gA, prec)
+    L, W, R, A = _dense(pb)
+    for k in range(2):
+        gH = b.empty_site_like(gA.qp, gA.left, gA.right)
+        op.apply(gA, gH)
+        b.dmrg3s_sync(ctx)
+        ref = contract.apply_heff(L, W, R, A)
+        got = site_to_dense(b, gH)
+        assert rel_err(got, ref) < tol
+        gA.data.mul_(-1.5)
+        A = A * -1.5
+    op.close()
