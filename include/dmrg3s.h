@@ -511,6 +511,38 @@ dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
                            const dmrg3s_sweep_opts* opts, double* energies,
                            dmrg3s_sweep_report* report, dmrg3s_stream stream);
 
+/* Batches of independent states (chains), one context.  The local updates
+ * of all states of a batch run together: every contraction stage (the H_eff
+ * products of the Lanczos recursion, the expansion terms, the environment
+ * updates, the energy after truncation) is one grouped launch over the
+ * blocks of every state (the plans of the states merged, their operands
+ * copied into shared arrays), the Lanczos dot products and updates are one
+ * launch each over all states' vectors, and the truncation SVD is one call
+ * over every charge sector of every state.  Each state keeps its own
+ * options, direction, alpha and stopping rules, so that every state gets
+ * the result of its own dmrg3s_local_update / dmrg3s_sweep (up to the
+ * summation order of the merged reductions).  The states must be distinct
+ * and share one context and one SVD method (update.svd).  Synchronous.
+ * Errors: those of dmrg3s_local_update; ARG (mixed contexts or SVD methods,
+ * a state twice). */
+/* One local update on each of nstates states: dirs[k], alphas[k], opts[k]
+ * for state k, infos[k] its result (as dmrg3s_local_update). */
+dmrg3s_status dmrg3s_local_update_batch(const dmrg3s_state* states, int32_t nstates,
+                                        const int32_t* dirs, const double* alphas,
+                                        const dmrg3s_update_opts* opts, dmrg3s_update_info* infos,
+                                        dmrg3s_stream stream);
+/* dmrg3s_sweep on each of nstates states with rules[k], opts[k] (its own
+ * max_sweeps, conv_tol, ladder and traces), energies[k] (may be NULL, or the
+ * array itself may be NULL) and reports[k].  The states advance one local
+ * update per step, all states that are still sweeping together; a state
+ * that has converged or run its max_sweeps leaves the batch.  The states may
+ * differ in length, bond dimensions, MPO and precision (states in different
+ * precisions share the launches of their precision). */
+dmrg3s_status dmrg3s_sweep_batch(const dmrg3s_state* states, int32_t nstates,
+                                 const dmrg3s_alpha_rule* rules, const dmrg3s_sweep_opts* opts,
+                                 double* const* energies, dmrg3s_sweep_report* reports,
+                                 dmrg3s_stream stream);
+
 /* Current centre and energy (E_f of the last update, or the Rayleigh quotient
  * at creation). */
 dmrg3s_status dmrg3s_state_centre(dmrg3s_state state, int32_t* centre, double* energy);

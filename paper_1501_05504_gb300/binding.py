@@ -453,6 +453,12 @@ def _setup_state_api(L):
                                       ctypes.c_void_p]
     L.dmrg3s_sweep.argtypes = [ctypes.c_void_p, ctypes.POINTER(_AlphaRule), ctypes.POINTER(_SweepOpts),
                                f64p, ctypes.POINTER(_SweepReport), ctypes.c_void_p]
+    L.dmrg3s_local_update_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, i32p, f64p,
+                                            ctypes.POINTER(_UpdateOpts), ctypes.POINTER(_UpdateInfo),
+                                            ctypes.c_void_p]
+    L.dmrg3s_sweep_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                     ctypes.POINTER(_AlphaRule), ctypes.POINTER(_SweepOpts),
+                                     ctypes.POINTER(f64p), ctypes.POINTER(_SweepReport), ctypes.c_void_p]
     L.dmrg3s_state_centre.argtypes = [ctypes.c_void_p, i32p, f64p]
     L.dmrg3s_state_site_info.argtypes = [ctypes.c_void_p, ctypes.c_int32, i32p, i32p, i64p, i32p,
                                          i32p, i64p, i64p]
@@ -593,6 +599,67 @@ def dmrg3s_local_update(state, direction, alpha, opts, stream=None):
             "discarded_weight": info.discarded_weight, "lanczos_iters": info.lanczos_iters,
             "new_bond_dim": info.new_bond_dim, "svd_fallback": bool(info.svd_fallback),
             "svd_sweeps": info.svd_sweeps}
+
+
+def _info_dict(info):
+    return {"lambda": info.lambda_, "energy_before": info.energy_before, "energy_after": info.energy_after,
+            "discarded_weight": info.discarded_weight, "lanczos_iters": info.lanczos_iters,
+            "new_bond_dim": info.new_bond_dim, "svd_fallback": bool(info.svd_fallback),
+            "svd_sweeps": info.svd_sweeps}
+
+
+def _handles(states):
+    return (ctypes.c_void_p * len(states))(*[st.handle for st in states])
+
+
+def dmrg3s_local_update_batch(states, directions, alphas, opts, stream=None):
+    """One local update on each state of a batch (one context), all in shared
+    launches; opts is one _UpdateOpts for all or a list.  Returns the infos."""
+    n = len(states)
+    if not isinstance(opts, (list, tuple)):
+        opts = [opts] * n
+    dirs = np.ascontiguousarray(directions, dtype=np.int32)
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    oa = (_UpdateOpts * n)(*opts)
+    infos = (_UpdateInfo * n)()
+    _check(slib().dmrg3s_local_update_batch(_handles(states), n, dirs.ctypes.data_as(i32p),
+                                            al.ctypes.data_as(f64p), oa, infos, _stream(stream)),
+           "dmrg3s_local_update_batch", states[0].ctx.handle)
+    return [_info_dict(x) for x in infos]
+
+
+def dmrg3s_sweep_batch(states, rules, max_sweeps, conv_tol, opts, final_prec=None, switch_tol=0.0,
+                       stream=None):
+    """dmrg3s_sweep on every state of a batch at once (shared launches per local
+    update step).  rules / opts / max_sweeps may be one value for all or a
+    list per state.  Returns one report per state (as dmrg3s_sweep)."""
+    n = len(states)
+
+    def per(v):
+        return list(v) if isinstance(v, (list, tuple)) else [v] * n
+    rules, opts, msw = per(rules), per(opts), [int(x) for x in per(max_sweeps)]
+    als = [np.zeros(max(m * 2 * (st.nsites - 1), 1), dtype=np.float64) for m, st in zip(msw, states)]
+    secs = [np.zeros(m, dtype=np.float64) for m in msw]
+    ens = [np.zeros(m, dtype=np.float64) for m in msw]
+    sos = (_SweepOpts * n)(*[_SweepOpts(msw[k], float(conv_tol), opts[k],
+                                        _prec(final_prec) if final_prec is not None else 0,
+                                        float(switch_tol), als[k].ctypes.data_as(f64p),
+                                        secs[k].ctypes.data_as(f64p)) for k in range(n)])
+    ra = (_AlphaRule * n)(*rules)
+    eptr = (f64p * n)(*[e.ctypes.data_as(f64p) for e in ens])
+    reps = (_SweepReport * n)()
+    _check(slib().dmrg3s_sweep_batch(_handles(states), n, ra, sos, eptr, reps, _stream(stream)),
+           "dmrg3s_sweep_batch", states[0].ctx.handle)
+    out = []
+    for k in range(n):
+        r = reps[k]
+        m = r.sweeps
+        out.append({"energies": ens[k][:m].tolist(), "sweeps": m, "converged": bool(r.converged),
+                    "energy": r.energy, "alpha": r.alpha, "lanczos_iters": r.lanczos_iters,
+                    "svd_fallbacks": r.svd_fallbacks, "bulk_sweeps": r.bulk_sweeps,
+                    "seconds": secs[k][:m].tolist(),
+                    "alphas": als[k][:m * 2 * (states[k].nsites - 1)].tolist()})
+    return out
 
 
 def alpha_rule(alpha0=1e-2, target=0.3, up=1.25, down=0.8, alpha_min=1e-14, alpha_max=1.0, fixed=False):

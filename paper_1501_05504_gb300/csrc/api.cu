@@ -371,7 +371,9 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
   }
   if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_lz[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_lz[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaFreeHost(c->pinned);
     cudaFree(c->ws);
     delete c;
@@ -392,6 +394,9 @@ dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
   if (c->d_err) cudaFree(c->d_err);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   if (c->ev_done) cudaEventDestroy(c->ev_done);
+  for (cudaEvent_t e : c->ev_lz)
+    if (e) cudaEventDestroy(e);
+  if (c->pinned_big) cudaFreeHost(c->pinned_big);
   if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
   return DMRG3S_OK;

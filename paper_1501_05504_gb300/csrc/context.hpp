@@ -118,6 +118,9 @@ struct Context {
   uint64_t wait_ns = 1000000000ull;   // limit of every bounded device wait (dmrg3s_set_wait_limit)
   cudaStream_t aux = nullptr;   // side stream: the Lanczos tridiagonal solve beside the next product
   cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_lz[2] = {nullptr, nullptr};   // Lanczos results of even / odd iterations
+  double* pinned_big = nullptr;   // pinned read-back area of the batched Lanczos (grown on demand)
+  size_t pinned_big_n = 0;        // its size in doubles
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;
   std::string last_error;
 };
@@ -187,6 +190,24 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
                           const double* Rdata, double* x, int64_t n, int kmax, double tol,
                           size_t cursor, cudaStream_t st, double* theta, int* iters,
                           dmrg3s_precision prec = DMRG3S_FP64);
+
+// The same for several independent problems at once: `heff` is a plan whose
+// vector operand holds every problem back to back (problem c at elements
+// [off, off + n) of X, off a multiple of 32, ldx >= every off + n), so that one
+// launch per stage applies all their H_eff.  Each problem keeps its own
+// stopping rule (kmax, tol); theta and iters get one entry per problem.
+struct LzSpec {
+  int64_t off, n;
+  int kmax;
+  double tol;
+};
+dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ldata,
+                            const double* Rdata, double* X, int64_t ldx,
+                            const std::vector<LzSpec>& probs, size_t cursor, cudaStream_t st,
+                            dmrg3s_precision prec, std::vector<double>* theta,
+                            std::vector<int>* iters);
+// Pinned host area of at least n doubles (c->pinned_big).
+dmrg3s_status pinned_reserve(Context* c, size_t n);
 
 // Upload a host plan (allocates the device tables).  Returns CUDA errors.
 dmrg3s_status upload_plan(Plan&& host, std::unique_ptr<DevicePlan>* out);

@@ -3,8 +3,11 @@
 // with full reorthogonalisation (classical Gram-Schmidt applied twice).  The
 // matrix-vector product is the grouped H_eff contraction; dots and updates
 // are FP64 device reductions; the tridiagonal eigenproblem is solved on the
-// device.  The host reads back one small struct per iteration to decide
-// whether to stop.
+// device.  The host reads back one small struct per problem and iteration to
+// decide whether to stop, one iteration behind the device.  Several
+// independent problems (the chains of a batch) run in one recursion, each
+// stage one launch over all of them.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -15,32 +18,87 @@
 
 namespace dmrg3s {
 
-dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldata,
-                          const double* Rdata, double* x, int64_t n, int kmax, double tol,
-                          size_t cursor, cudaStream_t st, double* theta, int* iters,
-                          dmrg3s_precision prec) {
-  if (kmax < 1 || kmax > 128) return fail(c, DMRG3S_ERR_ARG, "kmax must be in [1, 128]");
-  const size_t vbytes = (size_t)n * sizeof(double);
-  void *pV, *pw, *ppart, *ph, *palpha, *pbeta, *py, *pn2, *pout;
+dmrg3s_status pinned_reserve(Context* c, size_t n) {
+  if (c->pinned_big_n >= n) return DMRG3S_OK;
+  if (c->pinned_big) {
+    cudaFreeHost(c->pinned_big);
+    c->pinned_big = nullptr;
+    c->pinned_big_n = 0;
+  }
+  const size_t want = n < 4096 ? 4096 : n;
+  if (cudaMallocHost(&c->pinned_big, want * sizeof(double)) != cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "pinned read-back area");
+  c->pinned_big_n = want;
+  return DMRG3S_OK;
+}
+
+// Iteration k of every problem, on the main stream:
+//   two classical Gram-Schmidt passes of w = H v_k against v_0 .. v_k (each
+//   one dot launch and one update launch; the first pass's last coefficient is
+//   alpha_k, the second pass also forms the partial norms of w);
+// then, on the side stream, the tridiagonal solve of order k + 1 and the copy
+// of its results to the host, while the main stream already normalises
+// v_{k+1} and applies H to it.  The host reads iteration k's results only
+// after it has enqueued iteration k + 1, so the device never waits for the
+// host's stopping decision; a problem that has stopped keeps being iterated
+// (its results are no longer read) until every problem has stopped, and the
+// products of the iterations past the last stop are discarded (their flops
+// are not counted).
+dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ldata,
+                            const double* Rdata, double* X, int64_t ldx,
+                            const std::vector<LzSpec>& probs, size_t cursor, cudaStream_t st,
+                            dmrg3s_precision prec, std::vector<double>* theta,
+                            std::vector<int>* iters) {
+  const int np = (int)probs.size();
+  if (np < 1) return fail(c, DMRG3S_ERR_ARG, "no eigenproblem");
+  int kmax = 0;
+  for (const LzSpec& p : probs) {
+    if (p.kmax < 1 || p.kmax > 128) return fail(c, DMRG3S_ERR_ARG, "kmax must be in [1, 128]");
+    if (p.off < 0 || p.n < 1 || p.off % 32 != 0 || p.off + p.n > ldx)
+      return fail(c, DMRG3S_ERR_ARG, "eigenproblem vector range");
+    kmax = std::max(kmax, p.kmax);
+  }
+  const int kp = kmax + 1;
+  const int64_t ldv = (ldx + 31) / 32 * 32;
+  std::vector<std::pair<int64_t, int64_t>> ranges(np);
+  for (int i = 0; i < np; ++i) ranges[i] = {probs[i].off, probs[i].n};
+  std::vector<LzChunk> hch;
+  std::vector<LzChain> hcn;
+  lz_layout(ranges, 4 * plan_ctas(), &hch, &hcn);
+  const int nchunks = (int)hch.size();
+  void *pV, *pw, *ppart, *pnp, *palpha, *pbeta, *py, *pout, *pch, *pcn, *pks;
   dmrg3s_status s;
-  if ((s = carve(c, &cursor, vbytes * (kmax + 1), &pV)) || (s = carve(c, &cursor, vbytes, &pw)) ||
-      (s = carve(c, &cursor, sizeof(double) * kRedBlocks * (kmax + 1), &ppart)) ||
-      (s = carve(c, &cursor, sizeof(double) * (kmax + 1), &ph)) ||
-      (s = carve(c, &cursor, sizeof(double) * (kmax + 1), &palpha)) ||
-      (s = carve(c, &cursor, sizeof(double) * (kmax + 1), &pbeta)) ||
-      (s = carve(c, &cursor, sizeof(double) * (kmax + 1), &py)) ||
-      (s = carve(c, &cursor, sizeof(double) * 2, &pn2)) ||
-      (s = carve(c, &cursor, sizeof(TridiagOut), &pout)))
+  if ((s = carve(c, &cursor, sizeof(double) * ldv * kp, &pV)) ||
+      (s = carve(c, &cursor, sizeof(double) * ldv, &pw)) ||
+      (s = carve(c, &cursor, sizeof(double) * nchunks * kp, &ppart)) ||
+      (s = carve(c, &cursor, sizeof(double) * nchunks * 3, &pnp)) ||
+      (s = carve(c, &cursor, sizeof(double) * np * kp, &palpha)) ||
+      (s = carve(c, &cursor, sizeof(double) * np * kp, &pbeta)) ||
+      (s = carve(c, &cursor, sizeof(double) * np * kp * kp, &py)) ||
+      (s = carve(c, &cursor, sizeof(TridiagOut) * np * kp, &pout)) ||
+      (s = carve(c, &cursor, sizeof(LzChunk) * nchunks, &pch)) ||
+      (s = carve(c, &cursor, sizeof(LzChain) * np, &pcn)) ||
+      (s = carve(c, &cursor, sizeof(int32_t) * np, &pks)))
     return s;
+  // read-back slots: two iterations' results (4 doubles per problem) and the error word
+  const size_t slot = (size_t)np * 4 + 2;
+  if ((s = pinned_reserve(c, 2 * slot + (size_t)nchunks))) return s;
   double* V = (double*)pV;
   double* w = (double*)pw;
   double* part = (double*)ppart;
-  double* h = (double*)ph;
+  double* nrmp[3] = {(double*)pnp, (double*)pnp + nchunks, (double*)pnp + 2 * nchunks};
   double* alpha = (double*)palpha;
   double* beta = (double*)pbeta;
   double* y = (double*)py;
-  double* nrm2 = (double*)pn2;
   TridiagOut* out = (TridiagOut*)pout;
+  LzChunk* dch = (LzChunk*)pch;
+  LzChain* dcn = (LzChain*)pcn;
+  int32_t* dks = (int32_t*)pks;
+  if (cudaMemcpyAsync(dch, hch.data(), sizeof(LzChunk) * nchunks, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dcn, hcn.data(), sizeof(LzChain) * np, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return fail(c, DMRG3S_ERR_CUDA, "Lanczos tables");
   double* ws1 = reinterpret_cast<double*>(c->ws);
   double* ws2 = ws1 + heff.host.ws1;
   // tensor-core products: pack the environments once for the whole run
@@ -59,72 +117,127 @@ dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldat
     hints.g1A = true;
     hints.g3B = true;
   }
+  double* pin = c->pinned_big;
 
-  // v_0 = x / |x|
-  launch_multidot(x, 0, 1, x, n, part, nrm2, nullptr, st);
-  cudaMemcpyAsync(c->pinned, nrm2, sizeof(double), cudaMemcpyDeviceToHost, st);
+  // v_0 = x / |x| for every problem (a zero start vector is an error)
+  launch_lz_update(nullptr, ldv, 0, X, dch, nchunks, dcn, nullptr, kp, nullptr, nrmp[2], st);
+  cudaMemcpyAsync(pin, nrmp[2], sizeof(double) * nchunks, cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos start");
-  if (!(c->pinned[0] > 0.0)) return fail(c, DMRG3S_ERR_BREAKDOWN, "zero start vector");
-  launch_normalise(x, V, n, nrm2, st);
+  for (int i = 0; i < np; ++i) {
+    double n2 = 0.0;
+    for (int b = 0; b < hcn[i].nc; ++b) n2 += pin[hcn[i].c0 + b];
+    if (!(n2 > 0.0)) return fail(c, DMRG3S_ERR_BREAKDOWN, "zero start vector");
+  }
+  launch_lz_normalise(X, V, dch, nchunks, dcn, nrmp[2], st);
 
-  // Iteration k: w = H v_k was enqueued before; orthogonalise, then solve the
-  // tridiagonal problem on the side stream while the main stream already
-  // normalises v_{k+1} and applies H to it.  If iteration k turns out to be
-  // the last, that product is discarded (its flops are not counted).
-  int k = 0;
-  TridiagOut res{};
-  dmrg3s_status rs = run_plan(c, heff, Ldata, V, ws1, ws2, 1.0, ws2, Rdata, w, st, prec, &hints);
-  if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
-  for (;; ++k) {
-    launch_multidot(V, n, k + 1, w, n, part, h, alpha + k, st);   // alpha_k = <v_k, H v_k>
-    launch_multi_axpy(V, n, k + 1, h, w, n, st);
-    launch_multidot(V, n, k + 1, w, n, part, h, nullptr, st);     // second Gram-Schmidt pass
-    launch_multi_axpy(V, n, k + 1, h, w, n, st);
-    launch_multidot(w, 0, 1, w, n, part, nrm2, nullptr, st);
-    cudaEventRecord(c->ev_ready, st);
-    cudaStreamWaitEvent(c->aux, c->ev_ready, 0);
-    launch_tridiag_smallest(alpha, beta, k + 1, nrm2, y, out, c->aux);
-    cudaMemcpyAsync(c->pinned, out, sizeof(TridiagOut), cudaMemcpyDeviceToHost, c->aux);
-    cudaMemcpyAsync(c->pinned + 8, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->aux);
-    cudaEventRecord(c->ev_done, c->aux);
-    // speculative: the next basis vector and its product
-    const bool spec = k + 1 < kmax;
-    size_t rec0 = c->prof.recs.size();
-    if (spec) {
-      launch_normalise(w, V + (int64_t)(k + 1) * n, n, nrm2, st);
-      rs = run_plan(c, heff, Ldata, V + (int64_t)(k + 1) * n, ws1, ws2, 1.0, ws2, Rdata, w, st,
-                    prec, &hints);
-      if (rs != DMRG3S_OK) return fail(c, rs, "H_eff launch failed");
-    }
-    if (cudaEventSynchronize(c->ev_done) != cudaSuccess)
+  std::vector<int> kstop(np, -1);
+  theta->assign(np, 0.0);
+  iters->assign(np, 0);
+  int nstopped = 0;
+  // profiler records of the product that builds on iteration k (index k + 1)
+  std::vector<std::pair<size_t, size_t>> prod_recs(kp, {0, 0});
+  auto product = [&](int j) -> dmrg3s_status {   // w = H v_j
+    const size_t r0 = c->prof.recs.size();
+    dmrg3s_status r = run_plan(c, heff, Ldata, V + (int64_t)j * ldv, ws1, ws2, 1.0, ws2, Rdata,
+                               w, st, prec, &hints);
+    prod_recs[j] = {r0, c->prof.recs.size()};
+    return r != DMRG3S_OK ? fail(c, r, "H_eff launch failed") : DMRG3S_OK;
+  };
+  // the host's reading of iteration k
+  auto collect = [&](int k) -> dmrg3s_status {
+    if (cudaEventSynchronize(c->ev_lz[k & 1]) != cudaSuccess)
       return fail(c, DMRG3S_ERR_CUDA, "Lanczos step");
-    std::memcpy(&res, c->pinned, sizeof(res));
+    const double* sl = pin + (size_t)(k & 1) * slot;
     int dev_err = 0;
-    std::memcpy(&dev_err, c->pinned + 8, sizeof(int));
+    std::memcpy(&dev_err, sl + (size_t)np * 4, sizeof(int));
     if (dev_err) {
       cudaStreamSynchronize(st);
+      cudaStreamSynchronize(c->aux);
       cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+      cudaStreamSynchronize(st);
       return fail(c, DMRG3S_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
     }
-    if (res.nan_seen != 0.0) return fail(c, DMRG3S_ERR_NUMERIC, "NaN in the Lanczos recursion");
-    const bool conv = res.resid <= tol * std::fmax(1.0, std::fabs(res.theta));
-    if (conv || res.beta_last < 1e-14 || k + 1 == kmax) {
-      for (size_t r = rec0; r < c->prof.recs.size(); ++r) {   // the discarded product
-        c->prof.recs[r].flops = 0.0;
-        c->prof.recs[r].bytes = 0.0;
+    for (int i = 0; i < np; ++i) {
+      if (kstop[i] >= 0) continue;
+      TridiagOut res;
+      std::memcpy(&res, sl + (size_t)i * 4, sizeof(res));
+      if (res.nan_seen != 0.0) return fail(c, DMRG3S_ERR_NUMERIC, "NaN in the Lanczos recursion");
+      const bool conv = res.resid <= probs[i].tol * std::fmax(1.0, std::fabs(res.theta));
+      if (conv || res.beta_last < 1e-14 || k + 1 == probs[i].kmax) {
+        kstop[i] = k;
+        (*theta)[i] = res.theta;
+        (*iters)[i] = k + 1;
+        ++nstopped;
       }
-      break;
+    }
+    return DMRG3S_OK;
+  };
+  // an error after the recursion has started waits for both streams (the
+  // side stream still writes into the workspace the caller reuses)
+  auto bail = [&](dmrg3s_status r) {
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(c->aux);
+    return r;
+  };
+  if ((s = product(0))) return bail(s);
+  int last = -1;   // the last iteration enqueued
+  for (int k = 0; k < kmax; ++k) {
+    launch_lz_dots(V, ldv, k + 1, w, dch, nchunks, part, kp, st);
+    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, alpha, nullptr, st);
+    launch_lz_dots(V, ldv, k + 1, w, dch, nchunks, part, kp, st);     // second pass
+    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, nullptr, nrmp[k & 1], st);
+    cudaEventRecord(c->ev_ready, st);
+    cudaStreamWaitEvent(c->aux, c->ev_ready, 0);
+    launch_lz_tridiag(dcn, np, alpha, beta, kp, k, nrmp[k & 1], y, out, c->aux);
+    double* sl = pin + (size_t)(k & 1) * slot;
+    cudaMemcpyAsync(sl, out + (size_t)k * np, sizeof(TridiagOut) * np, cudaMemcpyDeviceToHost,
+                    c->aux);
+    cudaMemcpyAsync(sl + (size_t)np * 4, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->aux);
+    cudaEventRecord(c->ev_lz[k & 1], c->aux);
+    last = k;
+    if (k + 1 < kmax) {     // speculative: the next basis vector and its product
+      launch_lz_normalise(w, V + (int64_t)(k + 1) * ldv, dch, nchunks, dcn, nrmp[k & 1], st);
+      if ((s = product(k + 1))) return bail(s);
+    }
+    if (k >= 1) {
+      if ((s = collect(k - 1))) return bail(s);
+      if (nstopped == np) break;
     }
   }
-  // y was written on the side stream
-  cudaStreamWaitEvent(st, c->ev_done, 0);
-  // Ritz vector x = V y, normalised
-  launch_combine_vectors(V, n, k + 1, y, w, n, st);
-  launch_multidot(w, 0, 1, w, n, part, nrm2, nullptr, st);
-  launch_normalise(w, x, n, nrm2, st);
+  if (nstopped < np) {
+    if ((s = collect(last))) return bail(s);
+    if (nstopped < np) return bail(fail(c, DMRG3S_ERR_CUDA, "Lanczos did not stop"));
+  }
+  int kmaxstop = 0;
+  for (int i = 0; i < np; ++i) kmaxstop = std::max(kmaxstop, kstop[i]);
+  for (int j = kmaxstop + 1; j < kp; ++j)   // the discarded products
+    for (size_t r = prod_recs[j].first; r < prod_recs[j].second; ++r) {
+      c->prof.recs[r].flops = 0.0;
+      c->prof.recs[r].bytes = 0.0;
+    }
+  // Ritz vectors x = V y (y written on the side stream), normalised
+  cudaEventRecord(c->ev_ready, c->aux);
+  cudaStreamWaitEvent(st, c->ev_ready, 0);
+  if (cudaMemcpyAsync(dks, kstop.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return bail(fail(c, DMRG3S_ERR_CUDA, "Lanczos tables"));
+  launch_lz_ritz(V, ldv, dch, nchunks, dcn, dks, y, kp, w, nrmp[2], st);
+  launch_lz_normalise(w, X, dch, nchunks, dcn, nrmp[2], st);
   if (cudaGetLastError() != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos launch failed");
-  *theta = res.theta;
-  *iters = k + 1;
+  return DMRG3S_OK;
+}
+
+dmrg3s_status lanczos_run(Context* c, const DevicePlan& heff, const double* Ldata,
+                          const double* Rdata, double* x, int64_t n, int kmax, double tol,
+                          size_t cursor, cudaStream_t st, double* theta, int* iters,
+                          dmrg3s_precision prec) {
+  std::vector<LzSpec> one(1, LzSpec{0, n, kmax, tol});
+  std::vector<double> th;
+  std::vector<int> it;
+  dmrg3s_status s = lanczos_batch(c, heff, Ldata, Rdata, x, n, one, cursor, st, prec, &th, &it);
+  if (s != DMRG3S_OK) return s;
+  *theta = th[0];
+  *iters = it[0];
   return DMRG3S_OK;
 }
 

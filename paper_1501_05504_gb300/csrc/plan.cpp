@@ -496,6 +496,94 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
 
 }  // namespace
 
+namespace {
+// Appends stage `src` to `dst` with its operand offsets moved by oA / oB and
+// its output offsets by oC.
+void append_gemm(GemmStage& dst, const GemmStage& src, int64_t oA, int64_t oB, int64_t oC) {
+  const int32_t t0 = (int32_t)dst.tasks.size(), s0 = (int32_t)dst.segs.size();
+  for (GemmTask t : src.tasks) {
+    t.offC += oC;
+    t.seg0 += s0;
+    dst.tasks.push_back(t);
+  }
+  for (GemmSeg g : src.segs) {
+    g.offA += oA;
+    g.offB += oB;
+    dst.segs.push_back(g);
+  }
+  for (GemmTile t : src.tiles) {
+    t.task += t0;
+    dst.tiles.push_back(t);
+  }
+  dst.flops += src.flops;
+}
+void append_comb(CombStage& dst, const CombStage& src, int64_t oIn, int64_t oOut, double scale) {
+  const int32_t t0 = (int32_t)dst.tasks.size(), m0 = (int32_t)dst.terms.size();
+  for (CombTask t : src.tasks) {
+    t.offOut += oOut;
+    t.t0 += m0;
+    dst.tasks.push_back(t);
+  }
+  for (CombTerm m : src.terms) {
+    m.offIn += oIn;
+    if (scale != 1.0) {
+      m.coef *= scale;
+      m.chi = (float)m.coef;
+      m.clo = (float)(m.coef - (double)m.chi);
+    }
+    dst.terms.push_back(m);
+  }
+  for (CombChunk ch : src.chunks) {
+    ch.task += t0;
+    dst.chunks.push_back(ch);
+  }
+  dst.flops += src.flops;
+  dst.bytes += src.bytes;
+}
+}  // namespace
+
+dmrg3s_status merge_plans(Kind kind, const std::vector<PlanPart>& parts, int64_t nA1, int64_t nB1,
+                          int64_t nOut2, int64_t nA3, int64_t nB3, int64_t nC3, Plan* out,
+                          std::string* err) {
+  *out = Plan();
+  Plan& m = *out;
+  m.kind = kind;
+  m.has_g3 = kind == Kind::Heff || kind == Kind::EnvLR || kind == Kind::EnvRL;
+  if (parts.empty()) {
+    *err = "merge of no plans";
+    return DMRG3S_ERR_ARG;
+  }
+  m.g1.ta = parts[0].p->g1.ta;
+  m.g1.tb = parts[0].p->g1.tb;
+  m.g3.ta = parts[0].p->g3.ta;
+  m.g3.tb = parts[0].p->g3.tb;
+  int64_t o1 = 0, o2 = 0;
+  for (const PlanPart& q : parts) {
+    const Plan& p = *q.p;
+    if (p.kind != kind || p.g1.ta != m.g1.ta || p.g1.tb != m.g1.tb ||
+        (m.has_g3 && (p.g3.ta != m.g3.ta || p.g3.tb != m.g3.tb))) {
+      *err = "merged plans differ in kind";
+      return DMRG3S_ERR_ARG;
+    }
+    append_gemm(m.g1, p.g1, q.oA1, q.oB1, o1);
+    append_comb(m.c2, p.c2, o1, m.has_g3 ? o2 : q.oOut2, q.c2scale);
+    if (m.has_g3) {
+      const bool t2_is_a = kind == Kind::Heff;
+      append_gemm(m.g3, p.g3, t2_is_a ? o2 : q.oA3, t2_is_a ? q.oB3 : o2, q.oC3);
+    }
+    o1 += p.ws1;
+    o2 += m.has_g3 ? p.ws2 : 0;
+  }
+  m.ws1 = o1;
+  m.ws2 = o2;
+  if (m.has_g3) {
+    if (kind == Kind::Heff) nA3 = o2;
+    else nB3 = o2;
+    nOut2 = o2;
+  }
+  return finish(&m, nA1, nB1, nOut2, nA3, nB3, nC3, err);
+}
+
 dmrg3s_status check_site_mpo(const SiteLayout& s, const MpoLayout& W, std::string* err) {
   if (s.nsym != W.nsym) {
     *err = "site tensor and MPO have different nsym";

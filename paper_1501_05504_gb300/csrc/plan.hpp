@@ -99,6 +99,25 @@ struct Plan {
   double flops() const { return g1.flops + c2.flops + (has_g3 ? g3.flops : 0.0); }
 };
 
+// One plan of a merge and where its external operands sit in the merged
+// operand arrays (element offsets).  oOut2 places the stage-2 output of the
+// expansion kinds (P); for the kinds with stage 3 the stage-2 output is an
+// intermediate and the stage-3 operand that reads it (A for Heff, B for the
+// environments) is placed by the merge, so the corresponding field is unused.
+struct PlanPart {
+  const Plan* p = nullptr;
+  int64_t oA1 = 0, oB1 = 0, oOut2 = 0, oA3 = 0, oB3 = 0, oC3 = 0;
+  double c2scale = 1.0;     // folded into this part's MPO coefficients (the expansion's alpha)
+};
+// Plans of one kind side by side, as one plan: their task tables concatenated
+// with every operand offset moved by its part's base (the parts'
+// intermediates laid out back to back), then the split-K stage 3 and the
+// tensor-core form built over the whole, so that one launch per stage
+// serves every part.  n* are the sizes of the merged operand arrays.
+dmrg3s_status merge_plans(Kind kind, const std::vector<PlanPart>& parts, int64_t nA1, int64_t nB1,
+                          int64_t nOut2, int64_t nA3, int64_t nB3, int64_t nC3, Plan* out,
+                          std::string* err);
+
 // Number of CTAs of the persistent tensor-core launches (the SM count of the
 // device; set when a context is created, 152 for a GB300).
 void set_plan_ctas(int n);

@@ -390,6 +390,411 @@ dmrg3s_status svd_sectors(State& S, const std::vector<Sector>& secs, double* X, 
   return cuda_ok(c, cudaGetLastError(), "SVD launch");
 }
 
+// Host side of steps 3 and 4 of one update, left-to-right (dir = +1) or
+// right-to-left (dir = -1): the charge sectors of M~ = [M* P] (or [M*; P]),
+// the copy tasks that gather M* and P into them, and the placement of every
+// sector's SVD factors.
+struct Trunc {
+  std::vector<Sector> secs;
+  std::vector<CopyTask> gather_m, gather_p;
+  int64_t xoff = 0, foff = 0, soff = 0;   // elements of X (all sectors), of U / VT, of S
+  bool any_proj = false;                  // a copy of X is needed (projected remainders,
+                                          // or the restart of a Jacobi SVD)
+  // after the selection (truncate_centre): the new bond and the remainder
+  Bond nbnd;
+  std::vector<int> sec_of_new;            // sector of every sector of the new bond
+  std::vector<int64_t> rem_off;           // S V^dagger (or U S) block of every new sector
+  int64_t rem_size = 0;
+  double* rem = nullptr;                  // owned: freed by update_neighbour
+};
+
+void prepare_truncation(const SiteLayout& ml, int dir, bool expand, const FusedBond& fp,
+                        const SiteLayout& pl, dmrg3s_svd_method svd, Trunc* t) {
+  const Bond& old = dir == 1 ? ml.right : ml.left;
+  // Sector k of M~ is a rows x cols matrix X (rows: (s, a_l) for L->R, the
+  // expanded left states for R->L).  It is gathered column-major in the tall
+  // orientation m >= n that the FP64 SVD routine needs: X itself when
+  // rows >= cols, X^T otherwise.
+  std::vector<Charge> charges;
+  for (int k = 0; k < old.nsec(); ++k) charges.push_back(old.q[k]);
+  if (expand)
+    for (int k = 0; k < fp.bond.nsec(); ++k) charges.push_back(fp.bond.q[k]);
+  std::sort(charges.begin(), charges.end());
+  charges.erase(std::unique(charges.begin(), charges.end()), charges.end());
+  const Bond& keepb = dir == 1 ? ml.left : ml.right;   // the bond that is not expanded
+  std::vector<Sector>& secs = t->secs;
+  std::vector<CopyTask>& gather_m = t->gather_m;
+  std::vector<CopyTask>& gather_p = t->gather_p;
+  secs.clear();
+  gather_m.clear();
+  gather_p.clear();
+  int64_t xoff = 0;
+  // task placing a row-major block (rb x cb) at (row0, col0) of sector sc's X
+  auto place = [](const Sector& sc, int64_t src_off, int64_t rb, int64_t cb, int64_t row0,
+                  int64_t col0) {
+    if (sc.tall)   // column-major X (ld rows): write X^T rows = block columns
+      return copy_task(src_off, cb, sc.off + col0 * sc.rows + row0, sc.rows, cb, rb, true);
+    return copy_task(src_off, cb, sc.off + row0 * sc.cols + col0, sc.cols, rb, cb, false);
+  };
+  for (const Charge& q : charges) {
+    Sector sc;
+    sc.q = q;
+    sc.jbase = old.find(q);
+    if (ml.nsym == 0) sc.jbase = 0;
+    const int kp = expand ? (ml.nsym ? fp.bond.find(q) : 0) : -1;
+    const int64_t pwidth = kp >= 0 ? fp.bond.dim[kp] : 0;
+    sc.base = sc.jbase >= 0 ? old.dim[sc.jbase] : 0;
+    const int64_t exp_dim = sc.base + pwidth;
+    // the other dimension: sum over physical states of the matching sector of keepb
+    int64_t other = 0;
+    std::vector<std::pair<int, int64_t>> parts;   // (s, offset along the other dimension)
+    for (int ss = 0; ss < ml.d; ++ss) {
+      Charge qo = dir == 1 ? sub(q, ml.qp[ss]) : add(q, ml.qp[ss]);
+      const int io = ml.nsym ? keepb.find(qo) : 0;
+      if (io < 0) continue;
+      parts.push_back({ss, other});
+      other += keepb.dim[io];
+    }
+    if (other == 0 || exp_dim == 0) continue;
+    sc.rows = dir == 1 ? other : exp_dim;
+    sc.cols = dir == 1 ? exp_dim : other;
+    sc.tall = sc.rows >= sc.cols;
+    sc.m = sc.tall ? sc.rows : sc.cols;
+    sc.n = sc.tall ? sc.cols : sc.rows;
+    sc.r = sc.n;
+    sc.vt_only = dir == 1 ? !sc.tall : sc.tall;
+    sc.off = xoff;
+    xoff += sc.rows * sc.cols;
+    for (auto& pr : parts) {
+      const int ss = pr.first;
+      const int64_t o2 = pr.second;
+      Charge qo = dir == 1 ? sub(q, ml.qp[ss]) : add(q, ml.qp[ss]);
+      const int io = ml.nsym ? keepb.find(qo) : 0;
+      const int64_t dio = keepb.dim[io];
+      if (sc.jbase >= 0) {
+        // M* block (ss, io, jbase) for L->R; (ss, jbase, io) for R->L
+        const int bi = dir == 1 ? ml.block_of(ss, io) : ml.block_of(ss, sc.jbase);
+        if (bi >= 0) {
+          const Block& bk = ml.blocks[bi];
+          const bool match = dir == 1 ? bk.c == sc.jbase : bk.c == io;
+          if (match) {
+            if (dir == 1)
+              gather_m.push_back(place(sc, bk.off, dio, sc.base, o2, 0));
+            else
+              gather_m.push_back(place(sc, bk.off, sc.base, dio, 0, o2));
+          }
+        }
+      }
+      if (kp >= 0) {
+        const int bi = dir == 1 ? pl.block_of(ss, io) : pl.block_of(ss, kp);
+        if (bi >= 0) {
+          const Block& bk = pl.blocks[bi];
+          const bool match = dir == 1 ? bk.c == kp : bk.c == io;
+          if (match) {
+            if (dir == 1)
+              gather_p.push_back(place(sc, bk.off, dio, pwidth, o2, sc.base));
+            else
+              gather_p.push_back(place(sc, bk.off, pwidth, dio, sc.base, o2));
+          }
+        }
+      }
+    }
+    secs.push_back(sc);
+  }
+  t->xoff = xoff;
+  // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n
+  int64_t foff = 0, soff = 0;
+  for (Sector& sc : secs) {
+    sc.offU = foff;
+    if (!sc.vt_only) foff += sc.m * sc.r;
+    sc.offVT = foff;
+    foff += sc.r * sc.n;
+    sc.offS = soff;
+    soff += sc.r;
+  }
+  t->foff = foff;
+  t->soff = soff;
+  bool any_proj = svd == DMRG3S_SVD_JACOBI;
+  for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
+  t->any_proj = any_proj;
+}
+
+// Step 4 for the sectors `secs` (offsets into X, F, Sv): FP64 SVD of every
+// sector, the singular values read back into hs (host), every sector's
+// convergence checked.  X0 holds a copy of X (needed by the Jacobi method,
+// which restores X from it and falls back to gesvd when a sector's sweeps do
+// not converge).  dinfo: room for one int per sector.  Synchronises `st`.
+dmrg3s_status svd_all(State& S, dmrg3s_svd_method method, const std::vector<Sector>& secs,
+                      double* X, const double* X0, int64_t nX, double* F, double* Sv, int* dinfo,
+                      int64_t nS, std::vector<double>* hs, bool* fallback, int* sweeps,
+                      cudaStream_t st) {
+  Context* c = S.c;
+  dmrg3s_status s;
+  hs->assign(std::max<int64_t>(nS, 1), 0.0);
+  std::vector<int> hinfo(secs.size() + 1, 0);
+  if (method == DMRG3S_SVD_JACOBI) {
+    std::vector<SvdJob> jobs(secs.size());
+    for (size_t k = 0; k < secs.size(); ++k) {
+      const Sector& sc = secs[k];
+      jobs[k].m = sc.m;
+      jobs[k].n = sc.n;
+      jobs[k].offA = sc.off;
+      jobs[k].offS = sc.offS;
+      jobs[k].offVT = sc.offVT;
+      jobs[k].offU = sc.vt_only ? -1 : sc.offU;
+    }
+    int nw = (int)secs.size() / 4;
+    nw = std::min(std::max(nw, 4), (int)S.svd.size());
+    if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st, nullptr, sweeps)))
+      return s;
+    bool conv = true;
+    for (size_t k = 0; k < secs.size(); ++k) conv = conv && hinfo[k] == 0;
+    if (!conv) {   // redo the SVD with gesvd on the restored X
+      *fallback = true;
+      if ((s = cuda_ok(c, cudaMemcpyAsync(X, X0, (size_t)nX * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, st), "copy of M~")) ||
+          (s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
+          (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
+                                          cudaMemcpyDeviceToHost, st), "SVD info")))
+        return s;
+    }
+  } else if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
+             (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
+                                             cudaMemcpyDeviceToHost, st), "SVD info"))) {
+    return s;
+  }
+  if ((s = cuda_ok(c, cudaMemcpyAsync(hs->data(), Sv, nS * sizeof(double), cudaMemcpyDeviceToHost,
+                                      st), "singular values")) ||
+      (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
+    return s;
+  for (size_t k = 0; k < secs.size(); ++k)
+    if (hinfo[k] != 0) return fail(c, DMRG3S_ERR_NUMERIC, "SVD did not converge in a sector");
+  return DMRG3S_OK;
+}
+
+// Selection of step 4 and the new tensors: the states kept over all sectors
+// (the largest singular values, at most m_max, above eps times the largest),
+// the new centre tensor A~ (L->R) or B~ (R->L) in place of the old one, and
+// the remainder S V^dagger (or U S) of every kept sector into t.rem.  F / Sv
+// / X0 hold this update's SVD factors and copy of M~ (offsets of t.secs), hs
+// its singular values on the host.
+dmrg3s_status truncate_centre(State& S, int dir, const Opts& o, Trunc& t, const double* F,
+                              const double* Sv, const double* X0, const double* hs, Info* info,
+                              cudaStream_t st) {
+  Context* c = S.c;
+  DevSite& m = S.M[S.centre];
+  const SiteLayout& ml = m.lay;
+  const Bond& keepb = dir == 1 ? ml.left : ml.right;   // the bond that is not expanded
+  std::vector<Sector>& secs = t.secs;
+  dmrg3s_status s;
+  Scratch scr(c, st);
+  // global selection: order by (-s, sector, index), cut at eps * s_max and m_max
+  std::vector<std::tuple<double, int, int>> cand;
+  double smax = 0.0, total = 0.0;
+  for (size_t k = 0; k < secs.size(); ++k)
+    for (int64_t j = 0; j < secs[k].r; ++j) {
+      const double v = hs[secs[k].offS + j];
+      if (!(v == v)) return fail(c, DMRG3S_ERR_NUMERIC, "NaN singular value");
+      cand.emplace_back(-v, (int)k, (int)j);
+      smax = std::max(smax, v);
+      total += v * v;
+    }
+  std::sort(cand.begin(), cand.end());
+  double kept_w = 0.0;
+  int nkeep = 0;
+  for (auto& t : cand) {
+    const double v = -std::get<0>(t);
+    if (!(v > o.eps * smax) || nkeep >= o.m_max) break;
+    secs[std::get<1>(t)].keep++;
+    kept_w += v * v;
+    ++nkeep;
+  }
+  info->discarded = total - kept_w;
+  info->new_dim = nkeep;
+  if (nkeep == 0) return fail(c, DMRG3S_ERR_NUMERIC, "truncation kept no state");
+  // ---- new bond
+  Bond& nbnd = t.nbnd;
+  nbnd = Bond();
+  nbnd.nsym = ml.nsym;
+  std::vector<int>& sec_of_new = t.sec_of_new;
+  sec_of_new.clear();
+  for (size_t k = 0; k < secs.size(); ++k)
+    if (secs[k].keep > 0) {
+      nbnd.q.push_back(secs[k].q);
+      nbnd.dim.push_back(secs[k].keep);
+      sec_of_new.push_back((int)k);
+    }
+  nbnd.off.assign(nbnd.dim.size() + 1, 0);
+  for (size_t k = 0; k < nbnd.dim.size(); ++k) nbnd.off[k + 1] = nbnd.off[k] + nbnd.dim[k];
+  nbnd.total = nbnd.off.back();
+  if (nbnd.nsym == 0) nbnd.q.assign(1, Charge{});
+  // ---- new centre tensor A~ (L->R) or B~ (R->L), and the remainder SV / US.
+  // With X = U_X S V_X^T: tall sectors have U_X = U, V_X = VT^T; wide ones
+  // (X^T was factorised) have U_X = VT^T, V_X = U.
+  SiteLayout nl;
+  if (dir == 1)
+    make_site_from(ml.nsym, ml.d, ml.qp, ml.left, nbnd, &nl);
+  else
+    make_site_from(ml.nsym, ml.d, ml.qp, nbnd, ml.right, &nl);
+  // copy tasks reading U_X[row0 + a, c] (dst a x c) and V_X[col0 + a, c] (dst c x a, or a x c)
+  auto ux = [](const Sector& sc, int64_t row0, int64_t dst, int64_t ldd, int64_t na, int64_t nc,
+               int cs) {   // dst (na x nc): U_X[row0 + a, c] * S[c]
+    if (sc.tall) return copy_task(sc.offU + row0, sc.m, dst, ldd, na, nc, true, -1, cs);
+    return copy_task(sc.offVT + row0 * sc.r, sc.r, dst, ldd, na, nc, false, -1, cs);
+  };
+  auto vxt = [](const Sector& sc, int64_t col0, int64_t dst, int64_t ldd, int64_t nc, int64_t na,
+                int rs) {  // dst (nc x na): V_X[col0 + a, c] * S[c]
+    if (sc.tall) return copy_task(sc.offVT + col0 * sc.r, sc.r, dst, ldd, nc, na, true, rs, -1);
+    return copy_task(sc.offU + col0, sc.m, dst, ldd, nc, na, false, rs, -1);
+  };
+  std::vector<CopyTask> cp_new, cp_rem;
+  GemmStage proj_lr, proj_rl;   // remainder by projection (vt_only sectors)
+  proj_lr.ta = Trans::T;
+  proj_lr.tb = Trans::N;
+  proj_rl.ta = Trans::T;
+  proj_rl.tb = Trans::N;
+  t.rem_off.assign(nbnd.nsec(), 0);
+  std::vector<int64_t>& rem_off = t.rem_off;
+  int64_t rem_size = 0;
+  for (int kn = 0; kn < nbnd.nsec(); ++kn) {
+    const Sector& sc = secs[sec_of_new[kn]];
+    const int64_t nk = sc.keep;
+    rem_off[kn] = rem_size;
+    rem_size += nk * sc.base;
+    int64_t o2 = 0;
+    for (int ss = 0; ss < ml.d; ++ss) {
+      Charge qo = dir == 1 ? sub(sc.q, ml.qp[ss]) : add(sc.q, ml.qp[ss]);
+      const int io = ml.nsym ? keepb.find(qo) : 0;
+      if (io < 0) continue;
+      const int64_t dio = keepb.dim[io];
+      const int bi = dir == 1 ? nl.block_of(ss, io) : nl.block_of(ss, kn);
+      if (bi >= 0) {
+        const Block& bk = nl.blocks[bi];
+        if (dir == 1)   // A~ block (dio x nk) = U_X[o2 + a, c]
+          cp_new.push_back(ux(sc, o2, bk.off, bk.cols, dio, nk, -1));
+        else            // B~ block (nk x dio) = V_X[o2 + a, c]^T
+          cp_new.push_back(vxt(sc, o2, bk.off, bk.cols, nk, dio, -1));
+      }
+      o2 += dio;
+    }
+    if (sc.base > 0 && sc.vt_only) {
+      // L->R (X^T factorised): SV[c, j] = sum_a VT[c, a] X[a, j], X row-major (rows x cols)
+      // R->L (X factorised):   US[i, c] = sum_a X[i, a] VT[c, a], X column-major (rows x cols)
+      // Both read VT[c, a] at offVT + a r + c, i.e. K x nk row-major with ld r.
+      GemmSeg q{};
+      q.scale = 1.0;
+      q.K = (int32_t)sc.n;
+      if (dir == 1) {     // C (nk x base) = VT^T^T . X: A = VT (K x nk, ld r), B = X (K x base, ld cols)
+        q.offA = sc.offVT;
+        q.lda = (int32_t)sc.r;
+        q.offB = sc.off;
+        q.ldb = (int32_t)sc.cols;
+        proj_lr.add(rem_off[kn], (int)sc.base, (int)nk, (int)sc.base, {q});
+      } else {            // C (base x nk) = X^T^T . VT^T: A = X (K x base, ld rows), B = VT (K x nk, ld r)
+        q.offA = sc.off;
+        q.lda = (int32_t)sc.rows;
+        q.offB = sc.offVT;
+        q.ldb = (int32_t)sc.r;
+        proj_rl.add(rem_off[kn], (int)nk, (int)sc.base, (int)nk, {q});
+      }
+    } else if (sc.base > 0) {
+      if (dir == 1)     // SV (nk x base) = S[c] V_X[col, c]^T
+        cp_rem.push_back(vxt(sc, 0, rem_off[kn], sc.base, nk, sc.base, (int)sc.offS));
+      else              // US (base x nk) = U_X[row, c] S[c]
+        cp_rem.push_back(ux(sc, 0, rem_off[kn], nk, sc.base, nk, (int)sc.offS));
+    }
+  }
+  double *ndata, *rem;
+  if ((s = scr.get(&ndata, nl.size)) || (s = scr.get(&rem, rem_size))) return s;
+  cudaMemsetAsync(ndata, 0, (size_t)std::max<int64_t>(nl.size, 1) * sizeof(double), st);
+  if ((s = run_copies(c, cp_new, F, t.foff, ndata, nl.size, Sv, t.soff, st)) ||
+      (s = run_copies(c, cp_rem, F, t.foff, rem, rem_size, Sv, t.soff, st)))
+    return s;
+  if (dir == 1) {
+    if ((s = run_gemm(c, proj_lr, F, t.foff, X0, t.xoff, rem, rem_size, st))) return s;
+  } else {
+    if ((s = run_gemm(c, proj_rl, X0, t.xoff, F, t.foff, rem, rem_size, st))) return s;
+  }
+  const SiteLayout nlay = nl;
+  dfree(m.data, st);
+  m.lay = nlay;
+  m.data = scr.keep(ndata);
+  t.rem = scr.keep(rem);
+  t.rem_size = rem_size;
+  return DMRG3S_OK;
+}
+
+// Step 5: the remainder S V^dagger (L->R) or U S (R->L) of t multiplied into
+// the neighbour site nb, which replaces it (the grouped FP64 GEMM of one
+// launch over its blocks); frees t.rem.
+dmrg3s_status update_neighbour(State& S, int dir, int nb, Trunc& t, cudaStream_t st) {
+  Context* c = S.c;
+  const Bond& nbnd = t.nbnd;
+  const std::vector<Sector>& secs = t.secs;
+  const std::vector<int>& sec_of_new = t.sec_of_new;
+  const std::vector<int64_t>& rem_off = t.rem_off;
+  dmrg3s_status s;
+  Scratch scr(c, st);
+  DevSite& nbs = S.M[nb];
+  SiteLayout nnl;
+  if (dir == 1)
+    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbnd, nbs.lay.right, &nnl);
+  else
+    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbs.lay.left, nbnd, &nnl);
+  GemmStage g;
+  for (const Block& ob : nnl.blocks) {
+    const int ss = ob.a;
+    std::vector<GemmSeg> sg;
+    if (dir == 1) {       // B~[s](kn, j2) = SV_kn (nk x base) . B[s](jbase, j2)
+      const int kn = ob.b;
+      const Sector& sc = secs[sec_of_new[kn]];
+      if (sc.base > 0) {
+        const int bi = nbs.lay.block_of(ss, sc.jbase);
+        if (bi >= 0 && nbs.lay.blocks[bi].c == ob.c) {
+          GemmSeg q{};
+          q.offA = rem_off[kn];
+          q.lda = (int32_t)sc.base;
+          q.offB = nbs.lay.blocks[bi].off;
+          q.ldb = (int32_t)nbs.lay.blocks[bi].cols;
+          q.K = (int32_t)sc.base;
+          q.scale = 1.0;
+          sg.push_back(q);
+        }
+      }
+    } else {              // A~[s](i2, kn) = A[s](i2, jbase) . US_kn (base x nk)
+      const int kn = ob.c;
+      const Sector& sc = secs[sec_of_new[kn]];
+      if (sc.base > 0) {
+        const int bi = nbs.lay.block_of(ss, ob.b);
+        if (bi >= 0 && nbs.lay.blocks[bi].c == sc.jbase) {
+          GemmSeg q{};
+          q.offA = nbs.lay.blocks[bi].off;
+          q.lda = (int32_t)nbs.lay.blocks[bi].cols;
+          q.offB = rem_off[kn];
+          q.ldb = (int32_t)sc.keep;
+          q.K = (int32_t)sc.base;
+          q.scale = 1.0;
+          sg.push_back(q);
+        }
+      }
+    }
+    g.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, sg);
+  }
+  double* nbdata;
+  if ((s = scr.get(&nbdata, nnl.size))) return s;
+  if (dir == 1) {
+    if ((s = run_gemm(c, g, t.rem, t.rem_size, nbs.data, nbs.lay.size, nbdata, nnl.size, st))) return s;
+  } else {
+    if ((s = run_gemm(c, g, nbs.data, nbs.lay.size, t.rem, t.rem_size, nbdata, nnl.size, st))) return s;
+  }
+  dfree(t.rem, st);
+  t.rem = nullptr;
+  dfree(nbs.data, st);
+  nbs.lay = nnl;
+  nbs.data = scr.keep(nbdata);
+  return DMRG3S_OK;
+}
+
 dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info* info,
                            cudaStream_t st) {
   Context* c = S.c;
@@ -452,361 +857,44 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   }
   done(ph);
   ph = phase(kProfSvd);
-  // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L)
-  // Sector k of M~ is a rows x cols matrix X (rows: (s, a_l) for L->R, the
-  // expanded left states for R->L).  It is gathered column-major in the tall
-  // orientation m >= n that the FP64 SVD routine needs: X itself when
-  // rows >= cols, X^T otherwise.
-  std::vector<Charge> charges;
-  for (int k = 0; k < old.nsec(); ++k) charges.push_back(old.q[k]);
-  if (expand)
-    for (int k = 0; k < fp.bond.nsec(); ++k) charges.push_back(fp.bond.q[k]);
-  std::sort(charges.begin(), charges.end());
-  charges.erase(std::unique(charges.begin(), charges.end()), charges.end());
-  const Bond& keepb = dir == 1 ? m.lay.left : m.lay.right;   // the bond that is not expanded
-  std::vector<Sector> secs;
-  std::vector<CopyTask> gather_m, gather_p;
-  int64_t xoff = 0;
-  // task placing a row-major block (rb x cb) at (row0, col0) of sector sc's X
-  auto place = [](const Sector& sc, int64_t src_off, int64_t rb, int64_t cb, int64_t row0,
-                  int64_t col0) {
-    if (sc.tall)   // column-major X (ld rows): write X^T rows = block columns
-      return copy_task(src_off, cb, sc.off + col0 * sc.rows + row0, sc.rows, cb, rb, true);
-    return copy_task(src_off, cb, sc.off + row0 * sc.cols + col0, sc.cols, rb, cb, false);
-  };
-  for (const Charge& q : charges) {
-    Sector sc;
-    sc.q = q;
-    sc.jbase = old.find(q);
-    if (m.lay.nsym == 0) sc.jbase = 0;
-    const int kp = expand ? (m.lay.nsym ? fp.bond.find(q) : 0) : -1;
-    const int64_t pwidth = kp >= 0 ? fp.bond.dim[kp] : 0;
-    sc.base = sc.jbase >= 0 ? old.dim[sc.jbase] : 0;
-    const int64_t exp_dim = sc.base + pwidth;
-    // the other dimension: sum over physical states of the matching sector of keepb
-    int64_t other = 0;
-    std::vector<std::pair<int, int64_t>> parts;   // (s, offset along the other dimension)
-    for (int ss = 0; ss < m.lay.d; ++ss) {
-      Charge qo = dir == 1 ? sub(q, m.lay.qp[ss]) : add(q, m.lay.qp[ss]);
-      const int io = m.lay.nsym ? keepb.find(qo) : 0;
-      if (io < 0) continue;
-      parts.push_back({ss, other});
-      other += keepb.dim[io];
-    }
-    if (other == 0 || exp_dim == 0) continue;
-    sc.rows = dir == 1 ? other : exp_dim;
-    sc.cols = dir == 1 ? exp_dim : other;
-    sc.tall = sc.rows >= sc.cols;
-    sc.m = sc.tall ? sc.rows : sc.cols;
-    sc.n = sc.tall ? sc.cols : sc.rows;
-    sc.r = sc.n;
-    sc.vt_only = dir == 1 ? !sc.tall : sc.tall;
-    sc.off = xoff;
-    xoff += sc.rows * sc.cols;
-    for (auto& pr : parts) {
-      const int ss = pr.first;
-      const int64_t o2 = pr.second;
-      Charge qo = dir == 1 ? sub(q, m.lay.qp[ss]) : add(q, m.lay.qp[ss]);
-      const int io = m.lay.nsym ? keepb.find(qo) : 0;
-      const int64_t dio = keepb.dim[io];
-      if (sc.jbase >= 0) {
-        // M* block (ss, io, jbase) for L->R; (ss, jbase, io) for R->L
-        const int bi = dir == 1 ? m.lay.block_of(ss, io) : m.lay.block_of(ss, sc.jbase);
-        if (bi >= 0) {
-          const Block& bk = m.lay.blocks[bi];
-          const bool match = dir == 1 ? bk.c == sc.jbase : bk.c == io;
-          if (match) {
-            if (dir == 1)
-              gather_m.push_back(place(sc, bk.off, dio, sc.base, o2, 0));
-            else
-              gather_m.push_back(place(sc, bk.off, sc.base, dio, 0, o2));
-          }
-        }
-      }
-      if (kp >= 0) {
-        const int bi = dir == 1 ? pl.block_of(ss, io) : pl.block_of(ss, kp);
-        if (bi >= 0) {
-          const Block& bk = pl.blocks[bi];
-          const bool match = dir == 1 ? bk.c == kp : bk.c == io;
-          if (match) {
-            if (dir == 1)
-              gather_p.push_back(place(sc, bk.off, dio, pwidth, o2, sc.base));
-            else
-              gather_p.push_back(place(sc, bk.off, pwidth, dio, sc.base, o2));
-          }
-        }
-      }
-    }
-    secs.push_back(sc);
-  }
+  // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L), gathered
+  Trunc t;
+  prepare_truncation(m.lay, dir, expand, fp, pl, o.svd, &t);
   double* X;
-  if ((s = scr.get(&X, xoff))) return s;
-  cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(xoff, 1) * sizeof(double), st);
-  if ((s = run_copies(c, gather_m, m.data, m.lay.size, X, xoff, nullptr, 0, st))) return s;
-  if (expand && (s = run_copies(c, gather_p, P, pl.size, X, xoff, nullptr, 0, st))) return s;
+  if ((s = scr.get(&X, t.xoff))) return s;
+  cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(t.xoff, 1) * sizeof(double), st);
+  if ((s = run_copies(c, t.gather_m, m.data, m.lay.size, X, t.xoff, nullptr, 0, st))) return s;
+  if (expand && (s = run_copies(c, t.gather_p, P, pl.size, X, t.xoff, nullptr, 0, st))) return s;
   scr.drop(P);
-  // ---- 4. SVD per sector (FP64, on the tall orientation):
-  // X_tall = U S VT with U (m x r, ld m), VT (r x n, ld r), r = n.  cuSOLVER
-  // gesvd runs the independent sectors concurrently on the workers' streams;
-  // the Jacobi SVD (svd.cu) runs every sector in each of its launches.
-  int64_t foff = 0, soff = 0;
-  for (Sector& sc : secs) {
-    sc.offU = foff;
-    if (!sc.vt_only) foff += sc.m * sc.r;
-    sc.offVT = foff;
-    foff += sc.r * sc.n;
-    sc.offS = soff;
-    soff += sc.r;
-  }
-  double *F, *Sv;
-  int* dinfo;
-  double* dinfo_d = nullptr;
-  if ((s = scr.get(&F, foff)) || (s = scr.get(&Sv, soff)) ||
-      (s = scr.get(&dinfo_d, (int64_t)secs.size() + 1)))
+  // ---- 4. SVD per sector (FP64, on the tall orientation): cuSOLVER gesvd
+  // runs the independent sectors concurrently on the workers' streams; the
+  // Jacobi SVD (svd.cu) runs every sector in each of its launches.  The SVD
+  // overwrites its input: the projected remainder reads a copy of X, which
+  // also restores X when the Jacobi sweeps do not converge.
+  double *F, *Sv, *dinfo_d, *X0 = nullptr;
+  if ((s = scr.get(&F, t.foff)) || (s = scr.get(&Sv, t.soff)) ||
+      (s = scr.get(&dinfo_d, (int64_t)t.secs.size() + 1)))
     return s;
-  dinfo = reinterpret_cast<int*>(dinfo_d);
-  // the SVD overwrites its input: the projected remainder reads a copy of X,
-  // which also restores X when the Jacobi sweeps do not converge
-  double* X0 = nullptr;
-  bool any_proj = o.svd == DMRG3S_SVD_JACOBI;
-  for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
-  if (any_proj) {
-    if ((s = scr.get(&X0, xoff))) return s;
-    if ((s = cuda_ok(c, cudaMemcpyAsync(X0, X, (size_t)xoff * sizeof(double),
+  if (t.any_proj) {
+    if ((s = scr.get(&X0, t.xoff))) return s;
+    if ((s = cuda_ok(c, cudaMemcpyAsync(X0, X, (size_t)t.xoff * sizeof(double),
                                         cudaMemcpyDeviceToDevice, st), "copy of M~")))
       return s;
   }
-  std::vector<double> hs(std::max<int64_t>(soff, 1));
-  std::vector<int> hinfo(secs.size() + 1, 0);
-  if (o.svd == DMRG3S_SVD_JACOBI) {
-    std::vector<SvdJob> jobs(secs.size());
-    for (size_t k = 0; k < secs.size(); ++k) {
-      const Sector& sc = secs[k];
-      jobs[k].m = sc.m;
-      jobs[k].n = sc.n;
-      jobs[k].offA = sc.off;
-      jobs[k].offS = sc.offS;
-      jobs[k].offVT = sc.offVT;
-      jobs[k].offU = sc.vt_only ? -1 : sc.offU;
-    }
-    int nw = (int)secs.size() / 4;
-    nw = std::min(std::max(nw, 4), (int)S.svd.size());
-    if ((s = svd_jacobi(c, S.svd, nw, jobs, X, Sv, F, F, hinfo.data(), st, nullptr,
-                        &info->svd_sweeps)))
-      return s;
-    bool conv = true;
-    for (size_t k = 0; k < secs.size(); ++k) conv = conv && hinfo[k] == 0;
-    if (!conv) {   // redo this update's SVD with gesvd on the restored X
-      info->svd_fallback = true;
-      if ((s = cuda_ok(c, cudaMemcpyAsync(X, X0, (size_t)xoff * sizeof(double),
-                                          cudaMemcpyDeviceToDevice, st), "copy of M~")) ||
-          (s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
-          (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
-                                          cudaMemcpyDeviceToHost, st), "SVD info")))
-        return s;
-    }
-  } else if ((s = svd_sectors(S, secs, X, F, Sv, dinfo, st)) ||
-             (s = cuda_ok(c, cudaMemcpyAsync(hinfo.data(), dinfo, secs.size() * sizeof(int),
-                                             cudaMemcpyDeviceToHost, st), "SVD info"))) {
-    return s;
-  }
-  if ((s = cuda_ok(c, cudaMemcpyAsync(hs.data(), Sv, soff * sizeof(double), cudaMemcpyDeviceToHost, st),
-                   "singular values")) ||
-      (s = cuda_ok(c, cudaStreamSynchronize(st), "SVD")))
+  std::vector<double> hs;
+  if ((s = svd_all(S, o.svd, t.secs, X, X0, t.xoff, F, Sv, reinterpret_cast<int*>(dinfo_d), t.soff,
+                   &hs, &info->svd_fallback, &info->svd_sweeps, st)))
     return s;
   scr.drop(X);
   scr.drop(dinfo_d);
-  for (size_t k = 0; k < secs.size(); ++k)
-    if (hinfo[k] != 0) return fail(c, DMRG3S_ERR_NUMERIC, "SVD did not converge in a sector");
-  // global selection: order by (-s, sector, index), cut at eps * s_max and m_max
-  std::vector<std::tuple<double, int, int>> cand;
-  double smax = 0.0, total = 0.0;
-  for (size_t k = 0; k < secs.size(); ++k)
-    for (int64_t j = 0; j < secs[k].r; ++j) {
-      const double v = hs[secs[k].offS + j];
-      if (!(v == v)) return fail(c, DMRG3S_ERR_NUMERIC, "NaN singular value");
-      cand.emplace_back(-v, (int)k, (int)j);
-      smax = std::max(smax, v);
-      total += v * v;
-    }
-  std::sort(cand.begin(), cand.end());
-  double kept_w = 0.0;
-  int nkeep = 0;
-  for (auto& t : cand) {
-    const double v = -std::get<0>(t);
-    if (!(v > o.eps * smax) || nkeep >= o.m_max) break;
-    secs[std::get<1>(t)].keep++;
-    kept_w += v * v;
-    ++nkeep;
-  }
-  info->discarded = total - kept_w;
-  info->new_dim = nkeep;
-  if (nkeep == 0) return fail(c, DMRG3S_ERR_NUMERIC, "truncation kept no state");
-  // ---- new bond
-  Bond nbnd;
-  nbnd.nsym = m.lay.nsym;
-  std::vector<int> sec_of_new;
-  for (size_t k = 0; k < secs.size(); ++k)
-    if (secs[k].keep > 0) {
-      nbnd.q.push_back(secs[k].q);
-      nbnd.dim.push_back(secs[k].keep);
-      sec_of_new.push_back((int)k);
-    }
-  nbnd.off.assign(nbnd.dim.size() + 1, 0);
-  for (size_t k = 0; k < nbnd.dim.size(); ++k) nbnd.off[k + 1] = nbnd.off[k] + nbnd.dim[k];
-  nbnd.total = nbnd.off.back();
-  if (nbnd.nsym == 0) nbnd.q.assign(1, Charge{});
-  // ---- new centre tensor A~ (L->R) or B~ (R->L), and the remainder SV / US.
-  // With X = U_X S V_X^T: tall sectors have U_X = U, V_X = VT^T; wide ones
-  // (X^T was factorised) have U_X = VT^T, V_X = U.
-  SiteLayout nl;
-  if (dir == 1)
-    make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, m.lay.left, nbnd, &nl);
-  else
-    make_site_from(m.lay.nsym, m.lay.d, m.lay.qp, nbnd, m.lay.right, &nl);
-  // copy tasks reading U_X[row0 + a, c] (dst a x c) and V_X[col0 + a, c] (dst c x a, or a x c)
-  auto ux = [](const Sector& sc, int64_t row0, int64_t dst, int64_t ldd, int64_t na, int64_t nc,
-               int cs) {   // dst (na x nc): U_X[row0 + a, c] * S[c]
-    if (sc.tall) return copy_task(sc.offU + row0, sc.m, dst, ldd, na, nc, true, -1, cs);
-    return copy_task(sc.offVT + row0 * sc.r, sc.r, dst, ldd, na, nc, false, -1, cs);
-  };
-  auto vxt = [](const Sector& sc, int64_t col0, int64_t dst, int64_t ldd, int64_t nc, int64_t na,
-                int rs) {  // dst (nc x na): V_X[col0 + a, c] * S[c]
-    if (sc.tall) return copy_task(sc.offVT + col0 * sc.r, sc.r, dst, ldd, nc, na, true, rs, -1);
-    return copy_task(sc.offU + col0, sc.m, dst, ldd, nc, na, false, rs, -1);
-  };
-  std::vector<CopyTask> cp_new, cp_rem;
-  GemmStage proj_lr, proj_rl;   // remainder by projection (vt_only sectors)
-  proj_lr.ta = Trans::T;
-  proj_lr.tb = Trans::N;
-  proj_rl.ta = Trans::T;
-  proj_rl.tb = Trans::N;
-  std::vector<int64_t> rem_off(nbnd.nsec(), 0);
-  int64_t rem_size = 0;
-  for (int kn = 0; kn < nbnd.nsec(); ++kn) {
-    const Sector& sc = secs[sec_of_new[kn]];
-    const int64_t nk = sc.keep;
-    rem_off[kn] = rem_size;
-    rem_size += nk * sc.base;
-    int64_t o2 = 0;
-    for (int ss = 0; ss < m.lay.d; ++ss) {
-      Charge qo = dir == 1 ? sub(sc.q, m.lay.qp[ss]) : add(sc.q, m.lay.qp[ss]);
-      const int io = m.lay.nsym ? keepb.find(qo) : 0;
-      if (io < 0) continue;
-      const int64_t dio = keepb.dim[io];
-      const int bi = dir == 1 ? nl.block_of(ss, io) : nl.block_of(ss, kn);
-      if (bi >= 0) {
-        const Block& bk = nl.blocks[bi];
-        if (dir == 1)   // A~ block (dio x nk) = U_X[o2 + a, c]
-          cp_new.push_back(ux(sc, o2, bk.off, bk.cols, dio, nk, -1));
-        else            // B~ block (nk x dio) = V_X[o2 + a, c]^T
-          cp_new.push_back(vxt(sc, o2, bk.off, bk.cols, nk, dio, -1));
-      }
-      o2 += dio;
-    }
-    if (sc.base > 0 && sc.vt_only) {
-      // L->R (X^T factorised): SV[c, j] = sum_a VT[c, a] X[a, j], X row-major (rows x cols)
-      // R->L (X factorised):   US[i, c] = sum_a X[i, a] VT[c, a], X column-major (rows x cols)
-      // Both read VT[c, a] at offVT + a r + c, i.e. K x nk row-major with ld r.
-      GemmSeg q{};
-      q.scale = 1.0;
-      q.K = (int32_t)sc.n;
-      if (dir == 1) {     // C (nk x base) = VT^T^T . X: A = VT (K x nk, ld r), B = X (K x base, ld cols)
-        q.offA = sc.offVT;
-        q.lda = (int32_t)sc.r;
-        q.offB = sc.off;
-        q.ldb = (int32_t)sc.cols;
-        proj_lr.add(rem_off[kn], (int)sc.base, (int)nk, (int)sc.base, {q});
-      } else {            // C (base x nk) = X^T^T . VT^T: A = X (K x base, ld rows), B = VT (K x nk, ld r)
-        q.offA = sc.off;
-        q.lda = (int32_t)sc.rows;
-        q.offB = sc.offVT;
-        q.ldb = (int32_t)sc.r;
-        proj_rl.add(rem_off[kn], (int)nk, (int)sc.base, (int)nk, {q});
-      }
-    } else if (sc.base > 0) {
-      if (dir == 1)     // SV (nk x base) = S[c] V_X[col, c]^T
-        cp_rem.push_back(vxt(sc, 0, rem_off[kn], sc.base, nk, sc.base, (int)sc.offS));
-      else              // US (base x nk) = U_X[row, c] S[c]
-        cp_rem.push_back(ux(sc, 0, rem_off[kn], nk, sc.base, nk, (int)sc.offS));
-    }
-  }
-  double *ndata, *rem;
-  if ((s = scr.get(&ndata, nl.size)) || (s = scr.get(&rem, rem_size))) return s;
-  cudaMemsetAsync(ndata, 0, (size_t)std::max<int64_t>(nl.size, 1) * sizeof(double), st);
-  if ((s = run_copies(c, cp_new, F, foff, ndata, nl.size, Sv, soff, st)) ||
-      (s = run_copies(c, cp_rem, F, foff, rem, rem_size, Sv, soff, st)))
-    return s;
-  if (dir == 1) {
-    if ((s = run_gemm(c, proj_lr, F, foff, X0, xoff, rem, rem_size, st))) return s;
-  } else {
-    if ((s = run_gemm(c, proj_rl, X0, xoff, F, foff, rem, rem_size, st))) return s;
-  }
+  if ((s = truncate_centre(S, dir, o, t, F, Sv, X0, hs.data(), info, st))) return s;
   scr.drop(X0);
   scr.drop(F);
   scr.drop(Sv);
   done(ph);
   ph = phase(kProfRemainder);
   // ---- 5. remainder into the neighbour
-  DevSite& nbs = S.M[nb];
-  SiteLayout nnl;
-  if (dir == 1)
-    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbnd, nbs.lay.right, &nnl);
-  else
-    make_site_from(nbs.lay.nsym, nbs.lay.d, nbs.lay.qp, nbs.lay.left, nbnd, &nnl);
-  GemmStage g;
-  for (const Block& ob : nnl.blocks) {
-    const int ss = ob.a;
-    std::vector<GemmSeg> sg;
-    if (dir == 1) {       // B~[s](kn, j2) = SV_kn (nk x base) . B[s](jbase, j2)
-      const int kn = ob.b;
-      const Sector& sc = secs[sec_of_new[kn]];
-      if (sc.base > 0) {
-        const int bi = nbs.lay.block_of(ss, sc.jbase);
-        if (bi >= 0 && nbs.lay.blocks[bi].c == ob.c) {
-          GemmSeg q{};
-          q.offA = rem_off[kn];
-          q.lda = (int32_t)sc.base;
-          q.offB = nbs.lay.blocks[bi].off;
-          q.ldb = (int32_t)nbs.lay.blocks[bi].cols;
-          q.K = (int32_t)sc.base;
-          q.scale = 1.0;
-          sg.push_back(q);
-        }
-      }
-    } else {              // A~[s](i2, kn) = A[s](i2, jbase) . US_kn (base x nk)
-      const int kn = ob.c;
-      const Sector& sc = secs[sec_of_new[kn]];
-      if (sc.base > 0) {
-        const int bi = nbs.lay.block_of(ss, ob.b);
-        if (bi >= 0 && nbs.lay.blocks[bi].c == sc.jbase) {
-          GemmSeg q{};
-          q.offA = nbs.lay.blocks[bi].off;
-          q.lda = (int32_t)nbs.lay.blocks[bi].cols;
-          q.offB = rem_off[kn];
-          q.ldb = (int32_t)sc.keep;
-          q.K = (int32_t)sc.base;
-          q.scale = 1.0;
-          sg.push_back(q);
-        }
-      }
-    }
-    g.add(ob.off, (int)ob.cols, (int)ob.rows, (int)ob.cols, sg);
-  }
-  double* nbdata;
-  if ((s = scr.get(&nbdata, nnl.size))) return s;
-  if (dir == 1) {
-    if ((s = run_gemm(c, g, rem, rem_size, nbs.data, nbs.lay.size, nbdata, nnl.size, st))) return s;
-  } else {
-    if ((s = run_gemm(c, g, nbs.data, nbs.lay.size, rem, rem_size, nbdata, nnl.size, st))) return s;
-  }
-  scr.drop(rem);
-  dfree(m.data, st);
-  dfree(nbs.data, st);
-  m.lay = nl;
-  m.data = scr.keep(ndata);
-  nbs.lay = nnl;
-  nbs.data = scr.keep(nbdata);
+  if ((s = update_neighbour(S, dir, nb, t, st))) return s;
   done(ph);
   ph = phase(kProfEnv);
   // ---- 6. environment of the truncated tensor; the neighbour's old one is stale
@@ -821,9 +909,472 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   done(ph);
   ph = phase(kProfEnergy);
   // ---- 7. energy after truncation at the neighbour
-  if ((s = rayleigh(S, nb, nbs.data, st, &info->e_f))) return s;
+  if ((s = rayleigh(S, nb, S.M[nb].data, st, &info->e_f))) return s;
   done(ph);
   return cuda_ok(c, cudaGetLastError(), "local update");
+}
+
+// ---- batched local updates: one update on each of several states (the
+// chains of a batch, one context), each contraction stage one launch over all
+// of them.  The operands of the merged launches are copied into arenas (every
+// tensor at a multiple of 32 elements) and the results copied back out.
+
+inline int64_t align32(int64_t v) { return (v + 31) / 32 * 32; }
+
+struct BItem {
+  State* S = nullptr;
+  int dir = 1;
+  double alpha = 0.0;
+  Opts o;
+  Info info;
+  bool expand = false;
+  FusedBond fp;          // P part of the expanded bond
+  SiteLayout pl;         // layout of P
+  const double* P = nullptr;   // P inside the expansion arena
+  Trunc t;
+  int64_t xb = 0, fb = 0, sb = 0;   // bases of this update in the combined X, F, Sv
+};
+
+dmrg3s_status upload_merged(Context* c, Kind kind, const std::vector<PlanPart>& parts, int64_t nA1,
+                            int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3, int64_t nC3,
+                            std::unique_ptr<DevicePlan>* out) {
+  Plan mp;
+  std::string err;
+  dmrg3s_status s = merge_plans(kind, parts, nA1, nB1, nOut2, nA3, nB3, nC3, &mp, &err);
+  if (s) return fail(c, s, "merged plan: " + err);
+  if ((s = upload_plan(std::move(mp), out)))
+    return fail(c, s, "uploading a merged contraction plan failed");
+  return DMRG3S_OK;
+}
+
+dmrg3s_status copy_in(Context* c, double* dst, const double* src, int64_t n, cudaStream_t st) {
+  if (n <= 0) return DMRG3S_OK;
+  return cuda_ok(c, cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    st), "arena copy");
+}
+
+// Step 1 for every item: one Lanczos recursion per precision over all items
+// of that precision (merged H_eff plans).
+dmrg3s_status batch_eig(Context* c, std::vector<BItem>& items, cudaStream_t st) {
+  dmrg3s_status s;
+  const dmrg3s_precision precs[3] = {DMRG3S_FP64, DMRG3S_TF32X3, DMRG3S_TF32};
+  for (dmrg3s_precision prec : precs) {
+    std::vector<BItem*> g;
+    for (BItem& it : items)
+      if (it.o.optimise && it.o.prec == prec) g.push_back(&it);
+    if (g.empty()) continue;
+    if (g.size() == 1) {   // one problem: its own cached plan, no arenas
+      BItem& it = *g[0];
+      State& S = *it.S;
+      const int i = S.centre;
+      const DevicePlan* hp;
+      if ((s = heff_plan(c, S.Lenv[i].lay, S.W[i], S.Renv[i].lay, S.M[i].lay, &hp))) return s;
+      const size_t cursor = (size_t)plan_ws_doubles(hp->host, prec) * sizeof(double);
+      if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, S.M[i].data, S.M[i].lay.size,
+                           it.o.kmax, it.o.tol, cursor, st, &it.info.lambda, &it.info.iters, prec)))
+        return s;
+      continue;
+    }
+    std::vector<PlanPart> parts(g.size());
+    std::vector<LzSpec> specs(g.size());
+    int64_t nL = 0, nR = 0, nX = 0;
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      const DevicePlan* hp;
+      if ((s = heff_plan(c, S.Lenv[i].lay, S.W[i], S.Renv[i].lay, S.M[i].lay, &hp))) return s;
+      PlanPart& q = parts[k];
+      q.p = &hp->host;
+      q.oA1 = nL;
+      q.oB1 = nX;
+      q.oB3 = nR;
+      q.oC3 = nX;
+      specs[k] = LzSpec{nX, S.M[i].lay.size, g[k]->o.kmax, g[k]->o.tol};
+      nL += align32(S.Lenv[i].lay.size);
+      nR += align32(S.Renv[i].lay.size);
+      nX += align32(S.M[i].lay.size);
+    }
+    std::unique_ptr<DevicePlan> dp;
+    if ((s = upload_merged(c, Kind::Heff, parts, nL, nX, 0, 0, nR, nX, &dp))) return s;
+    Scratch scr(c, st);
+    double *La, *Ra, *Xa;
+    if ((s = scr.get(&La, nL)) || (s = scr.get(&Ra, nR)) || (s = scr.get(&Xa, nX))) return s;
+    cudaMemsetAsync(Xa, 0, (size_t)nX * sizeof(double), st);
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      if ((s = copy_in(c, La + parts[k].oA1, S.Lenv[i].data, S.Lenv[i].lay.size, st)) ||
+          (s = copy_in(c, Ra + parts[k].oB3, S.Renv[i].data, S.Renv[i].lay.size, st)) ||
+          (s = copy_in(c, Xa + parts[k].oB1, S.M[i].data, S.M[i].lay.size, st)))
+        return s;
+    }
+    const size_t cursor = (size_t)plan_ws_doubles(dp->host, prec) * sizeof(double);
+    std::vector<double> theta;
+    std::vector<int> iters;
+    if ((s = lanczos_batch(c, *dp, La, Ra, Xa, nX, specs, cursor, st, prec, &theta, &iters)))
+      return s;
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      if ((s = copy_in(c, S.M[i].data, Xa + parts[k].oB1, S.M[i].lay.size, st))) return s;
+      g[k]->info.lambda = theta[k];
+      g[k]->info.iters = iters[k];
+    }
+    // the merged tables are freed (cudaFree) only after the device is done with them
+    if ((s = cuda_ok(c, cudaStreamSynchronize(st), "batched eigensolver"))) return s;
+  }
+  for (BItem& it : items)
+    if (!it.o.optimise) {
+      if ((s = rayleigh(*it.S, it.S->centre, it.S->M[it.S->centre].data, st, &it.info.lambda)))
+        return s;
+      it.info.iters = 0;
+    }
+  return DMRG3S_OK;
+}
+
+// Step 2 for every item with alpha != 0: one merged expansion launch set per
+// direction (alpha folded into each item's MPO coefficients); every item's P
+// stays in the arena `Pa` (owned by the caller's scratch) until gathered.
+dmrg3s_status batch_expand(Context* c, std::vector<BItem>& items, Scratch& keep, cudaStream_t st) {
+  dmrg3s_status s;
+  for (BItem& it : items) {
+    it.expand = it.alpha != 0.0;
+    if (!it.expand) continue;
+    State& S = *it.S;
+    const int i = S.centre;
+    const SiteLayout& ml = S.M[i].lay;
+    const MpoLayout& w = S.W[i];
+    const Bond& old = it.dir == 1 ? ml.right : ml.left;
+    fuse_bond(old, it.dir == 1 ? w.wr : w.wl, it.dir == 1 ? w.tr : w.tl, false, &it.fp);
+    if (it.dir == 1)
+      make_site_from(ml.nsym, ml.d, ml.qp, ml.left, it.fp.bond, &it.pl);
+    else
+      make_site_from(ml.nsym, ml.d, ml.qp, it.fp.bond, ml.right, &it.pl);
+  }
+  for (int dir = -1; dir <= 1; dir += 2) {
+    std::vector<BItem*> g;
+    for (BItem& it : items)
+      if (it.expand && it.dir == dir) g.push_back(&it);
+    if (g.empty()) continue;
+    std::vector<PlanPart> parts(g.size());
+    int64_t nE = 0, nM = 0, nP = 0;
+    std::vector<int64_t> oE(g.size()), oM(g.size()), oP(g.size());
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      const DevEnv& env = dir == 1 ? S.Lenv[i] : S.Renv[i];
+      const DevicePlan* ep;
+      if ((s = expand_plan(c, dir, env.lay, S.W[i], S.M[i].lay, g[k]->pl, g[k]->fp, &ep))) return s;
+      oE[k] = nE;
+      oM[k] = nM;
+      oP[k] = nP;
+      nE += align32(env.lay.size);
+      nM += align32(S.M[i].lay.size);
+      nP += align32(g[k]->pl.size);
+      PlanPart& q = parts[k];
+      q.p = &ep->host;
+      q.oA1 = dir == 1 ? oE[k] : oM[k];
+      q.oB1 = dir == 1 ? oM[k] : oE[k];
+      q.oOut2 = oP[k];
+      q.c2scale = g[k]->alpha;
+    }
+    std::unique_ptr<DevicePlan> dp;
+    const Kind kind = dir == 1 ? Kind::ExpandLR : Kind::ExpandRL;
+    if ((s = upload_merged(c, kind, parts, dir == 1 ? nE : nM, dir == 1 ? nM : nE, nP, 0, 0, 0, &dp)))
+      return s;
+    if ((size_t)dp->host.ws1 * sizeof(double) > c->ws_bytes)
+      return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the expansion");
+    Scratch scr(c, st);
+    double *Ea, *Ma, *Pa;
+    if ((s = scr.get(&Ea, nE)) || (s = scr.get(&Ma, nM)) || (s = keep.get(&Pa, nP))) return s;
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      const DevEnv& env = dir == 1 ? S.Lenv[i] : S.Renv[i];
+      if ((s = copy_in(c, Ea + oE[k], env.data, env.lay.size, st)) ||
+          (s = copy_in(c, Ma + oM[k], S.M[i].data, S.M[i].lay.size, st)))
+        return s;
+      g[k]->P = Pa + oP[k];
+    }
+    if ((s = run_plan(c, *dp, dir == 1 ? Ea : Ma, dir == 1 ? Ma : Ea, reinterpret_cast<double*>(c->ws),
+                      Pa, 1.0, nullptr, nullptr, nullptr, st)))
+      return fail(c, s, "merged expansion launch");
+    if ((s = cuda_ok(c, cudaStreamSynchronize(st), "batched expansion"))) return s;
+  }
+  return DMRG3S_OK;
+}
+
+// Steps 3 to 5 for every item: the sectors of every item gathered into one
+// buffer, the SVD of all sectors of all items in one call (cuSOLVER lanes or
+// the Jacobi launches over every sector), then per item the selection, the new
+// centre tensor and the neighbour.
+dmrg3s_status batch_truncate(Context* c, std::vector<BItem>& items, dmrg3s_svd_method method,
+                             cudaStream_t st) {
+  dmrg3s_status s;
+  int64_t nX = 0, nF = 0, nS = 0;
+  size_t nsec = 0;
+  bool any_proj = method == DMRG3S_SVD_JACOBI;
+  for (BItem& it : items) {
+    State& S = *it.S;
+    prepare_truncation(S.M[S.centre].lay, it.dir, it.expand, it.fp, it.pl, method, &it.t);
+    it.xb = nX;
+    it.fb = nF;
+    it.sb = nS;
+    nX += align32(it.t.xoff);
+    nF += align32(it.t.foff);
+    nS += align32(it.t.soff);
+    nsec += it.t.secs.size();
+    any_proj = any_proj || it.t.any_proj;
+  }
+  Scratch scr(c, st);
+  double *X, *F, *Sv, *dinfo_d, *X0 = nullptr;
+  if ((s = scr.get(&X, nX)) || (s = scr.get(&F, nF)) || (s = scr.get(&Sv, nS)) ||
+      (s = scr.get(&dinfo_d, (int64_t)nsec + 1)))
+    return s;
+  cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(nX, 1) * sizeof(double), st);
+  std::vector<Sector> all;
+  all.reserve(nsec);
+  for (BItem& it : items) {
+    State& S = *it.S;
+    const DevSite& m = S.M[S.centre];
+    if ((s = run_copies(c, it.t.gather_m, m.data, m.lay.size, X + it.xb, it.t.xoff, nullptr, 0, st)))
+      return s;
+    if (it.expand &&
+        (s = run_copies(c, it.t.gather_p, it.P, it.pl.size, X + it.xb, it.t.xoff, nullptr, 0, st)))
+      return s;
+    for (Sector sc : it.t.secs) {
+      sc.off += it.xb;
+      sc.offU += it.fb;
+      sc.offVT += it.fb;
+      sc.offS += it.sb;
+      all.push_back(sc);
+    }
+  }
+  if (any_proj) {
+    if ((s = scr.get(&X0, nX))) return s;
+    if ((s = cuda_ok(c, cudaMemcpyAsync(X0, X, (size_t)nX * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        st), "copy of M~")))
+      return s;
+  }
+  std::vector<double> hs;
+  bool fallback = false;
+  int sweeps = 0;
+  if ((s = svd_all(*items[0].S, method, all, X, X0, nX, F, Sv, reinterpret_cast<int*>(dinfo_d), nS,
+                   &hs, &fallback, &sweeps, st)))
+    return s;
+  scr.drop(X);
+  for (BItem& it : items) {
+    it.info.svd_fallback = fallback;
+    it.info.svd_sweeps = sweeps;
+    State& S = *it.S;
+    if ((s = truncate_centre(S, it.dir, it.o, it.t, F + it.fb, Sv + it.sb, X0 ? X0 + it.xb : nullptr,
+                             hs.data() + it.sb, &it.info, st)) ||
+        (s = update_neighbour(S, it.dir, S.centre + it.dir, it.t, st)))
+      return s;
+  }
+  return DMRG3S_OK;
+}
+
+// Step 6 for every item: the environment of the truncated centre tensor, one
+// merged launch set per direction; the centres then move to the neighbours.
+dmrg3s_status batch_env(Context* c, std::vector<BItem>& items, cudaStream_t st) {
+  dmrg3s_status s;
+  for (int dir = -1; dir <= 1; dir += 2) {
+    std::vector<BItem*> g;
+    for (BItem& it : items)
+      if (it.dir == dir) g.push_back(&it);
+    if (g.empty()) continue;
+    std::vector<PlanPart> parts(g.size());
+    std::vector<EnvLayout> outl(g.size());
+    std::vector<int64_t> oE(g.size()), oA(g.size()), oO(g.size());
+    int64_t nE = 0, nA = 0, nO = 0;
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      const MpoLayout& w = S.W[i];
+      const DevSite& a = S.M[i];
+      const DevEnv& src = dir == 1 ? S.Lenv[i] : S.Renv[i];
+      if (!src.valid)
+        return fail(c, DMRG3S_ERR_ARG, "environment recursion from an invalid environment");
+      make_env_from(a.lay.nsym, dir == 1 ? w.wr : w.wl, dir == 1 ? w.tr : w.tl,
+                    dir == 1 ? a.lay.right : a.lay.left, &outl[k]);
+      const DevicePlan* p;
+      if ((s = env_plan(c, dir, src.lay, w, a.lay, outl[k], &p))) return s;
+      oE[k] = nE;
+      oA[k] = nA;
+      oO[k] = nO;
+      nE += align32(src.lay.size);
+      nA += align32(a.lay.size);
+      nO += align32(outl[k].size);
+      PlanPart& q = parts[k];
+      q.p = &p->host;
+      q.oA1 = dir == 1 ? oE[k] : oA[k];
+      q.oB1 = dir == 1 ? oA[k] : oE[k];
+      q.oA3 = oA[k];
+      q.oC3 = oO[k];
+    }
+    std::unique_ptr<DevicePlan> dp;
+    const Kind kind = dir == 1 ? Kind::EnvLR : Kind::EnvRL;
+    if ((s = upload_merged(c, kind, parts, dir == 1 ? nE : nA, dir == 1 ? nA : nE, 0, nA, 0, nO,
+                           &dp)))
+      return s;
+    if ((size_t)(dp->host.ws1 + dp->host.ws2) * sizeof(double) > c->ws_bytes)
+      return fail(c, DMRG3S_ERR_OOM, "context workspace too small for the environment update");
+    Scratch scr(c, st);
+    double *Ea, *Aa, *Oa;
+    if ((s = scr.get(&Ea, nE)) || (s = scr.get(&Aa, nA)) || (s = scr.get(&Oa, nO))) return s;
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      const DevEnv& src = dir == 1 ? S.Lenv[i] : S.Renv[i];
+      if ((s = copy_in(c, Ea + oE[k], src.data, src.lay.size, st)) ||
+          (s = copy_in(c, Aa + oA[k], S.M[i].data, S.M[i].lay.size, st)))
+        return s;
+    }
+    double* ws1 = reinterpret_cast<double*>(c->ws);
+    double* ws2 = ws1 + dp->host.ws1;
+    if ((s = run_plan(c, *dp, dir == 1 ? Ea : Aa, dir == 1 ? Aa : Ea, ws1, ws2, 1.0, Aa, ws2, Oa,
+                      st)))
+      return fail(c, s, "merged environment update launch");
+    for (size_t k = 0; k < g.size(); ++k) {
+      State& S = *g[k]->S;
+      const int i = S.centre;
+      double* nd;
+      if ((s = dalloc(c, &nd, outl[k].size, st))) return s;
+      if ((s = copy_in(c, nd, Oa + oO[k], outl[k].size, st))) {
+        dfree(nd, st);
+        return s;
+      }
+      // the environment built from the truncated tensor; the one on its other
+      // side (built from the old tensor) is stale
+      DevEnv& dst = dir == 1 ? S.Lenv[i + 1] : S.Renv[i - 1];
+      (dir == 1 ? S.Renv[i] : S.Lenv[i]).valid = false;
+      dfree(dst.data, st);
+      dst.data = nd;
+      dst.lay = outl[k];
+      dst.valid = true;
+      S.centre = i + dir;
+    }
+    if ((s = cuda_ok(c, cudaStreamSynchronize(st), "batched environment update"))) return s;
+  }
+  return DMRG3S_OK;
+}
+
+// Step 7 for every item: E_f = <x|H_eff|x> / <x|x> at the new centre, one
+// merged FP64 H_eff launch set and one pair of reductions for all items.
+dmrg3s_status batch_energy(Context* c, std::vector<BItem>& items, cudaStream_t st) {
+  dmrg3s_status s;
+  std::vector<PlanPart> parts(items.size());
+  std::vector<std::pair<int64_t, int64_t>> ranges(items.size());
+  int64_t nL = 0, nR = 0, nX = 0;
+  for (size_t k = 0; k < items.size(); ++k) {
+    State& S = *items[k].S;
+    const int i = S.centre;
+    if (!S.Lenv[i].valid || !S.Renv[i].valid)
+      return fail(c, DMRG3S_ERR_ARG, "environments of the new centre are not built");
+    const DevicePlan* hp;
+    if ((s = heff_plan(c, S.Lenv[i].lay, S.W[i], S.Renv[i].lay, S.M[i].lay, &hp))) return s;
+    PlanPart& q = parts[k];
+    q.p = &hp->host;
+    q.oA1 = nL;
+    q.oB1 = nX;
+    q.oB3 = nR;
+    q.oC3 = nX;
+    ranges[k] = {nX, S.M[i].lay.size};
+    nL += align32(S.Lenv[i].lay.size);
+    nR += align32(S.Renv[i].lay.size);
+    nX += align32(S.M[i].lay.size);
+  }
+  std::unique_ptr<DevicePlan> dp;
+  if ((s = upload_merged(c, Kind::Heff, parts, nL, nX, 0, 0, nR, nX, &dp))) return s;
+  if ((size_t)(dp->host.ws1 + dp->host.ws2) * sizeof(double) > c->ws_bytes)
+    return fail(c, DMRG3S_ERR_OOM, "context workspace too small for H_eff");
+  std::vector<LzChunk> hch;
+  std::vector<LzChain> hcn;
+  lz_layout(ranges, 2 * plan_ctas(), &hch, &hcn);
+  const int nch = (int)hch.size();
+  Scratch scr(c, st);
+  double *La, *Ra, *Xa, *Ya, *part, *tabs;
+  const int64_t tab_doubles =
+      (int64_t)((hch.size() * sizeof(LzChunk) + hcn.size() * sizeof(LzChain)) / sizeof(double)) + 2;
+  if ((s = scr.get(&La, nL)) || (s = scr.get(&Ra, nR)) || (s = scr.get(&Xa, nX)) ||
+      (s = scr.get(&Ya, nX)) || (s = scr.get(&part, 2 * (int64_t)nch)) ||
+      (s = scr.get(&tabs, tab_doubles)))
+    return s;
+  LzChunk* dch = reinterpret_cast<LzChunk*>(tabs);
+  LzChain* dcn = reinterpret_cast<LzChain*>(dch + nch);
+  if ((s = cuda_ok(c, cudaMemcpyAsync(dch, hch.data(), sizeof(LzChunk) * nch,
+                                      cudaMemcpyHostToDevice, st), "reduction tables")) ||
+      (s = cuda_ok(c, cudaMemcpyAsync(dcn, hcn.data(), sizeof(LzChain) * hcn.size(),
+                                      cudaMemcpyHostToDevice, st), "reduction tables")))
+    return s;
+  cudaMemsetAsync(Xa, 0, (size_t)nX * sizeof(double), st);
+  for (size_t k = 0; k < items.size(); ++k) {
+    State& S = *items[k].S;
+    const int i = S.centre;
+    if ((s = copy_in(c, La + parts[k].oA1, S.Lenv[i].data, S.Lenv[i].lay.size, st)) ||
+        (s = copy_in(c, Ra + parts[k].oB3, S.Renv[i].data, S.Renv[i].lay.size, st)) ||
+        (s = copy_in(c, Xa + parts[k].oB1, S.M[i].data, S.M[i].lay.size, st)))
+      return s;
+  }
+  double* ws1 = reinterpret_cast<double*>(c->ws);
+  double* ws2 = ws1 + dp->host.ws1;
+  if ((s = run_plan(c, *dp, La, Xa, ws1, ws2, 1.0, ws2, Ra, Ya, st)))
+    return fail(c, s, "merged H_eff launch");
+  launch_lz_dots(Xa, nX, 1, Ya, dch, nch, part, 1, st);                          // <x, Hx>
+  launch_lz_update(nullptr, nX, 0, Xa, dch, nch, dcn, nullptr, 1, nullptr, part + nch, st);   // <x, x>
+  if ((s = pinned_reserve(c, 2 * (size_t)nch))) return s;
+  double* pin = c->pinned_big;
+  if ((s = cuda_ok(c, cudaMemcpyAsync(pin, part, sizeof(double) * 2 * nch, cudaMemcpyDeviceToHost,
+                                      st), "energy read-back")) ||
+      (s = cuda_ok(c, cudaStreamSynchronize(st), "batched energy")))
+    return s;
+  for (size_t k = 0; k < items.size(); ++k) {
+    double num = 0.0, den = 0.0;
+    for (int b = 0; b < hcn[k].nc; ++b) {
+      num += pin[hcn[k].c0 + b];
+      den += pin[nch + hcn[k].c0 + b];
+    }
+    items[k].info.e_f = den > 0.0 ? num / den : 0.0;
+  }
+  return DMRG3S_OK;
+}
+
+// One local update on every item's state (each in its own direction, with its
+// own alpha and options); the same steps as local_update, batched.
+dmrg3s_status local_update_batch(Context* c, std::vector<BItem>& items, dmrg3s_svd_method method,
+                                 cudaStream_t st) {
+  dmrg3s_status s;
+  for (BItem& it : items) {
+    State& S = *it.S;
+    const int i = S.centre, nb = i + it.dir;
+    if (nb < 0 || nb >= S.n) return fail(c, DMRG3S_ERR_ARG, "local update would leave the chain");
+    if (!S.Lenv[i].valid || !S.Renv[i].valid)
+      return fail(c, DMRG3S_ERR_ARG, "environments of the centre site are not built");
+    it.info = Info();
+  }
+  Profiler& pr = c->prof;
+  auto phase = [&](int kind) { return pr.on ? pr.begin(kind, 0.0, 0.0, st) : -1; };
+  auto done = [&](int id) {
+    if (id >= 0) pr.end(id, st);
+  };
+  int ph = phase(kProfEig);
+  if ((s = batch_eig(c, items, st))) return s;
+  done(ph);
+  ph = phase(kProfExpand);
+  Scratch keep(c, st);    // the expansion terms, until gathered
+  if ((s = batch_expand(c, items, keep, st))) return s;
+  done(ph);
+  ph = phase(kProfSvd);
+  if ((s = batch_truncate(c, items, method, st))) return s;
+  done(ph);
+  ph = phase(kProfEnv);
+  if ((s = batch_env(c, items, st))) return s;
+  done(ph);
+  ph = phase(kProfEnergy);
+  if ((s = batch_energy(c, items, st))) return s;
+  done(ph);
+  return cuda_ok(c, cudaGetLastError(), "batched local update");
 }
 
 dmrg3s_status boundary_env(State& S, const dmrg3s_env* user, bool left, cudaStream_t st) {
@@ -949,12 +1500,10 @@ dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state) {
   return DMRG3S_OK;
 }
 
-dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
-                                  const dmrg3s_update_opts* opts, dmrg3s_update_info* info,
-                                  dmrg3s_stream stream) {
-  State* S = reinterpret_cast<State*>(state);
-  if (!S || !opts || !info) return DMRG3S_ERR_ARG;
-  Context* c = S->c;
+}  // extern "C"
+
+namespace {
+dmrg3s_status make_opts(Context* c, int32_t dir, const dmrg3s_update_opts* opts, Opts* o) {
   if (dir != 1 && dir != -1) return fail(c, DMRG3S_ERR_ARG, "dir must be +1 or -1");
   if (opts->precision != DMRG3S_FP64 && opts->precision != DMRG3S_TF32X3 &&
       opts->precision != DMRG3S_TF32)
@@ -962,19 +1511,17 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   if (opts->m_max < 1) return fail(c, DMRG3S_ERR_ARG, "m_max must be >= 1");
   if (opts->svd != DMRG3S_SVD_JACOBI && opts->svd != DMRG3S_SVD_GESVD)
     return fail(c, DMRG3S_ERR_ARG, "SVD method");
-  dmrg3s_status s;
-  if ((s = use_device(c))) return s;
-  Opts o;
-  o.m_max = opts->m_max;
-  o.kmax = opts->lanczos_kmax > 0 ? opts->lanczos_kmax : 40;
-  o.tol = opts->lanczos_tol > 0 ? opts->lanczos_tol : 1e-10;
-  o.eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-12;
-  o.optimise = opts->skip_eigensolver == 0;
-  o.prec = opts->precision;
-  o.svd = opts->svd;
-  Info inf;
-  s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));
-  if (s != DMRG3S_OK) return s;
+  o->m_max = opts->m_max;
+  o->kmax = opts->lanczos_kmax > 0 ? opts->lanczos_kmax : 40;
+  o->tol = opts->lanczos_tol > 0 ? opts->lanczos_tol : 1e-10;
+  o->eps = opts->trunc_eps > 0 ? opts->trunc_eps : 1e-12;
+  o->optimise = opts->skip_eigensolver == 0;
+  o->prec = opts->precision;
+  o->svd = opts->svd;
+  return DMRG3S_OK;
+}
+
+void report_info(State* S, const Info& inf, dmrg3s_update_info* info) {
   info->lambda = inf.lambda;
   info->energy_after = inf.e_f;
   info->energy_before = S->e_in;
@@ -984,6 +1531,66 @@ dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
   info->svd_fallback = inf.svd_fallback ? 1 : 0;
   info->svd_sweeps = inf.svd_sweeps;
   S->e_in = inf.e_f;
+}
+
+// Checks of a batch: distinct states of one context, one SVD method.
+dmrg3s_status check_batch(const dmrg3s_state* states, int32_t n, Context** cout) {
+  if (!states || n < 1) return DMRG3S_ERR_ARG;
+  State* S0 = reinterpret_cast<State*>(states[0]);
+  if (!S0) return DMRG3S_ERR_ARG;
+  Context* c = S0->c;
+  for (int k = 0; k < n; ++k) {
+    State* S = reinterpret_cast<State*>(states[k]);
+    if (!S) return fail(c, DMRG3S_ERR_ARG, "NULL state in a batch");
+    if (S->c != c) return fail(c, DMRG3S_ERR_ARG, "the states of a batch share one context");
+    for (int j = 0; j < k; ++j)
+      if (states[j] == states[k]) return fail(c, DMRG3S_ERR_ARG, "a state appears twice in a batch");
+  }
+  *cout = c;
+  return DMRG3S_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
+                                  const dmrg3s_update_opts* opts, dmrg3s_update_info* info,
+                                  dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || !opts || !info) return DMRG3S_ERR_ARG;
+  Context* c = S->c;
+  dmrg3s_status s;
+  Opts o;
+  if ((s = make_opts(c, dir, opts, &o))) return s;
+  if ((s = use_device(c))) return s;
+  Info inf;
+  s = local_update(*S, dir, alpha, o, &inf, reinterpret_cast<cudaStream_t>(stream));
+  if (s != DMRG3S_OK) return s;
+  report_info(S, inf, info);
+  return DMRG3S_OK;
+}
+
+dmrg3s_status dmrg3s_local_update_batch(const dmrg3s_state* states, int32_t nstates,
+                                        const int32_t* dirs, const double* alphas,
+                                        const dmrg3s_update_opts* opts, dmrg3s_update_info* infos,
+                                        dmrg3s_stream stream) {
+  Context* c = nullptr;
+  dmrg3s_status s;
+  if ((s = check_batch(states, nstates, &c))) return s;
+  if (!dirs || !alphas || !opts || !infos) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
+  std::vector<BItem> items(nstates);
+  for (int k = 0; k < nstates; ++k) {
+    if ((s = make_opts(c, dirs[k], &opts[k], &items[k].o))) return s;
+    if (opts[k].svd != opts[0].svd)
+      return fail(c, DMRG3S_ERR_ARG, "the updates of a batch use one SVD method");
+    items[k].S = reinterpret_cast<State*>(states[k]);
+    items[k].dir = dirs[k];
+    items[k].alpha = alphas[k];
+  }
+  if ((s = use_device(c))) return s;
+  if ((s = local_update_batch(c, items, opts[0].svd, reinterpret_cast<cudaStream_t>(stream))))
+    return s;
+  for (int k = 0; k < nstates; ++k) report_info(items[k].S, items[k].info, &infos[k]);
   return DMRG3S_OK;
 }
 
@@ -1208,49 +1815,59 @@ double alpha_update(const dmrg3s_alpha_rule& r, double alpha, double e_in, doubl
 }
 }  // namespace
 
-extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
-                                      const dmrg3s_sweep_opts* opts, double* energies,
-                                      dmrg3s_sweep_report* report, dmrg3s_stream stream) {
-  State* S = reinterpret_cast<State*>(state);
-  if (!S || !rule || !opts || !report) return DMRG3S_ERR_ARG;
-  Context* c = S->c;
-  if (S->n < 2) return fail(c, DMRG3S_ERR_ARG, "a sweep needs at least two sites");
-  if (S->centre != S->n - 1)
-    return fail(c, DMRG3S_ERR_ARG, "a sweep starts with the centre on the last site");
-  if (opts->max_sweeps < 1) return fail(c, DMRG3S_ERR_ARG, "max_sweeps must be >= 1");
-  const bool ladder = opts->switch_tol > 0.0;
-  if (ladder && opts->final_precision != DMRG3S_FP64 && opts->final_precision != DMRG3S_TF32X3 &&
-      opts->final_precision != DMRG3S_TF32)
-    return fail(c, DMRG3S_ERR_ARG, "final precision");
-  const auto t0 = std::chrono::steady_clock::now();
-  double alpha = rule->alpha0;
-  report->sweeps = 0;
-  report->converged = 0;
-  report->lanczos_iters = 0;
-  report->svd_fallbacks = 0;
-  report->bulk_sweeps = 0;
-  report->pad = 0;
-  dmrg3s_update_opts uo = opts->update;
-  bool final_stage = !ladder;       // without a ladder every sweep counts
-  int final_sweeps = 0;             // sweeps completed in the final precision
+namespace {
+// The sweep schedule of one state: right-to-left then left-to-right passes
+// of local updates with the adaptive alpha (Sec. VI), the precision ladder
+// (dmrg3s_sweep_opts.switch_tol) and the convergence rule, advanced one
+// local update at a time so that several states can share each step.
+struct Sweeper {
+  State* S = nullptr;
+  const dmrg3s_alpha_rule* rule = nullptr;
+  const dmrg3s_sweep_opts* opts = nullptr;
+  double* energies = nullptr;
+  dmrg3s_sweep_report* report = nullptr;
+  dmrg3s_update_opts uo{};
+  double alpha = 0.0, prev = 0.0, e = 0.0;
+  bool final_stage = true, done = false;
+  int final_sweeps = 0, sw = 0, pass = 0, k = 0;
   int64_t nupd = 0;
-  double prev = 0.0;
-  for (int sw = 0; sw < opts->max_sweeps; ++sw) {
-    double e = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
-      const int dir = pass == 0 ? -1 : 1;
-      for (int k = 0; k < S->n - 1; ++k) {
-        dmrg3s_update_info inf{};
-        dmrg3s_status s = dmrg3s_local_update(state, dir, alpha, &uo, &inf, stream);
-        if (s != DMRG3S_OK) return s;
-        alpha = alpha_update(*rule, alpha, inf.energy_before, inf.lambda, inf.energy_after);
-        if (opts->alphas) opts->alphas[nupd] = alpha;
-        ++nupd;
-        report->lanczos_iters += inf.lanczos_iters;
-        report->svd_fallbacks += inf.svd_fallback;
-        e = inf.energy_after;
-      }
-    }
+  std::chrono::steady_clock::time_point t0;
+
+  dmrg3s_status init(Context* c) {
+    if (S->n < 2) return fail(c, DMRG3S_ERR_ARG, "a sweep needs at least two sites");
+    if (S->centre != S->n - 1)
+      return fail(c, DMRG3S_ERR_ARG, "a sweep starts with the centre on the last site");
+    if (opts->max_sweeps < 1) return fail(c, DMRG3S_ERR_ARG, "max_sweeps must be >= 1");
+    const bool ladder = opts->switch_tol > 0.0;
+    if (ladder && opts->final_precision != DMRG3S_FP64 &&
+        opts->final_precision != DMRG3S_TF32X3 && opts->final_precision != DMRG3S_TF32)
+      return fail(c, DMRG3S_ERR_ARG, "final precision");
+    t0 = std::chrono::steady_clock::now();
+    alpha = rule->alpha0;
+    report->sweeps = 0;
+    report->converged = 0;
+    report->lanczos_iters = 0;
+    report->svd_fallbacks = 0;
+    report->bulk_sweeps = 0;
+    report->pad = 0;
+    uo = opts->update;
+    final_stage = !ladder;       // without a ladder every sweep counts
+    return DMRG3S_OK;
+  }
+  int dir() const { return pass == 0 ? -1 : 1; }
+  // bookkeeping after the local update `inf` of this state
+  void after(const dmrg3s_update_info& inf) {
+    alpha = alpha_update(*rule, alpha, inf.energy_before, inf.lambda, inf.energy_after);
+    if (opts->alphas) opts->alphas[nupd] = alpha;
+    ++nupd;
+    report->lanczos_iters += inf.lanczos_iters;
+    report->svd_fallbacks += inf.svd_fallback;
+    e = inf.energy_after;
+    if (++k < S->n - 1) return;
+    k = 0;
+    if (++pass < 2) return;
+    pass = 0;
+    // end of a sweep
     if (energies) energies[sw] = e;
     if (opts->seconds)
       opts->seconds[sw] =
@@ -1264,7 +1881,7 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
       ++final_sweeps;
       if (final_sweeps >= 2 && rel < opts->conv_tol) {
         report->converged = 1;
-        break;
+        done = true;
       }
     } else {
       ++report->bulk_sweeps;
@@ -1272,6 +1889,74 @@ extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rul
         final_stage = true;
         uo.precision = opts->final_precision;
       }
+    }
+    if (++sw >= opts->max_sweeps) done = true;
+  }
+};
+}  // namespace
+
+extern "C" dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
+                                      const dmrg3s_sweep_opts* opts, double* energies,
+                                      dmrg3s_sweep_report* report, dmrg3s_stream stream) {
+  State* S = reinterpret_cast<State*>(state);
+  if (!S || !rule || !opts || !report) return DMRG3S_ERR_ARG;
+  Sweeper w;
+  w.S = S;
+  w.rule = rule;
+  w.opts = opts;
+  w.energies = energies;
+  w.report = report;
+  dmrg3s_status s = w.init(S->c);
+  if (s) return s;
+  while (!w.done) {
+    dmrg3s_update_info inf{};
+    if ((s = dmrg3s_local_update(state, w.dir(), w.alpha, &w.uo, &inf, stream))) return s;
+    w.after(inf);
+  }
+  return DMRG3S_OK;
+}
+
+extern "C" dmrg3s_status dmrg3s_sweep_batch(const dmrg3s_state* states, int32_t nstates,
+                                            const dmrg3s_alpha_rule* rules,
+                                            const dmrg3s_sweep_opts* opts,
+                                            double* const* energies, dmrg3s_sweep_report* reports,
+                                            dmrg3s_stream stream) {
+  Context* c = nullptr;
+  dmrg3s_status s;
+  if ((s = check_batch(states, nstates, &c))) return s;
+  if (!rules || !opts || !reports) return fail(c, DMRG3S_ERR_ARG, "NULL argument");
+  std::vector<Sweeper> sw(nstates);
+  for (int k = 0; k < nstates; ++k) {
+    sw[k].S = reinterpret_cast<State*>(states[k]);
+    sw[k].rule = &rules[k];
+    sw[k].opts = &opts[k];
+    sw[k].energies = energies ? energies[k] : nullptr;
+    sw[k].report = &reports[k];
+    if ((s = sw[k].init(c))) return s;
+    if (opts[k].update.svd != opts[0].update.svd)
+      return fail(c, DMRG3S_ERR_ARG, "the states of a batch use one SVD method");
+  }
+  if ((s = use_device(c))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (;;) {
+    std::vector<BItem> items;
+    std::vector<int> who;
+    for (int k = 0; k < nstates; ++k) {
+      if (sw[k].done) continue;
+      BItem it;
+      if ((s = make_opts(c, sw[k].dir(), &sw[k].uo, &it.o))) return s;
+      it.S = sw[k].S;
+      it.dir = sw[k].dir();
+      it.alpha = sw[k].alpha;
+      items.push_back(std::move(it));
+      who.push_back(k);
+    }
+    if (items.empty()) break;
+    if ((s = local_update_batch(c, items, opts[0].update.svd, st))) return s;
+    for (size_t j = 0; j < items.size(); ++j) {
+      dmrg3s_update_info inf{};
+      report_info(items[j].S, items[j].info, &inf);
+      sw[who[j]].after(inf);
     }
   }
   return DMRG3S_OK;

@@ -65,35 +65,6 @@ __global__ void multidot_final(const double* __restrict__ partial, int nchunk, i
   }
 }
 
-__global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ldv, int k,
-                                  const double* __restrict__ h, double* __restrict__ w, int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    double acc = w[e];
-    for (int j = 0; j < k; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
-    w[e] = acc;
-  }
-}
-
-__global__ void combine_vectors_kernel(const double* __restrict__ V, int64_t ldv, int k,
-                                       const double* __restrict__ c, double* __restrict__ y,
-                                       int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    double acc = 0.0;
-    for (int j = 0; j < k; ++j) acc = fma(c[j], V[(int64_t)j * ldv + e], acc);
-    y[e] = acc;
-  }
-}
-
-__global__ void normalise_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
-                                 const double* __restrict__ nrm2) {
-  const double s = 1.0 / sqrt(*nrm2);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
-    y[e] = x[e] * s;
-}
-
 // Double-float numbers (an unevaluated sum hi + lo of two floats, about 44
 // significant bits) carry the Sturm counts: GB300 issues FP32 at ~60x its
 // FP64 rate, and the count only needs the sign of each pivot. Two-sum is
@@ -154,15 +125,13 @@ __device__ void tridiag_vector(const double* alpha, const double* beta, int k, d
 // Gershgorin span); thread 0 then runs the inverse iteration in FP64 and
 // returns the Rayleigh quotient of the vector, which is accurate to FP64
 // rounding whatever the width of the bracket was.
-__global__ void tridiag_multisection_kernel(const double* __restrict__ alpha,
-                                            double* __restrict__ beta, int k,
-                                            const double* __restrict__ nrm2,
-                                            double* __restrict__ y, TridiagOut* __restrict__ out) {
+// bl = the norm of the new residual vector (stored as beta[k - 1]).
+__device__ void tridiag_block(const double* __restrict__ alpha, double* __restrict__ beta, int k,
+                              double bl, double* __restrict__ y, TridiagOut* __restrict__ out) {
   __shared__ double sh_lo, sh_hi, sh_span, sh_c;
   __shared__ int sh_bad, sh_first;
   __shared__ DF sa[128], sbb[128];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double bl = sqrt(*nrm2);
   if (tid == 0) {
     double lo = 1e300, hi = -1e300;
     int bad = 0;
@@ -348,10 +317,120 @@ __global__ void copy_blocks_kernel(const CopyTask* __restrict__ tasks,
   }
 }
 
-int grid_for(int64_t n) {
-  int64_t g = (n + kThreads - 1) / kThreads;
-  if (g > 4 * 152) g = 4 * 152;
-  return g < 1 ? 1 : (int)g;
+// ---- batched Lanczos kernels (see vecops.hpp) ----
+constexpr int kLzThreads = 256;
+constexpr int kLzWarps = kLzThreads / 32;
+
+// Sum of partial[b * kp + j] over the chunks b of [c0, c0 + nc) in a fixed
+// order (lane-strided sums, then the xor tree); every lane returns the sum.
+__device__ __forceinline__ double chain_sum(const double* __restrict__ partial, int kp, int c0,
+                                            int nc, int j, int lane) {
+  double acc = 0.0;
+  for (int b = lane; b < nc; b += 32) acc += partial[(int64_t)(c0 + b) * kp + j];
+  return warp_sum(acc);
+}
+
+// The chunk of w is staged in shared memory once; warp q then forms the dot
+// products with V_j for j = q, q + 8, ...
+__global__ void __launch_bounds__(kLzThreads) lz_dots_kernel(const double* __restrict__ V,
+                                                             int64_t ldv, int k1,
+                                                             const double* __restrict__ w,
+                                                             const LzChunk* __restrict__ chunks,
+                                                             double* __restrict__ partial, int kp) {
+  extern __shared__ double wsh[];
+  const LzChunk ch = chunks[blockIdx.x];
+  const int len = (int)(ch.e1 - ch.e0);
+  for (int i = threadIdx.x; i < len; i += kLzThreads) wsh[i] = w[ch.e0 + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  for (int j = q; j < k1; j += kLzWarps) {
+    const double* v = V + (int64_t)j * ldv + ch.e0;
+    double acc = 0.0;
+    for (int i = lane; i < len; i += 32) acc = fma(v[i], wsh[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(int64_t)blockIdx.x * kp + j] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kLzThreads) lz_update_kernel(
+    const double* __restrict__ V, int64_t ldv, int k1, double* __restrict__ w,
+    const LzChunk* __restrict__ chunks, const LzChain* __restrict__ chains,
+    const double* __restrict__ partial, int kp, double* __restrict__ alpha,
+    double* __restrict__ nrm_partial) {
+  __shared__ double h[kLzMaxK];
+  __shared__ double red[32];
+  const LzChunk ch = chunks[blockIdx.x];
+  const LzChain cn = chains[ch.chain];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  for (int j = q; j < k1; j += kLzWarps) {
+    const double s = chain_sum(partial, kp, cn.c0, cn.nc, j, lane);
+    if (lane == 0) {
+      h[j] = s;
+      if (alpha && j == k1 - 1 && (int)blockIdx.x == cn.c0) alpha[(int64_t)ch.chain * kp + j] = s;
+    }
+  }
+  __syncthreads();
+  double nacc = 0.0;
+  for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) {
+    double acc = w[e];
+    for (int j = 0; j < k1; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
+    if (k1 > 0) w[e] = acc;
+    nacc = fma(acc, acc, nacc);
+  }
+  if (nrm_partial) {
+    const double t = block_sum(nacc, red);
+    if (threadIdx.x == 0) nrm_partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kLzThreads) lz_normalise_kernel(
+    const double* __restrict__ x, double* __restrict__ y, const LzChunk* __restrict__ chunks,
+    const LzChain* __restrict__ chains, const double* __restrict__ nrm_partial) {
+  __shared__ double scale;
+  const LzChunk ch = chunks[blockIdx.x];
+  if (threadIdx.x < 32) {
+    const LzChain cn = chains[ch.chain];
+    const double n2 = chain_sum(nrm_partial, 1, cn.c0, cn.nc, 0, threadIdx.x);
+    if (threadIdx.x == 0) scale = (n2 > 0.0 && n2 < 1e308) ? 1.0 / sqrt(n2) : 0.0;
+  }
+  __syncthreads();
+  const double sc = scale;
+  for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) y[e] = x[e] * sc;
+}
+
+__global__ void lz_tridiag_kernel(const LzChain* __restrict__ chains, const double* __restrict__ alpha,
+                                  double* __restrict__ beta, int kp, int k,
+                                  const double* __restrict__ nrm_partial, double* __restrict__ y,
+                                  TridiagOut* __restrict__ out) {
+  __shared__ double bl;
+  const int c = blockIdx.x;
+  const LzChain cn = chains[c];
+  if (threadIdx.x < 32) {
+    const double n2 = chain_sum(nrm_partial, 1, cn.c0, cn.nc, 0, threadIdx.x);
+    if (threadIdx.x == 0) bl = sqrt(fmax(n2, 0.0));
+  }
+  __syncthreads();
+  tridiag_block(alpha + (int64_t)c * kp, beta + (int64_t)c * kp, k + 1, bl,
+                y + ((int64_t)c * kp + k) * kp, out + (int64_t)k * gridDim.x + c);
+}
+
+__global__ void __launch_bounds__(kLzThreads) lz_ritz_kernel(
+    const double* __restrict__ V, int64_t ldv, const LzChunk* __restrict__ chunks,
+    const LzChain* __restrict__ chains, const int32_t* __restrict__ kstop,
+    const double* __restrict__ y, int kp, double* __restrict__ x, double* __restrict__ nrm_partial) {
+  __shared__ double red[32];
+  const LzChunk ch = chunks[blockIdx.x];
+  const int ks = kstop[ch.chain];
+  const double* yc = y + ((int64_t)ch.chain * kp + ks) * kp;
+  double nacc = 0.0;
+  for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) {
+    double acc = 0.0;
+    for (int j = 0; j <= ks; ++j) acc = fma(yc[j], V[(int64_t)j * ldv + e], acc);
+    x[e] = acc;
+    nacc = fma(acc, acc, nacc);
+  }
+  const double t = block_sum(nacc, red);
+  if (threadIdx.x == 0) nrm_partial[blockIdx.x] = t;
 }
 
 }  // namespace
@@ -370,27 +449,45 @@ void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64
   multidot_final<<<k, 128, 0, st>>>(partial, nchunk, k, h, copy_last);
 }
 
-void launch_multi_axpy(const double* V, int64_t ldv, int k, const double* h, double* w, int64_t n,
+void launch_lz_dots(const double* V, int64_t ldv, int k1, const double* w, const LzChunk* chunks,
+                    int nchunks, double* partial, int kp, cudaStream_t st) {
+  if (k1 <= 0 || nchunks <= 0) return;
+  count_launch();
+  lz_dots_kernel<<<nchunks, kLzThreads, kLzChunkMax * sizeof(double), st>>>(V, ldv, k1, w, chunks,
+                                                                             partial, kp);
+}
+
+void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
+                      int nchunks, const LzChain* chains, const double* partial, int kp,
+                      double* alpha, double* nrm_partial, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  count_launch();
+  lz_update_kernel<<<nchunks, kLzThreads, 0, st>>>(V, ldv, k1, w, chunks, chains, partial, kp,
+                                                   alpha, nrm_partial);
+}
+
+void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,
+                         const LzChain* chains, const double* nrm_partial, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  count_launch();
+  lz_normalise_kernel<<<nchunks, kLzThreads, 0, st>>>(x, y, chunks, chains, nrm_partial);
+}
+
+void launch_lz_tridiag(const LzChain* chains, int nchains, const double* alpha, double* beta,
+                       int kp, int k, const double* nrm_partial, double* y, TridiagOut* out,
                        cudaStream_t st) {
+  if (nchains <= 0) return;
   count_launch();
-  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, h, w, n);
+  lz_tridiag_kernel<<<nchains, 256, 0, st>>>(chains, alpha, beta, kp, k, nrm_partial, y, out);
 }
 
-void launch_combine_vectors(const double* V, int64_t ldv, int k, const double* c, double* y,
-                            int64_t n, cudaStream_t st) {
+void launch_lz_ritz(const double* V, int64_t ldv, const LzChunk* chunks, int nchunks,
+                    const LzChain* chains, const int32_t* kstop, const double* y, int kp,
+                    double* x, double* nrm_partial, cudaStream_t st) {
+  if (nchunks <= 0) return;
   count_launch();
-  combine_vectors_kernel<<<grid_for(n), kThreads, 0, st>>>(V, ldv, k, c, y, n);
-}
-
-void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2, cudaStream_t st) {
-  count_launch();
-  normalise_kernel<<<grid_for(n), kThreads, 0, st>>>(x, y, n, nrm2);
-}
-
-void launch_tridiag_smallest(const double* alpha, double* beta, int k, const double* nrm2,
-                             double* y, TridiagOut* out, cudaStream_t st) {
-  count_launch();
-  tridiag_multisection_kernel<<<1, 256, 0, st>>>(alpha, beta, k, nrm2, y, out);
+  lz_ritz_kernel<<<nchunks, kLzThreads, 0, st>>>(V, ldv, chunks, chains, kstop, y, kp, x,
+                                                 nrm_partial);
 }
 
 void launch_copy_blocks(const CopyTask* tasks, int ntasks, const double* src, double* dst,

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace dmrg3s {
@@ -19,27 +21,90 @@ constexpr int kRedBlocks = 304;
 void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                      double* partial, double* h, double* copy_last, cudaStream_t st);
 
-// w -= sum_{j<k} h[j] V_j
-void launch_multi_axpy(const double* V, int64_t ldv, int k, const double* h, double* w, int64_t n,
-                       cudaStream_t st);
-
-// y = sum_{j<k} c[j] V_j    (c on the device)
-void launch_combine_vectors(const double* V, int64_t ldv, int k, const double* c, double* y,
-                            int64_t n, cudaStream_t st);
-
-// y = x / sqrt(*nrm2)   (nrm2 on the device)
-void launch_normalise(const double* x, double* y, int64_t n, const double* nrm2, cudaStream_t st);
-
-// Smallest eigenpair of the symmetric tridiagonal Lanczos matrix of order k
-// (diagonal alpha, off-diagonal beta[0..k-2]) in one CTA: Sturm multisection
-// (double-float counts) brackets the eigenvalue, one thread runs inverse
-// iteration for the eigenvector and returns its Rayleigh quotient.
-// beta[k-1] is set to sqrt(*nrm2) (the norm of the new residual vector).
+// Result of the smallest eigenpair of a symmetric tridiagonal Lanczos matrix
+// of order k (diagonal alpha, off-diagonal beta[0..k-2]), solved in one CTA:
+// Sturm multisection (double-float counts) brackets the eigenvalue, one
+// thread runs inverse iteration for the eigenvector and returns its Rayleigh
+// quotient; beta[k-1] is set to the norm of the new residual vector.
 struct TridiagOut {
   double theta, resid, beta_last, nan_seen;
 };
-void launch_tridiag_smallest(const double* alpha, double* beta, int k, const double* nrm2,
-                             double* y, TridiagOut* out, cudaStream_t st);
+
+// ---- Lanczos over a batch of independent problems ("chains") ----
+// The vectors of all chains are stored back to back: chain c owns elements
+// [off, off + n) of every vector (off a multiple of 32).  The vector space is
+// cut into chunks (one CTA each) that never straddle two chains; every
+// reduction writes one partial per chunk and is finished by summing the
+// chain's partials in chunk order (lane-strided, then a fixed shuffle tree),
+// so every CTA that needs a chain's sum computes the identical value.
+struct LzChunk {
+  int64_t e0, e1;       // element range [e0, e1)
+  int32_t chain, pad;
+};
+struct LzChain {
+  int64_t off, n;       // element range of the chain
+  int32_t c0, nc;       // its chunks [c0, c0 + nc)
+};
+constexpr int kLzMaxK = 129;   // most basis vectors of one run (kmax <= 128, plus one)
+constexpr int kLzChunkMax = 4096;   // most elements of one chunk
+
+// Chunks of `ranges` (one (off, n) per chain): each chain's range cut into
+// about equal chunks of at most kLzChunkMax elements, `target` chunks in all
+// where the sizes allow (a chain of n elements gets at least one chunk).
+inline void lz_layout(const std::vector<std::pair<int64_t, int64_t>>& ranges, int target,
+                      std::vector<LzChunk>* chunks, std::vector<LzChain>* chains) {
+  int64_t total = 0;
+  for (auto& r : ranges) total += r.second;
+  int64_t len = target > 0 ? (total + target - 1) / target : total;
+  len = (len + 255) / 256 * 256;
+  if (len < 256) len = 256;
+  if (len > kLzChunkMax) len = kLzChunkMax;
+  chunks->clear();
+  chains->clear();
+  for (size_t c = 0; c < ranges.size(); ++c) {
+    LzChain cn{};
+    cn.off = ranges[c].first;
+    cn.n = ranges[c].second;
+    cn.c0 = (int32_t)chunks->size();
+    const int64_t nch = cn.n > 0 ? (cn.n + len - 1) / len : 0;
+    for (int64_t b = 0; b < nch; ++b) {
+      LzChunk ch{};
+      ch.e0 = cn.off + cn.n * b / nch;
+      ch.e1 = cn.off + cn.n * (b + 1) / nch;
+      ch.chain = (int32_t)c;
+      chunks->push_back(ch);
+    }
+    cn.nc = (int32_t)(chunks->size() - cn.c0);
+    chains->push_back(cn);
+  }
+}
+
+// partial[b * kp + j] = <V_j, w> over chunk b, for j < k1 (V_j = V + j * ldv).
+void launch_lz_dots(const double* V, int64_t ldv, int k1, const double* w, const LzChunk* chunks,
+                    int nchunks, double* partial, int kp, cudaStream_t st);
+// One Gram-Schmidt pass: h_j = (chain sum of partial[., j]), w -= sum_{j<k1} h_j V_j.
+// alpha (optional): alpha[chain * kp + k1 - 1] = h_{k1-1} (the Lanczos alpha_k).
+// nrm_partial (optional): the chunk's sum of squares of the updated w.
+// k1 = 0 leaves w unchanged and only forms nrm_partial.
+void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
+                      int nchunks, const LzChain* chains, const double* partial, int kp,
+                      double* alpha, double* nrm_partial, cudaStream_t st);
+// y[e] = x[e] / sqrt(chain sum of nrm_partial); a chain whose squared norm is
+// not positive and finite gets zeros.
+void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,
+                         const LzChain* chains, const double* nrm_partial, cudaStream_t st);
+// Smallest eigenpair of every chain's tridiagonal Lanczos matrix of order
+// k + 1 (one CTA per chain; the algorithm above):
+// beta[c * kp + k] = sqrt(chain sum of nrm_partial), the Ritz vector into
+// y + (c * kp + k) * kp, the result into out[k * nchains + c].
+void launch_lz_tridiag(const LzChain* chains, int nchains, const double* alpha, double* beta,
+                       int kp, int k, const double* nrm_partial, double* y, TridiagOut* out,
+                       cudaStream_t st);
+// Ritz vectors: x[e] = sum_{j <= kstop[c]} y[(c * kp + kstop[c]) * kp + j] V_j[e] for the
+// chain c of element e, and the chunk's sum of squares of x into nrm_partial.
+void launch_lz_ritz(const double* V, int64_t ldv, const LzChunk* chunks, int nchunks,
+                    const LzChain* chains, const int32_t* kstop, const double* y, int kp,
+                    double* x, double* nrm_partial, cudaStream_t st);
 
 // Copy of rectangular blocks with optional transpose and row/column scaling:
 //   dst[off_d + r*ld_d + c] = src(r, c) * rs[r] * cs[c]

@@ -285,3 +285,24 @@ def _parity_filter(bnd, m):
     while d2.sum() < m:
         d2[int(np.argmax(d2))] += 1
     return bond(q2, d2)
+
+
+# ---- batched chains --------------------------------------------------------------
+
+BATCH_M_CHOICES = (64, 128, 256, 512)
+
+
+def batch_xxz_chains(n=64, seed=1005):
+    """The batched-chain workload: n independent open XXZ chains, J = 1, with
+    L drawn uniformly from the even lengths 16, 18, ..., 128 (an S^z = 0
+    sector needs an even length), Delta uniformly from [0.5, 1.5] and m_max
+    uniformly from BATCH_M_CHOICES, in that order per chain, from
+    numpy.random.default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        L = 2 * int(rng.integers(8, 65))
+        delta = float(rng.uniform(0.5, 1.5))
+        m = int(BATCH_M_CHOICES[int(rng.integers(0, len(BATCH_M_CHOICES)))])
+        out.append({"L": L, "J": 1.0, "Delta": delta, "m_max": m})
+    return out
