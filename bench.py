@@ -1,24 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of the DMRG3S hot path on one GB300 (or N independent replicas).
 
-A *step* is one DMRG3S local update (Sec. V of arXiv:1501.05504, steps 1-7):
-Lanczos eigensolver over H_eff = L W A R, expansion term alpha L M W,
-per-sector FP64 SVD truncation to m_max, S V^dagger into the neighbour,
-environment update and the energy after truncation.  Workload: the central
-two-site window of the S=1/2 Heisenberg (XXZ, Delta = 1) chain with L = 100,
-d = 2, w = 5, U(1) S^z blocks and m_max = 512; the boundary environments are
-seeded synthetic symmetric block tensors with Gaussian sector dimensions (a
-stand-in for converged environments: seeded_inputs.central_bonds and
-symmetric_env build them).  Steps
-alternate direction (left-to-right, right-to-left) so every step is a full
-update of the same window.
-
-Metric: algorithmic TFLOP/s of the step's contractions (grouped-GEMM block
-products + MPO combinations, counted as sum 2 M N K over the block tasks;
-the SVD is not counted).  ``e2e`` repeats the step through the C ABI with the
-window's tensors in pinned host memory, copied in and out every step.
-``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload (H_eff applications, the step's dominant cost) on the host cores.
+Headline (``value``): algorithmic TFLOP/s of the single-site effective
+Hamiltonian application HA = L W A R (Sec. V of arXiv:1501.05504, order
+(((L A) W) R)), the operation the Lanczos eigensolver repeats, on the largest
+dense contraction of the workloads: the central site of the S=1/2 Heisenberg
+model on the 4 x 16 cylinder (snake order, periodic in width, w = 14, U(1)
+S^z) at m = 2048, in 3xTF32 with FP64 data, one application of the prepared
+operator (dmrg3s_heff_apply) per step with L2 flushed.  ``roofline`` is the
+tensor-core kernel's share against the measured TF32 peak; ``e2e`` repeats the
+product through the C ABI from pinned host buffers.  Secondary fields: one
+full local update on the XXZ L = 100, m = 512 window (``local_update``), the
+sweep-to-1e-9 time of the mixed-precision ladder against FP64 (``sweep``),
+and the batched-chain workload (``batch``: XXZ chains solved together, with
+their coupling derivatives).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same H_eff on the host cores.
 """
 import argparse
 import hashlib
@@ -423,6 +419,9 @@ def run_ours(args):
     sweep = None
     if not args.no_sweep and rank == 0 and world == 1:
         sweep = run_sweep(args)
+    batch = None
+    if not args.no_batch and rank == 0 and world == 1:
+        batch = run_batch(args)
     if rank != 0:
         return None
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.cpu_sample_s, name,
@@ -446,7 +445,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "heff_whole": whole, "heff_oneshot": oneshot, "cpu_baseline": cpu,
             "e2e": e2e,
-            "local_update": upd, "sweep": sweep, "gpu_launches": int(launches),
+            "local_update": upd, "sweep": sweep, "batch": batch, "gpu_launches": int(launches),
             "clocks": clk.summary()}
 
 
@@ -695,6 +694,58 @@ def run_sweep(args):
             "data": "synthetic"}
 
 
+def run_batch(args):
+    """Batched chains: the first --batch-chains chains of the 64-chain XXZ
+    workload (seeded_inputs.batch_xxz_chains, seed 1005) swept together from
+    Neel states by one dmrg3s_sweep_batch call (every local-update step of all
+    chains in shared launches), to |dE|/|E| < 1e-9 between two sweeps, then
+    dE/dJ and dE/dDelta of every chain (dmrg3s_energy_grad).  chains_per_s =
+    chains solved (sweeps and gradients) per second of wall time."""
+    import torch
+    import seeded_inputs as si
+    from paper_1501_05504_gb300 import binding as b
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), int(args.workspace_gb * (1 << 30)))
+    chains = si.batch_xxz_chains()[:args.batch_chains]
+    states = []
+    for c in chains:
+        W = b.Mpo(b.MODEL_XXZ, c["L"], (c["J"], c["Delta"])).sites()
+        states.append(b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [0, 1] * (c["L"] // 2)),
+                                            None, None, c["L"] - 1))
+    mixed = args.batch_prec == "mixed"
+    opts = [b.update_opts(c["m_max"], prec="tf32x3" if mixed else "fp64", svd=args.svd)
+            for c in chains]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if mixed:
+        reps = b.dmrg3s_sweep_batch(states, b.alpha_rule(ALPHA), args.batch_sweeps, 1e-9, opts,
+                                    final_prec="fp64", switch_tol=1e-7)
+    else:
+        reps = b.dmrg3s_sweep_batch(states, b.alpha_rule(ALPHA), args.batch_sweeps, 1e-9, opts)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    grads = [b.dmrg3s_energy_grad(st, b.MODEL_XXZ, (c["J"], c["Delta"])) for st, c in zip(states, chains)]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for st in states:
+        st.close()
+    ctx.close()
+    n = len(chains)
+    return {"metric": "batched chains solved per second (sweeps to 1e-9 and dE/dJ, dE/dDelta)",
+            "value": n / (t2 - t0), "unit": "chains/s", "higher_is_better": True,
+            "chains": n, "sweep_s": t1 - t0, "gradient_s": t2 - t1,
+            "converged": int(sum(r["converged"] for r in reps)),
+            "sweeps": [r["sweeps"] for r in reps], "lanczos_iters": [r["lanczos_iters"] for r in reps],
+            "energies": [r["energy"] for r in reps],
+            "dE_dJ": [float(g[1][0]) for g in grads], "dE_dDelta": [float(g[1][1]) for g in grads],
+            "config": {"workload": "64 open XXZ chains, J=1, L even in [16,128], Delta in [0.5,1.5], "
+                                   "m_max in {64,128,256,512} (seed 1005); the first %d" % n,
+                       "L": [c["L"] for c in chains], "m_max": [c["m_max"] for c in chains],
+                       "Delta": [round(c["Delta"], 6) for c in chains],
+                       "precision": "3xTF32 then FP64 (ladder at 1e-7)" if mixed else "fp64",
+                       "svd": args.svd, "max_sweeps": args.batch_sweeps, "alpha0": ALPHA},
+            "data": "synthetic"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -725,6 +776,11 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=512)
     ap.add_argument("--sweep-model", default="xxz", choices=sorted(SWEEP_MODELS))
     ap.add_argument("--sweep-max", type=int, default=16, help="sweeps per arm at most")
+    ap.add_argument("--batch", action="store_true", help="run only the batched-chain field")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-chain field")
+    ap.add_argument("--batch-chains", type=int, default=16)
+    ap.add_argument("--batch-sweeps", type=int, default=12)
+    ap.add_argument("--batch-prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--measure-peaks", action="store_true",
                     help="measure the cuBLAS TF32 and FP64 GEMM peaks into profiles/")
     args = ap.parse_args()
@@ -734,6 +790,8 @@ def main():
         res = measure_peaks()
     elif args.sweep:
         res = run_sweep(args)
+    elif args.batch:
+        res = run_batch(args)
     elif args.heff_only:
         res = run_heff_only(args)
     else:
