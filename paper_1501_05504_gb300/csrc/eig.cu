@@ -33,9 +33,9 @@ dmrg3s_status pinned_reserve(Context* c, size_t n) {
 }
 
 // Iteration k of every problem, on the main stream:
-//   two classical Gram-Schmidt passes of w = H v_k against v_0 .. v_k (each
-//   one dot launch and one update launch; the first pass's last coefficient is
-//   alpha_k, the second pass also forms the partial norms of w);
+//   two classical Gram-Schmidt passes of w = H v_k against v_0 .. v_k in three
+//   launches (dots; update fused with the second pass's dots; update with
+//   the partial norms of w); the first pass's last coefficient is alpha_k;
 // then, on the side stream, the tridiagonal solve of order k + 1 and the copy
 // of its results to the host, while the main stream already normalises
 // v_{k+1} and applies H to it.  The host reads iteration k's results only
@@ -70,7 +70,7 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   dmrg3s_status s;
   if ((s = carve(c, &cursor, sizeof(double) * ldv * kp, &pV)) ||
       (s = carve(c, &cursor, sizeof(double) * ldv, &pw)) ||
-      (s = carve(c, &cursor, sizeof(double) * nchunks * kp, &ppart)) ||
+      (s = carve(c, &cursor, sizeof(double) * nchunks * kp * 2, &ppart)) ||
       (s = carve(c, &cursor, sizeof(double) * nchunks * 3, &pnp)) ||
       (s = carve(c, &cursor, sizeof(double) * np * kp, &palpha)) ||
       (s = carve(c, &cursor, sizeof(double) * np * kp, &pbeta)) ||
@@ -86,6 +86,7 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   double* V = (double*)pV;
   double* w = (double*)pw;
   double* part = (double*)ppart;
+  double* part2 = part + (int64_t)nchunks * kp;
   double* nrmp[3] = {(double*)pnp, (double*)pnp + nchunks, (double*)pnp + 2 * nchunks};
   double* alpha = (double*)palpha;
   double* beta = (double*)pbeta;
@@ -182,10 +183,10 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   if ((s = product(0))) return bail(s);
   int last = -1;   // the last iteration enqueued
   for (int k = 0; k < kmax; ++k) {
+    // pass 1 dots; pass 1 update with the pass 2 dots; pass 2 update with the norm
     launch_lz_dots(V, ldv, k + 1, w, dch, nchunks, part, kp, st);
-    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, alpha, nullptr, st);
-    launch_lz_dots(V, ldv, k + 1, w, dch, nchunks, part, kp, st);     // second pass
-    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, nullptr, nrmp[k & 1], st);
+    launch_lz_update_dots(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, alpha, part2, st);
+    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part2, kp, nullptr, nrmp[k & 1], st);
     cudaEventRecord(c->ev_ready, st);
     cudaStreamWaitEvent(c->aux, c->ev_ready, 0);
     launch_lz_tridiag(dcn, np, alpha, beta, kp, k, nrmp[k & 1], y, out, c->aux);

@@ -51,8 +51,8 @@ struct JacJob {
   int64_t offA, offY, offV, offTau;   // Y = R^T (n x n, ld n); V1 (n x n) or offV = -1
   int64_t offS, offVT, offU;          // outputs (offU = -1: no left vectors)
   int32_t m, n, npad, cta0;           // cta0: first CTA of the matrix in a round launch
-  int32_t col0;                       // first column of the matrix in the batch numbering
-  int32_t nbp, bcta0, pad;            // column blocks (even), first CTA of a block-round launch
+  int32_t col0, pad;                  // first column of the matrix in the batch numbering
+  double tol2;                        // the square of the pair tolerance
 };
 
 // Sum of v over the CTA (kJacThreads threads), returned to every thread.
@@ -106,6 +106,49 @@ jac_permute_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_
   const double* x = A + J.offA + (int64_t)perm[blockIdx.x] * J.m;
   double* t = T + J.offA + (int64_t)j * J.m;
   for (int i = threadIdx.x; i < J.m; i += kJacThreads) t[i] = x[i];
+}
+
+// The rotation (c, s) of a pair with Gram entries alpha = saa, beta = sbb,
+// gamma = sab: t = tan(theta) the smaller root of t^2 + 2 zeta t - 1 = 0,
+// zeta = (beta - alpha) / (2 gamma), c = 1 / sqrt(1 + t^2), s = c t.  GB300
+// issues FP64 at 1/64 of its FP32 rate, and a division or square root in
+// FP64 is a long chain of such instructions, so the angle is computed in
+// FP32 on (beta - alpha, 2 gamma) scaled by a common power of two (so that
+// neither underflows nor overflows), and (c, s) is then made orthonormal to
+// FP64 accuracy by two Newton steps on c^2 + s^2 = 1 (FP64 multiply-adds
+// only).  The angle carries FP32 rounding (~1e-7 relative): the rotated pair
+// is orthogonal to ~1e-7 of its former cosine rather than exactly, which the
+// next sweep removes; the rotation itself is orthogonal to FP64 rounding, so
+// the singular values are unaffected.
+__device__ __forceinline__ void jacobi_rotation(double saa, double sbb, double sab, double* c,
+                                                double* s) {
+  const double d = sbb - saa, g2 = 2.0 * sab;
+  const double big = fmax(fabs(d), fabs(g2));
+  // 2^-e with e the binary exponent of big (a normal number here)
+  const long long eb = (__double_as_longlong(big) >> 52) & 0x7ff;
+  const double scale = __longlong_as_double((long long)(2046 - eb) << 52);
+  const double ds = d * scale, gs = g2 * scale;   // the larger magnitude in [1, 2)
+  const float df = (float)ds, gf = (float)gs;
+  double t;
+  if (fabs(ds) > 1048576.0 * fabs(gs)) {
+    // |zeta| > 2^20: t = 1 / (2 zeta) = gamma / (beta - alpha) to FP32 rounding, in
+    // FP64 (it may be far below the FP32 range) with an FP32 reciprocal of ds
+    t = 0.5 * gs * (double)(1.0f / df);
+  } else {
+    const float z = df / gf;
+    t = (double)(copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f))));
+  }
+  const float tf = (float)t;
+  const float c32 = rsqrtf(fmaf(tf, tf, 1.0f));
+  double cc = c32, ss = (double)c32 * t;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double r = fma(-0.5, fma(cc, cc, ss * ss), 1.5);
+    cc *= r;
+    ss *= r;
+  }
+  *c = cc;
+  *s = ss;
 }
 
 // Advances the sweep counter read by the round kernels (first node of a sweep).
@@ -183,19 +226,13 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
     }
     int g = 0;
     // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
-    if (saa > 0.0 && sbb > 0.0) {
-      const double tol = fmax(sqrt((double)n), 32.0) * DBL_EPSILON;
-      if (fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
-        const double zeta = (sbb - saa) / (2.0 * sab);
-        const double az = fabs(zeta);
-        const double t =
-            az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + az * az));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        cs_sn[0] = c;
-        cs_sn[1] = c * t;
-        g = 1;
-        atomicAdd(rot + sw * njobs + jb, 1);
-      }
+    if (saa > 0.0 && sbb > 0.0 && sab * sab > J.tol2 * saa * sbb) {
+      double cs, sn;
+      jacobi_rotation(saa, sbb, sab, &cs, &sn);
+      cs_sn[0] = cs;
+      cs_sn[1] = sn;
+      g = 1;
+      atomicAdd(rot + sw * njobs + jb, 1);
     }
     go = g;
   }
@@ -225,145 +262,6 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
     }
   }
 }
-
-// Block form of a round.  The columns of Y are taken in blocks of KB (nbp
-// blocks, an even count, the last ones partly or wholly padding); round r of
-// the circle schedule over blocks pairs block r with nbp - 1 and (r + k) mod
-// (nbp - 1) with (r - k) mod (nbp - 1), one CTA per block pair.  The CTA
-// holds its 2 KB columns in shared memory and runs one cyclic sweep over all
-// their pairs (the circle schedule over the 2 KB columns: 2 KB - 1 inner
-// rounds, one pair per warp), with the test and rotation of the scalar round;
-// then writes them back and applies the same rotations, in the same order,
-// to the columns of V1.  A sweep of nbp - 1 block rounds meets every column
-// pair at least once, so it is a valid cyclic sweep; the pairs inside a block
-// are visited once per block round.  Padding columns are zero and never rotate.
-template <int KB>
-__global__ void __launch_bounds__(KB * 32)
-jac_block_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_job,
-                       int njobs, int r, const int* __restrict__ sweep, int* __restrict__ rot,
-                       double* __restrict__ Y, double* __restrict__ V) {
-  extern __shared__ double sm[];
-  constexpr int M = 2 * KB;
-  const int sw = *sweep;
-  if (sw < 0 || sw >= kJacobiMaxSweeps) return;
-  const int jb = cta_job[blockIdx.x];
-  if (sw > 0 && rot[(sw - 1) * njobs + jb] == 0) return;   // converged in the previous sweep
-  const JacJob J = jobs[jb];
-  const int N = J.nbp - 1;
-  if (r >= N) return;
-  const int k = blockIdx.x - J.bcta0;
-  int ba, bb;
-  if (k == 0) {
-    ba = r;
-    bb = N;
-  } else {
-    ba = (r + k) % N;
-    bb = (r - k + N) % N;
-  }
-  const int n = J.n;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  double* cols = sm;                                 // M columns of n
-  double2* logr = reinterpret_cast<double2*>(sm + (int64_t)M * n);   // (c, s) per inner pair
-  auto gcol = [&](int l) { return l < KB ? ba * KB + l : bb * KB + (l - KB); };
-  for (int l = 0; l < M; ++l) {
-    const int g = gcol(l);
-    const double* src = Y + J.offY + (int64_t)g * n;
-    for (int i = tid; i < n; i += KB * 32) cols[l * n + i] = g < n ? src[i] : 0.0;
-  }
-  __syncthreads();
-  const double tol = fmax(sqrt((double)n), 32.0) * DBL_EPSILON;
-  int nrot = 0;
-  for (int ir = 0; ir < M - 1; ++ir) {
-    int a, b;
-    if (w == 0) {
-      a = ir;
-      b = M - 1;
-    } else {
-      a = (ir + w) % (M - 1);
-      b = (ir - w + M - 1) % (M - 1);
-    }
-    double* ya = cols + a * n;
-    double* yb = cols + b * n;
-    double saa = 0.0, sbb = 0.0, sab = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const double u = ya[i], v = yb[i];
-      saa = fma(u, u, saa);
-      sbb = fma(v, v, sbb);
-      sab = fma(u, v, sab);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      saa += __shfl_xor_sync(0xffffffffu, saa, o);
-      sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-      sab += __shfl_xor_sync(0xffffffffu, sab, o);
-    }
-    double cs = 1.0, sn = 0.0;
-    // zero columns (padding) and NaN leave the pair unrotated
-    if (saa > 0.0 && sbb > 0.0 && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
-      const double zeta = (sbb - saa) / (2.0 * sab);
-      const double az = fabs(zeta);
-      const double t =
-          az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + az * az));
-      cs = 1.0 / sqrt(1.0 + t * t);
-      sn = cs * t;
-      ++nrot;
-      for (int i = lane; i < n; i += 32) {
-        const double u = ya[i], v = yb[i];
-        ya[i] = cs * u - sn * v;
-        yb[i] = sn * u + cs * v;
-      }
-    }
-    if (lane == 0) logr[ir * KB + w] = make_double2(cs, sn);
-    __syncthreads();
-  }
-  for (int l = 0; l < M; ++l) {
-    const int g = gcol(l);
-    if (g >= n) continue;
-    double* dst = Y + J.offY + (int64_t)g * n;
-    for (int i = tid; i < n; i += KB * 32) dst[i] = cols[l * n + i];
-  }
-  if (lane == 0 && nrot > 0) atomicAdd(rot + sw * njobs + jb, nrot);
-  if (J.offV < 0) return;
-  __syncthreads();
-  for (int l = 0; l < M; ++l) {
-    const int g = gcol(l);
-    const double* src = V + J.offV + (int64_t)g * n;
-    for (int i = tid; i < n; i += KB * 32) cols[l * n + i] = g < n ? src[i] : 0.0;
-  }
-  __syncthreads();
-  for (int ir = 0; ir < M - 1; ++ir) {
-    int a, b;
-    if (w == 0) {
-      a = ir;
-      b = M - 1;
-    } else {
-      a = (ir + w) % (M - 1);
-      b = (ir - w + M - 1) % (M - 1);
-    }
-    const double2 r2 = logr[ir * KB + w];
-    if (r2.y != 0.0) {
-      double* va = cols + a * n;
-      double* vb = cols + b * n;
-      for (int i = lane; i < n; i += 32) {
-        const double u = va[i], v = vb[i];
-        va[i] = r2.x * u - r2.y * v;
-        vb[i] = r2.y * u + r2.x * v;
-      }
-    }
-    __syncthreads();
-  }
-  for (int l = 0; l < M; ++l) {
-    const int g = gcol(l);
-    if (g >= n) continue;
-    double* dst = V + J.offV + (int64_t)g * n;
-    for (int i = tid; i < n; i += KB * 32) dst[i] = cols[l * n + i];
-  }
-}
-
-// Shared memory of a block round with KB-column blocks on columns of n.
-inline size_t jac_block_smem(int kb, int n) {
-  return ((size_t)2 * kb * n + (size_t)(2 * kb - 1) * kb * 2) * sizeof(double);
-}
-constexpr size_t kJacBlockSmemMax = 200 * 1024;
 
 // sigma of every column of every Y.  One CTA per column.
 __global__ void __launch_bounds__(kJacThreads)
@@ -418,21 +316,6 @@ jac_scatter_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_
 dmrg3s_status cuda_ok(Context* c, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return DMRG3S_OK;
   return fail(c, DMRG3S_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-// Dynamic shared memory of the block rounds (above the 48 KB default).
-dmrg3s_status jac_block_prepare(Context* c, int kb, size_t smem) {
-  cudaError_t e = cudaSuccess;
-  if (kb == 16)
-    e = cudaFuncSetAttribute(jac_block_round_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-  else if (kb == 8)
-    e = cudaFuncSetAttribute(jac_block_round_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-  else if (kb == 4)
-    e = cudaFuncSetAttribute(jac_block_round_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-  return cuda_ok(c, e, "Jacobi block rounds");
 }
 
 }  // namespace
@@ -497,37 +380,19 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     t.cta0 = (int32_t)cta_job.size();
     t.col0 = (int32_t)col_job.size();
     t.pad = 0;
+    const double tol = std::max(std::sqrt((double)t.n), 32.0) * DBL_EPSILON;
+    t.tol2 = tol * tol;
     cta_job.insert(cta_job.end(), t.npad / 2, k);
     col_job.insert(col_job.end(), t.n, k);
     maxr = std::max(maxr, t.npad - 1);
   }
-  // block rounds (jac_block_round_kernel) when the widest matrix's 2 KB
-  // columns fit in shared memory, with the widest such blocks up to 16
-  int nmax = 0;
-  for (const JacJob& t : tab) nmax = std::max(nmax, (int)t.n);
-  int kb = 0;
-  for (int cand : {16, 8, 4})
-    if (!kb && jac_block_smem(cand, nmax) <= kJacBlockSmemMax) kb = cand;
-  std::vector<int> bcta_job;
-  int maxrb = 0;
-  if (kb) {
-    for (int k = 0; k < nj; ++k) {
-      JacJob& t = tab[k];
-      const int nb = (t.n + kb - 1) / kb;
-      t.nbp = nb + (nb & 1);
-      t.bcta0 = (int32_t)bcta_job.size();
-      bcta_job.insert(bcta_job.end(), t.nbp / 2, k);
-      maxrb = std::max(maxrb, t.nbp - 1);
-    }
-  }
-  const int nbcta = (int)bcta_job.size();
   const int ncta = (int)cta_job.size(), ncol = (int)col_job.size();
   int64_t na = 0;   // extent of the A buffer used by the jobs
   for (const JacJob& t : tab) na = std::max(na, t.offA + (int64_t)t.m * t.n);
   // ---- device buffers: doubles [tau | Y | V1 | sigma | column norms | T = A P],
   //      ints [cta_job | col_job | perm | rot | sweep | qinfo]
   const int64_t nd = ntau + ny + nv + 2 * (int64_t)ncol + na;
-  const int64_t ni = ncta + 2 * (int64_t)ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj + nbcta;
+  const int64_t ni = ncta + 2 * (int64_t)ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj;
   double* dd = nullptr;
   int* di = nullptr;
   JacJob* dt = nullptr;
@@ -551,11 +416,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   int* rot = d_perm + ncol;
   int* d_sweep = rot + (int64_t)kJacobiMaxSweeps * nj;
   int* qinfo = d_sweep + 1;
-  int* d_bcta = qinfo + nj;
   cudaMemcpyAsync(dt, tab.data(), tab.size() * sizeof(JacJob), cudaMemcpyHostToDevice, st);
-  if (nbcta)
-    cudaMemcpyAsync(d_bcta, bcta_job.data(), bcta_job.size() * sizeof(int), cudaMemcpyHostToDevice,
-                    st);
   cudaMemcpyAsync(d_cta, cta_job.data(), cta_job.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_col, col_job.data(), col_job.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(rot, 0, (size_t)kJacobiMaxSweeps * nj * sizeof(int), st);
@@ -676,30 +537,15 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     count_launch();
     s = cuda_ok(c, cudaGetLastError(), "Jacobi set-up");
   }
-  // ---- 3. sweeps: one CUDA graph of (sweep counter, rounds 0 .. maxr-1),
-  // block rounds where they fit
-  const size_t bsmem = kb ? jac_block_smem(kb, nmax) : 0;
-  if (!s && kb && (s = jac_block_prepare(c, kb, bsmem))) kb = 0;
-  const int nround = kb ? maxrb : maxr;
-  auto enqueue_sweep = [&](cudaStream_t q) {
-    jac_next_sweep_kernel<<<1, 1, 0, q>>>(d_sweep);
-    for (int r = 0; r < nround; ++r) {
-      if (kb == 16)
-        jac_block_round_kernel<16><<<nbcta, 16 * 32, bsmem, q>>>(dt, d_bcta, nj, r, d_sweep, rot, Y, V1);
-      else if (kb == 8)
-        jac_block_round_kernel<8><<<nbcta, 8 * 32, bsmem, q>>>(dt, d_bcta, nj, r, d_sweep, rot, Y, V1);
-      else if (kb == 4)
-        jac_block_round_kernel<4><<<nbcta, 4 * 32, bsmem, q>>>(dt, d_bcta, nj, r, d_sweep, rot, Y, V1);
-      else
-        jac_round_kernel<<<ncta, kJacThreads, 0, q>>>(dt, d_cta, nj, r, d_sweep, rot, Y, V1);
-    }
-  };
+  // ---- 3. sweeps: one CUDA graph of (sweep counter, rounds 0 .. maxr-1)
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   if (!s && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
       cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    enqueue_sweep(cap);
+    jac_next_sweep_kernel<<<1, 1, 0, cap>>>(d_sweep);
+    for (int r = 0; r < maxr; ++r)
+      jac_round_kernel<<<ncta, kJacThreads, 0, cap>>>(dt, d_cta, nj, r, d_sweep, rot, Y, V1);
     if (cudaStreamEndCapture(cap, &graph) != cudaSuccess ||
         cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
       gexec = nullptr;
@@ -716,36 +562,29 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     if (gexec) {
       s = cuda_ok(c, cudaGraphLaunch(gexec, st), "Jacobi sweep");
     } else {
-      enqueue_sweep(st);
+      jac_next_sweep_kernel<<<1, 1, 0, st>>>(d_sweep);
+      for (int r = 0; r < maxr; ++r)
+        jac_round_kernel<<<ncta, kJacThreads, 0, st>>>(dt, d_cta, nj, r, d_sweep, rot, Y, V1);
       s = cuda_ok(c, cudaGetLastError(), "Jacobi sweep");
     }
-    count_launch(nround + 1);
+    count_launch(maxr + 1);
     if (id >= 0) pr.end(id, st);
     if (s) break;
     if ((s = cuda_ok(c, cudaMemcpyAsync(hrot.data(), rot + (int64_t)sw * nj, nj * sizeof(int),
                                         cudaMemcpyDeviceToHost, st), "Jacobi rotations")) ||
         (s = cuda_ok(c, cudaStreamSynchronize(st), "Jacobi sweep")))
       break;
-    // cost of the sweep: a pair test reads two columns (16n bytes) for three
-    // dot products (6n flops); a rotation of a column pair of Y and of V1
-    // takes 6n flops each and writes 16n bytes each (V1 also read).  Block
-    // rounds test every pair of their 2 kb columns, from shared memory, and
-    // move each column between memory and the CTA twice (Y, and V1).
+    // algorithmic cost of the sweep: a pair test reads two columns (16n bytes)
+    // for three dot products (6n flops); a rotation of a column pair of Y and
+    // of V1 takes 6n flops each and writes 16n bytes each (V1 also read)
     double fl = 0.0, by = 0.0;
     bool more = false;
     for (int k = 0; k < nj; ++k) {
       if (!active[k]) continue;
-      const double n = tab[k].n;
+      const double n = tab[k].n, pairs = 0.5 * n * (n - 1.0);
       const bool v = tab[k].offV >= 0;
-      if (kb) {
-        const double ctas = (tab[k].nbp - 1.0) * (tab[k].nbp / 2), m2 = 2.0 * kb;
-        fl += ctas * 0.5 * m2 * (m2 - 1.0) * 6.0 * n + hrot[k] * 6.0 * n * (v ? 2.0 : 1.0);
-        by += ctas * m2 * 16.0 * n * (v ? 2.0 : 1.0);
-      } else {
-        const double pairs = 0.5 * n * (n - 1.0);
-        fl += pairs * 6.0 * n + hrot[k] * 6.0 * n * (v ? 2.0 : 1.0);
-        by += pairs * 16.0 * n + hrot[k] * 16.0 * n * (v ? 3.0 : 1.0);
-      }
+      fl += pairs * 6.0 * n + hrot[k] * 6.0 * n * (v ? 2.0 : 1.0);
+      by += pairs * 16.0 * n + hrot[k] * 16.0 * n * (v ? 3.0 : 1.0);
       if (hrot[k] == 0) {
         active[k] = 0;
         conv[k] = 1;
@@ -756,7 +595,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     if (id >= 0) {
       pr.recs[id].flops = fl;
       pr.recs[id].bytes = by;
-      pr.recs[id].launches = nround + 1;
+      pr.recs[id].launches = maxr + 1;
     }
     if (!more) break;
   }

@@ -383,6 +383,44 @@ __global__ void __launch_bounds__(kLzThreads) lz_update_kernel(
   }
 }
 
+// The first Gram-Schmidt pass's update fused with the second pass's dots:
+// the updated chunk of w stays in shared memory for the dots against V_j.
+__global__ void __launch_bounds__(kLzThreads) lz_update_dots_kernel(
+    const double* __restrict__ V, int64_t ldv, int k1, double* __restrict__ w,
+    const LzChunk* __restrict__ chunks, const LzChain* __restrict__ chains,
+    const double* __restrict__ partial, int kp, double* __restrict__ alpha,
+    double* __restrict__ partial2) {
+  extern __shared__ double wsh[];
+  __shared__ double h[kLzMaxK];
+  const LzChunk ch = chunks[blockIdx.x];
+  const LzChain cn = chains[ch.chain];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  for (int j = q; j < k1; j += kLzWarps) {
+    const double s = chain_sum(partial, kp, cn.c0, cn.nc, j, lane);
+    if (lane == 0) {
+      h[j] = s;
+      if (alpha && j == k1 - 1 && (int)blockIdx.x == cn.c0) alpha[(int64_t)ch.chain * kp + j] = s;
+    }
+  }
+  __syncthreads();
+  const int len = (int)(ch.e1 - ch.e0);
+  for (int i = threadIdx.x; i < len; i += kLzThreads) {
+    const int64_t e = ch.e0 + i;
+    double acc = w[e];
+    for (int j = 0; j < k1; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
+    w[e] = acc;
+    wsh[i] = acc;
+  }
+  __syncthreads();
+  for (int j = q; j < k1; j += kLzWarps) {
+    const double* v = V + (int64_t)j * ldv + ch.e0;
+    double acc = 0.0;
+    for (int i = lane; i < len; i += 32) acc = fma(v[i], wsh[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) partial2[(int64_t)blockIdx.x * kp + j] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(kLzThreads) lz_normalise_kernel(
     const double* __restrict__ x, double* __restrict__ y, const LzChunk* __restrict__ chunks,
     const LzChain* __restrict__ chains, const double* __restrict__ nrm_partial) {
@@ -464,6 +502,15 @@ void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzC
   count_launch();
   lz_update_kernel<<<nchunks, kLzThreads, 0, st>>>(V, ldv, k1, w, chunks, chains, partial, kp,
                                                    alpha, nrm_partial);
+}
+
+void launch_lz_update_dots(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
+                           int nchunks, const LzChain* chains, const double* partial, int kp,
+                           double* alpha, double* partial2, cudaStream_t st) {
+  if (nchunks <= 0 || k1 <= 0) return;
+  count_launch();
+  lz_update_dots_kernel<<<nchunks, kLzThreads, kLzChunkMax * sizeof(double), st>>>(
+      V, ldv, k1, w, chunks, chains, partial, kp, alpha, partial2);
 }
 
 void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,

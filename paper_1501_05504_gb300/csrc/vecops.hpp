@@ -89,6 +89,12 @@ void launch_lz_dots(const double* V, int64_t ldv, int k1, const double* w, const
 void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
                       int nchunks, const LzChain* chains, const double* partial, int kp,
                       double* alpha, double* nrm_partial, cudaStream_t st);
+// The update of one pass followed by the dots of the next: as launch_lz_update
+// (without the norm) and then launch_lz_dots of the updated w into partial2
+// (which must not be `partial`).
+void launch_lz_update_dots(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
+                           int nchunks, const LzChain* chains, const double* partial, int kp,
+                           double* alpha, double* partial2, cudaStream_t st);
 // y[e] = x[e] / sqrt(chain sum of nrm_partial); a chain whose squared norm is
 // not positive and finite gets zeros.
 void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,
