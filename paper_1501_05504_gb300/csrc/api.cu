@@ -373,7 +373,9 @@ dmrg3s_status dmrg3s_create(dmrg3s_ctx* ctx, int device, size_t workspace_bytes)
       cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_lz[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_lz[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_lz[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_lz[2], cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFreeHost(c->pinned);
     cudaFree(c->ws);
     delete c;
@@ -398,6 +400,7 @@ dmrg3s_status dmrg3s_destroy(dmrg3s_ctx ctx) {
     if (e) cudaEventDestroy(e);
   if (c->pinned_big) cudaFreeHost(c->pinned_big);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return DMRG3S_OK;
 }

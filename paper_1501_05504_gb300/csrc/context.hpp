@@ -118,7 +118,8 @@ struct Context {
   uint64_t wait_ns = 1000000000ull;   // limit of every bounded device wait (dmrg3s_set_wait_limit)
   cudaStream_t aux = nullptr;   // side stream: the Lanczos tridiagonal solve beside the next product
   cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
-  cudaEvent_t ev_lz[2] = {nullptr, nullptr};   // Lanczos results of even / odd iterations
+  cudaEvent_t ev_lz[3] = {nullptr, nullptr, nullptr};   // Lanczos results of iterations k mod 3
+  cudaStream_t cap = nullptr;   // private stream for capturing the Lanczos iteration graph
   double* pinned_big = nullptr;   // pinned read-back area of the batched Lanczos (grown on demand)
   size_t pinned_big_n = 0;        // its size in doubles
   std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> plans;

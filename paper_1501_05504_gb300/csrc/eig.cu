@@ -36,10 +36,10 @@ dmrg3s_status pinned_reserve(Context* c, size_t n) {
 //   two classical Gram-Schmidt passes of w = H v_k against v_0 .. v_k in three
 //   launches (dots; update fused with the second pass's dots; update with
 //   the partial norms of w); the first pass's last coefficient is alpha_k;
+//   v_{k+1} = w / |w|; w = H v_{k+1};
 // then, on the side stream, the tridiagonal solve of order k + 1 and the copy
-// of its results to the host, while the main stream already normalises
-// v_{k+1} and applies H to it.  The host reads iteration k's results only
-// after it has enqueued iteration k + 1, so the device never waits for the
+// of its results to the host.  The host reads iteration k's results only
+// after it has enqueued iteration k + 2, so the device never waits for the
 // host's stopping decision; a problem that has stopped keeps being iterated
 // (its results are no longer read) until every problem has stopped, and the
 // products of the iterations past the last stop are discarded (their flops
@@ -66,28 +66,32 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   std::vector<LzChain> hcn;
   lz_layout(ranges, 4 * plan_ctas(), &hch, &hcn);
   const int nchunks = (int)hch.size();
-  void *pV, *pw, *ppart, *pnp, *palpha, *pbeta, *py, *pout, *pch, *pcn, *pks;
+  void *pV, *pw, *pvc, *ppart, *pnp, *palpha, *pbeta, *py, *pout, *pch, *pcn, *pks, *pk;
   dmrg3s_status s;
   if ((s = carve(c, &cursor, sizeof(double) * ldv * kp, &pV)) ||
       (s = carve(c, &cursor, sizeof(double) * ldv, &pw)) ||
+      (s = carve(c, &cursor, sizeof(double) * ldv, &pvc)) ||
       (s = carve(c, &cursor, sizeof(double) * nchunks * kp * 2, &ppart)) ||
-      (s = carve(c, &cursor, sizeof(double) * nchunks * 3, &pnp)) ||
+      (s = carve(c, &cursor, sizeof(double) * nchunks * (kLzLag + 1), &pnp)) ||
       (s = carve(c, &cursor, sizeof(double) * np * kp, &palpha)) ||
       (s = carve(c, &cursor, sizeof(double) * np * kp, &pbeta)) ||
       (s = carve(c, &cursor, sizeof(double) * np * kp * kp, &py)) ||
       (s = carve(c, &cursor, sizeof(TridiagOut) * np * kp, &pout)) ||
       (s = carve(c, &cursor, sizeof(LzChunk) * nchunks, &pch)) ||
       (s = carve(c, &cursor, sizeof(LzChain) * np, &pcn)) ||
-      (s = carve(c, &cursor, sizeof(int32_t) * np, &pks)))
+      (s = carve(c, &cursor, sizeof(int32_t) * np, &pks)) ||
+      (s = carve(c, &cursor, sizeof(int), &pk)))
     return s;
-  // read-back slots: two iterations' results (4 doubles per problem) and the error word
+  // read-back slots: kLzLag iterations' results (4 doubles per problem) and the error word
   const size_t slot = (size_t)np * 4 + 2;
-  if ((s = pinned_reserve(c, 2 * slot + (size_t)nchunks))) return s;
+  if ((s = pinned_reserve(c, kLzLag * slot + (size_t)nchunks))) return s;
   double* V = (double*)pV;
   double* w = (double*)pw;
+  double* vcur = (double*)pvc;     // the vector the product reads: v_k
   double* part = (double*)ppart;
   double* part2 = part + (int64_t)nchunks * kp;
-  double* nrmp[3] = {(double*)pnp, (double*)pnp + nchunks, (double*)pnp + 2 * nchunks};
+  double* nrm = (double*)pnp;      // kLzLag rotating norm-partial buffers, then one more
+  double* nrm_x = nrm + (int64_t)kLzLag * nchunks;
   double* alpha = (double*)palpha;
   double* beta = (double*)pbeta;
   double* y = (double*)py;
@@ -95,6 +99,7 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   LzChunk* dch = (LzChunk*)pch;
   LzChain* dcn = (LzChain*)pcn;
   int32_t* dks = (int32_t*)pks;
+  int* kdev = (int*)pk;
   if (cudaMemcpyAsync(dch, hch.data(), sizeof(LzChunk) * nchunks, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(dcn, hcn.data(), sizeof(LzChain) * np, cudaMemcpyHostToDevice, st) !=
@@ -121,34 +126,71 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   double* pin = c->pinned_big;
 
   // v_0 = x / |x| for every problem (a zero start vector is an error)
-  launch_lz_update(nullptr, ldv, 0, X, dch, nchunks, dcn, nullptr, kp, nullptr, nrmp[2], st);
-  cudaMemcpyAsync(pin, nrmp[2], sizeof(double) * nchunks, cudaMemcpyDeviceToHost, st);
+  launch_lz_update(nullptr, ldv, 0, X, dch, nchunks, dcn, nullptr, kp, nullptr, nrm_x, st);
+  cudaMemcpyAsync(pin, nrm_x, sizeof(double) * nchunks, cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos start");
   for (int i = 0; i < np; ++i) {
     double n2 = 0.0;
     for (int b = 0; b < hcn[i].nc; ++b) n2 += pin[hcn[i].c0 + b];
     if (!(n2 > 0.0)) return fail(c, DMRG3S_ERR_BREAKDOWN, "zero start vector");
   }
-  launch_lz_normalise(X, V, dch, nchunks, dcn, nrmp[2], st);
+  launch_lz_normalise(X, V, dch, nchunks, dcn, nrm_x, st);
+  cudaMemcpyAsync(vcur, V, sizeof(double) * ldv, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(kdev, 0, sizeof(int), st);
 
   std::vector<int> kstop(np, -1);
   theta->assign(np, 0.0);
   iters->assign(np, 0);
   int nstopped = 0;
+  // an error after the recursion has started waits for both streams (the
+  // side stream still writes into the workspace the caller reuses)
+  auto bail = [&](dmrg3s_status r) {
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(c->aux);
+    return r;
+  };
   // profiler records of the product that builds on iteration k (index k + 1)
-  std::vector<std::pair<size_t, size_t>> prod_recs(kp, {0, 0});
-  auto product = [&](int j) -> dmrg3s_status {   // w = H v_j
+  std::vector<std::pair<size_t, size_t>> prod_recs(kp + 1, {0, 0});
+  auto product = [&](int j, cudaStream_t q) -> dmrg3s_status {   // w = H v_j (v_j in vcur)
     const size_t r0 = c->prof.recs.size();
-    dmrg3s_status r = run_plan(c, heff, Ldata, V + (int64_t)j * ldv, ws1, ws2, 1.0, ws2, Rdata,
-                               w, st, prec, &hints);
-    prod_recs[j] = {r0, c->prof.recs.size()};
+    dmrg3s_status r = run_plan(c, heff, Ldata, vcur, ws1, ws2, 1.0, ws2, Rdata, w, q, prec,
+                               &hints);
+    if (j >= 0) prod_recs[j] = {r0, c->prof.recs.size()};
     return r != DMRG3S_OK ? fail(c, r, "H_eff launch failed") : DMRG3S_OK;
   };
+  // Iteration k on stream q with k from the device counter: two Gram-Schmidt
+  // passes (the update of the first fused with the dots of the second),
+  // v_{k+1} into the basis and vcur, w = H v_{k+1}, k += 1.
+  auto body = [&](cudaStream_t q, int j) -> dmrg3s_status {
+    launch_lz_dots(V, ldv, 0, w, dch, nchunks, part, kp, q, kdev);
+    launch_lz_update_dots(V, ldv, 0, w, dch, nchunks, dcn, part, kp, alpha, part2, q, kdev);
+    launch_lz_update(V, ldv, 0, w, dch, nchunks, dcn, part2, kp, nullptr, nrm, q, kdev, nchunks);
+    launch_lz_next(w, V, ldv, kdev, vcur, dch, nchunks, dcn, nrm, nchunks, q);
+    dmrg3s_status r = product(j, q);
+    launch_lz_advance(kdev, q);
+    return r;
+  };
+  if ((s = product(0, st))) return bail(s);
+  // Without the profiler, the iteration is captured once into a CUDA graph
+  // (every kernel reads k from the device counter) and replayed; with it,
+  // the launches are issued directly so that each product is recorded.
+  cudaGraphExec_t gexec = nullptr;
+  if (!c->prof.on && c->cap) {
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const dmrg3s_status r = body(c->cap, -1);
+      ok = cudaStreamEndCapture(c->cap, &graph) == cudaSuccess && r == DMRG3S_OK;
+    }
+    if (ok && cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a failed capture leaves the direct launches
+  }
   // the host's reading of iteration k
   auto collect = [&](int k) -> dmrg3s_status {
-    if (cudaEventSynchronize(c->ev_lz[k & 1]) != cudaSuccess)
+    if (cudaEventSynchronize(c->ev_lz[k % kLzLag]) != cudaSuccess)
       return fail(c, DMRG3S_ERR_CUDA, "Lanczos step");
-    const double* sl = pin + (size_t)(k & 1) * slot;
+    const double* sl = pin + (size_t)(k % kLzLag) * slot;
     int dev_err = 0;
     std::memcpy(&dev_err, sl + (size_t)np * 4, sizeof(int));
     if (dev_err) {
@@ -173,45 +215,47 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
     }
     return DMRG3S_OK;
   };
-  // an error after the recursion has started waits for both streams (the
-  // side stream still writes into the workspace the caller reuses)
-  auto bail = [&](dmrg3s_status r) {
-    cudaStreamSynchronize(st);
-    cudaStreamSynchronize(c->aux);
-    return r;
-  };
-  if ((s = product(0))) return bail(s);
+  // The host reads iteration k's results two iterations later, so that the
+  // device always has the next iteration queued while the side stream solves
+  // the tridiagonal problem.
+  constexpr int kLagRead = kLzLag - 1;
   int last = -1;   // the last iteration enqueued
+  int next_read = 0;
   for (int k = 0; k < kmax; ++k) {
-    // pass 1 dots; pass 1 update with the pass 2 dots; pass 2 update with the norm
-    launch_lz_dots(V, ldv, k + 1, w, dch, nchunks, part, kp, st);
-    launch_lz_update_dots(V, ldv, k + 1, w, dch, nchunks, dcn, part, kp, alpha, part2, st);
-    launch_lz_update(V, ldv, k + 1, w, dch, nchunks, dcn, part2, kp, nullptr, nrmp[k & 1], st);
+    if (gexec) {
+      if (cudaGraphLaunch(gexec, st) != cudaSuccess)
+        s = fail(c, DMRG3S_ERR_CUDA, "Lanczos iteration graph");
+    } else {
+      s = body(st, k + 1);
+    }
+    if (s) {
+      if (gexec) cudaGraphExecDestroy(gexec);
+      return bail(s);
+    }
     cudaEventRecord(c->ev_ready, st);
     cudaStreamWaitEvent(c->aux, c->ev_ready, 0);
-    launch_lz_tridiag(dcn, np, alpha, beta, kp, k, nrmp[k & 1], y, out, c->aux);
-    double* sl = pin + (size_t)(k & 1) * slot;
+    launch_lz_tridiag(dcn, np, alpha, beta, kp, k, nrm + (int64_t)(k % kLzLag) * nchunks, y, out,
+                      c->aux);
+    double* sl = pin + (size_t)(k % kLzLag) * slot;
     cudaMemcpyAsync(sl, out + (size_t)k * np, sizeof(TridiagOut) * np, cudaMemcpyDeviceToHost,
                     c->aux);
     cudaMemcpyAsync(sl + (size_t)np * 4, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->aux);
-    cudaEventRecord(c->ev_lz[k & 1], c->aux);
+    cudaEventRecord(c->ev_lz[k % kLzLag], c->aux);
     last = k;
-    if (k + 1 < kmax) {     // speculative: the next basis vector and its product
-      launch_lz_normalise(w, V + (int64_t)(k + 1) * ldv, dch, nchunks, dcn, nrmp[k & 1], st);
-      if ((s = product(k + 1))) return bail(s);
-    }
-    if (k >= 1) {
-      if ((s = collect(k - 1))) return bail(s);
+    if (k >= kLagRead) {
+      if ((s = collect(next_read++))) break;
       if (nstopped == np) break;
     }
   }
-  if (nstopped < np) {
-    if ((s = collect(last))) return bail(s);
-    if (nstopped < np) return bail(fail(c, DMRG3S_ERR_CUDA, "Lanczos did not stop"));
+  while (!s && nstopped < np && next_read <= last) s = collect(next_read++);
+  if (!s && nstopped < np) s = fail(c, DMRG3S_ERR_CUDA, "Lanczos did not stop");
+  if (s) {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    return bail(s);
   }
   int kmaxstop = 0;
   for (int i = 0; i < np; ++i) kmaxstop = std::max(kmaxstop, kstop[i]);
-  for (int j = kmaxstop + 1; j < kp; ++j)   // the discarded products
+  for (int j = kmaxstop + 1; j <= kp; ++j)   // the discarded products (direct launches only)
     for (size_t r = prod_recs[j].first; r < prod_recs[j].second; ++r) {
       c->prof.recs[r].flops = 0.0;
       c->prof.recs[r].bytes = 0.0;
@@ -220,10 +264,16 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   cudaEventRecord(c->ev_ready, c->aux);
   cudaStreamWaitEvent(st, c->ev_ready, 0);
   if (cudaMemcpyAsync(dks, kstop.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
+      cudaSuccess) {
+    if (gexec) cudaGraphExecDestroy(gexec);
     return bail(fail(c, DMRG3S_ERR_CUDA, "Lanczos tables"));
-  launch_lz_ritz(V, ldv, dch, nchunks, dcn, dks, y, kp, w, nrmp[2], st);
-  launch_lz_normalise(w, X, dch, nchunks, dcn, nrmp[2], st);
+  }
+  launch_lz_ritz(V, ldv, dch, nchunks, dcn, dks, y, kp, w, nrm_x, st);
+  launch_lz_normalise(w, X, dch, nchunks, dcn, nrm_x, st);
+  if (gexec) {   // its last replays may still run: free it once they are done
+    cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(gexec);
+  }
   if (cudaGetLastError() != cudaSuccess) return fail(c, DMRG3S_ERR_CUDA, "Lanczos launch failed");
   return DMRG3S_OK;
 }

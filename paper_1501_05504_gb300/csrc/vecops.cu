@@ -334,10 +334,12 @@ __device__ __forceinline__ double chain_sum(const double* __restrict__ partial, 
 // products with V_j for j = q, q + 8, ...
 __global__ void __launch_bounds__(kLzThreads) lz_dots_kernel(const double* __restrict__ V,
                                                              int64_t ldv, int k1,
+                                                             const int* __restrict__ kdev,
                                                              const double* __restrict__ w,
                                                              const LzChunk* __restrict__ chunks,
                                                              double* __restrict__ partial, int kp) {
   extern __shared__ double wsh[];
+  if (kdev) k1 = *kdev + 1;
   const LzChunk ch = chunks[blockIdx.x];
   const int len = (int)(ch.e1 - ch.e0);
   for (int i = threadIdx.x; i < len; i += kLzThreads) wsh[i] = w[ch.e0 + i];
@@ -353,12 +355,16 @@ __global__ void __launch_bounds__(kLzThreads) lz_dots_kernel(const double* __res
 }
 
 __global__ void __launch_bounds__(kLzThreads) lz_update_kernel(
-    const double* __restrict__ V, int64_t ldv, int k1, double* __restrict__ w,
-    const LzChunk* __restrict__ chunks, const LzChain* __restrict__ chains,
+    const double* __restrict__ V, int64_t ldv, int k1, const int* __restrict__ kdev,
+    double* __restrict__ w, const LzChunk* __restrict__ chunks, const LzChain* __restrict__ chains,
     const double* __restrict__ partial, int kp, double* __restrict__ alpha,
-    double* __restrict__ nrm_partial) {
+    double* __restrict__ nrm_partial, int64_t nrm_stride) {
   __shared__ double h[kLzMaxK];
   __shared__ double red[32];
+  if (kdev) {
+    k1 = *kdev + 1;
+    if (nrm_partial) nrm_partial += (int64_t)(*kdev % kLzLag) * nrm_stride;
+  }
   const LzChunk ch = chunks[blockIdx.x];
   const LzChain cn = chains[ch.chain];
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
@@ -389,9 +395,10 @@ __global__ void __launch_bounds__(kLzThreads) lz_update_dots_kernel(
     const double* __restrict__ V, int64_t ldv, int k1, double* __restrict__ w,
     const LzChunk* __restrict__ chunks, const LzChain* __restrict__ chains,
     const double* __restrict__ partial, int kp, double* __restrict__ alpha,
-    double* __restrict__ partial2) {
+    double* __restrict__ partial2, const int* __restrict__ kdev) {
   extern __shared__ double wsh[];
   __shared__ double h[kLzMaxK];
+  if (kdev) k1 = *kdev + 1;
   const LzChunk ch = chunks[blockIdx.x];
   const LzChain cn = chains[ch.chain];
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
@@ -435,6 +442,34 @@ __global__ void __launch_bounds__(kLzThreads) lz_normalise_kernel(
   const double sc = scale;
   for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) y[e] = x[e] * sc;
 }
+
+// v_{k+1} = w / |w| (norm partials of iteration k, k from the device
+// counter), written into the basis and into the fixed product input vcur.
+__global__ void __launch_bounds__(kLzThreads) lz_next_kernel(
+    const double* __restrict__ w, double* __restrict__ V, int64_t ldv, const int* __restrict__ kdev,
+    double* __restrict__ vcur, const LzChunk* __restrict__ chunks,
+    const LzChain* __restrict__ chains, const double* __restrict__ nrm_partial,
+    int64_t nrm_stride) {
+  __shared__ double scale;
+  const int k = *kdev;
+  const LzChunk ch = chunks[blockIdx.x];
+  if (threadIdx.x < 32) {
+    const LzChain cn = chains[ch.chain];
+    const double n2 = chain_sum(nrm_partial + (int64_t)(k % kLzLag) * nrm_stride, 1, cn.c0, cn.nc,
+                                0, threadIdx.x);
+    if (threadIdx.x == 0) scale = (n2 > 0.0 && n2 < 1e308) ? 1.0 / sqrt(n2) : 0.0;
+  }
+  __syncthreads();
+  const double sc = scale;
+  double* vn = V + (int64_t)(k + 1) * ldv;
+  for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) {
+    const double v = w[e] * sc;
+    vn[e] = v;
+    vcur[e] = v;
+  }
+}
+
+__global__ void lz_advance_kernel(int* kdev) { *kdev += 1; }
 
 __global__ void lz_tridiag_kernel(const LzChain* __restrict__ chains, const double* __restrict__ alpha,
                                   double* __restrict__ beta, int kp, int k,
@@ -488,29 +523,44 @@ void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64
 }
 
 void launch_lz_dots(const double* V, int64_t ldv, int k1, const double* w, const LzChunk* chunks,
-                    int nchunks, double* partial, int kp, cudaStream_t st) {
-  if (k1 <= 0 || nchunks <= 0) return;
+                    int nchunks, double* partial, int kp, cudaStream_t st, const int* kdev) {
+  if ((!kdev && k1 <= 0) || nchunks <= 0) return;
   count_launch();
-  lz_dots_kernel<<<nchunks, kLzThreads, kLzChunkMax * sizeof(double), st>>>(V, ldv, k1, w, chunks,
-                                                                             partial, kp);
+  lz_dots_kernel<<<nchunks, kLzThreads, kLzChunkMax * sizeof(double), st>>>(V, ldv, k1, kdev, w,
+                                                                             chunks, partial, kp);
 }
 
 void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
                       int nchunks, const LzChain* chains, const double* partial, int kp,
-                      double* alpha, double* nrm_partial, cudaStream_t st) {
+                      double* alpha, double* nrm_partial, cudaStream_t st, const int* kdev,
+                      int64_t nrm_stride) {
   if (nchunks <= 0) return;
   count_launch();
-  lz_update_kernel<<<nchunks, kLzThreads, 0, st>>>(V, ldv, k1, w, chunks, chains, partial, kp,
-                                                   alpha, nrm_partial);
+  lz_update_kernel<<<nchunks, kLzThreads, 0, st>>>(V, ldv, k1, kdev, w, chunks, chains, partial,
+                                                   kp, alpha, nrm_partial, nrm_stride);
+}
+
+void launch_lz_next(const double* w, double* V, int64_t ldv, const int* kdev, double* vcur,
+                    const LzChunk* chunks, int nchunks, const LzChain* chains,
+                    const double* nrm_partial, int64_t nrm_stride, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  count_launch();
+  lz_next_kernel<<<nchunks, kLzThreads, 0, st>>>(w, V, ldv, kdev, vcur, chunks, chains,
+                                                 nrm_partial, nrm_stride);
+}
+
+void launch_lz_advance(int* kdev, cudaStream_t st) {
+  count_launch();
+  lz_advance_kernel<<<1, 1, 0, st>>>(kdev);
 }
 
 void launch_lz_update_dots(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
                            int nchunks, const LzChain* chains, const double* partial, int kp,
-                           double* alpha, double* partial2, cudaStream_t st) {
-  if (nchunks <= 0 || k1 <= 0) return;
+                           double* alpha, double* partial2, cudaStream_t st, const int* kdev) {
+  if (nchunks <= 0 || (!kdev && k1 <= 0)) return;
   count_launch();
   lz_update_dots_kernel<<<nchunks, kLzThreads, kLzChunkMax * sizeof(double), st>>>(
-      V, ldv, k1, w, chunks, chains, partial, kp, alpha, partial2);
+      V, ldv, k1, w, chunks, chains, partial, kp, alpha, partial2, kdev);
 }
 
 void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,

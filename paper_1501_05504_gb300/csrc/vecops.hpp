@@ -47,6 +47,7 @@ struct LzChain {
 };
 constexpr int kLzMaxK = 129;   // most basis vectors of one run (kmax <= 128, plus one)
 constexpr int kLzChunkMax = 4096;   // most elements of one chunk
+constexpr int kLzLag = 3;           // rotating norm-partial buffers of the iterations in flight
 
 // Chunks of `ranges` (one (off, n) per chain): each chain's range cut into
 // about equal chunks of at most kLzChunkMax elements, `target` chunks in all
@@ -79,22 +80,38 @@ inline void lz_layout(const std::vector<std::pair<int64_t, int64_t>>& ranges, in
   }
 }
 
+// Device-counter form: the kernels below that take `kdev` (non-null) read the
+// iteration k from that device word instead of their k1 argument (k1 = k + 1),
+// so that one captured launch sequence serves every iteration.
+//
 // partial[b * kp + j] = <V_j, w> over chunk b, for j < k1 (V_j = V + j * ldv).
 void launch_lz_dots(const double* V, int64_t ldv, int k1, const double* w, const LzChunk* chunks,
-                    int nchunks, double* partial, int kp, cudaStream_t st);
+                    int nchunks, double* partial, int kp, cudaStream_t st,
+                    const int* kdev = nullptr);
 // One Gram-Schmidt pass: h_j = (chain sum of partial[., j]), w -= sum_{j<k1} h_j V_j.
 // alpha (optional): alpha[chain * kp + k1 - 1] = h_{k1-1} (the Lanczos alpha_k).
 // nrm_partial (optional): the chunk's sum of squares of the updated w.
-// k1 = 0 leaves w unchanged and only forms nrm_partial.
+// k1 = 0 leaves w unchanged and only forms nrm_partial.  With kdev, the norm
+// partials go to nrm_partial + (k % kLzLag) * nrm_stride.
 void launch_lz_update(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
                       int nchunks, const LzChain* chains, const double* partial, int kp,
-                      double* alpha, double* nrm_partial, cudaStream_t st);
+                      double* alpha, double* nrm_partial, cudaStream_t st,
+                      const int* kdev = nullptr, int64_t nrm_stride = 0);
+// v_{k+1} = w / |w| into V + (k + 1) ldv and into vcur, k = *kdev, the norm
+// partials at nrm_partial + (k % kLzLag) * nrm_stride (zeros for a problem
+// whose squared norm is not positive and finite).
+void launch_lz_next(const double* w, double* V, int64_t ldv, const int* kdev, double* vcur,
+                    const LzChunk* chunks, int nchunks, const LzChain* chains,
+                    const double* nrm_partial, int64_t nrm_stride, cudaStream_t st);
+// *kdev += 1 (one thread).
+void launch_lz_advance(int* kdev, cudaStream_t st);
 // The update of one pass followed by the dots of the next: as launch_lz_update
 // (without the norm) and then launch_lz_dots of the updated w into partial2
 // (which must not be `partial`).
 void launch_lz_update_dots(const double* V, int64_t ldv, int k1, double* w, const LzChunk* chunks,
                            int nchunks, const LzChain* chains, const double* partial, int kp,
-                           double* alpha, double* partial2, cudaStream_t st);
+                           double* alpha, double* partial2, cudaStream_t st,
+                           const int* kdev = nullptr);
 // y[e] = x[e] / sqrt(chain sum of nrm_partial); a chain whose squared norm is
 // not positive and finite gets zeros.
 void launch_lz_normalise(const double* x, double* y, const LzChunk* chunks, int nchunks,
