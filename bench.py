@@ -694,6 +694,53 @@ def run_sweep(args):
             "data": "synthetic"}
 
 
+def run_lanczos(args):
+    """Lanczos iteration time: dmrg3s_eigensolve on a workload's central site
+    with a tolerance it cannot reach, so that exactly k iterations run (wall
+    time / k, profiler off), beside the time of one prepared H_eff product."""
+    import torch
+    from paper_1501_05504_gb300 import binding as b
+    ctx = b.dmrg3s_create(torch.cuda.current_device(), int(args.workspace_gb * (1 << 30)))
+    W, Le, Re, M0 = heff_problem_specs(b, args.workload, args.workload_m)
+    gL, gR = b.env_from_neutral(Le), b.env_from_neutral(Re)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec in [args.precision]:
+        gM, gH = b.site_from_neutral(M0), b.site_from_neutral(M0)
+        op = b.HeffOp(ctx, gL, W, gR, gM, prec)
+        for _ in range(args.warmup):
+            op.apply(gM, gH)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            op.apply(gM, gH)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        heff_us = 1e3 * e0.elapsed_time(e1) / 20
+        op.close()
+        per = {}
+        for k in args.lanczos_k:
+            ts = []
+            for r in range(args.warmup + args.steps):
+                gM = b.site_from_neutral(M0)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                _, it = b.dmrg3s_eigensolve(ctx, gL, W, gR, gM, kmax=k, tol=1e-30, prec=prec)
+                torch.cuda.synchronize()
+                if r >= args.warmup:
+                    ts.append((time.perf_counter() - t) / it)
+            per[str(k)] = 1e6 * min(ts)
+        out[prec] = {"heff_us": heff_us, "us_per_iteration": per}
+    ctx.close()
+    return {"metric": "Lanczos iteration time (us) on the central site", "unit": "us",
+            "higher_is_better": False, "results": out,
+            "config": {"workload": HEFF_DESCR.get(args.workload, args.workload), "name": args.workload,
+                       "m": args.workload_m, "steps": args.steps, "warmup": args.warmup,
+                       "what": "best of the timed runs; the graph-captured iteration (profiler off)"},
+            "data": "synthetic"}
+
+
 def run_batch(args):
     """Batched chains: the first --batch-chains chains of the 64-chain XXZ
     workload (seeded_inputs.batch_xxz_chains, seed 1005) swept together from
@@ -728,11 +775,28 @@ def run_batch(args):
     t2 = time.perf_counter()
     for st in states:
         st.close()
+    seq = None
+    if args.batch_compare:      # the same chains one at a time (dmrg3s_sweep), for comparison
+        ts = time.perf_counter()
+        for c, o in zip(chains, opts):
+            W = b.Mpo(b.MODEL_XXZ, c["L"], (c["J"], c["Delta"])).sites()
+            st = b.dmrg3s_state_create(ctx, W, b.product_state(W[0].qp, [0, 1] * (c["L"] // 2)),
+                                       None, None, c["L"] - 1)
+            if mixed:
+                b.dmrg3s_sweep(st, b.alpha_rule(ALPHA), args.batch_sweeps, 1e-9, o,
+                               final_prec="fp64", switch_tol=1e-7)
+            else:
+                b.dmrg3s_sweep(st, b.alpha_rule(ALPHA), args.batch_sweeps, 1e-9, o)
+            b.dmrg3s_energy_grad(st, b.MODEL_XXZ, (c["J"], c["Delta"]))
+            st.close()
+        torch.cuda.synchronize()
+        seq = time.perf_counter() - ts
     ctx.close()
     n = len(chains)
     return {"metric": "batched chains solved per second (sweeps to 1e-9 and dE/dJ, dE/dDelta)",
             "value": n / (t2 - t0), "unit": "chains/s", "higher_is_better": True,
             "chains": n, "sweep_s": t1 - t0, "gradient_s": t2 - t1,
+            "sequential_s": seq, "speedup_vs_sequential": (seq / (t2 - t0)) if seq else None,
             "converged": int(sum(r["converged"] for r in reps)),
             "sweeps": [r["sweeps"] for r in reps], "lanczos_iters": [r["lanczos_iters"] for r in reps],
             "energies": [r["energy"] for r in reps],
@@ -754,7 +818,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "tf32"])
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--svd", default="gesvd", choices=["gesvd", "jacobi"],
+    ap.add_argument("--svd", default="jacobi", choices=["gesvd", "jacobi"],
                     help="factorisation of the truncation's per-sector SVD")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -776,11 +840,16 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=512)
     ap.add_argument("--sweep-model", default="xxz", choices=sorted(SWEEP_MODELS))
     ap.add_argument("--sweep-max", type=int, default=16, help="sweeps per arm at most")
+    ap.add_argument("--lanczos", action="store_true",
+                    help="Lanczos iteration time on --workload's central site (--lanczos-k iterations)")
+    ap.add_argument("--lanczos-k", type=int, nargs="+", default=[10, 20, 40])
     ap.add_argument("--batch", action="store_true", help="run only the batched-chain field")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-chain field")
-    ap.add_argument("--batch-chains", type=int, default=16)
+    ap.add_argument("--batch-chains", type=int, default=8)
     ap.add_argument("--batch-sweeps", type=int, default=12)
     ap.add_argument("--batch-prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--batch-compare", action="store_true",
+                    help="also solve the same chains one at a time (dmrg3s_sweep)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="measure the cuBLAS TF32 and FP64 GEMM peaks into profiles/")
     args = ap.parse_args()
@@ -792,6 +861,8 @@ def main():
         res = run_sweep(args)
     elif args.batch:
         res = run_batch(args)
+    elif args.lanczos:
+        res = run_lanczos(args)
     elif args.heff_only:
         res = run_heff_only(args)
     else:

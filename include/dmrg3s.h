@@ -397,7 +397,9 @@ dmrg3s_status dmrg3s_mpo_get_site(dmrg3s_mpo mpo, int32_t i, dmrg3s_mpo_site* si
 
 typedef struct dmrg3s_state_s* dmrg3s_state;
 
-/* Factorisation of the truncation's per-sector SVD (Sec. V step 4); both FP64. */
+/* Factorisation of the truncation's per-sector SVD (Sec. V step 4); both FP64.
+ * DMRG3S_SVD_JACOBI is the faster one on GB300 (the Python binding's
+ * default); DMRG3S_SVD_GESVD is the value of a zero-initialised struct. */
 typedef enum dmrg3s_svd_method {
   DMRG3S_SVD_GESVD = 0,   /* cuSOLVER gesvd per sector on concurrent streams      */
   DMRG3S_SVD_JACOBI = 1   /* cuSOLVER QR, then one-sided Jacobi on R^T in this

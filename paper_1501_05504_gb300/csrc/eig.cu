@@ -64,7 +64,9 @@ dmrg3s_status lanczos_batch(Context* c, const DevicePlan& heff, const double* Ld
   for (int i = 0; i < np; ++i) ranges[i] = {probs[i].off, probs[i].n};
   std::vector<LzChunk> hch;
   std::vector<LzChain> hcn;
-  lz_layout(ranges, 4 * plan_ctas(), &hch, &hcn);
+  // about one chunk per SM: few partials per problem to finish the sums
+  // from, several elements per thread
+  lz_layout(ranges, plan_ctas(), &hch, &hcn);
   const int nchunks = (int)hch.size();
   void *pV, *pw, *pvc, *ppart, *pnp, *palpha, *pbeta, *py, *pout, *pch, *pcn, *pks, *pk;
   dmrg3s_status s;

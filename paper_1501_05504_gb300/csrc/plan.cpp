@@ -403,6 +403,25 @@ bool build_fused(Plan* p, const std::map<int64_t, CombPacked>& c2p, std::string*
   return true;
 }
 
+// Smaller combination chunks when a stage would have fewer than `target`
+// of them (small blocks: more CTAs, each with fewer rows).
+void rechunk(CombStage& c, int target) {
+  int rpc = kCombRows;
+  auto count = [&](int r) {
+    int64_t n = 0;
+    for (const CombTask& t : c.tasks) n += (t.rows + r - 1) / r;
+    return n;
+  };
+  while (rpc > 1 && count(rpc) < target) rpc /= 2;
+  if (rpc == kCombRows) return;
+  c.chunks.clear();
+  for (size_t id = 0; id < c.tasks.size(); ++id) {
+    const int rows = c.tasks[id].rows;
+    for (int r = 0; r < rows; r += rpc)
+      c.chunks.push_back(CombChunk{(int32_t)id, r, rows - r < rpc ? rows - r : rpc, 0});
+  }
+}
+
 // Bounds of every table against the buffers the stages address.
 dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t nA3, int64_t nB3,
                      int64_t nC3, std::string* err) {
@@ -491,6 +510,8 @@ dmrg3s_status finish(Plan* p, int64_t nA1, int64_t nB1, int64_t nOut2, int64_t n
     *err = "internal planning error: " + *err;
     return DMRG3S_ERR_SHAPE;
   }
+  rechunk(p->c2, 2 * plan_ctas());
+  rechunk(p->c3r, 2 * plan_ctas());
   return DMRG3S_OK;
 }
 

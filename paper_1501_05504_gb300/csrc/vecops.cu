@@ -325,9 +325,50 @@ constexpr int kLzWarps = kLzThreads / 32;
 // order (lane-strided sums, then the xor tree); every lane returns the sum.
 __device__ __forceinline__ double chain_sum(const double* __restrict__ partial, int kp, int c0,
                                             int nc, int j, int lane) {
-  double acc = 0.0;
-  for (int b = lane; b < nc; b += 32) acc += partial[(int64_t)(c0 + b) * kp + j];
-  return warp_sum(acc);
+  double a0 = 0.0, a1 = 0.0;
+  int b = lane;
+  for (; b + 32 < nc; b += 64) {     // two loads in flight per lane
+    const double x0 = partial[(int64_t)(c0 + b) * kp + j];
+    const double x1 = partial[(int64_t)(c0 + b + 32) * kp + j];
+    a0 += x0;
+    a1 += x1;
+  }
+  if (b < nc) a0 += partial[(int64_t)(c0 + b) * kp + j];
+  return warp_sum(a0 + a1);
+}
+
+// <v, x> over len elements by one warp (lane-strided), four loads in flight
+// per lane; the lanes' partial sums in a fixed order, then the xor tree.
+__device__ __forceinline__ double warp_dot(const double* __restrict__ v, const double* x, int len,
+                                           int lane) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = lane;
+  for (; i + 96 < len; i += 128) {
+    const double v0 = v[i], v1 = v[i + 32], v2 = v[i + 64], v3 = v[i + 96];
+    a0 = fma(v0, x[i], a0);
+    a1 = fma(v1, x[i + 32], a1);
+    a2 = fma(v2, x[i + 64], a2);
+    a3 = fma(v3, x[i + 96], a3);
+  }
+  for (; i < len; i += 32) a0 = fma(v[i], x[i], a0);
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// x - sum_{j < k1} h[j] V_j[e], the loads of four basis vectors in flight at a
+// time (the basis is L2-resident; the loop is latency-bound otherwise).
+__device__ __forceinline__ double lz_project(const double* __restrict__ V, int64_t ldv, int k1,
+                                             const double* h, int64_t e, double x) {
+  int j = 0;
+  for (; j + 4 <= k1; j += 4) {
+    const double v0 = V[(int64_t)j * ldv + e], v1 = V[(int64_t)(j + 1) * ldv + e];
+    const double v2 = V[(int64_t)(j + 2) * ldv + e], v3 = V[(int64_t)(j + 3) * ldv + e];
+    x = fma(-h[j], v0, x);
+    x = fma(-h[j + 1], v1, x);
+    x = fma(-h[j + 2], v2, x);
+    x = fma(-h[j + 3], v3, x);
+  }
+  for (; j < k1; ++j) x = fma(-h[j], V[(int64_t)j * ldv + e], x);
+  return x;
 }
 
 // The chunk of w is staged in shared memory once; warp q then forms the dot
@@ -346,10 +387,7 @@ __global__ void __launch_bounds__(kLzThreads) lz_dots_kernel(const double* __res
   __syncthreads();
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   for (int j = q; j < k1; j += kLzWarps) {
-    const double* v = V + (int64_t)j * ldv + ch.e0;
-    double acc = 0.0;
-    for (int i = lane; i < len; i += 32) acc = fma(v[i], wsh[i], acc);
-    acc = warp_sum(acc);
+    const double acc = warp_dot(V + (int64_t)j * ldv + ch.e0, wsh, len, lane);
     if (lane == 0) partial[(int64_t)blockIdx.x * kp + j] = acc;
   }
 }
@@ -378,8 +416,7 @@ __global__ void __launch_bounds__(kLzThreads) lz_update_kernel(
   __syncthreads();
   double nacc = 0.0;
   for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) {
-    double acc = w[e];
-    for (int j = 0; j < k1; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
+    double acc = lz_project(V, ldv, k1, h, e, w[e]);
     if (k1 > 0) w[e] = acc;
     nacc = fma(acc, acc, nacc);
   }
@@ -413,17 +450,13 @@ __global__ void __launch_bounds__(kLzThreads) lz_update_dots_kernel(
   const int len = (int)(ch.e1 - ch.e0);
   for (int i = threadIdx.x; i < len; i += kLzThreads) {
     const int64_t e = ch.e0 + i;
-    double acc = w[e];
-    for (int j = 0; j < k1; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + e], acc);
+    const double acc = lz_project(V, ldv, k1, h, e, w[e]);
     w[e] = acc;
     wsh[i] = acc;
   }
   __syncthreads();
   for (int j = q; j < k1; j += kLzWarps) {
-    const double* v = V + (int64_t)j * ldv + ch.e0;
-    double acc = 0.0;
-    for (int i = lane; i < len; i += 32) acc = fma(v[i], wsh[i], acc);
-    acc = warp_sum(acc);
+    const double acc = warp_dot(V + (int64_t)j * ldv + ch.e0, wsh, len, lane);
     if (lane == 0) partial2[(int64_t)blockIdx.x * kp + j] = acc;
   }
 }
@@ -497,8 +530,7 @@ __global__ void __launch_bounds__(kLzThreads) lz_ritz_kernel(
   const double* yc = y + ((int64_t)ch.chain * kp + ks) * kp;
   double nacc = 0.0;
   for (int64_t e = ch.e0 + threadIdx.x; e < ch.e1; e += kLzThreads) {
-    double acc = 0.0;
-    for (int j = 0; j <= ks; ++j) acc = fma(yc[j], V[(int64_t)j * ldv + e], acc);
+    const double acc = -lz_project(V, ldv, ks + 1, yc, e, 0.0);
     x[e] = acc;
     nacc = fma(acc, acc, nacc);
   }
