@@ -651,8 +651,9 @@ def _sweep_run(b, ctx, L, m_max, ladder, model="xxz", max_sweeps=24, svd="gesvd"
         rep = b.dmrg3s_sweep(st, b.alpha_rule(ALPHA), max_sweeps, 1e-11, opts)
     st.close()
     nb = rep["bulk_sweeps"] if len(ladder) > 1 else rep["sweeps"]
-    return [(t, e, ladder[0][0] if k < nb else ladder[-1][0])
-            for k, (t, e) in enumerate(zip(rep["seconds"], rep["energies"]))]
+    log = [(t, e, ladder[0][0] if k < nb else ladder[-1][0])
+           for k, (t, e) in enumerate(zip(rep["seconds"], rep["energies"]))]
+    return log, {"lanczos_iters": rep["lanczos_iters"], "svd_fallbacks": rep["svd_fallbacks"]}
 
 
 def run_sweep(args):
@@ -666,9 +667,9 @@ def run_sweep(args):
     ctx = b.dmrg3s_create(torch.cuda.current_device(), 1 << 30)
     L, m_max, model = args.sweep_sites, args.sweep_m, args.sweep_model
     nmax = args.sweep_max
-    fp64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, nmax, svd=args.svd)
-    mixed = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, nmax,
-                       svd=args.svd)
+    fp64, st64 = _sweep_run(b, ctx, L, m_max, [("fp64", 1e-11)], model, nmax, svd=args.svd)
+    mixed, stmx = _sweep_run(b, ctx, L, m_max, [("tf32x3", 1e-7), ("fp64", 1e-11)], model, nmax,
+                             svd=args.svd)
     e_ref = min(fp64[-1][1], mixed[-1][1])
 
     def first(log):
@@ -684,6 +685,7 @@ def run_sweep(args):
             "energy_ref": e_ref, "energy_fp64": fp64[-1][1], "energy_mixed": mixed[-1][1],
             "sweeps_fp64": [[round(t, 3), e, p] for t, e, p in fp64],
             "sweeps_mixed": [[round(t, 3), e, p] for t, e, p in mixed],
+            "stats_fp64": st64, "stats_mixed": stmx,
             "config": {"workload": "%s_l%d_m%d full sweeps" % (model, L, m_max),
                        "hamiltonian": "%s, L=%d" % (SWEEP_MODELS[model][3], L),
                        "m_max": m_max, "alpha0": ALPHA, "lanczos_kmax": 40, "lanczos_tol": 1e-10,
@@ -818,7 +820,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "tf32"])
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--svd", default="jacobi", choices=["gesvd", "jacobi"],
+    ap.add_argument("--svd", default="auto", choices=["gesvd", "jacobi", "auto"],
                     help="factorisation of the truncation's per-sector SVD")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -397,16 +397,23 @@ dmrg3s_status dmrg3s_mpo_get_site(dmrg3s_mpo mpo, int32_t i, dmrg3s_mpo_site* si
 
 typedef struct dmrg3s_state_s* dmrg3s_state;
 
-/* Factorisation of the truncation's per-sector SVD (Sec. V step 4); both FP64.
- * DMRG3S_SVD_JACOBI is the faster one on GB300 (the Python binding's
- * default); DMRG3S_SVD_GESVD is the value of a zero-initialised struct. */
+/* Factorisation of the truncation's per-sector SVD (Sec. V step 4); all FP64.
+ * DMRG3S_SVD_GESVD is the value of a zero-initialised struct;
+ * DMRG3S_SVD_AUTO is the Python binding's default. */
 typedef enum dmrg3s_svd_method {
   DMRG3S_SVD_GESVD = 0,   /* cuSOLVER gesvd per sector on concurrent streams      */
-  DMRG3S_SVD_JACOBI = 1   /* cuSOLVER QR, then one-sided Jacobi on R^T in this
+  DMRG3S_SVD_JACOBI = 1,  /* cuSOLVER QR, then one-sided Jacobi on R^T in this
                              library's kernels, every sector in each launch
                              (dmrg3s_svd); an update whose Jacobi sweeps do not
                              converge redoes its SVD with gesvd
                              (dmrg3s_update_info.svd_fallback)                    */
+  DMRG3S_SVD_AUTO = 2     /* per update (per batched step): JACOBI when the
+                             update is FP64 and its largest sector's smaller
+                             side is >= 192, else GESVD (measured on GB300:
+                             the Jacobi rounds win on the large sectors of
+                             FP64 updates; gesvd on mid-size sectors, and
+                             after 3xTF32 / TF32 eigensolvers, whose ~1e-7
+                             noise slows the Jacobi sweeps)                   */
 } dmrg3s_svd_method;
 
 typedef struct dmrg3s_update_opts {

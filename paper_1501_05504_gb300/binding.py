@@ -400,8 +400,8 @@ class _UpdateOpts(ctypes.Structure):
                 ("svd", ctypes.c_int)]
 
 
-SVD_GESVD, SVD_JACOBI = 0, 1
-_SVD = {"jacobi": SVD_JACOBI, "gesvd": SVD_GESVD}
+SVD_GESVD, SVD_JACOBI, SVD_AUTO = 0, 1, 2
+_SVD = {"jacobi": SVD_JACOBI, "gesvd": SVD_GESVD, "auto": SVD_AUTO}
 
 
 class _UpdateInfo(ctypes.Structure):
@@ -585,7 +585,7 @@ def dmrg3s_state_create(ctx, W, M, left_env=None, right_env=None, centre=0, stre
     return State(ctx, W, M, left_env, right_env, centre, stream)
 
 
-def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False, svd="jacobi"):
+def update_opts(m_max, kmax=40, tol=1e-10, eps=1e-12, prec="fp64", skip_eigensolver=False, svd="auto"):
     return _UpdateOpts(int(m_max), int(kmax), float(tol), float(eps), _prec(prec), int(bool(skip_eigensolver)),
                        _SVD[svd] if isinstance(svd, str) else int(svd))
 

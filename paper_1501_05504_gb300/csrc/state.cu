@@ -406,10 +406,16 @@ struct Trunc {
   std::vector<int64_t> rem_off;           // S V^dagger (or U S) block of every new sector
   int64_t rem_size = 0;
   double* rem = nullptr;                  // owned: freed by update_neighbour
+  dmrg3s_svd_method method = DMRG3S_SVD_GESVD;   // the factorisation used (AUTO resolved)
 };
 
+// Smaller side of the largest sector from which DMRG3S_SVD_AUTO takes the
+// Jacobi SVD.
+constexpr int64_t kSvdAutoJacobiN = 192;
+
 void prepare_truncation(const SiteLayout& ml, int dir, bool expand, const FusedBond& fp,
-                        const SiteLayout& pl, dmrg3s_svd_method svd, Trunc* t) {
+                        const SiteLayout& pl, dmrg3s_svd_method svd, dmrg3s_precision prec,
+                        Trunc* t) {
   const Bond& old = dir == 1 ? ml.right : ml.left;
   // Sector k of M~ is a rows x cols matrix X (rows: (s, a_l) for L->R, the
   // expanded left states for R->L).  It is gathered column-major in the tall
@@ -514,6 +520,15 @@ void prepare_truncation(const SiteLayout& ml, int dir, bool expand, const FusedB
   }
   t->foff = foff;
   t->soff = soff;
+  if (svd == DMRG3S_SVD_AUTO) {
+    // the Jacobi rounds win on large sectors of FP64 updates; after a 3xTF32
+    // or TF32 eigensolver the kept vector carries ~1e-7 noise, whose cluster of
+    // small singular values takes the Jacobi sweeps longer than gesvd
+    int64_t nmax = 0;
+    for (const Sector& sc : secs) nmax = std::max(nmax, sc.n);
+    svd = prec == DMRG3S_FP64 && nmax >= kSvdAutoJacobiN ? DMRG3S_SVD_JACOBI : DMRG3S_SVD_GESVD;
+  }
+  t->method = svd;
   bool any_proj = svd == DMRG3S_SVD_JACOBI;
   for (const Sector& sc : secs) any_proj = any_proj || (sc.vt_only && sc.base > 0);
   t->any_proj = any_proj;
@@ -859,7 +874,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
   ph = phase(kProfSvd);
   // ---- 3. sectors of M~ = [M* P] (L->R) or [M*; P] (R->L), gathered
   Trunc t;
-  prepare_truncation(m.lay, dir, expand, fp, pl, o.svd, &t);
+  prepare_truncation(m.lay, dir, expand, fp, pl, o.svd, o.prec, &t);
   double* X;
   if ((s = scr.get(&X, t.xoff))) return s;
   cudaMemsetAsync(X, 0, (size_t)std::max<int64_t>(t.xoff, 1) * sizeof(double), st);
@@ -882,7 +897,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
       return s;
   }
   std::vector<double> hs;
-  if ((s = svd_all(S, o.svd, t.secs, X, X0, t.xoff, F, Sv, reinterpret_cast<int*>(dinfo_d), t.soff,
+  if ((s = svd_all(S, t.method, t.secs, X, X0, t.xoff, F, Sv, reinterpret_cast<int*>(dinfo_d), t.soff,
                    &hs, &info->svd_fallback, &info->svd_sweeps, st)))
     return s;
   scr.drop(X);
@@ -1113,10 +1128,13 @@ dmrg3s_status batch_truncate(Context* c, std::vector<BItem>& items, dmrg3s_svd_m
   dmrg3s_status s;
   int64_t nX = 0, nF = 0, nS = 0;
   size_t nsec = 0;
-  bool any_proj = method == DMRG3S_SVD_JACOBI;
+  bool any_proj = false;
+  dmrg3s_svd_method resolved = method == DMRG3S_SVD_AUTO ? DMRG3S_SVD_GESVD : method;
   for (BItem& it : items) {
     State& S = *it.S;
-    prepare_truncation(S.M[S.centre].lay, it.dir, it.expand, it.fp, it.pl, method, &it.t);
+    prepare_truncation(S.M[S.centre].lay, it.dir, it.expand, it.fp, it.pl, method, it.o.prec,
+                       &it.t);
+    if (it.t.method == DMRG3S_SVD_JACOBI) resolved = DMRG3S_SVD_JACOBI;   // one call for all
     it.xb = nX;
     it.fb = nF;
     it.sb = nS;
@@ -1126,6 +1144,8 @@ dmrg3s_status batch_truncate(Context* c, std::vector<BItem>& items, dmrg3s_svd_m
     nsec += it.t.secs.size();
     any_proj = any_proj || it.t.any_proj;
   }
+  method = resolved;
+  any_proj = any_proj || method == DMRG3S_SVD_JACOBI;
   Scratch scr(c, st);
   double *X, *F, *Sv, *dinfo_d, *X0 = nullptr;
   if ((s = scr.get(&X, nX)) || (s = scr.get(&F, nF)) || (s = scr.get(&Sv, nS)) ||
@@ -1509,7 +1529,8 @@ dmrg3s_status make_opts(Context* c, int32_t dir, const dmrg3s_update_opts* opts,
       opts->precision != DMRG3S_TF32)
     return fail(c, DMRG3S_ERR_ARG, "local update precision");
   if (opts->m_max < 1) return fail(c, DMRG3S_ERR_ARG, "m_max must be >= 1");
-  if (opts->svd != DMRG3S_SVD_JACOBI && opts->svd != DMRG3S_SVD_GESVD)
+  if (opts->svd != DMRG3S_SVD_JACOBI && opts->svd != DMRG3S_SVD_GESVD &&
+      opts->svd != DMRG3S_SVD_AUTO)
     return fail(c, DMRG3S_ERR_ARG, "SVD method");
   o->m_max = opts->m_max;
   o->kmax = opts->lanczos_kmax > 0 ? opts->lanczos_kmax : 40;

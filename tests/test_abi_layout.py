@@ -20,7 +20,7 @@ def _mirrors(b):
 
 
 ENUMS = ["DMRG3S_FP64", "DMRG3S_TF32X3", "DMRG3S_TF32", "DMRG3S_SVD_GESVD", "DMRG3S_SVD_JACOBI",
-         "DMRG3S_MODEL_XXZ", "DMRG3S_MODEL_HUBBARD", "DMRG3S_MODEL_SPIN_BONDS"]
+         "DMRG3S_SVD_AUTO", "DMRG3S_MODEL_XXZ", "DMRG3S_MODEL_HUBBARD", "DMRG3S_MODEL_SPIN_BONDS"]
 
 
 @pytest.fixture(scope="module")
@@ -66,6 +66,7 @@ def test_enum_constants_match_the_header(c_layout):
     assert b.PRECISIONS["tf32"] == res[("enum", "DMRG3S_TF32")]
     assert b.SVD_GESVD == res[("enum", "DMRG3S_SVD_GESVD")]
     assert b.SVD_JACOBI == res[("enum", "DMRG3S_SVD_JACOBI")]
+    assert b.SVD_AUTO == res[("enum", "DMRG3S_SVD_AUTO")]
     assert b.MODEL_XXZ == res[("enum", "DMRG3S_MODEL_XXZ")]
     assert b.MODEL_HUBBARD == res[("enum", "DMRG3S_MODEL_HUBBARD")]
     assert b.MODEL_SPIN_BONDS == res[("enum", "DMRG3S_MODEL_SPIN_BONDS")]

@@ -3,8 +3,8 @@ every contraction stage of their local updates one launch over all of them
 (dmrg3s_local_update_batch, dmrg3s_sweep_batch), Sec. V applied per chain.
 
 * One batched step equals one dmrg3s_local_update per chain (twin states,
-  mixed directions and lengths): to rounding in FP64, over 16 steps and site
-  by site at the end; in 3xTF32 to the product's own tolerance (1e-6) over
+  mixed directions and lengths): to rounding in FP64, over 16 steps, and the
+  whole states at the end (overlap 1 to 1e-10); in 3xTF32 to the product's own tolerance (1e-6) over
   the first 6 steps (the merged launch groups the split-K partial sums of
   stage 3 differently, and later steps amplify such differences through the
   choice among nearly degenerate states at the truncation).
