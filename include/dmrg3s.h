@@ -419,7 +419,8 @@ typedef enum dmrg3s_svd_method {
 typedef struct dmrg3s_update_opts {
   int32_t m_max;            /* bond dimension kept after truncation (Sec. V step 4) */
   int32_t lanczos_kmax;     /* <= 0: 40                                            */
-  double lanczos_tol;       /* <= 0: 1e-10                                         */
+  double lanczos_tol;       /* <= 0: 1e-10; with 3xTF32 products at least 3e-7 and
+                               with TF32 at least 3e-4 (the products' accuracy)      */
   double trunc_eps;         /* singular values <= eps * s_max are dropped; <= 0: 1e-12 */
   dmrg3s_precision precision;
   int32_t skip_eigensolver; /* != 0: keep M as is (a pure gauge/expansion move)    */

@@ -279,12 +279,21 @@ dmrg3s_status rayleigh(State& S, int i, const double* x, cudaStream_t st, double
 struct Opts {
   int m_max = 64;
   int kmax = 40;
-  double tol = 1e-10;
+  double tol = 1e-10;       // the caller's Lanczos tolerance (lanczos_tol below applies the floor)
   double eps = 1e-12;
   bool optimise = true;
   dmrg3s_precision prec = DMRG3S_FP64;   // arithmetic of the eigensolver's H_eff products
   dmrg3s_svd_method svd = DMRG3S_SVD_GESVD;
 };
+
+// The Lanczos tolerance of a local update: the caller's, but not below the
+// accuracy of the products (3xTF32 H_eff ~2e-7 relative, TF32 ~1e-3): below
+// it the recursion only resolves the products' rounding.
+inline double lanczos_tol(const Opts& o) {
+  if (o.prec == DMRG3S_TF32X3) return std::max(o.tol, 3e-7);
+  if (o.prec == DMRG3S_TF32) return std::max(o.tol, 3e-4);
+  return o.tol;
+}
 
 struct Info {
   double lambda = 0.0, e_f = 0.0, discarded = 0.0;
@@ -835,7 +844,7 @@ dmrg3s_status local_update(State& S, int dir, double alpha, const Opts& o, Info*
     size_t cursor = (size_t)plan_ws_doubles(hp->host, o.prec) * sizeof(double);
     double lam = 0.0;
     int it = 0;
-    if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, m.data, m.lay.size, o.kmax, o.tol,
+    if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, m.data, m.lay.size, o.kmax, lanczos_tol(o),
                          cursor, st, &lam, &it, o.prec)))
       return s;
     info->lambda = lam;
@@ -986,7 +995,7 @@ dmrg3s_status batch_eig(Context* c, std::vector<BItem>& items, cudaStream_t st) 
       if ((s = heff_plan(c, S.Lenv[i].lay, S.W[i], S.Renv[i].lay, S.M[i].lay, &hp))) return s;
       const size_t cursor = (size_t)plan_ws_doubles(hp->host, prec) * sizeof(double);
       if ((s = lanczos_run(c, *hp, S.Lenv[i].data, S.Renv[i].data, S.M[i].data, S.M[i].lay.size,
-                           it.o.kmax, it.o.tol, cursor, st, &it.info.lambda, &it.info.iters, prec)))
+                           it.o.kmax, lanczos_tol(it.o), cursor, st, &it.info.lambda, &it.info.iters, prec)))
         return s;
       continue;
     }
@@ -1004,7 +1013,7 @@ dmrg3s_status batch_eig(Context* c, std::vector<BItem>& items, cudaStream_t st) 
       q.oB1 = nX;
       q.oB3 = nR;
       q.oC3 = nX;
-      specs[k] = LzSpec{nX, S.M[i].lay.size, g[k]->o.kmax, g[k]->o.tol};
+      specs[k] = LzSpec{nX, S.M[i].lay.size, g[k]->o.kmax, lanczos_tol(g[k]->o)};
       nL += align32(S.Lenv[i].lay.size);
       nR += align32(S.Renv[i].lay.size);
       nX += align32(S.M[i].lay.size);
