@@ -4,10 +4,11 @@ every contraction stage of their local updates one launch over all of them
 
 * One batched step equals one dmrg3s_local_update per chain (twin states,
   mixed directions and lengths): to rounding in FP64, over 16 steps, and the
-  whole states at the end (overlap 1 to 1e-10); in 3xTF32 to the product's own tolerance (1e-6) over
-  the first 6 steps (the merged launch groups the split-K partial sums of
-  stage 3 differently, and later steps amplify such differences through the
-  choice among nearly degenerate states at the truncation).
+  whole states at the end (overlap 1 to 1e-10); in 3xTF32 to the product's
+  own tolerance (1e-6) over the first 6 steps (the merged launch groups the
+  split-K partial sums of stage 3 differently, and later steps amplify such
+  differences through the choice among nearly degenerate states at the
+  truncation).
 * The chains of the batched-chain workload (seed 1005) that exact
   diagonalisation reaches (L <= 20), with three short chains beside them,
   swept as one batch: every energy within 1e-9 of sparse exact
