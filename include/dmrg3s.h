@@ -465,7 +465,9 @@ dmrg3s_status dmrg3s_state_destroy(dmrg3s_state state);
  *     L_i from A~_i; E_f = <B~|H_eff(i+1)|B~> / <B~|B~>.
  *   dir = -1: the mirror image with P_i = alpha R_{i+1} M_i W_i, M~ = [M_i; P_i].
  * alpha = 0 skips the expansion (plain single-site update).  Synchronous
- * (the SVD's singular values are read back to choose the kept states). */
+ * (the SVD's singular values are read back to choose the kept states).  An
+ * error in the middle of an update leaves the state in an unspecified (but
+ * freeable) condition. */
 dmrg3s_status dmrg3s_local_update(dmrg3s_state state, int32_t dir, double alpha,
                                   const dmrg3s_update_opts* opts, dmrg3s_update_info* info,
                                   dmrg3s_stream stream);
@@ -534,7 +536,9 @@ dmrg3s_status dmrg3s_sweep(dmrg3s_state state, const dmrg3s_alpha_rule* rule,
  * summation order of the merged reductions).  The states must be distinct
  * and share one context and one SVD method (update.svd).  Synchronous.
  * Errors: those of dmrg3s_local_update; ARG (mixed contexts or SVD methods,
- * a state twice). */
+ * a state twice).  As with dmrg3s_local_update, an error in the middle of a
+ * step leaves the states of the batch in an unspecified (but freeable)
+ * condition: destroy them and start again. */
 /* One local update on each of nstates states: dirs[k], alphas[k], opts[k]
  * for state k, infos[k] its result (as dmrg3s_local_update). */
 dmrg3s_status dmrg3s_local_update_batch(const dmrg3s_state* states, int32_t nstates,
