@@ -57,7 +57,7 @@ inline void lz_layout(const std::vector<std::pair<int64_t, int64_t>>& ranges, in
   int64_t total = 0;
   for (auto& r : ranges) total += r.second;
   int64_t len = target > 0 ? (total + target - 1) / target : total;
-  len = (len + 255) / 256 * 256;
+  len = (len + 31) / 32 * 32;
   if (len < 256) len = 256;
   if (len > kLzChunkMax) len = kLzChunkMax;
   chunks->clear();
