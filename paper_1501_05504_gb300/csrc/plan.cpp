@@ -83,8 +83,8 @@ namespace {
 
 // Static schedule of a stage's units over the persistent CTAs: longest
 // processing time first onto the least loaded CTA.  A unit's cost is its
-// k-chunks, each weighted half as a fixed share (the A slab's copy and the
-// issue latency, the same for every width) and half by its MMA width, plus a
+// k-chunks, each weighted 0.7 as a fixed share (the A slab's copy and the
+// issue latency, the same for every width) and 0.3 by its MMA width, plus a
 // fixed share for its drain and store.
 void schedule_units(TcStage& tc, const std::vector<GemmTask>& tasks) {
   const int n = (int)tc.units.size();
@@ -93,7 +93,7 @@ void schedule_units(TcStage& tc, const std::vector<GemmTask>& tasks) {
   for (int i = 0; i < n; ++i) {
     const TcUnit& u = tc.units[i];
     const int nrem = std::min(128, tasks[u.task].N - u.tn * 128);
-    cost[i] = u.nchunks * (0.5 + 0.5 * (double)((nrem + 15) / 16 * 16) / 128.0) + 4.0;
+    cost[i] = u.nchunks * (0.7 + 0.3 * (double)((nrem + 15) / 16 * 16) / 128.0) + 4.0;
   }
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
