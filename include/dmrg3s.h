@@ -208,7 +208,7 @@ dmrg3s_status dmrg3s_expanded_bond(int32_t nsym, const dmrg3s_bond* bond, int32_
  * (device; not modified).  With its columns in descending norm order (A P),
  * each is factorised A P = Q R (cuSOLVER Householder QR, on a copy) and R^T
  * is orthogonalised by one-sided Jacobi rotations (the parallel
- * round-robin order over column pairs, one CTA per pair, every matrix in each
+ * round-robin order over column pairs, one warp per pair, every matrix in each
  * launch) until no pair has |<y_a, y_b>| > max(sqrt(n), 32) 2^-52 |y_a| |y_b|.
  * Outputs, back to back per matrix (device): S (n[k] singular values,
  * descending), VT (n[k] x n[k], ld n[k]; row c = right singular vector c,

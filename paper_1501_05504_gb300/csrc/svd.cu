@@ -25,9 +25,9 @@
 // (r + k) mod N with (r - k) mod N for k = 1 .. n'/2 - 1; the N rounds of a
 // sweep meet every pair exactly once and the pairs of one round are disjoint
 // (a pair with the padding column N = n, n odd, is skipped).  Every pair of a
-// round is one CTA and one launch runs a round of every matrix of the batch;
+// round is one warp and one launch runs a round of every matrix of the batch;
 // one sweep (a launch per round) is a CUDA graph.  A matrix with no rotation
-// in a sweep is converged and its CTAs exit at once in later sweeps.
+// in a sweep is converged and its warps exit at once in later sweeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,7 +50,7 @@ constexpr int kJacThreads = 128;
 struct JacJob {
   int64_t offA, offY, offV, offTau;   // Y = R^T (n x n, ld n); V1 (n x n) or offV = -1
   int64_t offS, offVT, offU;          // outputs (offU = -1: no left vectors)
-  int32_t m, n, npad, cta0;           // cta0: first CTA of the matrix in a round launch
+  int32_t m, n, npad, pair0;          // pair0: first pair of the matrix in a round launch
   int32_t col0, pad;                  // first column of the matrix in the batch numbering
   double tol2;                        // the square of the pair tolerance
 };
@@ -154,27 +154,52 @@ __device__ __forceinline__ void jacobi_rotation(double saa, double sbb, double s
 // Advances the sweep counter read by the round kernels (first node of a sweep).
 __global__ void jac_next_sweep_kernel(int* sweep) { *sweep += 1; }
 
-// One round r of the current sweep for every matrix: one CTA per pair.
-// rot[s * njobs + job] counts the rotations of sweep s.  The first kJacCache
-// elements of each thread's share stay in registers between the dot products
-// and the rotation; the rotation itself (a few FP64 divisions and square
-// roots) is computed once, by thread 0.
-constexpr int kJacCache = 4;
-__global__ void __launch_bounds__(kJacThreads)
-jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_job, int njobs, int r,
-                 const int* __restrict__ sweep, int* __restrict__ rot, double* __restrict__ Y,
-                 double* __restrict__ V) {
-  __shared__ double red[3][kJacThreads / 32];
-  __shared__ double cs_sn[2];
-  __shared__ int go;
+// Sums of three per-lane values over the warp, returned to every lane with
+// the same bits in every lane.  The first two levels exchange halves of the
+// values a lane carries (the lower 16 lanes go on with x and y, the upper
+// with z and a zero; then each group of 8 with one of those), so the five
+// levels take 6 FP64 additions instead of the 15 of a butterfly per value;
+// the last three levels are a butterfly within each group of 8 lanes, whose
+// lanes then hold identical sums (IEEE addition commutes bit for bit).
+__device__ __forceinline__ void warp_sum3(double& x, double& y, double& z) {
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+  const double w = 0.0;
+  const double a = (hi16 ? z : x) + __shfl_xor_sync(0xffffffffu, hi16 ? x : z, 16);
+  const double b = (hi16 ? w : y) + __shfl_xor_sync(0xffffffffu, hi16 ? y : w, 16);
+  double c = (hi8 ? b : a) + __shfl_xor_sync(0xffffffffu, hi8 ? a : b, 8);
+  for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  x = __shfl_sync(0xffffffffu, c, 0);    // lanes 0-7: the sum of x
+  y = __shfl_sync(0xffffffffu, c, 8);    // lanes 8-15: of y
+  z = __shfl_sync(0xffffffffu, c, 16);   // lanes 16-23: of z
+}
+
+// One round r of the current sweep for every matrix: one warp per pair,
+// kJacPairsPerCta pairs per CTA.  rot[s * njobs + job] counts the rotations
+// of sweep s.  GB300 runs an FP64 warp instruction in ~64 cycles of a
+// sub-partition, so the round is priced in FP64 instructions: a warp per
+// pair does the pair's three dot products and its rotation with the same
+// count as a CTA would, but reduces once instead of once per warp, and every
+// lane computes the (identical) rotation itself, with no shared memory, CTA
+// barrier or single-thread step.  The first kJacCache elements of each
+// lane's share stay in registers between the dot products and the rotation.
+constexpr int kJacPairsPerCta = 4;
+constexpr int kJacCache = 8;
+__global__ void __launch_bounds__(32 * kJacPairsPerCta)
+jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ pair_job, int npairs,
+                 int njobs, int r, const int* __restrict__ sweep, int* __restrict__ rot,
+                 double* __restrict__ Y, double* __restrict__ V) {
+  const int p = blockIdx.x * kJacPairsPerCta + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= npairs) return;
   const int sw = *sweep;
   if (sw < 0 || sw >= kJacobiMaxSweeps) return;
-  const int jb = cta_job[blockIdx.x];
+  const int jb = pair_job[p];
   if (sw > 0 && rot[(sw - 1) * njobs + jb] == 0) return;   // converged in the previous sweep
   const JacJob J = jobs[jb];
   const int N = J.npad - 1;
   if (r >= N) return;
-  const int k = blockIdx.x - J.cta0;
+  const int k = p - J.pair0;
   int a, b;
   if (k == 0) {
     a = r;
@@ -191,63 +216,34 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
   double saa = 0.0, sbb = 0.0, sab = 0.0;
 #pragma unroll
   for (int e = 0; e < kJacCache; ++e) {
-    const int i = threadIdx.x + e * kJacThreads;
+    const int i = lane + e * 32;
     ua[e] = i < n ? ya[i] : 0.0;
     ub[e] = i < n ? yb[i] : 0.0;
     saa = fma(ua[e], ua[e], saa);
     sbb = fma(ub[e], ub[e], sbb);
     sab = fma(ua[e], ub[e], sab);
   }
-  for (int i = threadIdx.x + kJacCache * kJacThreads; i < n; i += kJacThreads) {
+  for (int i = lane + kJacCache * 32; i < n; i += 32) {
     const double u = ya[i], v = yb[i];
     saa = fma(u, u, saa);
     sbb = fma(v, v, sbb);
     sab = fma(u, v, sab);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    saa += __shfl_xor_sync(0xffffffffu, saa, o);
-    sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-    sab += __shfl_xor_sync(0xffffffffu, sab, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = saa;
-    red[1][threadIdx.x >> 5] = sbb;
-    red[2][threadIdx.x >> 5] = sab;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    saa = red[0][0];
-    sbb = red[1][0];
-    sab = red[2][0];
-    for (int w = 1; w < kJacThreads / 32; ++w) {
-      saa += red[0][w];
-      sbb += red[1][w];
-      sab += red[2][w];
-    }
-    int g = 0;
-    // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
-    if (saa > 0.0 && sbb > 0.0 && sab * sab > J.tol2 * saa * sbb) {
-      double cs, sn;
-      jacobi_rotation(saa, sbb, sab, &cs, &sn);
-      cs_sn[0] = cs;
-      cs_sn[1] = sn;
-      g = 1;
-      atomicAdd(rot + sw * njobs + jb, 1);
-    }
-    go = g;
-  }
-  __syncthreads();
-  if (!go) return;
-  const double cs = cs_sn[0], sn = cs_sn[1];
+  warp_sum3(saa, sbb, sab);
+  // zero columns and NaN leave the pair unrotated (NaN reaches the singular values)
+  if (!(saa > 0.0 && sbb > 0.0 && sab * sab > J.tol2 * saa * sbb)) return;
+  double cs, sn;
+  jacobi_rotation(saa, sbb, sab, &cs, &sn);
+  if (lane == 0) atomicAdd(rot + sw * njobs + jb, 1);
 #pragma unroll
   for (int e = 0; e < kJacCache; ++e) {
-    const int i = threadIdx.x + e * kJacThreads;
+    const int i = lane + e * 32;
     if (i < n) {
       ya[i] = cs * ua[e] - sn * ub[e];
       yb[i] = sn * ua[e] + cs * ub[e];
     }
   }
-  for (int i = threadIdx.x + kJacCache * kJacThreads; i < n; i += kJacThreads) {
+  for (int i = lane + kJacCache * 32; i < n; i += 32) {
     const double u = ya[i], v = yb[i];
     ya[i] = cs * u - sn * v;
     yb[i] = sn * u + cs * v;
@@ -255,7 +251,7 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
   if (J.offV >= 0) {
     double* va = V + J.offV + (int64_t)a * n;
     double* vb = V + J.offV + (int64_t)b * n;
-    for (int i = threadIdx.x; i < n; i += kJacThreads) {
+    for (int i = lane; i < n; i += 32) {
       const double u = va[i], v = vb[i];
       va[i] = cs * u - sn * v;
       vb[i] = sn * u + cs * v;
@@ -263,7 +259,6 @@ jac_round_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ cta_jo
   }
 }
 
-// sigma of every column of every Y.  One CTA per column.
 __global__ void __launch_bounds__(kJacThreads)
 jac_norm_kernel(const JacJob* __restrict__ jobs, const int* __restrict__ col_job,
                 const double* __restrict__ Y, double* __restrict__ sig) {
@@ -355,7 +350,7 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   if (nlanes < 1) return fail(c, DMRG3S_ERR_ARG, "no SVD lane");
   // ---- tables
   std::vector<JacJob> tab(nj);
-  std::vector<int> cta_job, col_job;
+  std::vector<int> pair_job, col_job;
   int64_t ny = 0, nv = 0, ntau = 0;
   int maxr = 0;
   for (int k = 0; k < nj; ++k) {
@@ -377,22 +372,23 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     t.m = (int32_t)jb.m;
     t.n = (int32_t)jb.n;
     t.npad = t.n + (t.n & 1);
-    t.cta0 = (int32_t)cta_job.size();
+    t.pair0 = (int32_t)pair_job.size();
     t.col0 = (int32_t)col_job.size();
     t.pad = 0;
     const double tol = std::max(std::sqrt((double)t.n), 32.0) * DBL_EPSILON;
     t.tol2 = tol * tol;
-    cta_job.insert(cta_job.end(), t.npad / 2, k);
+    pair_job.insert(pair_job.end(), t.npad / 2, k);
     col_job.insert(col_job.end(), t.n, k);
     maxr = std::max(maxr, t.npad - 1);
   }
-  const int ncta = (int)cta_job.size(), ncol = (int)col_job.size();
+  const int npair = (int)pair_job.size(), ncol = (int)col_job.size();
+  const int ncta = (npair + kJacPairsPerCta - 1) / kJacPairsPerCta;
   int64_t na = 0;   // extent of the A buffer used by the jobs
   for (const JacJob& t : tab) na = std::max(na, t.offA + (int64_t)t.m * t.n);
   // ---- device buffers: doubles [tau | Y | V1 | sigma | column norms | T = A P],
-  //      ints [cta_job | col_job | perm | rot | sweep | qinfo]
+  //      ints [pair_job | col_job | perm | rot | sweep | qinfo]
   const int64_t nd = ntau + ny + nv + 2 * (int64_t)ncol + na;
-  const int64_t ni = ncta + 2 * (int64_t)ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj;
+  const int64_t ni = npair + 2 * (int64_t)ncol + (int64_t)kJacobiMaxSweeps * nj + 1 + nj;
   double* dd = nullptr;
   int* di = nullptr;
   JacJob* dt = nullptr;
@@ -410,14 +406,14 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
   double* sig = V1 + nv;
   double* anrm = sig + ncol;
   double* T = anrm + ncol;
-  int* d_cta = di;
-  int* d_col = d_cta + ncta;
+  int* d_pair = di;
+  int* d_col = d_pair + npair;
   int* d_perm = d_col + ncol;
   int* rot = d_perm + ncol;
   int* d_sweep = rot + (int64_t)kJacobiMaxSweeps * nj;
   int* qinfo = d_sweep + 1;
   cudaMemcpyAsync(dt, tab.data(), tab.size() * sizeof(JacJob), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_cta, cta_job.data(), cta_job.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_pair, pair_job.data(), pair_job.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_col, col_job.data(), col_job.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(rot, 0, (size_t)kJacobiMaxSweeps * nj * sizeof(int), st);
   cudaMemsetAsync(d_sweep, 0xff, sizeof(int), st);   // -1: the first sweep advances it to 0
@@ -545,7 +541,8 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
       cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     jac_next_sweep_kernel<<<1, 1, 0, cap>>>(d_sweep);
     for (int r = 0; r < maxr; ++r)
-      jac_round_kernel<<<ncta, kJacThreads, 0, cap>>>(dt, d_cta, nj, r, d_sweep, rot, Y, V1);
+      jac_round_kernel<<<ncta, 32 * kJacPairsPerCta, 0, cap>>>(dt, d_pair, npair, nj, r, d_sweep,
+                                                              rot, Y, V1);
     if (cudaStreamEndCapture(cap, &graph) != cudaSuccess ||
         cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
       gexec = nullptr;
@@ -564,7 +561,8 @@ dmrg3s_status svd_jacobi(Context* c, std::vector<SvdLane>& lanes, int nlanes,
     } else {
       jac_next_sweep_kernel<<<1, 1, 0, st>>>(d_sweep);
       for (int r = 0; r < maxr; ++r)
-        jac_round_kernel<<<ncta, kJacThreads, 0, st>>>(dt, d_cta, nj, r, d_sweep, rot, Y, V1);
+        jac_round_kernel<<<ncta, 32 * kJacPairsPerCta, 0, st>>>(dt, d_pair, npair, nj, r, d_sweep,
+                                                              rot, Y, V1);
       s = cuda_ok(c, cudaGetLastError(), "Jacobi sweep");
     }
     count_launch(maxr + 1);
